@@ -1,0 +1,192 @@
+"""FP64 CPU oracle (test infrastructure only).
+
+Only `tests/`, `__graft_entry__.smoke()` and the CPU-baseline leg of
+`bench.py` may import this package.  It is a plain, slow statement of the
+method, written from the paper, and shares no code with the CUDA library.
+See `oracle/oracle.c` for the passages each function follows and for the
+readings taken where the paper is silent.
+
+Parity pins: tests/test_oracle_refine.py, tests/test_oracle_fuse.py,
+tests/test_oracle_splat.py (closed forms, invariants, brute force, golden
+fixtures under tests/golden/).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_OUT = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+DEFAULT_WEIGHT_CONST = 0.001   # Supplement A.1
+DEFAULT_WINDOW = 7             # Supplement A.1, w = 7
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no FP contraction) into oracle/_build/liboracle.so."""
+    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
+        tmp = _OUT + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off", "-fno-fast-math",
+                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm", "-lpthread"])
+        os.replace(tmp, _OUT)
+    return _OUT
+
+
+class _Cam(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("fx", ctypes.c_double), ("fy", ctypes.c_double), ("cx", ctypes.c_double), ("cy", ctypes.c_double),
+                ("R", ctypes.c_double * 9), ("t", ctypes.c_double * 3)]
+
+
+def _cam(c) -> _Cam:
+    s = _Cam()
+    s.width, s.height = int(c.width), int(c.height)
+    s.fx, s.fy, s.cx, s.cy = float(c.fx), float(c.fy), float(c.cx), float(c.cy)
+    R = np.asarray(c.R, np.float64).reshape(9)
+    t = np.asarray(c.t, np.float64).reshape(3)
+    for a in range(9):
+        s.R[a] = R[a]
+    for a in range(3):
+        s.t[a] = t[a]
+    return s
+
+
+def _cams(cs):
+    arr = (_Cam * len(cs))()
+    for k, c in enumerate(cs):
+        arr[k] = _cam(c)
+    return arr
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            vp, i32, i64, dbl, flt = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_float
+            cp = ctypes.POINTER(_Cam)
+            lib.orc_refine_depth.argtypes = [i32, i32, i32, vp, vp, vp, vp, flt, vp, vp]
+            lib.orc_weight.argtypes = [vp, i32, i32, i32, i32, dbl, dbl, i32]
+            lib.orc_weight.restype = dbl
+            lib.orc_fuse_depth.argtypes = [cp, vp, i32, cp, i32, dbl, dbl, dbl, dbl, i32, i32, vp, i64,
+                                           vp, vp, vp, vp, i32]
+            lib.orc_forward_splat.argtypes = [cp, vp, vp, i32, cp, i32, flt, flt, vp, vp, vp, vp, vp, vp, vp, vp]
+            lib.orc_splat_bruteforce.argtypes = [cp, vp, i32, cp, i32, flt, vp]
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def _threads(n):
+    return n if n else min(64, os.cpu_count() or 1)
+
+
+def refine_depth(rgba_t, rgba_prev, depth_t, state_prev, tau: float = 0.03):
+    """Eq. 1-2, binary form.  Arrays [N, H, W(, 4)]; rgba_prev None at t = 0.
+
+    Returns (state_out float32 [N, H, W], mask uint8 [N, H, W])."""
+    lib = _load()
+    rgba_t = np.ascontiguousarray(rgba_t, np.uint8)
+    N, H, W = rgba_t.shape[:3]
+    depth_t = np.ascontiguousarray(depth_t, np.float32)
+    rp = None if rgba_prev is None else np.ascontiguousarray(rgba_prev, np.uint8)
+    sp = None if state_prev is None else np.ascontiguousarray(state_prev, np.float32)
+    out = np.empty((N, H, W), np.float32)
+    mask = np.empty((N, H, W), np.uint8)
+    rc = lib.orc_refine_depth(N, H, W, _ptr(rgba_t), _ptr(rp), _ptr(depth_t), _ptr(sp), ctypes.c_float(tau),
+                              _ptr(out), _ptr(mask))
+    if rc != 0:
+        raise ValueError("orc_refine_depth rejected its arguments")
+    return out, mask
+
+
+def weight(depth, u: int, v: int, mu: float, weight_const=DEFAULT_WEIGHT_CONST, window=DEFAULT_WINDOW) -> float:
+    """Supplement A.1 confidence weight of one view at pixel (u, v)."""
+    lib = _load()
+    d = np.ascontiguousarray(depth, np.float32)
+    H, W = d.shape
+    return lib.orc_weight(_ptr(d), H, W, int(u), int(v), float(mu), float(weight_const), int(window))
+
+
+def fuse_depth(in_cams, depths, target, num_samples, z_near, z_far, mu,
+               weight_const=DEFAULT_WEIGHT_CONST, window=DEFAULT_WINDOW, normalize=False,
+               pixels=None, threads=None, count_fp64=False):
+    """Fused target depth by D uniform samples and the first +/- crossing.
+
+    `pixels`: optional int array [P, 2] of (column, row); default every pixel.
+    Returns dict(depth float64, index int32 (-1 none), ambiguous uint8,
+    fp64_mismatch int) shaped [Ht, Wt] or [P]."""
+    lib = _load()
+    depths = np.ascontiguousarray(depths, np.float32)
+    if pixels is not None:
+        pix = np.ascontiguousarray(pixels, np.int32).reshape(-1, 2)
+        n = pix.shape[0]
+        shape = (n,)
+    else:
+        pix = None
+        n = target.width * target.height
+        shape = (target.height, target.width)
+    out_d = np.empty(n, np.float64)
+    out_i = np.empty(n, np.int32)
+    out_a = np.empty(n, np.uint8)
+    mism = ctypes.c_int64(0)
+    rc = lib.orc_fuse_depth(_cams(in_cams), _ptr(depths), len(in_cams), ctypes.byref(_cam(target)),
+                            int(num_samples), float(np.float32(z_near)), float(np.float32(z_far)),
+                            float(np.float32(mu)), float(weight_const), int(window), int(bool(normalize)),
+                            _ptr(pix), n, _ptr(out_d), _ptr(out_i), _ptr(out_a),
+                            ctypes.addressof(mism) if count_fp64 else None, _threads(threads))
+    if rc != 0:
+        raise ValueError("orc_fuse_depth rejected its arguments")
+    return {"depth": out_d.reshape(shape), "index": out_i.reshape(shape), "ambiguous": out_a.reshape(shape),
+            "fp64_mismatch": int(mism.value)}
+
+
+def forward_splat(in_cams, depths, rgba_u32, target, footprint=True, max_half_width=2.0, mu_guide=0.04,
+                  fused=None, count_fp64=False):
+    """Per-view z-buffered forward render into the target.
+
+    Returns dict(winner int32 [N, Ht, Wt] (-1 none), warped_rgba uint32, warped_depth float32,
+    alpha uint8, guided uint8, guided_ambiguous uint8, fp64_mismatch int)."""
+    lib = _load()
+    depths = np.ascontiguousarray(depths, np.float32)
+    rgba_u32 = np.ascontiguousarray(rgba_u32, np.uint32)
+    N = len(in_cams)
+    shape = (N, target.height, target.width)
+    win = np.empty(shape, np.int32)
+    wr = np.empty(shape, np.uint32)
+    wd = np.empty(shape, np.float32)
+    al = np.empty(shape, np.uint8)
+    gu = np.zeros(shape, np.uint8)
+    ga = np.zeros(shape, np.uint8)
+    fz = None if fused is None else np.ascontiguousarray(fused, np.float64)
+    mism = ctypes.c_int64(0)
+    rc = lib.orc_forward_splat(_cams(in_cams), _ptr(depths), _ptr(rgba_u32), N, ctypes.byref(_cam(target)),
+                               int(bool(footprint)), ctypes.c_float(max_half_width), ctypes.c_float(mu_guide),
+                               _ptr(fz), _ptr(win), _ptr(wr), _ptr(wd), _ptr(al), _ptr(gu), _ptr(ga),
+                               ctypes.addressof(mism) if count_fp64 else None)
+    if rc != 0:
+        raise ValueError("orc_forward_splat rejected its arguments")
+    return {"winner": win, "warped_rgba": wr, "warped_depth": wd, "alpha": al, "guided": gu,
+            "guided_ambiguous": ga, "fp64_mismatch": int(mism.value)}
+
+
+def splat_bruteforce(in_cams, depths, target, footprint=True, max_half_width=2.0):
+    """Target-major enumeration of every (source, covered target) candidate; winner map only."""
+    lib = _load()
+    depths = np.ascontiguousarray(depths, np.float32)
+    N = len(in_cams)
+    win = np.empty((N, target.height, target.width), np.int32)
+    lib.orc_splat_bruteforce(_cams(in_cams), _ptr(depths), N, ctypes.byref(_cam(target)), int(bool(footprint)),
+                             ctypes.c_float(max_half_width), _ptr(win))
+    return win

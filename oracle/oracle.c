@@ -1,0 +1,479 @@
+/*
+ * FP64 CPU oracle for the geometry core of "Geometry-guided Online 3D Video
+ * Synthesis with Multi-View Temporal Consistency" (arXiv 2505.18932).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may call this; it
+ * exists so that the CUDA library can be checked against a plain, slow,
+ * obviously-correct statement of what the method computes.  It shares no
+ * code, header or table with the CUDA library.
+ *
+ * What it follows:
+ *   refine     Sec. 3.2, Eq. 1 and Eq. 2 (temporal depth filtering), in the
+ *              binary form: m = [max_c |I^t_c - I^{t-1}_c| > floor(255 tau)],
+ *              D'^t = m ? D^t : D'^{t-1}; at t = 0, m = 1.
+ *   weight     Supplement A.1 (confidence weight): nu = sum over the w x w
+ *              window of min((D[c] - D[n])^2, tau^2); omega = min(0.001 *
+ *              (nu / w^2)^(-1/2), 1).  Evaluated PER SAMPLE at the sampled
+ *              pixel (no precomputed map).
+ *   fuse       Supplement A.1 (projection, signed distance, weighted sum of
+ *              clamped distances, omega = 0 behind the truncation band),
+ *              Eq. 3 (raymarch), with D uniform samples and the first +/-
+ *              zero crossing interpolated linearly.
+ *   splat      Sec. 3.1 and Supplement A.3 (each input view forward-rendered
+ *              separately with pixel-sized, fully opaque primitives, depth
+ *              test for occlusion), as a z-buffer with a pixel footprint.
+ *
+ * Readings where the paper is silent or inconsistent:
+ *   - sign: sdf = (d_in - z_proj) / mu, positive in front of the surface,
+ *     omega = 0 where sdf < -1; the printed s_k = z_k - D_k would make free
+ *     space negative, at odds with the "omega = 0 if s_k < -tau" rule and the
+ *     forward stepping by 0.8 s.
+ *   - D_k[u,v] samples the NEAREST pixel (ties to even); the window is
+ *     clamped at image borders; a neighbour with invalid depth contributes
+ *     mu^2; an invalid centre gives omega = 0; nu = 0 gives omega = 1.
+ *   - out of image, behind the camera (z <= 1e-6) or invalid depth: the
+ *     view contributes nothing at that sample.
+ *   - the fused value is the plain weighted sum (normalize = 0) or S/W.
+ *   - crossing: first s with W_s > 0, W_{s+1} > 0, S_s > 0, S_{s+1} <= 0.
+ *
+ * Precision: FP64 throughout, EXCEPT the decisions that turn floating point
+ * into integers, which are taken in the GPU kernel's precision (FP32) by an
+ * explicit address contract that both sides evaluate op for op:
+ *   fuse : per-view FP32 matrix M, offset b (composed in FP64, rounded once),
+ *          a = M [i j 1]^T by fused multiply-adds, sample z_s = fma(s, dz, zn),
+ *          h = fma(z_s, a, b); the sampled pixel is the nearest integer to the
+ *          exact quotients h.x/h.z, h.y/h.z.  The sample point is the FP32 z_s
+ *          and the projected depth is h.z; everything after is FP64.
+ *   splat: per-view FP32 A, c, f_ratio; m = A [u v 1]^T, h = fma(d, m, c),
+ *          x = h.x/h.z, y = h.y/h.z rounded to FP32; footprint half-width
+ *          hw = min(max(0.5 f_ratio (d/h.z), 0.5), max_hw); covered target
+ *          pixels [ceil(x-hw), floor(x+hw)]; key (bits(z) << 32 | source).
+ * Compile with -ffp-contract=off so that no other expression is fused.
+ *
+ * Parity pins live in tests/test_oracle_*.py.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+    int32_t width, height;
+    double fx, fy, cx, cy;
+    double R[9];
+    double t[3];
+} orc_camera;
+
+static int depth_valid(float d) { return isfinite(d) && d > 0.0f; }
+
+/* ------------------------------------------------------------------------ */
+/* Eq. 1 / Eq. 2 in the binary-mask form.                                   */
+/* ------------------------------------------------------------------------ */
+int orc_refine_depth(int n_views, int H, int W, const uint8_t *rgba_t, const uint8_t *rgba_prev,
+                     const float *depth_t, const float *state_prev, float tau,
+                     float *state_out, uint8_t *mask_out) {
+    if (n_views <= 0 || H <= 0 || W <= 0 || !rgba_t || !depth_t || !state_out) return -1;
+    int T = (int)floor(255.0 * (double)tau);
+    size_t n = (size_t)n_views * H * W;
+    for (size_t p = 0; p < n; ++p) {
+        int m = 1;
+        if (rgba_prev) {
+            int dmax = 0;
+            for (int c = 0; c < 3; ++c) {
+                int d = abs((int)rgba_t[4 * p + c] - (int)rgba_prev[4 * p + c]);
+                if (d > dmax) dmax = d;
+            }
+            m = dmax > T;
+        }
+        if (mask_out) mask_out[p] = (uint8_t)m;
+        state_out[p] = (m || !rgba_prev || !state_prev) ? depth_t[p] : state_prev[p];
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Supplement A.1: confidence weight of view k at pixel (u, v).             */
+/* ------------------------------------------------------------------------ */
+double orc_weight(const float *depth, int H, int W, int u, int v, double mu, double wconst, int window) {
+    float dc = depth[(size_t)v * W + u];
+    if (!depth_valid(dc)) return 0.0;
+    int r = window / 2;
+    double nu = 0.0;
+    for (int dy = -r; dy <= r; ++dy) {
+        for (int dx = -r; dx <= r; ++dx) {
+            int q = v + dy, p = u + dx;
+            q = q < 0 ? 0 : (q >= H ? H - 1 : q);
+            p = p < 0 ? 0 : (p >= W ? W - 1 : p);
+            float dn = depth[(size_t)q * W + p];
+            if (!depth_valid(dn)) { nu += mu * mu; continue; }
+            double diff = (double)dc - (double)dn;
+            double sq = diff * diff;
+            nu += sq < mu * mu ? sq : mu * mu;
+        }
+    }
+    if (nu == 0.0) return 1.0;
+    double w = wconst * pow(nu / (double)(window * window), -0.5);
+    return w < 1.0 ? w : 1.0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* FP64 composition of the per-view FP32 contract coefficients.             */
+/* Maps depth * [i j 1] in camera `from` to homogeneous pixel coordinates in */
+/* camera `to`:  h = depth * (M [i j 1]^T) + b, with                         */
+/* M = K_to R_to R_from^T K_from^-1 and b = K_to (t_to - R_to R_from^T t_from). */
+/* ------------------------------------------------------------------------ */
+static void compose(const orc_camera *to, const orc_camera *from, float M[9], float b[3]) {
+    double Q[9], g[3], N[9], bb[3];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c)
+            Q[3 * r + c] = to->R[3 * r + 0] * from->R[3 * c + 0] + to->R[3 * r + 1] * from->R[3 * c + 1] +
+                           to->R[3 * r + 2] * from->R[3 * c + 2];
+    for (int r = 0; r < 3; ++r)
+        g[r] = to->t[r] - (Q[3 * r + 0] * from->t[0] + Q[3 * r + 1] * from->t[1] + Q[3 * r + 2] * from->t[2]);
+    for (int c = 0; c < 3; ++c) {
+        N[0 + c] = to->fx * Q[0 + c] + to->cx * Q[6 + c];
+        N[3 + c] = to->fy * Q[3 + c] + to->cy * Q[6 + c];
+        N[6 + c] = Q[6 + c];
+    }
+    bb[0] = to->fx * g[0] + to->cx * g[2];
+    bb[1] = to->fy * g[1] + to->cy * g[2];
+    bb[2] = g[2];
+    for (int r = 0; r < 3; ++r) {
+        M[3 * r + 0] = (float)(N[3 * r + 0] / from->fx);
+        M[3 * r + 1] = (float)(N[3 * r + 1] / from->fy);
+        M[3 * r + 2] = (float)((N[3 * r + 2] - (N[3 * r + 0] * from->cx) / from->fx) - (N[3 * r + 1] * from->cy) / from->fy);
+        b[r] = (float)bb[r];
+    }
+}
+
+/* nearest integer (ties to even) of the exact real quotient num/den, den > 0 */
+static double nearest_of_quotient(float num, float den) {
+    return nearbyint((double)num / (double)den);
+}
+
+/* FP64 geometry of the same sample, used only for the informational count of
+ * address decisions where FP32 and FP64 disagree. */
+static void project_fp64(const orc_camera *view, const orc_camera *tgt, double i, double j, double z,
+                         double *x, double *y, double *zk) {
+    double P[3] = {z * (i - tgt->cx) / tgt->fx, z * (j - tgt->cy) / tgt->fy, z};
+    double pw[3];
+    for (int a = 0; a < 3; ++a)
+        pw[a] = tgt->R[0 * 3 + a] * (P[0] - tgt->t[0]) + tgt->R[1 * 3 + a] * (P[1] - tgt->t[1]) +
+                tgt->R[2 * 3 + a] * (P[2] - tgt->t[2]);
+    double pc[3];
+    for (int a = 0; a < 3; ++a)
+        pc[a] = view->R[3 * a + 0] * pw[0] + view->R[3 * a + 1] * pw[1] + view->R[3 * a + 2] * pw[2] + view->t[a];
+    *zk = pc[2];
+    *x = (view->fx * pc[0] + view->cx * pc[2]) / pc[2];
+    *y = (view->fy * pc[1] + view->cy * pc[2]) / pc[2];
+}
+
+typedef struct {
+    const orc_camera *in_cams; const float *depths; int n_views;
+    const orc_camera *target;
+    int D; double z_near, z_far, mu, wconst; int window, normalize;
+    const int32_t *pixels; int64_t n_pixels;
+    double *out_depth; int32_t *out_index; uint8_t *out_amb;
+    int64_t *addr_fp64_mismatch;
+    float (*M)[9]; float (*b)[3];
+    int64_t p0, p1;
+} fuse_job;
+
+/* One target pixel: Supplement A.1 + Eq. 3 with D uniform samples. */
+static void fuse_pixel(const fuse_job *jb, int i, int j, double *out_d, int32_t *out_s, uint8_t *out_a,
+                       int64_t *mism) {
+    const int K = jb->n_views;
+    const int D = jb->D;
+    const float zn = (float)jb->z_near;
+    const float dz = (float)((jb->z_far - jb->z_near) / (double)(D - 1));
+    const double mu = jb->mu;
+    int amb = 0;
+    double S_prev = 0.0, W_prev = 0.0, z_prev = 0.0;
+    *out_d = 0.0;
+    *out_s = -1;
+    for (int s = 0; s < D; ++s) {
+        float zs = fmaf((float)s, dz, zn);
+        double S = 0.0, Wt = 0.0;
+        for (int k = 0; k < K; ++k) {
+            const orc_camera *vc = &jb->in_cams[k];
+            const float *M = jb->M[k];
+            const float *b = jb->b[k];
+            float a0 = fmaf(M[0], (float)i, fmaf(M[1], (float)j, M[2]));
+            float a1 = fmaf(M[3], (float)i, fmaf(M[4], (float)j, M[5]));
+            float a2 = fmaf(M[6], (float)i, fmaf(M[7], (float)j, M[8]));
+            float h0 = fmaf(zs, a0, b[0]);
+            float h1 = fmaf(zs, a1, b[1]);
+            float h2 = fmaf(zs, a2, b[2]);
+            if (!(h2 > 1e-6f)) continue;
+            double u = nearest_of_quotient(h0, h2);
+            double v = nearest_of_quotient(h1, h2);
+            if (mism) {
+                double x64, y64, z64;
+                project_fp64(vc, jb->target, i, j, (double)zs, &x64, &y64, &z64);
+                if (nearbyint(x64) != u || nearbyint(y64) != v) ++*mism;
+            }
+            if (u < 0 || v < 0 || u > vc->width - 1 || v > vc->height - 1) continue;
+            const float *dep = jb->depths + (size_t)k * vc->width * vc->height;
+            float d = dep[(size_t)v * vc->width + (size_t)u];
+            if (!depth_valid(d)) continue;
+            double sdf = ((double)d - (double)h2) / mu;
+            if (fabs(sdf + 1.0) < 1e-5) amb = 1;
+            if (sdf < -1.0) continue; /* hidden behind the truncation band */
+            double w = orc_weight(dep, vc->height, vc->width, (int)u, (int)v, mu, jb->wconst, jb->window);
+            double c = sdf < -1.0 ? -1.0 : (sdf > 1.0 ? 1.0 : sdf);
+            S += w * c;
+            Wt += w;
+        }
+        if (jb->normalize && Wt > 0.0) S /= Wt;
+        double scale = jb->normalize ? 1.0 : Wt;
+        if (Wt > 0.0 && fabs(S) <= 1e-5 * scale) amb = 1;
+        if (s > 0 && W_prev > 0.0 && Wt > 0.0 && S_prev > 0.0 && S <= 0.0) {
+            double t = S_prev / (S_prev - S);
+            *out_d = z_prev + ((double)zs - z_prev) * t;
+            *out_s = s - 1;
+            /* conditioning of the interpolation against FP32 rounding of S */
+            double sens = ((double)zs - z_prev) * 1e-5 * (jb->normalize ? 2.0 : (W_prev + Wt)) / (S_prev - S);
+            if (sens > 0.25e-4 * fabs(*out_d)) amb = 1;
+            break;
+        }
+        S_prev = S;
+        W_prev = Wt;
+        z_prev = (double)zs;
+    }
+    *out_a = (uint8_t)amb;
+}
+
+static void *fuse_worker(void *arg) {
+    fuse_job *jb = (fuse_job *)arg;
+    int Wt = jb->target->width;
+    for (int64_t p = jb->p0; p < jb->p1; ++p) {
+        int i, j;
+        if (jb->pixels) { i = jb->pixels[2 * p]; j = jb->pixels[2 * p + 1]; }
+        else { i = (int)(p % Wt); j = (int)(p / Wt); }
+        uint8_t a;
+        fuse_pixel(jb, i, j, &jb->out_depth[p], &jb->out_index[p], &a, jb->addr_fp64_mismatch);
+        if (jb->out_amb) jb->out_amb[p] = a;
+    }
+    return NULL;
+}
+
+int orc_fuse_depth(const orc_camera *in_cams, const float *depths, int n_views, const orc_camera *target,
+                   int num_samples, double z_near, double z_far, double mu, double weight_const, int window,
+                   int normalize, const int32_t *pixels, int64_t n_pixels,
+                   double *out_depth, int32_t *out_index, uint8_t *out_amb, int64_t *addr_fp64_mismatch,
+                   int n_threads) {
+    if (!in_cams || !depths || n_views <= 0 || !target || num_samples < 2 || !(z_near < z_far) || !(mu > 0) ||
+        window < 1 || !out_depth || !out_index)
+        return -1;
+    if (!pixels) n_pixels = (int64_t)target->width * target->height;
+    float (*M)[9] = malloc(sizeof(float[9]) * n_views);
+    float (*b)[3] = malloc(sizeof(float[3]) * n_views);
+    for (int k = 0; k < n_views; ++k) compose(&in_cams[k], target, M[k], b[k]);
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > 256) n_threads = 256;
+    int64_t mism[256];
+    fuse_job jobs[256];
+    pthread_t th[256];
+    for (int t = 0; t < n_threads; ++t) {
+        mism[t] = 0;
+        fuse_job jb = {in_cams, depths, n_views, target, num_samples, z_near, z_far, mu, weight_const, window,
+                       normalize, pixels, n_pixels, out_depth, out_index, out_amb,
+                       addr_fp64_mismatch ? &mism[t] : NULL, M, b,
+                       n_pixels * t / n_threads, n_pixels * (t + 1) / n_threads};
+        jobs[t] = jb;
+    }
+    int started = 0;
+    for (int t = 1; t < n_threads; ++t) {
+        if (pthread_create(&th[t], NULL, fuse_worker, &jobs[t]) != 0) break;
+        started = t;
+    }
+    fuse_worker(&jobs[0]);
+    for (int t = 1; t <= started; ++t) pthread_join(th[t], NULL);
+    for (int t = started + 1; t < n_threads; ++t) fuse_worker(&jobs[t]);
+    if (addr_fp64_mismatch) {
+        int64_t tot = 0;
+        for (int t = 0; t < n_threads; ++t) tot += mism[t];
+        *addr_fp64_mismatch = tot;
+    }
+    free(M);
+    free(b);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 3.1 / Supplement A.3: per-view forward render with a depth test.    */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int ok;
+    float x, y, z;
+    int i0, i1, j0, j1; /* covered target pixels, inclusive, clipped */
+} splat_geo;
+
+static splat_geo splat_contract(const float A[9], const float c[3], float f_ratio, int footprint, float max_hw,
+                                int u, int v, float d, int Wt, int Ht) {
+    splat_geo g = {0};
+    if (!depth_valid(d)) return g;
+    float m0 = fmaf(A[0], (float)u, fmaf(A[1], (float)v, A[2]));
+    float m1 = fmaf(A[3], (float)u, fmaf(A[4], (float)v, A[5]));
+    float m2 = fmaf(A[6], (float)u, fmaf(A[7], (float)v, A[8]));
+    float h0 = fmaf(d, m0, c[0]);
+    float h1 = fmaf(d, m1, c[1]);
+    float h2 = fmaf(d, m2, c[2]);
+    if (!(h2 > 1e-6f)) return g;
+    float x = h0 / h2, y = h1 / h2;
+    float lo_x, hi_x, lo_y, hi_y;
+    if (footprint) {
+        float rho = f_ratio * (d / h2);
+        float hw = 0.5f * rho;
+        hw = hw > 0.5f ? hw : 0.5f;
+        hw = hw < max_hw ? hw : max_hw;
+        lo_x = ceilf(x - hw); hi_x = floorf(x + hw);
+        lo_y = ceilf(y - hw); hi_y = floorf(y + hw);
+    } else {
+        lo_x = hi_x = rintf(x);
+        lo_y = hi_y = rintf(y);
+    }
+    if (lo_x < 0.0f) lo_x = 0.0f;
+    if (lo_y < 0.0f) lo_y = 0.0f;
+    if (hi_x > (float)(Wt - 1)) hi_x = (float)(Wt - 1);
+    if (hi_y > (float)(Ht - 1)) hi_y = (float)(Ht - 1);
+    if (!(lo_x <= hi_x) || !(lo_y <= hi_y)) return g;
+    g.ok = 1; g.x = x; g.y = y; g.z = h2;
+    g.i0 = (int)lo_x; g.i1 = (int)hi_x; g.j0 = (int)lo_y; g.j1 = (int)hi_y;
+    return g;
+}
+
+static uint64_t make_key(float z, uint32_t src) {
+    uint32_t zb;
+    memcpy(&zb, &z, 4);
+    return ((uint64_t)zb << 32) | (uint64_t)src;
+}
+
+int orc_forward_splat(const orc_camera *in_cams, const float *depths, const uint32_t *rgba, int n_views,
+                      const orc_camera *target, int footprint, float max_hw, float mu_guide,
+                      const double *fused, int32_t *winner, uint32_t *warped_rgba, float *warped_depth,
+                      uint8_t *alpha, uint8_t *guided, uint8_t *guided_amb, int64_t *fp64_mismatch) {
+    if (!in_cams || !depths || !rgba || n_views <= 0 || !target || !winner) return -1;
+    int Wt = target->width, Ht = target->height;
+    size_t np = (size_t)Wt * Ht;
+    uint64_t *key = malloc(sizeof(uint64_t) * np);
+    double *zb64 = fp64_mismatch ? malloc(sizeof(double) * np) : NULL;
+    int64_t *src64 = fp64_mismatch ? malloc(sizeof(int64_t) * np) : NULL;
+    if (fp64_mismatch) *fp64_mismatch = 0;
+    size_t in_off = 0;
+    for (int k = 0; k < n_views; ++k) {
+        const orc_camera *vc = &in_cams[k];
+        int W = vc->width, H = vc->height;
+        float A[9], c[3];
+        compose(target, vc, A, c);
+        float f_ratio = (float)(target->fx / vc->fx);
+        for (size_t p = 0; p < np; ++p) key[p] = ~(uint64_t)0;
+        for (int v = 0; v < H; ++v) {
+            for (int u = 0; u < W; ++u) {
+                float d = depths[in_off + (size_t)v * W + u];
+                splat_geo g = splat_contract(A, c, f_ratio, footprint, max_hw, u, v, d, Wt, Ht);
+                if (!g.ok) continue;
+                uint64_t kk = make_key(g.z, (uint32_t)(v * W + u));
+                for (int jj = g.j0; jj <= g.j1; ++jj)
+                    for (int ii = g.i0; ii <= g.i1; ++ii) {
+                        uint64_t *slot = &key[(size_t)jj * Wt + ii];
+                        if (kk < *slot) *slot = kk;
+                    }
+            }
+        }
+        if (fp64_mismatch) {
+            /* same rule with FP64 geometry; informational only */
+            for (size_t p = 0; p < np; ++p) { zb64[p] = INFINITY; src64[p] = -1; }
+            for (int v = 0; v < H; ++v) {
+                for (int u = 0; u < W; ++u) {
+                    float d = depths[in_off + (size_t)v * W + u];
+                    if (!depth_valid(d)) continue;
+                    double x, y, z;
+                    project_fp64(target, vc, u, v, d, &x, &y, &z);
+                    if (!(z > 1e-6)) continue;
+                    double lx, hx, ly, hy;
+                    if (footprint) {
+                        double hw = 0.5 * (target->fx / vc->fx) * ((double)d / z);
+                        hw = hw > 0.5 ? hw : 0.5;
+                        hw = hw < max_hw ? hw : max_hw;
+                        lx = ceil(x - hw); hx = floor(x + hw); ly = ceil(y - hw); hy = floor(y + hw);
+                    } else {
+                        lx = hx = nearbyint(x); ly = hy = nearbyint(y);
+                    }
+                    if (lx < 0) lx = 0;
+                    if (ly < 0) ly = 0;
+                    if (hx > Wt - 1) hx = Wt - 1;
+                    if (hy > Ht - 1) hy = Ht - 1;
+                    for (double jj = ly; jj <= hy; jj += 1.0)
+                        for (double ii = lx; ii <= hx; ii += 1.0) {
+                            size_t q = (size_t)jj * Wt + (size_t)ii;
+                            int64_t s = (int64_t)v * W + u;
+                            if (z < zb64[q] || (z == zb64[q] && s < src64[q])) { zb64[q] = z; src64[q] = s; }
+                        }
+                }
+            }
+        }
+        for (size_t p = 0; p < np; ++p) {
+            size_t o = (size_t)k * np + p;
+            uint64_t kk = key[p];
+            int has = kk != ~(uint64_t)0;
+            int32_t w = has ? (int32_t)(uint32_t)(kk & 0xffffffffu) : -1;
+            uint32_t zb = (uint32_t)(kk >> 32);
+            float z;
+            memcpy(&z, &zb, 4);
+            if (!has) z = 0.0f;
+            winner[o] = w;
+            if (warped_rgba) warped_rgba[o] = has ? rgba[in_off + (size_t)w] : 0u;
+            if (warped_depth) warped_depth[o] = z;
+            if (alpha) alpha[o] = (uint8_t)has;
+            if (guided) {
+                int gk = 0, ga = 0;
+                if (has && fused) {
+                    double diff = fabs((double)z - fused[p]) - (double)mu_guide;
+                    gk = diff <= 0.0;
+                    ga = fabs(diff) <= 1e-4 * fabs(fused[p]) + 1e-6;
+                }
+                guided[o] = (uint8_t)gk;
+                if (guided_amb) guided_amb[o] = (uint8_t)ga;
+            }
+            if (fp64_mismatch && (int64_t)w != src64[p]) ++*fp64_mismatch;
+        }
+        in_off += (size_t)W * H;
+    }
+    free(key);
+    free(zb64);
+    free(src64);
+    return 0;
+}
+
+/* Brute force of the same rule, target-major: for every target pixel scan
+ * every source pixel.  Used on tiny images to check the scatter bookkeeping. */
+int orc_splat_bruteforce(const orc_camera *in_cams, const float *depths, int n_views, const orc_camera *target,
+                         int footprint, float max_hw, int32_t *winner) {
+    int Wt = target->width, Ht = target->height;
+    size_t in_off = 0;
+    for (int k = 0; k < n_views; ++k) {
+        const orc_camera *vc = &in_cams[k];
+        int W = vc->width, H = vc->height;
+        float A[9], c[3];
+        compose(target, vc, A, c);
+        float f_ratio = (float)(target->fx / vc->fx);
+        for (int jj = 0; jj < Ht; ++jj)
+            for (int ii = 0; ii < Wt; ++ii) {
+                uint64_t best = ~(uint64_t)0;
+                for (int v = 0; v < H; ++v)
+                    for (int u = 0; u < W; ++u) {
+                        float d = depths[in_off + (size_t)v * W + u];
+                        splat_geo g = splat_contract(A, c, f_ratio, footprint, max_hw, u, v, d, Wt, Ht);
+                        if (!g.ok || ii < g.i0 || ii > g.i1 || jj < g.j0 || jj > g.j1) continue;
+                        uint64_t kk = make_key(g.z, (uint32_t)(v * W + u));
+                        if (kk < best) best = kk;
+                    }
+                winner[(size_t)k * Wt * Ht + (size_t)jj * Wt + ii] =
+                    best == ~(uint64_t)0 ? -1 : (int32_t)(uint32_t)(best & 0xffffffffu);
+            }
+        in_off += (size_t)W * H;
+    }
+    return 0;
+}
