@@ -1,0 +1,463 @@
+"""Benchmark: one online frame of the geometry core per step.
+
+A step is the whole hot path for one frame: temporal depth refinement of all
+input views, the confidence-weight map, TSDF fusion with zero-crossing
+extraction into the target view, and the per-view forward splat (clear,
+scatter, resolve with the guided mask).  The workload is 8 input views at
+1920x1080 (2x4 rig, 10 cm spacing) fused into one 1920x1080 target, D = 128
+samples on [0.3, 8] m, mu = 0.04 m, synthetic seeded scene.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gvs|reference]
+
+Under torchrun each rank runs its own frames (replicas, weak scaling); rank 0
+prints one JSON line.  `--impl reference` times the FP64 CPU oracle on a
+bounded sample of the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "target-view Mpix/s (TSDF fuse+splat, 8x1080p inputs, D=128); fwd+bwd Mpix/s; % HBM peak"
+WORKLOAD = "headline_8x1080p"
+RING = 4                 # distinct frames resident in HBM, cycled step by step
+OPS_PER_SAMPLE_VIEW = 20  # algorithmic FP32 instructions per (sample, view) of the fusion loop
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gvs", choices=["gvs", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured", d
+    return 6800.0, "fallback", {}
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, enabled: bool = True):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+        if not enabled:
+            return
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ inputs --
+
+def render_frames(w, frames):
+    from synth import rgba_to_u32
+    out = []
+    for t in frames:
+        rgb, d = w.render_inputs(t)
+        out.append((rgba_to_u32(rgb), d))
+    return out
+
+
+# --------------------------------------------------------------- GPU path --
+
+class Pipeline:
+    """Device buffers and the per-frame call sequence through the C ABI."""
+
+    def __init__(self, w, frames_np, device):
+        import torch
+        from paper_2505_18932_gb300 import gvs
+        self.torch, self.gvs, self.w = torch, gvs, w
+        self.tgt = w.targets[0]
+        N = len(w.inputs)
+        H, W = w.inputs[0].height, w.inputs[0].width
+        Ht, Wt = self.tgt.height, self.tgt.width
+        self.N, self.H, self.W, self.Ht, self.Wt = N, H, W, Ht, Wt
+        self.rgba = [torch.from_numpy(c.view(np.int32)).to(device) for c, _ in frames_np]
+        self.depth = [torch.from_numpy(d).to(device) for _, d in frames_np]
+        self.state = self.depth[0].clone()
+        self.mask = torch.empty((N, H, W), dtype=torch.uint8, device=device)
+        self.fused = torch.empty((Ht, Wt), dtype=torch.float32, device=device)
+        self.cross = torch.empty((Ht, Wt), dtype=torch.int16, device=device)
+        self.ws_fuse = gvs.workspace(gvs.fuse_workspace_bytes(N, W, H), device)
+        self.ws_splat = gvs.workspace(gvs.splat_workspace_bytes(N, Wt, Ht), device)
+        shape = (N, Ht, Wt)
+        self.outs = {"winner": torch.empty(shape, dtype=torch.int32, device=device),
+                     "warped_rgba": torch.empty(shape, dtype=torch.int32, device=device),
+                     "warped_depth": torch.empty(shape, dtype=torch.float32, device=device),
+                     "alpha": torch.empty(shape, dtype=torch.uint8, device=device),
+                     "guided": torch.empty(shape, dtype=torch.uint8, device=device)}
+
+    def step(self, i, events=None):
+        """Frame i of the ring: refine -> fuse -> splat.  `events`: 4 CUDA events bracketing the stages."""
+        w, gvs = self.w, self.gvs
+        cur, prev = i % len(self.rgba), (i - 1) % len(self.rgba)
+        if events:
+            events[0].record()
+        gvs.refine_depth(self.rgba[cur], self.rgba[prev], self.depth[cur], self.state, self.mask, tau=w.tau)
+        if events:
+            events[1].record()
+        gvs.fuse_depth(w.inputs, self.state, self.tgt, w.num_samples, w.z_near, w.z_far, w.mu,
+                       fused=self.fused, crossing=self.cross, ws=self.ws_fuse)
+        if events:
+            events[2].record()
+        gvs.forward_splat(w.inputs, self.state, self.rgba[cur], self.tgt, fused=self.fused, mu_guide=w.mu,
+                          outputs=self.outs, ws=self.ws_splat)
+        if events:
+            events[3].record()
+
+    def launches_per_step(self):
+        # refine (vec4 kernel), weight map, fuse, splat clear + scatter/resolve per group of views
+        slots = max(1, min(self.N, self.ws_splat.numel() // (self.Ht * self.Wt * 8)))
+        groups = (self.N + slots - 1) // slots
+        n_refine = 1 + (1 if (self.N * self.H * self.W) % 4 else 0)
+        return n_refine + 2 + 1 + 2 * groups
+
+
+def algorithmic_fuse(cross_np, D, K):
+    """Sample-views the method evaluates: every sample up to the crossing's second
+    bracket (s + 2), all D where there is no crossing, times K views."""
+    s = cross_np.astype(np.int64)
+    n = np.where(s >= 0, np.minimum(s + 2, D), D)
+    return int(n.sum()) * K
+
+
+def alg_bytes(N, H, W, Ht, Wt):
+    """Compulsory HBM bytes of one step (each input read once, each output written once)."""
+    px, tpx = N * H * W, Ht * Wt
+    refine = px * (4 + 4 + 4 + 4) + px * (4 + 1)
+    wmap = px * 4 + px * 8
+    fuse = px * 8 + tpx * (4 + 2)
+    splat = px * (4 + 4) + tpx * N * (4 + 4 + 4 + 1 + 1) + tpx * 4
+    return {"refine": refine, "weight_map": wmap, "fuse": fuse, "splat": splat}
+
+
+def run_gvs(args, rank, local_rank, world):
+    import torch
+    import torch.distributed as dist
+    from synth import configs
+
+    torch.cuda.set_device(local_rank)
+    device = torch.device("cuda", local_rank)
+    w = configs.headline_8x1080p()
+    # each rank streams its own frames (weak scaling)
+    frames = [rank * RING + t for t in range(RING)]
+    frames_np = render_frames(w, frames)
+    pipe = Pipeline(w, frames_np, device)
+    stream = torch.cuda.current_stream()
+
+    def flush_barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for i in range(max(3, args.warmup)):
+        pipe.step(i)
+    torch.cuda.synchronize()
+
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    clocks = ClockSampler(local_rank, enabled=(rank == 0 and not args.no_clocks))
+    time.sleep(0.25 if clocks.proc else 0.0)
+    flush_barrier()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    wall0 = time.perf_counter()
+    t_start.record(stream)
+    for i in range(K):
+        pipe.step(i + 1, ev[i])
+    t_end.record(stream)
+    flush_barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    stage = {"refine": [], "fuse": [], "splat": []}
+    for e in ev:
+        stage["refine"].append(e[0].elapsed_time(e[1]))
+        stage["fuse"].append(e[1].elapsed_time(e[2]))
+        stage["splat"].append(e[2].elapsed_time(e[3]))
+    if world > 1:
+        t = torch.tensor([total_ms], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    # fuse-only kernel duration for the roofline: time the fusion stage alone, weight map excluded
+    fuse_kernel_ms = time_fuse_kernel(pipe, K=min(K, 50))
+    crosses = []
+    for r in range(RING):
+        pipe.step(r)
+        torch.cuda.synchronize()
+        crosses.append(pipe.cross.cpu().numpy())
+    units = statistics.mean(algorithmic_fuse(c, w.num_samples, pipe.N) for c in crosses)
+    holes = statistics.mean(float((c < 0).mean()) for c in crosses)
+
+    e2e = run_e2e(pipe, frames_np, args.e2e_steps) if args.e2e_steps > 0 else None
+
+    if rank != 0:
+        return
+    tpx = pipe.Ht * pipe.Wt
+    ms_per_step = total_ms / K
+    value = world * tpx / (ms_per_step * 1e-3) / 1e6
+    hbm_peak, peak_src, peaks = measured_peaks()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    alu_peak = device_sms() * 128 * sm_max * 1e6 / 1e12  # T lane-ops/s
+    achieved = units * OPS_PER_SAMPLE_VIEW / (fuse_kernel_ms * 1e-3) / 1e12
+    ab = alg_bytes(pipe.N, pipe.H, pipe.W, pipe.Ht, pipe.Wt)
+    step_bytes = sum(ab.values())
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "target Mpix/s", "n_gpus": world, "steps": K,
+        "warmup": max(3, args.warmup), "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "inputs": f"{pipe.N}x{pipe.W}x{pipe.H}", "target": f"{pipe.Wt}x{pipe.Ht}",
+                   "num_samples": w.num_samples, "z_range": [w.z_near, w.z_far], "mu": w.mu, "tau": w.tau,
+                   "l2": f"inputs > L2: {RING}-frame ring, {round((pipe.N * pipe.H * pipe.W * 16) / 1e6)} MB read per step",
+                   "parallelism": f"replicas{world}"},
+        "stage_ms": {k: round(statistics.median(v), 4) for k, v in stage.items()},
+        "hbm": {"alg_bytes_per_step": step_bytes, "achieved_gbs": round(step_bytes / (ms_per_step * 1e-3) / 1e9, 1),
+                "peak_gbs": hbm_peak, "frac": round(step_bytes / (ms_per_step * 1e-3) / 1e9 / hbm_peak, 4),
+                "peak_source": peak_src},
+        "roofline": {"kernel": "fuse_kernel", "bound": "alu", "achieved": round(achieved, 3),
+                     "peak": round(alu_peak, 2), "unit": "T FP32 lane-ops/s",
+                     "frac": round(achieved / alu_peak, 4), "traffic": None,
+                     "units_per_launch": units, "ops_per_unit": OPS_PER_SAMPLE_VIEW,
+                     "kernel_ms": round(fuse_kernel_ms, 4), "hole_fraction": round(holes, 4),
+                     "peak_source": "152 SMs x 128 FP32 lanes x max SM clock"},
+        "e2e": e2e,
+        "gpu_launches": pipe.launches_per_step() * K,
+        "clocks": clk,
+        "wall_s": round(wall, 3),
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(w, frames_np, budget_s=15.0)
+    print(json.dumps(line), flush=True)
+
+
+def device_sms():
+    import torch
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+
+
+def time_fuse_kernel(pipe, K):
+    """Average duration of the fusion kernel alone (weight map already in the workspace),
+    via the two-stage entry points, CUDA events on the launching stream."""
+    import torch
+    from paper_2505_18932_gb300 import gvs
+    w = pipe.w
+    durs = []
+    for i in range(K + 3):
+        cur = i % len(pipe.rgba)
+        gvs.weight_map(pipe.depth[cur], w.mu, ws=pipe.ws_fuse)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        gvs.fuse_depth_from_map(w.inputs, pipe.ws_fuse, (pipe.N, pipe.H, pipe.W), pipe.tgt, w.num_samples,
+                                w.z_near, w.z_far, w.mu, fused=pipe.fused, crossing=pipe.cross)
+        b.record()
+        if i >= 3:
+            durs.append((a, b))
+    torch.cuda.synchronize()
+    return statistics.mean(a.elapsed_time(b) for a, b in durs)
+
+
+def run_e2e(pipe, frames_np, steps):
+    """Same metric through the public API with host buffers: per step the new
+    frame (colour + depth) goes host->device and the fused depth plus the warped
+    views come back device->host, all inside the timed region."""
+    import torch
+    host_in = [(torch.from_numpy(c.view(np.int32)).pin_memory(), torch.from_numpy(d).pin_memory())
+               for c, d in frames_np]
+    names = ["warped_rgba", "warped_depth", "alpha", "guided"]
+    host_out = {n: torch.empty(pipe.outs[n].shape, dtype=pipe.outs[n].dtype).pin_memory() for n in names}
+    host_fused = torch.empty(pipe.fused.shape, dtype=torch.float32).pin_memory()
+    dev_rgba = [torch.empty_like(x) for x in pipe.rgba]
+    dev_depth = [torch.empty_like(x) for x in pipe.depth]
+    h2d = host_in[0][0].numel() * 4 + host_in[0][1].numel() * 4
+    d2h = sum(host_out[n].numel() * host_out[n].element_size() for n in names) + host_fused.numel() * 4
+
+    def one(i):
+        cur = i % len(host_in)
+        dev_rgba[cur].copy_(host_in[cur][0], non_blocking=True)
+        dev_depth[cur].copy_(host_in[cur][1], non_blocking=True)
+        pipe.rgba, pipe.depth = dev_rgba, dev_depth
+        pipe.step(i)
+        host_fused.copy_(pipe.fused, non_blocking=True)
+        for n in names:
+            host_out[n].copy_(pipe.outs[n], non_blocking=True)
+
+    saved = (pipe.rgba, pipe.depth)
+    for i in range(len(host_in)):  # every ring slot filled before timing
+        one(i)
+    for i in range(3):
+        one(i)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for i in range(steps):
+        one(i)
+    b.record()
+    torch.cuda.synchronize()
+    pipe.rgba, pipe.depth = saved
+    ms = a.elapsed_time(b) / steps
+    return {"value": round(pipe.Ht * pipe.Wt / (ms * 1e-3) / 1e6, 3), "unit": "target Mpix/s",
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ms, 4)}
+
+
+# ------------------------------------------------------------ CPU oracle --
+
+def oracle_step(w, frames_np, i, n_pixels, seed, threads):
+    """One bounded-sample step of the FP64 oracle on frame i of the ring.
+    Returns (seconds, estimated seconds for the full frame)."""
+    import oracle
+    cur, prev = frames_np[i % len(frames_np)], frames_np[(i - 1) % len(frames_np)]
+    rgba_t = cur[0].view(np.uint8).reshape(cur[0].shape + (4,))
+    rgba_p = prev[0].view(np.uint8).reshape(prev[0].shape + (4,))
+    tgt = w.targets[0]
+    t0 = time.perf_counter()
+    state, _ = oracle.refine_depth(rgba_t, rgba_p, cur[1], prev[1], w.tau)
+    t1 = time.perf_counter()
+    rng = np.random.default_rng(seed)
+    pix = np.stack([rng.integers(0, tgt.width, n_pixels), rng.integers(0, tgt.height, n_pixels)], 1).astype(np.int32)
+    r = oracle.fuse_depth(w.inputs, state, tgt, w.num_samples, w.z_near, w.z_far, w.mu, pixels=pix, threads=threads)
+    t2 = time.perf_counter()
+    # the splat runs on a band of source rows (the same fraction of every view)
+    band = max(1, int(round(w.inputs[0].height * n_pixels / (tgt.width * tgt.height))))
+    crop = [c.__class__(**{**c.__dict__, "height": band}) for c in w.inputs]
+    fused_band = np.zeros((tgt.height, tgt.width))
+    oracle.forward_splat(crop, np.ascontiguousarray(state[:, :band]), np.ascontiguousarray(cur[0][:, :band]),
+                         tgt, mu_guide=w.mu, fused=fused_band)
+    t3 = time.perf_counter()
+    full = (t1 - t0) + (t2 - t1) * (tgt.width * tgt.height / n_pixels) + (t3 - t2) * (w.inputs[0].height / band)
+    return t3 - t0, full
+
+
+def cpu_baseline(w, frames_np, budget_s=15.0):
+    threads = os.cpu_count() or 1
+    n_pixels = 8192
+    spent, est = 0.0, []
+    i = 1
+    while spent < budget_s and i < 50:
+        s, full = oracle_step(w, frames_np, i, n_pixels, seed=i, threads=threads)
+        spent += s
+        est.append(full)
+        i += 1
+    full = statistics.median(est)
+    tpx = w.targets[0].width * w.targets[0].height
+    return {"value": round(tpx / full / 1e6, 6), "unit": "target Mpix/s", "cores": threads, "kind": "oracle",
+            "sample": (f"{len(est)} frames; per frame: full-frame refine, fuse on {n_pixels} random target px "
+                       f"({threads} threads), splat on a band of source rows of the same fraction (1 thread); "
+                       f"scaled to the full frame")}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from synth import configs
+    w = configs.headline_8x1080p()
+    frames_np = render_frames(w, list(range(RING)))
+    threads = os.cpu_count() or 1
+    n_pixels = 2048
+    for i in range(max(3, args.warmup)):
+        oracle_step(w, frames_np, i + 1, n_pixels, seed=i, threads=threads)
+    t0 = time.perf_counter()
+    ests = []
+    for i in range(args.steps):
+        _, full = oracle_step(w, frames_np, i + 1, n_pixels, seed=100 + i, threads=threads)
+        ests.append(full)
+    wall = time.perf_counter() - t0
+    ms = statistics.mean(ests) * 1e3
+    tpx = w.targets[0].width * w.targets[0].height
+    value = tpx / (ms * 1e-3) / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "target Mpix/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(ms, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "inputs": "8x1920x1080", "target": "1920x1080",
+                       "num_samples": w.num_samples, "parallelism": "cpu"},
+            "cpu_baseline": {"value": round(value, 6), "unit": "target Mpix/s", "cores": threads, "kind": "oracle",
+                             "sample": (f"per step: full-frame refine, fuse on {n_pixels} random target px, splat on "
+                                        "a band of source rows of the same fraction; time scaled to the full frame")},
+            "e2e": {"value": round(value, 6), "unit": "target Mpix/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "wall_s": round(wall, 3)}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, local_rank, world = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    try:
+        run_gvs(args, rank, local_rank, world)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,227 @@
+/*
+ * gvs.h -- C ABI of libgvs.so, the GB300 (sm_103a) geometry core of
+ * "Geometry-guided Online 3D Video Synthesis with Multi-View Temporal
+ * Consistency" (arXiv 2505.18932).
+ *
+ * The calls follow the paper's problem statement (Sec. 3, "Method"): fixed
+ * calibrated cameras (intrinsics K, world->camera R, t), one RGB-D frame per
+ * input view, a target camera; out come the target-view fused depth (Eq. 3,
+ * Supplement A.1) and the per-view forward-rendered colour, depth and
+ * coverage (Sec. 3.1, Supplement A.3).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Memory   : every array argument is a DEVICE pointer to caller-owned,
+ *            densely packed memory (no row padding).  The library never
+ *            allocates; scratch lives in a caller-provided workspace whose
+ *            size the matching *_workspace_bytes() call returns.  Arrays
+ *            must be 16-byte aligned; workspaces 256-byte aligned.
+ * Layouts  : per-view arrays are [n_views][height][width], row-major.
+ *            Colour is RGBA8 packed in one little-endian uint32 per pixel
+ *            (R in the low byte); alpha is carried but never read.
+ *            Depth is z-depth in metres, float32; a value <= 0 or not finite
+ *            marks an invalid pixel.
+ * Cameras  : host memory, read during the call only.  x_cam = R x_world + t,
+ *            R row-major; pixel (i, j) has its centre at integer coordinates
+ *            (column i, row j).  All input views of one call share one size.
+ * Streams  : `stream` is a cudaStream_t (NULL = legacy default stream).
+ *            Every call only enqueues work; outputs are ready once the stream
+ *            reaches that point.  Calls that share a workspace must not run
+ *            concurrently.
+ * Errors   : arguments are checked on the host before anything is enqueued;
+ *            on GVS_ERR_INVALID_ARG nothing is written.  A failed launch
+ *            returns GVS_ERR_CUDA.  gvs_last_error() gives a message for the
+ *            calling thread's last failure.  No C++ exception crosses the ABI.
+ *
+ * Address contracts (what makes integer maps reproducible bit for bit)
+ * -------------------------------------------------------------------
+ * For an ordered camera pair (to, from) the host composes in FP64, in this
+ * order, and rounds each entry once to FP32:
+ *   Q = R_to R_from^T  (Q[r][c] = sum_m R_to[r][m] R_from[c][m], m = 0,1,2)
+ *   g = t_to - Q t_from
+ *   N = K_to Q,  b = K_to g   (row 0: fx*row0 + cx*row2; row 1: fy*row1 + cy*row2)
+ *   M[r][0] = N[r][0]/fx_from,  M[r][1] = N[r][1]/fy_from,
+ *   M[r][2] = (N[r][2] - N[r][0]*cx_from/fx_from) - N[r][1]*cy_from/fy_from
+ * so that depth * (M [i j 1]^T) + b are the homogeneous pixel coordinates in
+ * `to` of pixel (i, j) of `from` at that depth.  All device arithmetic that
+ * decides an integer uses correctly rounded FP32 operations in a fixed order
+ * (given with each call below).
+ */
+#ifndef GVS_H_
+#define GVS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define GVS_API __attribute__((visibility("default")))
+#else
+#define GVS_API
+#endif
+
+#define GVS_MAX_VIEWS 32        /* input views per call */
+#define GVS_MAX_DIM 16384       /* width and height limit of every image */
+#define GVS_MAX_SAMPLES 32767   /* samples per ray (crossing index is int16) */
+#define GVS_MAX_WINDOW 15       /* confidence window side (odd) */
+
+typedef enum {
+    GVS_OK = 0,
+    GVS_ERR_INVALID_ARG = 1,   /* bad pointer, size, parameter or camera; nothing enqueued */
+    GVS_ERR_UNSUPPORTED = 2,   /* valid request outside what this build implements */
+    GVS_ERR_WORKSPACE = 3,     /* workspace missing, misaligned or too small */
+    GVS_ERR_CUDA = 4,          /* a CUDA launch or runtime call failed */
+    GVS_ERR_DEVICE = 5         /* no usable CUDA device */
+} gvs_status;
+
+typedef struct {
+    int32_t width, height;
+    double fx, fy, cx, cy;     /* pinhole intrinsics, pixels */
+    double R[9];               /* world->camera rotation, row-major */
+    double t[3];               /* world->camera translation */
+} gvs_camera;
+
+/* Temporal refinement (Sec. 3.2, Eq. 1-2), binary mask form. */
+typedef struct {
+    float tau;                 /* colour threshold in [0,1]; integer T = floor(255 * tau) */
+} gvs_refine_params;
+
+/* TSDF fusion (Supplement A.1, Eq. 3). */
+typedef struct {
+    int32_t num_samples;       /* D >= 2 uniform samples of target z-depth in [z_near, z_far] */
+    float z_near, z_far;       /* 0 < z_near < z_far */
+    float mu;                  /* truncation (metres) > 0; also clamps the weight's variation */
+    float weight_const;        /* 0.001 in the paper */
+    int32_t window;            /* w, odd, 1..GVS_MAX_WINDOW; 7 in the paper */
+    int32_t normalize;         /* 0: S = sum w*clamp (paper); 1: S / W */
+} gvs_fuse_params;
+
+/* Forward splat (Sec. 3.1, Supplement A.3). */
+typedef struct {
+    int32_t footprint;         /* 1: pixel-sized footprint; 0: single nearest pixel */
+    float max_half_width;      /* footprint half-width cap in target pixels (>= 0.5), e.g. 2 */
+    float mu_guide;            /* guided mask: |warped depth - fused depth| <= mu_guide */
+} gvs_splat_params;
+
+/* Library identification and diagnostics. */
+GVS_API const char *gvs_version(void);
+GVS_API const char *gvs_status_string(gvs_status s);
+/* Message of the calling thread's most recent failed call ("" if none). */
+GVS_API const char *gvs_last_error(void);
+
+/*
+ * gvs_refine_depth -- temporal depth refinement, Sec. 3.2, Eq. 1 and Eq. 2,
+ * with the difference mask taken as a hard decision:
+ *   m(p)        = [ max_{c in R,G,B} |rgba_t_c(p) - rgba_prev_c(p)| > T ],
+ *                 T = floor(255 * tau) (integers; alpha ignored)
+ *   depth_state = m ? depth_t : depth_state       (in place, bit-exact copy)
+ * rgba_prev == NULL marks the first frame: m = 1 everywhere.
+ *   rgba_t, rgba_prev : uint32 [n_views][height][width]
+ *   depth_t           : float  [n_views][height][width]
+ *   depth_state       : float  [n_views][height][width], in: previous filtered
+ *                       depth (ignored when rgba_prev == NULL), out: new one
+ *   mask              : uint8  [n_views][height][width] or NULL
+ */
+GVS_API gvs_status gvs_refine_depth(const uint32_t *rgba_t, const uint32_t *rgba_prev, const float *depth_t,
+                            float *depth_state, uint8_t *mask, int32_t n_views, int32_t width,
+                            int32_t height, const gvs_refine_params *params, void *stream);
+
+/* Workspace bytes for gvs_fuse_depth: a packed (depth, weight) float2 map per input view. */
+GVS_API size_t gvs_fuse_workspace_bytes(int32_t n_views, int32_t width, int32_t height);
+
+/*
+ * gvs_fuse_depth -- image-based TSDF fusion and zero-crossing extraction,
+ * Supplement A.1 (projection, signed distance, confidence weight, omega = 0
+ * behind the band) and Eq. 3 (raymarch), with D uniform samples.
+ *
+ * For target pixel (i, j) and sample s = 0..D-1 (FP32 contract):
+ *   z_s = fma(s, dz, zn),  zn = (float)z_near,
+ *         dz = (float)(((double)z_far - (double)z_near) / (D - 1))
+ *   a   = M_k [i j 1]^T  by fma(M[r][0], i, fma(M[r][1], j, M[r][2]))
+ *         with (M_k, b_k) composed for (to = view k, from = target)
+ *   h   = fma(z_s, a, b_k);  the view contributes only if h.z > 1e-6
+ *   (u, v) = nearest integers (ties to even) of the EXACT quotients
+ *         h.x/h.z, h.y/h.z; the view contributes only if inside its image
+ *   d   = depth_k(u, v); omega = confidence weight of view k at (u, v):
+ *         nu = sum over the w x w window (clamped to the image) of
+ *         min((d - d_n)^2, mu^2), an invalid neighbour counting mu^2;
+ *         omega = min(weight_const * (nu / w^2)^(-1/2), 1), 1 if nu = 0,
+ *         0 if d is invalid
+ *   sdf = (d - h.z) / mu;  omega = 0 where sdf < -1 (hidden behind the band)
+ *   S_s = sum_k omega_k clamp(sdf_k, -1, 1),  W_s = sum_k omega_k
+ *         (normalize: S_s / W_s where W_s > 0)
+ * fused_depth(i, j) = z_s + (z_{s+1} - z_s) S_s / (S_s - S_{s+1}) at the first
+ *   s with W_s > 0, W_{s+1} > 0, S_s > 0, S_{s+1} <= 0; 0 if there is none.
+ *   in_cams   : n_views cameras, all of one size (width x height)
+ *   in_depths : float [n_views][height][width]
+ *   fused_depth : float [target.height][target.width]
+ *   crossing  : int16 [target.height][target.width] (s, or -1) or NULL
+ *   workspace : >= gvs_fuse_workspace_bytes(n_views, width, height) bytes
+ */
+GVS_API gvs_status gvs_fuse_depth(const gvs_camera *in_cams, const float *in_depths, int32_t n_views,
+                          const gvs_camera *target, const gvs_fuse_params *params, float *fused_depth,
+                          int16_t *crossing, void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * gvs_weight_map -- the two stages of gvs_fuse_depth, callable separately.
+ * Stage 1: the confidence weight of Supplement A.1 at every input pixel.
+ * With nearest-pixel sampling the weight at a sample is a function of the
+ * sampled pixel only, so it is computed once per pixel:
+ *   dw_map[k][y][x] = (d, omega) as float2, with omega as in gvs_fuse_depth,
+ *   and (0, 0) where d is invalid.
+ *   in_depths : float [n_views][height][width];  dw_map : float2, same shape
+ *               (8 bytes per pixel, gvs_fuse_workspace_bytes() in total)
+ */
+GVS_API gvs_status gvs_weight_map(const float *in_depths, int32_t n_views, int32_t width, int32_t height,
+                                  float mu, float weight_const, int32_t window, void *dw_map, void *stream);
+
+/*
+ * gvs_fuse_depth_from_map -- stage 2: the TSDF march and zero crossing of
+ * gvs_fuse_depth (Supplement A.1, Eq. 3) reading a map written by
+ * gvs_weight_map.  params->weight_const and params->window are not used.
+ */
+GVS_API gvs_status gvs_fuse_depth_from_map(const gvs_camera *in_cams, const void *dw_map, int32_t n_views,
+                                           const gvs_camera *target, const gvs_fuse_params *params,
+                                           float *fused_depth, int16_t *crossing, void *stream);
+
+/* Workspace bytes for gvs_forward_splat: one 64-bit z-buffer of the target size.
+ * A workspace holding several such buffers lets several views splat in one pass. */
+GVS_API size_t gvs_splat_workspace_bytes(int32_t n_views, int32_t target_width, int32_t target_height);
+
+/*
+ * gvs_forward_splat -- per-view forward rendering into the target camera with
+ * a depth test, Sec. 3.1 and Supplement A.3 (each view rendered separately,
+ * fully opaque pixel-sized primitives, occlusion by depth).
+ *
+ * For source pixel (u, v) of view k with valid depth d (FP32 contract, with
+ * (A, c) composed for (to = target, from = view k), f = fx_target / fx_k):
+ *   m = A [u v 1]^T by fma as above;  h = fma(d, m, c);  skip unless h.z > 1e-6
+ *   x = h.x / h.z,  y = h.y / h.z            (correctly rounded FP32)
+ *   footprint: rho = f * (d / h.z);  hw = min(max(0.5 * rho, 0.5), max_half_width)
+ *              covers target pixels ceil(x - hw)..floor(x + hw) (and y alike)
+ *   point    : covers (rint(x), rint(y))
+ *   key = (float bits of h.z) << 32 | (v * width + u); per target pixel the
+ *   smallest key wins: the nearest surface, ties to the lower source index.
+ * Outputs, each [n_views][target.height][target.width] (NULL to skip, except winner):
+ *   winner       int32  source pixel index v*width+u, or -1
+ *   warped_rgba  uint32 source colour of the winner (0 if none)
+ *   warped_depth float  h.z of the winner (0 if none)
+ *   alpha        uint8  1 where a winner exists
+ *   guided       uint8  alpha && |warped_depth - fused_depth| <= mu_guide;
+ *                needs fused_depth [target.height][target.width]
+ *   workspace : >= gvs_splat_workspace_bytes(...) bytes
+ */
+GVS_API gvs_status gvs_forward_splat(const gvs_camera *in_cams, const float *in_depths, const uint32_t *in_rgba,
+                             int32_t n_views, const gvs_camera *target, const gvs_splat_params *params,
+                             const float *fused_depth, int32_t *winner, uint32_t *warped_rgba,
+                             float *warped_depth, uint8_t *alpha, uint8_t *guided, void *workspace,
+                             size_t workspace_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GVS_H_ */

@@ -1,0 +1,323 @@
+// Host side of the C ABI declared in include/gvs.h: argument checks, FP64
+// composition of the per-view FP32 contract coefficients, kernel dispatch.
+// Built with -ffp-contract=off so that the FP64 composition is evaluated in
+// exactly the documented order.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "gvs_internal.cuh"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+gvs_status fail(gvs_status s, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+gvs_status cuda_fail(cudaError_t e, const char *where) {
+    return fail(GVS_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+bool camera_ok(const gvs_camera *c) {
+    if (!c) return false;
+    if (c->width < 1 || c->height < 1 || c->width > GVS_MAX_DIM || c->height > GVS_MAX_DIM) return false;
+    if (!(isfinite(c->fx) && isfinite(c->fy) && isfinite(c->cx) && isfinite(c->cy))) return false;
+    if (!(c->fx > 0.0) || !(c->fy > 0.0)) return false;
+    for (int i = 0; i < 9; ++i)
+        if (!isfinite(c->R[i])) return false;
+    for (int i = 0; i < 3; ++i)
+        if (!isfinite(c->t[i])) return false;
+    return true;
+}
+
+// FP64 composition in the order documented in gvs.h, rounded once to FP32.
+gvs::ViewXform compose(const gvs_camera &to, const gvs_camera &from) {
+    double Q[9], g[3], N[9], bb[3];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c)
+            Q[3 * r + c] = to.R[3 * r + 0] * from.R[3 * c + 0] + to.R[3 * r + 1] * from.R[3 * c + 1] +
+                           to.R[3 * r + 2] * from.R[3 * c + 2];
+    for (int r = 0; r < 3; ++r)
+        g[r] = to.t[r] - (Q[3 * r + 0] * from.t[0] + Q[3 * r + 1] * from.t[1] + Q[3 * r + 2] * from.t[2]);
+    for (int c = 0; c < 3; ++c) {
+        N[0 + c] = to.fx * Q[0 + c] + to.cx * Q[6 + c];
+        N[3 + c] = to.fy * Q[3 + c] + to.cy * Q[6 + c];
+        N[6 + c] = Q[6 + c];
+    }
+    bb[0] = to.fx * g[0] + to.cx * g[2];
+    bb[1] = to.fy * g[1] + to.cy * g[2];
+    bb[2] = g[2];
+    gvs::ViewXform x;
+    for (int r = 0; r < 3; ++r) {
+        x.M[3 * r + 0] = (float)(N[3 * r + 0] / from.fx);
+        x.M[3 * r + 1] = (float)(N[3 * r + 1] / from.fy);
+        x.M[3 * r + 2] = (float)((N[3 * r + 2] - (N[3 * r + 0] * from.cx) / from.fx) - (N[3 * r + 1] * from.cy) / from.fy);
+        x.b[r] = (float)bb[r];
+    }
+    return x;
+}
+
+size_t align_up(size_t n, size_t a) { return (n + a - 1) / a * a; }
+
+bool views_ok(const gvs_camera *cams, int32_t n, int32_t *W, int32_t *H) {
+    if (n < 0 || n > GVS_MAX_VIEWS) return false;
+    if (n == 0) { *W = *H = 0; return true; }
+    if (!cams) return false;
+    for (int k = 0; k < n; ++k) {
+        if (!camera_ok(&cams[k])) return false;
+        if (cams[k].width != cams[0].width || cams[k].height != cams[0].height) return false;
+    }
+    *W = cams[0].width;
+    *H = cams[0].height;
+    return true;
+}
+
+}  // namespace
+
+namespace gvs {
+
+int device_sm_count() {
+    static std::mutex mu;
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    std::lock_guard<std::mutex> lock(mu);
+    if (cache[dev] == 0) {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
+        cache[dev] = sms;
+    }
+    return cache[dev];
+}
+
+}  // namespace gvs
+
+extern "C" {
+
+const char *gvs_version(void) { return "gvs 0.1.0 (sm_103a)"; }
+
+const char *gvs_status_string(gvs_status s) {
+    switch (s) {
+        case GVS_OK: return "ok";
+        case GVS_ERR_INVALID_ARG: return "invalid argument";
+        case GVS_ERR_UNSUPPORTED: return "unsupported";
+        case GVS_ERR_WORKSPACE: return "workspace too small or misaligned";
+        case GVS_ERR_CUDA: return "CUDA error";
+        case GVS_ERR_DEVICE: return "no usable CUDA device";
+    }
+    return "unknown status";
+}
+
+const char *gvs_last_error(void) { return g_err; }
+
+gvs_status gvs_refine_depth(const uint32_t *rgba_t, const uint32_t *rgba_prev, const float *depth_t,
+                            float *depth_state, uint8_t *mask, int32_t n_views, int32_t width, int32_t height,
+                            const gvs_refine_params *params, void *stream) {
+    if (!params) return fail(GVS_ERR_INVALID_ARG, "refine: params is NULL");
+    if (n_views < 0 || n_views > GVS_MAX_VIEWS) return fail(GVS_ERR_INVALID_ARG, "refine: n_views out of range");
+    if (width < 1 || height < 1 || width > GVS_MAX_DIM || height > GVS_MAX_DIM)
+        return fail(GVS_ERR_INVALID_ARG, "refine: image size out of range");
+    if (!(params->tau >= 0.0f && params->tau <= 1.0f)) return fail(GVS_ERR_INVALID_ARG, "refine: tau not in [0,1]");
+    if (n_views == 0) return GVS_OK;
+    if (!rgba_t || !depth_t || !depth_state) return fail(GVS_ERR_INVALID_ARG, "refine: NULL array");
+    if (!aligned(rgba_t, 16) || !aligned(depth_t, 16) || !aligned(depth_state, 16) ||
+        (rgba_prev && !aligned(rgba_prev, 16)) || (mask && !aligned(mask, 16)))
+        return fail(GVS_ERR_INVALID_ARG, "refine: arrays must be 16-byte aligned");
+    const int threshold = (int)floor(255.0 * (double)params->tau);
+    const int64_t n = (int64_t)n_views * width * height;
+    cudaError_t e = gvs::launch_refine(rgba_t, rgba_prev, depth_t, depth_state, mask, n, threshold,
+                                       (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "refine launch");
+    return GVS_OK;
+}
+
+size_t gvs_fuse_workspace_bytes(int32_t n_views, int32_t width, int32_t height) {
+    if (n_views < 0 || width < 0 || height < 0) return 0;
+    return align_up((size_t)n_views * (size_t)width * (size_t)height * sizeof(float2), 256);
+}
+
+}  // extern "C"
+
+namespace {
+
+gvs_status check_fuse_common(const gvs_camera *in_cams, int32_t n_views, const gvs_camera *target,
+                             const gvs_fuse_params *params, const float *fused_depth, const int16_t *crossing,
+                             int32_t *W, int32_t *H) {
+    if (!params) return fail(GVS_ERR_INVALID_ARG, "fuse: params is NULL");
+    if (!views_ok(in_cams, n_views, W, H))
+        return fail(GVS_ERR_INVALID_ARG, "fuse: input cameras invalid, of different sizes, or n_views out of range");
+    if (!camera_ok(target)) return fail(GVS_ERR_INVALID_ARG, "fuse: target camera invalid");
+    const gvs_fuse_params &p = *params;
+    if (p.num_samples < 2 || p.num_samples > GVS_MAX_SAMPLES) return fail(GVS_ERR_INVALID_ARG, "fuse: num_samples");
+    if (!(isfinite(p.z_near) && isfinite(p.z_far) && p.z_near > 0.0f && p.z_near < p.z_far))
+        return fail(GVS_ERR_INVALID_ARG, "fuse: need 0 < z_near < z_far");
+    if (!(isfinite(p.mu) && p.mu > 0.0f)) return fail(GVS_ERR_INVALID_ARG, "fuse: mu must be > 0");
+    if (p.normalize != 0 && p.normalize != 1) return fail(GVS_ERR_INVALID_ARG, "fuse: normalize must be 0 or 1");
+    if (!fused_depth) return fail(GVS_ERR_INVALID_ARG, "fuse: fused_depth is NULL");
+    if (!aligned(fused_depth, 16) || (crossing && !aligned(crossing, 16)))
+        return fail(GVS_ERR_INVALID_ARG, "fuse: arrays must be 16-byte aligned");
+    return GVS_OK;
+}
+
+gvs_status check_weight_params(float mu, float weight_const, int32_t window) {
+    if (!(isfinite(mu) && mu > 0.0f)) return fail(GVS_ERR_INVALID_ARG, "weight map: mu must be > 0");
+    if (!(isfinite(weight_const) && weight_const > 0.0f))
+        return fail(GVS_ERR_INVALID_ARG, "weight map: weight_const must be > 0");
+    if (window < 1 || window > GVS_MAX_WINDOW || (window & 1) == 0)
+        return fail(GVS_ERR_INVALID_ARG, "weight map: window must be odd in [1, %d]", GVS_MAX_WINDOW);
+    return GVS_OK;
+}
+
+gvs::FuseArgs fuse_args(const gvs_camera *in_cams, const void *dw, int32_t n_views, int32_t W, int32_t H,
+                        const gvs_camera *target, const gvs_fuse_params &p, float *fused, int16_t *crossing) {
+    gvs::FuseArgs a;
+    memset(&a, 0, sizeof(a));
+    a.dw = reinterpret_cast<const float2 *>(dw);
+    a.K = n_views;
+    a.W = W;
+    a.H = H;
+    a.Wt = target->width;
+    a.Ht = target->height;
+    a.D = p.num_samples;
+    a.zn = p.z_near;
+    a.dz = (float)(((double)p.z_far - (double)p.z_near) / (double)(p.num_samples - 1));
+    a.inv_mu = (float)(1.0 / (double)p.mu);
+    a.normalize = p.normalize;
+    a.fused = fused;
+    a.crossing = crossing;
+    for (int k = 0; k < n_views; ++k) a.xf[k] = compose(in_cams[k], *target);
+    return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+gvs_status gvs_weight_map(const float *in_depths, int32_t n_views, int32_t width, int32_t height, float mu,
+                          float weight_const, int32_t window, void *dw_map, void *stream) {
+    if (n_views < 0 || n_views > GVS_MAX_VIEWS) return fail(GVS_ERR_INVALID_ARG, "weight map: n_views out of range");
+    if (width < 1 || height < 1 || width > GVS_MAX_DIM || height > GVS_MAX_DIM)
+        return fail(GVS_ERR_INVALID_ARG, "weight map: image size out of range");
+    gvs_status s = check_weight_params(mu, weight_const, window);
+    if (s != GVS_OK) return s;
+    if (n_views == 0) return GVS_OK;
+    if (!in_depths || !dw_map) return fail(GVS_ERR_INVALID_ARG, "weight map: NULL array");
+    if (!aligned(in_depths, 16) || !aligned(dw_map, 16))
+        return fail(GVS_ERR_INVALID_ARG, "weight map: arrays must be 16-byte aligned");
+    cudaError_t e = gvs::launch_weight_map(in_depths, reinterpret_cast<float2 *>(dw_map), n_views, width, height,
+                                           mu, weight_const, window, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "weight map launch");
+    return GVS_OK;
+}
+
+gvs_status gvs_fuse_depth_from_map(const gvs_camera *in_cams, const void *dw_map, int32_t n_views,
+                                   const gvs_camera *target, const gvs_fuse_params *params, float *fused_depth,
+                                   int16_t *crossing, void *stream) {
+    int32_t W = 0, H = 0;
+    gvs_status s = check_fuse_common(in_cams, n_views, target, params, fused_depth, crossing, &W, &H);
+    if (s != GVS_OK) return s;
+    if (n_views > 0 && (!dw_map || !aligned(dw_map, 16)))
+        return fail(GVS_ERR_INVALID_ARG, "fuse: dw_map is NULL or not 16-byte aligned");
+    gvs::FuseArgs a = fuse_args(in_cams, dw_map, n_views, W, H, target, *params, fused_depth, crossing);
+    cudaError_t e = gvs::launch_fuse(a, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "fuse: launch");
+    return GVS_OK;
+}
+
+gvs_status gvs_fuse_depth(const gvs_camera *in_cams, const float *in_depths, int32_t n_views,
+                          const gvs_camera *target, const gvs_fuse_params *params, float *fused_depth,
+                          int16_t *crossing, void *workspace, size_t workspace_bytes, void *stream) {
+    int32_t W = 0, H = 0;
+    gvs_status s = check_fuse_common(in_cams, n_views, target, params, fused_depth, crossing, &W, &H);
+    if (s != GVS_OK) return s;
+    s = check_weight_params(params->mu, params->weight_const, params->window);
+    if (s != GVS_OK) return s;
+    if (n_views > 0 && (!in_depths || !aligned(in_depths, 16)))
+        return fail(GVS_ERR_INVALID_ARG, "fuse: in_depths is NULL or not 16-byte aligned");
+    const size_t need = gvs_fuse_workspace_bytes(n_views, W, H);
+    if (need > 0 && (!workspace || workspace_bytes < need || !aligned(workspace, 256)))
+        return fail(GVS_ERR_WORKSPACE, "fuse: workspace needs %zu bytes, 256-byte aligned", need);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = gvs::launch_weight_map(in_depths, reinterpret_cast<float2 *>(workspace), n_views, W, H,
+                                           params->mu, params->weight_const, params->window, st);
+    if (e != cudaSuccess) return cuda_fail(e, "fuse: weight map launch");
+    gvs::FuseArgs a = fuse_args(in_cams, workspace, n_views, W, H, target, *params, fused_depth, crossing);
+    e = gvs::launch_fuse(a, st);
+    if (e != cudaSuccess) return cuda_fail(e, "fuse: launch");
+    return GVS_OK;
+}
+
+size_t gvs_splat_workspace_bytes(int32_t n_views, int32_t target_width, int32_t target_height) {
+    (void)n_views;
+    if (target_width < 0 || target_height < 0) return 0;
+    return align_up((size_t)target_width * (size_t)target_height * sizeof(unsigned long long), 256);
+}
+
+gvs_status gvs_forward_splat(const gvs_camera *in_cams, const float *in_depths, const uint32_t *in_rgba,
+                             int32_t n_views, const gvs_camera *target, const gvs_splat_params *params,
+                             const float *fused_depth, int32_t *winner, uint32_t *warped_rgba, float *warped_depth,
+                             uint8_t *alpha, uint8_t *guided, void *workspace, size_t workspace_bytes,
+                             void *stream) {
+    int32_t W = 0, H = 0;
+    if (!params) return fail(GVS_ERR_INVALID_ARG, "splat: params is NULL");
+    if (!views_ok(in_cams, n_views, &W, &H))
+        return fail(GVS_ERR_INVALID_ARG, "splat: input cameras invalid, of different sizes, or n_views out of range");
+    if (!camera_ok(target)) return fail(GVS_ERR_INVALID_ARG, "splat: target camera invalid");
+    const gvs_splat_params &p = *params;
+    if (p.footprint != 0 && p.footprint != 1) return fail(GVS_ERR_INVALID_ARG, "splat: footprint must be 0 or 1");
+    if (!(isfinite(p.max_half_width) && p.max_half_width >= 0.5f && p.max_half_width <= 64.0f))
+        return fail(GVS_ERR_INVALID_ARG, "splat: max_half_width must be in [0.5, 64]");
+    if (guided && !(isfinite(p.mu_guide) && p.mu_guide >= 0.0f))
+        return fail(GVS_ERR_INVALID_ARG, "splat: mu_guide must be >= 0");
+    if (guided && !fused_depth) return fail(GVS_ERR_INVALID_ARG, "splat: guided mask needs fused_depth");
+    if (n_views == 0) return GVS_OK;
+    if (!in_depths || !in_rgba || !winner) return fail(GVS_ERR_INVALID_ARG, "splat: NULL array");
+    const void *arrs[] = {in_depths, in_rgba, fused_depth, winner, warped_rgba, warped_depth, alpha, guided};
+    for (const void *q : arrs)
+        if (q && !aligned(q, 16)) return fail(GVS_ERR_INVALID_ARG, "splat: arrays must be 16-byte aligned");
+    const size_t slot = gvs_splat_workspace_bytes(n_views, target->width, target->height);
+    if (!workspace || workspace_bytes < slot || !aligned(workspace, 256))
+        return fail(GVS_ERR_WORKSPACE, "splat: workspace needs at least %zu bytes, 256-byte aligned", slot);
+
+    gvs::SplatArgs a;
+    memset(&a, 0, sizeof(a));
+    a.depth = in_depths;
+    a.rgba = in_rgba;
+    a.W = W;
+    a.H = H;
+    a.Wt = target->width;
+    a.Ht = target->height;
+    a.footprint = p.footprint;
+    a.max_hw = p.max_half_width;
+    a.mu_guide = p.mu_guide;
+    a.fused = fused_depth;
+    a.winner = winner;
+    a.warped_rgba = warped_rgba;
+    a.warped_depth = warped_depth;
+    a.alpha = alpha;
+    a.guided = guided;
+    a.keys = reinterpret_cast<unsigned long long *>(workspace);
+    const size_t slot_keys = (size_t)target->width * target->height * sizeof(unsigned long long);
+    size_t slots = workspace_bytes / slot_keys;
+    a.slots = (int)(slots > (size_t)n_views ? (size_t)n_views : slots);
+    for (int k = 0; k < n_views; ++k) {
+        a.v[k].xf = compose(*target, in_cams[k]);
+        a.v[k].f_ratio = (float)(target->fx / in_cams[k].fx);
+    }
+    cudaError_t e = gvs::launch_splat(a, n_views, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "splat: launch");
+    return GVS_OK;
+}
+
+}  // extern "C"

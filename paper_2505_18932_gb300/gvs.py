@@ -1,0 +1,247 @@
+"""Thin ctypes binding of libgvs.so (include/gvs.h).
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels.  PyTorch supplies device memory and the current stream.  There is no
+CPU fallback: if the library is missing or a call fails, this raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libgvs.so")
+
+GVS_OK = 0
+MAX_VIEWS = 32
+_lock = threading.Lock()
+_lib = None
+
+
+class GvsError(RuntimeError):
+    def __init__(self, fn, status, msg):
+        super().__init__(f"{fn} failed with status {status}: {msg}")
+        self.status = status
+
+
+class GvsCamera(ctypes.Structure):
+    """Mirror of gvs_camera."""
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("fx", ctypes.c_double), ("fy", ctypes.c_double), ("cx", ctypes.c_double), ("cy", ctypes.c_double),
+                ("R", ctypes.c_double * 9), ("t", ctypes.c_double * 3)]
+
+
+class GvsRefineParams(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_float)]
+
+
+class GvsFuseParams(ctypes.Structure):
+    _fields_ = [("num_samples", ctypes.c_int32), ("z_near", ctypes.c_float), ("z_far", ctypes.c_float),
+                ("mu", ctypes.c_float), ("weight_const", ctypes.c_float), ("window", ctypes.c_int32),
+                ("normalize", ctypes.c_int32)]
+
+
+class GvsSplatParams(ctypes.Structure):
+    _fields_ = [("footprint", ctypes.c_int32), ("max_half_width", ctypes.c_float), ("mu_guide", ctypes.c_float)]
+
+
+API = {
+    # name: (restype, argtypes)
+    "gvs_version": (ctypes.c_char_p, []),
+    "gvs_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "gvs_last_error": (ctypes.c_char_p, []),
+    "gvs_refine_depth": (ctypes.c_int, [ctypes.c_void_p] * 5 + [ctypes.c_int32] * 3 +
+                         [ctypes.POINTER(GvsRefineParams), ctypes.c_void_p]),
+    "gvs_fuse_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32] * 3),
+    "gvs_fuse_depth": (ctypes.c_int, [ctypes.POINTER(GvsCamera), ctypes.c_void_p, ctypes.c_int32,
+                                      ctypes.POINTER(GvsCamera), ctypes.POINTER(GvsFuseParams),
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                      ctypes.c_void_p]),
+    "gvs_weight_map": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_float, ctypes.c_float, ctypes.c_int32, ctypes.c_void_p,
+                                      ctypes.c_void_p]),
+    "gvs_fuse_depth_from_map": (ctypes.c_int, [ctypes.POINTER(GvsCamera), ctypes.c_void_p, ctypes.c_int32,
+                                               ctypes.POINTER(GvsCamera), ctypes.POINTER(GvsFuseParams),
+                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "gvs_splat_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32] * 3),
+    "gvs_forward_splat": (ctypes.c_int, [ctypes.POINTER(GvsCamera), ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_int32, ctypes.POINTER(GvsCamera), ctypes.POINTER(GvsSplatParams),
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                         ctypes.c_void_p]),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load libgvs.so (built in-tree by __graft_entry__.build()); raise if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library {path} is not built; run __graft_entry__.build() first")
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in API.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(fn, status):
+    if status != GVS_OK:
+        lib = load()
+        raise GvsError(fn, status, lib.gvs_last_error().decode(errors="replace"))
+
+
+def camera_struct(c) -> GvsCamera:
+    """gvs_camera from any object with width, height, fx, fy, cx, cy, R (3x3), t (3)."""
+    s = GvsCamera()
+    s.width, s.height = int(c.width), int(c.height)
+    s.fx, s.fy, s.cx, s.cy = float(c.fx), float(c.fy), float(c.cx), float(c.cy)
+    R = [float(x) for row in (c.R.tolist() if hasattr(c.R, "tolist") else c.R) for x in
+         (row if hasattr(row, "__iter__") else [row])]
+    t = [float(x) for x in (c.t.tolist() if hasattr(c.t, "tolist") else c.t)]
+    for a in range(9):
+        s.R[a] = R[a]
+    for a in range(3):
+        s.t[a] = t[a]
+    return s
+
+
+def camera_array(cams):
+    arr = (GvsCamera * max(1, len(cams)))()
+    for k, c in enumerate(cams):
+        arr[k] = camera_struct(c)
+    return arr
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("gvs: tensors must live on a CUDA device")
+    if not t.is_contiguous():
+        raise ValueError("gvs: tensors must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _want(t, dtype, shape, name):
+    if t.dtype != dtype or tuple(t.shape) != tuple(shape):
+        raise ValueError(f"gvs: {name} must be {dtype} of shape {tuple(shape)}, got {t.dtype} {tuple(t.shape)}")
+
+
+def refine_depth(rgba_t, rgba_prev, depth_t, depth_state, mask=None, tau: float = 0.03, stream=None):
+    """Sec. 3.2 Eq. 1-2 (binary mask).  rgba_* int32/uint32 [N, H, W] packed RGBA8 (or uint8 [N, H, W, 4]);
+    depth_t, depth_state float32 [N, H, W] (depth_state updated in place); mask uint8 [N, H, W] or None."""
+    lib = load()
+    N, H, W = depth_t.shape
+    p = GvsRefineParams(float(tau))
+    st = lib.gvs_refine_depth(_ptr(rgba_t), _ptr(rgba_prev), _ptr(depth_t), _ptr(depth_state), _ptr(mask),
+                              N, W, H, ctypes.byref(p), _stream(stream))
+    _check("gvs_refine_depth", st)
+    return depth_state, mask
+
+
+def fuse_workspace_bytes(n_views, width, height) -> int:
+    return int(load().gvs_fuse_workspace_bytes(n_views, width, height))
+
+
+def splat_workspace_bytes(n_views, target_width, target_height) -> int:
+    return int(load().gvs_splat_workspace_bytes(n_views, target_width, target_height))
+
+
+def workspace(nbytes: int, device=None) -> torch.Tensor:
+    """Caller-owned workspace (torch's allocator returns 256-byte aligned blocks)."""
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device or "cuda")
+
+
+def fuse_depth(in_cams, in_depths, target, num_samples, z_near, z_far, mu, weight_const=0.001, window=7,
+               normalize=False, fused=None, crossing=None, ws=None, want_crossing=True, stream=None):
+    """Supplement A.1 / Eq. 3.  in_depths float32 [N, H, W] on the GPU.
+    Returns (fused float32 [Ht, Wt], crossing int16 [Ht, Wt] or None)."""
+    lib = load()
+    N = len(in_cams)
+    dev = in_depths.device
+    if fused is None:
+        fused = torch.empty((target.height, target.width), dtype=torch.float32, device=dev)
+    if crossing is None and want_crossing:
+        crossing = torch.empty((target.height, target.width), dtype=torch.int16, device=dev)
+    H, W = (in_depths.shape[1], in_depths.shape[2]) if N else (0, 0)
+    need = fuse_workspace_bytes(N, W, H)
+    if ws is None:
+        ws = workspace(need, dev)
+    p = GvsFuseParams(int(num_samples), float(z_near), float(z_far), float(mu), float(weight_const), int(window),
+                      int(bool(normalize)))
+    st = lib.gvs_fuse_depth(camera_array(in_cams), _ptr(in_depths), N, ctypes.byref(camera_struct(target)),
+                            ctypes.byref(p), _ptr(fused), _ptr(crossing), _ptr(ws), ws.numel(), _stream(stream))
+    _check("gvs_fuse_depth", st)
+    return fused, crossing
+
+
+def weight_map(in_depths, mu, weight_const=0.001, window=7, ws=None, stream=None):
+    """Stage 1 of fusion: packed (depth, weight) map [N, H, W] float2, written into `ws` (bytes)."""
+    lib = load()
+    N, H, W = in_depths.shape
+    if ws is None:
+        ws = workspace(fuse_workspace_bytes(N, W, H), in_depths.device)
+    if ws.numel() * ws.element_size() < N * H * W * 8:
+        raise ValueError("gvs: weight-map buffer too small")
+    st = lib.gvs_weight_map(_ptr(in_depths), N, W, H, float(mu), float(weight_const), int(window), _ptr(ws),
+                            _stream(stream))
+    _check("gvs_weight_map", st)
+    return ws
+
+
+def fuse_depth_from_map(in_cams, dw_map, shape, target, num_samples, z_near, z_far, mu, normalize=False,
+                        fused=None, crossing=None, want_crossing=True, stream=None):
+    """Stage 2 of fusion reading a map from weight_map(); `shape` = (N, H, W) of the inputs."""
+    lib = load()
+    N = len(in_cams)
+    dev = dw_map.device
+    if fused is None:
+        fused = torch.empty((target.height, target.width), dtype=torch.float32, device=dev)
+    if crossing is None and want_crossing:
+        crossing = torch.empty((target.height, target.width), dtype=torch.int16, device=dev)
+    p = GvsFuseParams(int(num_samples), float(z_near), float(z_far), float(mu), 0.001, 7, int(bool(normalize)))
+    st = lib.gvs_fuse_depth_from_map(camera_array(in_cams), _ptr(dw_map), N, ctypes.byref(camera_struct(target)),
+                                     ctypes.byref(p), _ptr(fused), _ptr(crossing), _stream(stream))
+    _check("gvs_fuse_depth_from_map", st)
+    return fused, crossing
+
+
+def forward_splat(in_cams, in_depths, in_rgba, target, fused=None, footprint=True, max_half_width=2.0,
+                  mu_guide=0.04, outputs=None, ws=None, want=("warped_rgba", "warped_depth", "alpha", "guided"),
+                  stream=None):
+    """Sec. 3.1 / Supplement A.3.  in_depths float32 [N, H, W]; in_rgba int32 [N, H, W] packed RGBA8.
+    Returns dict of [N, Ht, Wt] tensors: winner int32, warped_rgba int32, warped_depth float32,
+    alpha uint8, guided uint8 (guided only when `fused` is given)."""
+    lib = load()
+    N = len(in_cams)
+    dev = in_depths.device
+    shape = (N, target.height, target.width)
+    out = dict(outputs or {})
+    dtypes = {"winner": torch.int32, "warped_rgba": torch.int32, "warped_depth": torch.float32,
+              "alpha": torch.uint8, "guided": torch.uint8}
+    names = ["winner"] + [n for n in want if n != "guided" or fused is not None]
+    for n in names:
+        if n not in out:
+            out[n] = torch.empty(shape, dtype=dtypes[n], device=dev)
+    if ws is None:
+        ws = workspace(splat_workspace_bytes(N, target.width, target.height), dev)
+    p = GvsSplatParams(int(bool(footprint)), float(max_half_width), float(mu_guide))
+    st = lib.gvs_forward_splat(camera_array(in_cams), _ptr(in_depths), _ptr(in_rgba), N,
+                               ctypes.byref(camera_struct(target)), ctypes.byref(p), _ptr(fused),
+                               _ptr(out["winner"]), _ptr(out.get("warped_rgba")), _ptr(out.get("warped_depth")),
+                               _ptr(out.get("alpha")), _ptr(out.get("guided")), _ptr(ws), ws.numel(),
+                               _stream(stream))
+    _check("gvs_forward_splat", st)
+    return out

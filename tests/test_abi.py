@@ -1,0 +1,142 @@
+"""Host-side checks of the C ABI: the library loads, exports every symbol that
+include/*.h declares, and rejects bad arguments before enqueuing anything.
+No call here reaches a kernel, so none needs a GPU."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2505_18932_gb300 import build as b
+    b.build()
+    from paper_2505_18932_gb300 import gvs
+    return gvs.load()
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"GVS_API\s+[\w\s\*]*?\b(gvs_\w+)\s*\(", src):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_entry_points():
+    names = declared_symbols()
+    for n in ["gvs_refine_depth", "gvs_fuse_depth", "gvs_forward_splat", "gvs_fuse_workspace_bytes",
+              "gvs_splat_workspace_bytes", "gvs_last_error", "gvs_version", "gvs_status_string"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for n in declared_symbols():
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_2505_18932_gb300 import gvs
+    assert set(declared_symbols()) <= set(gvs.API)
+
+
+def _cam(gvs, W=64, H=48):
+    from synth import camera_at
+    return gvs.camera_struct(camera_at(W, H, (0.0, 0.0, 0.0)))
+
+
+FAKE = 0x10000  # a 256-byte aligned stand-in address; never dereferenced on these paths
+
+
+def test_fuse_rejects_bad_arguments(lib):
+    from paper_2505_18932_gb300 import gvs
+    cams = (gvs.GvsCamera * 2)(_cam(gvs), _cam(gvs))
+    tgt = _cam(gvs)
+    good = dict(num_samples=64, z_near=0.5, z_far=5.0, mu=0.05, weight_const=0.001, window=7, normalize=0)
+    ws = lib.gvs_fuse_workspace_bytes(2, 64, 48)
+    assert ws == 2 * 64 * 48 * 8
+
+    def call(params=good, cams=cams, n=2, target=tgt, fused=FAKE, wsp=FAKE, wsb=ws, depths=FAKE):
+        p = gvs.GvsFuseParams(**params)
+        return lib.gvs_fuse_depth(cams, depths, n, ctypes.byref(target) if target is not None else None,
+                                  ctypes.byref(p), fused, None, wsp, wsb, None)
+
+    for bad in [dict(num_samples=1), dict(z_near=0.0), dict(z_near=5.0), dict(mu=0.0), dict(mu=float("nan")),
+                dict(window=6), dict(window=17), dict(normalize=2), dict(weight_const=-1.0),
+                dict(num_samples=40000)]:
+        assert call(params={**good, **bad}) == 1, bad
+        assert lib.gvs_last_error()
+    assert call(n=33) == 1
+    assert call(n=-1) == 1
+    assert call(fused=None) == 1
+    assert call(fused=FAKE + 4) == 1           # misaligned
+    assert call(depths=None) == 1
+    assert call(wsb=ws - 1) == 3                # workspace too small
+    assert call(wsp=FAKE + 16) == 3             # workspace misaligned
+    bad_cam = _cam(gvs)
+    bad_cam.fx = -1.0
+    assert call(target=bad_cam) == 1
+    odd = (gvs.GvsCamera * 2)(_cam(gvs), _cam(gvs, 32, 48))   # different input sizes
+    assert call(cams=odd) == 1
+    nan_cam = (gvs.GvsCamera * 2)(_cam(gvs), _cam(gvs))
+    nan_cam[1].R[4] = float("nan")
+    assert call(cams=nan_cam) == 1
+
+
+def test_splat_rejects_bad_arguments(lib):
+    from paper_2505_18932_gb300 import gvs
+    cams = (gvs.GvsCamera * 1)(_cam(gvs))
+    tgt = _cam(gvs)
+    ws = lib.gvs_splat_workspace_bytes(1, 64, 48)
+    assert ws == 64 * 48 * 8
+
+    def call(fp=1, mhw=2.0, mug=0.04, fused=FAKE, guided=FAKE, winner=FAKE, wsb=ws):
+        p = gvs.GvsSplatParams(fp, mhw, mug)
+        return lib.gvs_forward_splat(cams, FAKE, FAKE, 1, ctypes.byref(tgt), ctypes.byref(p), fused, winner,
+                                     None, None, None, guided, FAKE, wsb, None)
+
+    assert call(fp=2) == 1
+    assert call(mhw=0.25) == 1
+    assert call(mug=-1.0) == 1
+    assert call(fused=None) == 1       # guided mask without the fused depth
+    assert call(winner=None) == 1
+    assert call(winner=FAKE + 8) == 1
+    assert call(wsb=ws - 8) == 3
+
+
+def test_refine_rejects_bad_arguments(lib):
+    from paper_2505_18932_gb300 import gvs
+
+    def call(tau=0.03, n=2, W=64, H=48, rgba=FAKE, depth=FAKE, state=FAKE):
+        p = gvs.GvsRefineParams(tau)
+        return lib.gvs_refine_depth(rgba, FAKE, depth, state, None, n, W, H, ctypes.byref(p), None)
+
+    assert call(tau=-0.1) == 1
+    assert call(tau=1.5) == 1
+    assert call(tau=float("nan")) == 1
+    assert call(n=33) == 1
+    assert call(W=0) == 1
+    assert call(H=20000) == 1
+    assert call(rgba=None) == 1
+    assert call(state=FAKE + 4) == 1
+    assert call(n=0) == 0           # no views: nothing to do
+    assert lib.gvs_refine_depth(FAKE, FAKE, FAKE, FAKE, None, 1, 4, 4, None, None) == 1
+
+
+def test_status_strings(lib):
+    for s in range(6):
+        assert lib.gvs_status_string(s)
+    assert lib.gvs_version().startswith(b"gvs")
+
+
+def test_binding_refuses_cpu_tensors():
+    import torch
+    from paper_2505_18932_gb300 import gvs
+    with pytest.raises(ValueError):
+        gvs._ptr(torch.zeros(4))

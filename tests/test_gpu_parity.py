@@ -1,0 +1,252 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Integer and byte outputs (mask, filtered depth copy, winner, warped colour,
+warped depth bits, alpha) must match bit for bit; the fused depth must match
+within 1e-4 relative on every pixel the oracle does not flag as ambiguous
+(a sign or cut-off decision within FP32 rounding of its threshold)."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_util import compare_fused, to_dev, u32
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gvs():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2505_18932_gb300 import gvs as g
+    g.load()
+    return g
+
+
+def _workload(name, **kw):
+    from synth import configs
+    return getattr(configs, name)(**kw)
+
+
+# ---------------------------------------------------------------- refine --
+
+@pytest.mark.parametrize("shape", [(3, 23, 37), (1, 1, 5), (8, 1080, 1920)])
+def test_refine_matches_oracle(gvs, oracle_mod, shape):
+    N, H, W = shape
+    rng = np.random.default_rng(N * 1000 + H)
+    a = rng.integers(0, 256, (N, H, W, 4), dtype=np.uint8)
+    b = a.copy()
+    sel = rng.random((N, H, W)) < 0.3
+    b[sel] = np.clip(a[sel].astype(int) + rng.integers(-12, 13, (sel.sum(), 4)), 0, 255).astype(np.uint8)
+    d = rng.uniform(0.5, 6.0, (N, H, W)).astype(np.float32)
+    d[rng.random((N, H, W)) < 0.01] = np.nan
+    prev = rng.uniform(0.5, 6.0, (N, H, W)).astype(np.float32)
+    ref_s, ref_m = oracle_mod.refine_depth(a, b, d, prev, 0.03)
+    st = to_dev(prev)
+    mask = torch.empty((N, H, W), dtype=torch.uint8, device="cuda")
+    gvs.refine_depth(to_dev(u32(a)), to_dev(u32(b)), to_dev(d), st, mask, tau=0.03)
+    torch.cuda.synchronize()
+    assert np.array_equal(mask.cpu().numpy(), ref_m)
+    assert np.array_equal(st.cpu().numpy().view(np.uint32), ref_s.view(np.uint32))
+    # first frame: depth copied, mask all ones
+    st2 = to_dev(prev)
+    gvs.refine_depth(to_dev(u32(a)), None, to_dev(d), st2, mask, tau=0.03)
+    torch.cuda.synchronize()
+    assert mask.cpu().numpy().min() == 1
+    assert np.array_equal(st2.cpu().numpy().view(np.uint32), d.view(np.uint32))
+
+
+# ------------------------------------------------------------------ fuse --
+
+def _fuse_case(gvs, oracle_mod, w, frame=0, normalize=False, window=7, pixels=None, mu=None):
+    rgb, d = w.render_inputs(frame)
+    mu = w.mu if mu is None else mu
+    tgt = w.targets_at(frame)[0]
+    fused, cross = gvs.fuse_depth(w.inputs, to_dev(d), tgt, w.num_samples, w.z_near, w.z_far, mu,
+                                  window=window, normalize=normalize)
+    torch.cuda.synchronize()
+    ref = oracle_mod.fuse_depth(w.inputs, d, tgt, w.num_samples, w.z_near, w.z_far, mu, window=window,
+                                normalize=normalize, pixels=pixels)
+    if pixels is not None:
+        where = (pixels[:, 1], pixels[:, 0])
+        return compare_fused(fused, cross, ref, where), ref
+    return compare_fused(fused, cross, ref), ref
+
+
+def test_fuse_tiny_ragged(gvs, oracle_mod):
+    from synth import configs
+    w = configs.tiny(70, 45, 3, 24)
+    frac, ref = _fuse_case(gvs, oracle_mod, w)
+    assert (ref["index"] >= 0).mean() > 0.3
+
+
+@pytest.mark.parametrize("normalize", [False, True])
+def test_fuse_plain_320x240(gvs, oracle_mod, normalize):
+    _fuse_case(gvs, oracle_mod, _workload("plain_320x240"), normalize=normalize)
+
+
+@pytest.mark.parametrize("window", [1, 3, 9, 15])
+def test_fuse_windows(gvs, oracle_mod, window):
+    from synth import configs
+    _fuse_case(gvs, oracle_mod, configs.tiny(40, 30, 2, 20), window=window)
+
+
+@pytest.mark.parametrize("K", [1, 5, 12, 32])
+def test_fuse_view_counts(gvs, oracle_mod, K):
+    from synth import configs
+    _fuse_case(gvs, oracle_mod, configs.tiny(24, 18, K, 16))
+
+
+def test_fuse_full_size_sampled(gvs, oracle_mod):
+    """8 x 1920x1080 inputs, D=128, in the launch configuration the benchmark times;
+    2048 seeded target pixels checked against the oracle one by one."""
+    w = _workload("headline_8x1080p")
+    rng = np.random.default_rng(7)
+    pix = np.stack([rng.integers(0, 1920, 2048), rng.integers(0, 1080, 2048)], 1).astype(np.int32)
+    _fuse_case(gvs, oracle_mod, w, frame=1, pixels=pix)
+
+
+def test_fuse_video_720p_sampled(gvs, oracle_mod):
+    w = _workload("video_8x720p")
+    rng = np.random.default_rng(8)
+    pix = np.stack([rng.integers(0, 1280, 1024), rng.integers(0, 720, 1024)], 1).astype(np.int32)
+    _fuse_case(gvs, oracle_mod, w, frame=12, pixels=pix)
+
+
+def test_fuse_invalid_depths_and_no_views(gvs, oracle_mod):
+    from synth import configs
+    w = configs.tiny(40, 30, 3, 24)
+    _, d = w.render_inputs(0)
+    rng = np.random.default_rng(1)
+    for bad in [0.0, -1.0, np.nan, np.inf]:
+        d[rng.random(d.shape) < 0.05] = bad
+    tgt = w.targets[0]
+    fused, cross = gvs.fuse_depth(w.inputs, to_dev(d), tgt, w.num_samples, w.z_near, w.z_far, w.mu)
+    ref = oracle_mod.fuse_depth(w.inputs, d, tgt, w.num_samples, w.z_near, w.z_far, w.mu)
+    torch.cuda.synchronize()
+    compare_fused(fused, cross, ref)
+    # no input views: every ray has W = 0, no crossing anywhere
+    fused0, cross0 = gvs.fuse_depth([], torch.empty((0, 30, 40), device="cuda"), tgt, 16, 0.5, 5.0, 0.05)
+    torch.cuda.synchronize()
+    assert (fused0.cpu().numpy() == 0).all() and (cross0.cpu().numpy() == -1).all()
+
+
+def test_fuse_deterministic(gvs):
+    w = _workload("plain_320x240")
+    _, d = w.render_inputs(0)
+    dd = to_dev(d)
+    a, ai = gvs.fuse_depth(w.inputs, dd, w.targets[0], w.num_samples, w.z_near, w.z_far, w.mu)
+    b, bi = gvs.fuse_depth(w.inputs, dd, w.targets[0], w.num_samples, w.z_near, w.z_far, w.mu)
+    torch.cuda.synchronize()
+    assert torch.equal(a.view(torch.int32), b.view(torch.int32)) and torch.equal(ai, bi)
+
+
+# ----------------------------------------------------------------- splat --
+
+def _splat_case(gvs, oracle_mod, w, frame=0, footprint=True, max_hw=2.0, slots=None, fused=None):
+    rgb, d = w.render_inputs(frame)
+    tgt = w.targets_at(frame)[0]
+    if fused is None:
+        _, gt = w.render_target_gt(tgt, frame)
+        fused = gt   # seeded analytic depth: the same input for both sides
+    N = len(w.inputs)
+    ws = None
+    if slots:
+        ws = gvs.workspace(slots * gvs.splat_workspace_bytes(N, tgt.width, tgt.height))
+    out = gvs.forward_splat(w.inputs, to_dev(d), to_dev(u32(rgb)), tgt, fused=to_dev(fused.astype(np.float32)),
+                            footprint=footprint, max_half_width=max_hw, mu_guide=w.mu, ws=ws)
+    torch.cuda.synchronize()
+    ref = oracle_mod.forward_splat(w.inputs, d, u32(rgb), tgt, footprint=footprint, max_half_width=max_hw,
+                                   mu_guide=w.mu, fused=fused.astype(np.float32).astype(np.float64))
+    assert np.array_equal(out["winner"].cpu().numpy(), ref["winner"])
+    assert np.array_equal(out["warped_rgba"].cpu().numpy().view(np.uint32), ref["warped_rgba"])
+    assert np.array_equal(out["warped_depth"].cpu().numpy().view(np.uint32), ref["warped_depth"].view(np.uint32))
+    assert np.array_equal(out["alpha"].cpu().numpy(), ref["alpha"])
+    amb = ref["guided_ambiguous"].astype(bool)
+    g = out["guided"].cpu().numpy()
+    assert np.array_equal(g[~amb], ref["guided"][~amb])
+    assert amb.mean() < 1e-3
+    return ref
+
+
+@pytest.mark.parametrize("footprint", [True, False])
+def test_splat_tiny_ragged(gvs, oracle_mod, footprint):
+    from synth import configs
+    _splat_case(gvs, oracle_mod, configs.tiny(70, 45, 3, 24), footprint=footprint)
+
+
+@pytest.mark.parametrize("slots", [None, 2, 4])
+def test_splat_plain_320x240(gvs, oracle_mod, slots):
+    _splat_case(gvs, oracle_mod, _workload("plain_320x240"), slots=slots)
+
+
+def test_splat_magnified_footprints(gvs, oracle_mod):
+    """Target with twice the focal length: footprints span several pixels (cap 3.5)."""
+    from synth import configs
+    w = configs.tiny(64, 48, 2, 16)
+    t = w.targets[0]
+    t.fx, t.fy = t.fx * 3.0, t.fy * 3.0
+    _splat_case(gvs, oracle_mod, w, max_hw=3.5)
+
+
+def test_splat_full_size(gvs, oracle_mod):
+    """8 x 1920x1080 inputs into one 1920x1080 target: every winner, bit for bit."""
+    _splat_case(gvs, oracle_mod, _workload("headline_8x1080p"), frame=1)
+
+
+def test_splat_end_to_end_with_fused(gvs, oracle_mod):
+    """Guided mask from each side's own fused depth (oracle fused vs GPU fused)."""
+    from synth import configs
+    w = configs.tiny(70, 45, 3, 40)
+    rgb, d = w.render_inputs(0)
+    tgt = w.targets[0]
+    fused, _ = gvs.fuse_depth(w.inputs, to_dev(d), tgt, w.num_samples, w.z_near, w.z_far, w.mu)
+    out = gvs.forward_splat(w.inputs, to_dev(d), to_dev(u32(rgb)), tgt, fused=fused, mu_guide=w.mu)
+    torch.cuda.synchronize()
+    rf = oracle_mod.fuse_depth(w.inputs, d, tgt, w.num_samples, w.z_near, w.z_far, w.mu)
+    ref = oracle_mod.forward_splat(w.inputs, d, u32(rgb), tgt, mu_guide=w.mu, fused=rf["depth"])
+    amb = ref["guided_ambiguous"].astype(bool) | rf["ambiguous"].astype(bool)[None]
+    g = out["guided"].cpu().numpy()
+    assert np.array_equal(g[~amb], ref["guided"][~amb])
+
+
+def test_splat_deterministic(gvs):
+    w = _workload("plain_320x240")
+    rgb, d = w.render_inputs(0)
+    dd, cc = to_dev(d), to_dev(u32(rgb))
+    a = gvs.forward_splat(w.inputs, dd, cc, w.targets[0])
+    b = gvs.forward_splat(w.inputs, dd, cc, w.targets[0])
+    torch.cuda.synchronize()
+    for k in a:
+        assert torch.equal(a[k], b[k]), k
+
+
+def test_fuse_two_stage_equals_one_call(gvs):
+    """gvs_weight_map + gvs_fuse_depth_from_map give the same bits as gvs_fuse_depth."""
+    from synth import configs
+    w = configs.tiny(70, 45, 4, 32)
+    _, d = w.render_inputs(0)
+    dd = to_dev(d)
+    a, ai = gvs.fuse_depth(w.inputs, dd, w.targets[0], w.num_samples, w.z_near, w.z_far, w.mu)
+    m = gvs.weight_map(dd, w.mu)
+    b, bi = gvs.fuse_depth_from_map(w.inputs, m, tuple(d.shape), w.targets[0], w.num_samples, w.z_near, w.z_far,
+                                    w.mu)
+    torch.cuda.synchronize()
+    assert torch.equal(a.view(torch.int32), b.view(torch.int32)) and torch.equal(ai, bi)
+
+
+def test_weight_map_matches_oracle_weight(gvs, oracle_mod):
+    """The per-pixel map equals the Supplement A.1 weight evaluated at that pixel (FP32 vs FP64)."""
+    from synth import configs
+    w = configs.tiny(37, 29, 2, 16)
+    _, d = w.render_inputs(0)
+    d[0, 3, 4] = np.nan
+    d[1, 10:12, 7] = 0.0
+    m = gvs.weight_map(to_dev(d), w.mu)
+    torch.cuda.synchronize()
+    mp = m[: d.size * 8].view(torch.float32).cpu().numpy().reshape(d.shape + (2,))
+    for k in range(d.shape[0]):
+        for v in range(d.shape[1]):
+            for u in range(d.shape[2]):
+                ref = oracle_mod.weight(d[k], u, v, w.mu)
+                assert abs(mp[k, v, u, 1] - ref) <= 2e-6 * max(ref, 1e-3), (k, v, u)
+                dv = d[k, v, u]
+                assert mp[k, v, u, 0] == (dv if (np.isfinite(dv) and dv > 0) else 0.0)
