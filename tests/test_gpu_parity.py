@@ -73,7 +73,7 @@ def _fuse_case(gvs, oracle_mod, w, frame=0, normalize=False, window=7, pixels=No
 
 def test_fuse_tiny_ragged(gvs, oracle_mod):
     from synth import configs
-    w = configs.tiny(70, 45, 3, 24)
+    w = configs.tiny(70, 45, 3, 96)
     frac, ref = _fuse_case(gvs, oracle_mod, w)
     assert (ref["index"] >= 0).mean() > 0.3
 
@@ -86,13 +86,13 @@ def test_fuse_plain_320x240(gvs, oracle_mod, normalize):
 @pytest.mark.parametrize("window", [1, 3, 9, 15])
 def test_fuse_windows(gvs, oracle_mod, window):
     from synth import configs
-    _fuse_case(gvs, oracle_mod, configs.tiny(40, 30, 2, 20), window=window)
+    _fuse_case(gvs, oracle_mod, configs.tiny(40, 30, 2, 96), window=window)
 
 
 @pytest.mark.parametrize("K", [1, 5, 12, 32])
 def test_fuse_view_counts(gvs, oracle_mod, K):
     from synth import configs
-    _fuse_case(gvs, oracle_mod, configs.tiny(24, 18, K, 16))
+    _fuse_case(gvs, oracle_mod, configs.tiny(24, 18, K, 96))
 
 
 def test_fuse_full_size_sampled(gvs, oracle_mod):
@@ -113,7 +113,7 @@ def test_fuse_video_720p_sampled(gvs, oracle_mod):
 
 def test_fuse_invalid_depths_and_no_views(gvs, oracle_mod):
     from synth import configs
-    w = configs.tiny(40, 30, 3, 24)
+    w = configs.tiny(40, 30, 3, 96)
     _, d = w.render_inputs(0)
     rng = np.random.default_rng(1)
     for bad in [0.0, -1.0, np.nan, np.inf]:
@@ -160,10 +160,9 @@ def _splat_case(gvs, oracle_mod, w, frame=0, footprint=True, max_hw=2.0, slots=N
     assert np.array_equal(out["warped_rgba"].cpu().numpy().view(np.uint32), ref["warped_rgba"])
     assert np.array_equal(out["warped_depth"].cpu().numpy().view(np.uint32), ref["warped_depth"].view(np.uint32))
     assert np.array_equal(out["alpha"].cpu().numpy(), ref["alpha"])
-    amb = ref["guided_ambiguous"].astype(bool)
-    g = out["guided"].cpu().numpy()
-    assert np.array_equal(g[~amb], ref["guided"][~amb])
-    assert amb.mean() < 1e-3
+    # both sides get the same FP32 fused depth; |z - fused| of two floats within a factor
+    # of two is exact in FP32, so the guided mask must match everywhere
+    assert np.array_equal(out["guided"].cpu().numpy(), ref["guided"])
     return ref
 
 
@@ -195,7 +194,7 @@ def test_splat_full_size(gvs, oracle_mod):
 def test_splat_end_to_end_with_fused(gvs, oracle_mod):
     """Guided mask from each side's own fused depth (oracle fused vs GPU fused)."""
     from synth import configs
-    w = configs.tiny(70, 45, 3, 40)
+    w = configs.tiny(70, 45, 3, 96)
     rgb, d = w.render_inputs(0)
     tgt = w.targets[0]
     fused, _ = gvs.fuse_depth(w.inputs, to_dev(d), tgt, w.num_samples, w.z_near, w.z_far, w.mu)
