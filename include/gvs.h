@@ -129,7 +129,9 @@ GVS_API gvs_status gvs_refine_depth(const uint32_t *rgba_t, const uint32_t *rgba
                             float *depth_state, uint8_t *mask, int32_t n_views, int32_t width,
                             int32_t height, const gvs_refine_params *params, void *stream);
 
-/* Workspace bytes for gvs_fuse_depth: a packed (depth, weight) float2 map per input view. */
+/* Workspace bytes for gvs_fuse_depth (the "map" of gvs_weight_map): the packed
+ * (depth, weight) float2 of every input pixel followed by per-view depth
+ * bounds over 8, 32 and 128 pixel tiles and over the whole view. */
 GVS_API size_t gvs_fuse_workspace_bytes(int32_t n_views, int32_t width, int32_t height);
 
 /*
@@ -169,23 +171,28 @@ GVS_API gvs_status gvs_fuse_depth(const gvs_camera *in_cams, const float *in_dep
  * gvs_weight_map -- the two stages of gvs_fuse_depth, callable separately.
  * Stage 1: the confidence weight of Supplement A.1 at every input pixel.
  * With nearest-pixel sampling the weight at a sample is a function of the
- * sampled pixel only, so it is computed once per pixel:
- *   dw_map[k][y][x] = (d, omega) as float2, with omega as in gvs_fuse_depth,
- *   and (0, 0) where d is invalid.
- *   in_depths : float [n_views][height][width];  dw_map : float2, same shape
- *               (8 bytes per pixel, gvs_fuse_workspace_bytes() in total)
+ * sampled pixel only, so it is computed once per pixel and stored with the
+ * depth as (d, omega), (0, 0) where d is invalid; with it go the min and max
+ * valid depth of every 8, 32 and 128 pixel tile and of each whole view,
+ * which let the march skip runs of samples that provably hold no crossing.
+ *   in_depths : float [n_views][height][width]
+ *   map       : >= gvs_fuse_workspace_bytes(n_views, width, height) bytes,
+ *               256-byte aligned; its layout is private to the library
  */
 GVS_API gvs_status gvs_weight_map(const float *in_depths, int32_t n_views, int32_t width, int32_t height,
-                                  float mu, float weight_const, int32_t window, void *dw_map, void *stream);
+                                  float mu, float weight_const, int32_t window, void *map, size_t map_bytes,
+                                  void *stream);
 
 /*
  * gvs_fuse_depth_from_map -- stage 2: the TSDF march and zero crossing of
  * gvs_fuse_depth (Supplement A.1, Eq. 3) reading a map written by
- * gvs_weight_map.  params->weight_const and params->window are not used.
+ * gvs_weight_map for the same depths.  params->weight_const and
+ * params->window are not used.
  */
-GVS_API gvs_status gvs_fuse_depth_from_map(const gvs_camera *in_cams, const void *dw_map, int32_t n_views,
-                                           const gvs_camera *target, const gvs_fuse_params *params,
-                                           float *fused_depth, int16_t *crossing, void *stream);
+GVS_API gvs_status gvs_fuse_depth_from_map(const gvs_camera *in_cams, const void *map, size_t map_bytes,
+                                           int32_t n_views, const gvs_camera *target,
+                                           const gvs_fuse_params *params, float *fused_depth, int16_t *crossing,
+                                           void *stream);
 
 /* Workspace bytes for gvs_forward_splat: one 64-bit z-buffer of the target size.
  * A workspace holding several such buffers lets several views splat in one pass. */

@@ -144,7 +144,7 @@ gvs_status gvs_refine_depth(const uint32_t *rgba_t, const uint32_t *rgba_prev, c
 
 size_t gvs_fuse_workspace_bytes(int32_t n_views, int32_t width, int32_t height) {
     if (n_views < 0 || width < 0 || height < 0) return 0;
-    return align_up((size_t)n_views * (size_t)width * (size_t)height * sizeof(float2), 256);
+    return gvs::map_layout(n_views, width, height).total;
 }
 
 }  // extern "C"
@@ -179,11 +179,22 @@ gvs_status check_weight_params(float mu, float weight_const, int32_t window) {
     return GVS_OK;
 }
 
-gvs::FuseArgs fuse_args(const gvs_camera *in_cams, const void *dw, int32_t n_views, int32_t W, int32_t H,
+gvs::FuseArgs fuse_args(const gvs_camera *in_cams, const void *map, int32_t n_views, int32_t W, int32_t H,
                         const gvs_camera *target, const gvs_fuse_params &p, float *fused, int16_t *crossing) {
     gvs::FuseArgs a;
     memset(&a, 0, sizeof(a));
-    a.dw = reinterpret_cast<const float2 *>(dw);
+    const gvs::MapLayout L = gvs::map_layout(n_views, W, H);
+    const char *m = reinterpret_cast<const char *>(map);
+    if (n_views > 0) {
+        a.dw = reinterpret_cast<const float2 *>(m + L.off_dw);
+        a.t3 = reinterpret_cast<const float2 *>(m + L.off_t3);
+        a.t5 = reinterpret_cast<const float2 *>(m + L.off_t5);
+        a.t7 = reinterpret_cast<const float2 *>(m + L.off_t7);
+        a.tg = reinterpret_cast<const float2 *>(m + L.off_g);
+    }
+    a.t3w = L.t3w; a.t3h = L.t3h;
+    a.t5w = L.t5w; a.t5h = L.t5h;
+    a.t7w = L.t7w; a.t7h = L.t7h;
     a.K = n_views;
     a.W = W;
     a.H = H;
@@ -193,6 +204,7 @@ gvs::FuseArgs fuse_args(const gvs_camera *in_cams, const void *dw, int32_t n_vie
     a.zn = p.z_near;
     a.dz = (float)(((double)p.z_far - (double)p.z_near) / (double)(p.num_samples - 1));
     a.inv_mu = (float)(1.0 / (double)p.mu);
+    a.behind = (float)(1.0001 * (double)p.mu);
     a.normalize = p.normalize;
     a.fused = fused;
     a.crossing = crossing;
@@ -205,31 +217,33 @@ gvs::FuseArgs fuse_args(const gvs_camera *in_cams, const void *dw, int32_t n_vie
 extern "C" {
 
 gvs_status gvs_weight_map(const float *in_depths, int32_t n_views, int32_t width, int32_t height, float mu,
-                          float weight_const, int32_t window, void *dw_map, void *stream) {
+                          float weight_const, int32_t window, void *map, size_t map_bytes, void *stream) {
     if (n_views < 0 || n_views > GVS_MAX_VIEWS) return fail(GVS_ERR_INVALID_ARG, "weight map: n_views out of range");
     if (width < 1 || height < 1 || width > GVS_MAX_DIM || height > GVS_MAX_DIM)
         return fail(GVS_ERR_INVALID_ARG, "weight map: image size out of range");
     gvs_status s = check_weight_params(mu, weight_const, window);
     if (s != GVS_OK) return s;
     if (n_views == 0) return GVS_OK;
-    if (!in_depths || !dw_map) return fail(GVS_ERR_INVALID_ARG, "weight map: NULL array");
-    if (!aligned(in_depths, 16) || !aligned(dw_map, 16))
-        return fail(GVS_ERR_INVALID_ARG, "weight map: arrays must be 16-byte aligned");
-    cudaError_t e = gvs::launch_weight_map(in_depths, reinterpret_cast<float2 *>(dw_map), n_views, width, height,
-                                           mu, weight_const, window, (cudaStream_t)stream);
+    if (!in_depths || !aligned(in_depths, 16)) return fail(GVS_ERR_INVALID_ARG, "weight map: in_depths is NULL or misaligned");
+    const size_t need = gvs_fuse_workspace_bytes(n_views, width, height);
+    if (!map || map_bytes < need || !aligned(map, 256))
+        return fail(GVS_ERR_WORKSPACE, "weight map: map needs %zu bytes, 256-byte aligned", need);
+    cudaError_t e = gvs::launch_weight_map(in_depths, map, n_views, width, height, mu, weight_const, window,
+                                           (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "weight map launch");
     return GVS_OK;
 }
 
-gvs_status gvs_fuse_depth_from_map(const gvs_camera *in_cams, const void *dw_map, int32_t n_views,
+gvs_status gvs_fuse_depth_from_map(const gvs_camera *in_cams, const void *map, size_t map_bytes, int32_t n_views,
                                    const gvs_camera *target, const gvs_fuse_params *params, float *fused_depth,
                                    int16_t *crossing, void *stream) {
     int32_t W = 0, H = 0;
     gvs_status s = check_fuse_common(in_cams, n_views, target, params, fused_depth, crossing, &W, &H);
     if (s != GVS_OK) return s;
-    if (n_views > 0 && (!dw_map || !aligned(dw_map, 16)))
-        return fail(GVS_ERR_INVALID_ARG, "fuse: dw_map is NULL or not 16-byte aligned");
-    gvs::FuseArgs a = fuse_args(in_cams, dw_map, n_views, W, H, target, *params, fused_depth, crossing);
+    const size_t need = gvs_fuse_workspace_bytes(n_views, W, H);
+    if (n_views > 0 && (!map || map_bytes < need || !aligned(map, 256)))
+        return fail(GVS_ERR_WORKSPACE, "fuse: map needs %zu bytes, 256-byte aligned", need);
+    gvs::FuseArgs a = fuse_args(in_cams, map, n_views, W, H, target, *params, fused_depth, crossing);
     cudaError_t e = gvs::launch_fuse(a, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "fuse: launch");
     return GVS_OK;
@@ -249,8 +263,8 @@ gvs_status gvs_fuse_depth(const gvs_camera *in_cams, const float *in_depths, int
     if (need > 0 && (!workspace || workspace_bytes < need || !aligned(workspace, 256)))
         return fail(GVS_ERR_WORKSPACE, "fuse: workspace needs %zu bytes, 256-byte aligned", need);
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = gvs::launch_weight_map(in_depths, reinterpret_cast<float2 *>(workspace), n_views, W, H,
-                                           params->mu, params->weight_const, params->window, st);
+    cudaError_t e = gvs::launch_weight_map(in_depths, workspace, n_views, W, H, params->mu, params->weight_const,
+                                           params->window, st);
     if (e != cudaSuccess) return cuda_fail(e, "fuse: weight map launch");
     gvs::FuseArgs a = fuse_args(in_cams, workspace, n_views, W, H, target, *params, fused_depth, crossing);
     e = gvs::launch_fuse(a, st);

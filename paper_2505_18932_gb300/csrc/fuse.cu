@@ -1,14 +1,20 @@
 // Image-based TSDF fusion in the target view (Supplement A.1, Eq. 3).
 //
-// Two kernels:
-//  * weight_map: the confidence weight of Supplement A.1 depends only on the
-//    sampled input pixel (nearest-pixel sampling), so it is computed once per
-//    input pixel and packed with the depth as float2 (d, omega).  An invalid
-//    pixel is stored as (0, 0): its signed distance is then below -1 and it
-//    never contributes.  7x7 stencil over a shared-memory tile with halo.
-//  * fuse: one thread per target pixel marches the D samples in registers,
-//    one 8-byte gather per (sample, view), and stops at the first +/-
-//    crossing.  Per-ray affine coefficients make each projection three FMAs.
+// weight_map  : the confidence weight of Supplement A.1 depends only on the
+//               sampled input pixel (nearest-pixel sampling), so it is
+//               computed once per input pixel and packed with the depth as
+//               float2 (d, omega); an invalid pixel is stored as (0, 0), whose
+//               signed distance is below -1 so it never contributes.  7x7
+//               stencil over a shared-memory tile with halo.  The same kernel
+//               writes the min/max valid depth of every 8x8 tile.
+// depth_bounds: reduces the 8x8 tiles to 32x32, 128x128 and whole-view bounds.
+// fuse        : one thread per target pixel marches the D samples in
+//               registers (one 8-byte gather per sample and view) and stops at
+//               the first +/- crossing.  Before evaluating samples it tries to
+//               prove that a run of them holds no crossing end (see
+//               segment_is_free); such runs are skipped.  A skipped sample
+//               provably has S > 0 or W = 0, so the first crossing, its index
+//               and its interpolated depth are exactly those of the full march.
 #include <math.h>
 
 #include "gvs_internal.cuh"
@@ -18,22 +24,29 @@ namespace {
 
 constexpr int WM_TX = 32;
 constexpr int WM_TY = 8;
+#define kInf __int_as_float(0x7f800000)
 
 __device__ __forceinline__ bool valid_depth(float d) { return isfinite(d) && d > 0.0f; }
 
 // R = window / 2.  Tile of WM_TX x WM_TY outputs; halo replicated at borders.
 template <int R>
 __global__ void __launch_bounds__(WM_TX *WM_TY) weight_map_kernel(const float *__restrict__ depth,
-                                                                  float2 *__restrict__ dw, int W, int H,
-                                                                  float mu, float wconst, float inv_w2) {
+                                                                  char *__restrict__ map, MapLayout L, float mu,
+                                                                  float wconst, float inv_w2) {
     constexpr int SW = WM_TX + 2 * R;
     constexpr int SH = WM_TY + 2 * R;
     __shared__ float tile[SH][SW];
+    __shared__ float2 red[WM_TY][WM_TX / 8];
+    const int W = L.W, H = L.H;
     const int k = blockIdx.z;
     const float *dep = depth + (size_t)k * W * H;
     const int x0 = blockIdx.x * WM_TX - R;
     const int y0 = blockIdx.y * WM_TY - R;
     const int tid = threadIdx.y * WM_TX + threadIdx.x;
+    if (blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) {
+        // whole-view bounds, reduced into by depth_bounds with integer atomics on the float bits
+        reinterpret_cast<int2 *>(map + L.off_g)[k] = make_int2(0x7f800000, (int)0xff800000u);
+    }
     for (int e = tid; e < SW * SH; e += WM_TX * WM_TY) {
         const int sy = e / SW, sx = e - sy * SW;
         const int gx = min(max(x0 + sx, 0), W - 1);
@@ -44,10 +57,10 @@ __global__ void __launch_bounds__(WM_TX *WM_TY) weight_map_kernel(const float *_
     __syncthreads();
     const int x = blockIdx.x * WM_TX + threadIdx.x;
     const int y = blockIdx.y * WM_TY + threadIdx.y;
-    if (x >= W || y >= H) return;
+    const bool inside = x < W && y < H;
     const float dc = tile[threadIdx.y + R][threadIdx.x + R];
-    float2 out = make_float2(0.0f, 0.0f);
-    if (dc == dc) {  // valid centre
+    const bool valid = inside && (dc == dc);
+    if (valid) {
         float nu = 0.0f;
 #pragma unroll
         for (int dy = 0; dy <= 2 * R; ++dy) {
@@ -59,9 +72,70 @@ __global__ void __launch_bounds__(WM_TX *WM_TY) weight_map_kernel(const float *_
             }
         }
         const float w = nu > 0.0f ? fminf(wconst * rsqrtf(nu * inv_w2), 1.0f) : 1.0f;
-        out = make_float2(dc, w);
+        reinterpret_cast<float2 *>(map + L.off_dw)[(size_t)k * W * H + (size_t)y * W + x] = make_float2(dc, w);
+    } else if (inside) {
+        reinterpret_cast<float2 *>(map + L.off_dw)[(size_t)k * W * H + (size_t)y * W + x] = make_float2(0.0f, 0.0f);
     }
-    dw[(size_t)k * W * H + (size_t)y * W + x] = out;
+    // 8x8 tile bounds: reduce over the 8 lanes of a tile row, then over the 8 rows
+    float lo = valid ? dc : kInf, hi = valid ? dc : -kInf;
+#pragma unroll
+    for (int m = 1; m < 8; m <<= 1) {
+        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, m));
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, m));
+    }
+    if ((threadIdx.x & 7) == 0) red[threadIdx.y][threadIdx.x >> 3] = make_float2(lo, hi);
+    __syncthreads();
+    if (threadIdx.y == 0 && threadIdx.x < WM_TX / 8) {
+        float2 b = red[0][threadIdx.x];
+#pragma unroll
+        for (int r = 1; r < WM_TY; ++r) {
+            b.x = fminf(b.x, red[r][threadIdx.x].x);
+            b.y = fmaxf(b.y, red[r][threadIdx.x].y);
+        }
+        const int tx = blockIdx.x * (WM_TX / 8) + threadIdx.x;
+        const int ty = blockIdx.y;  // WM_TY == 8
+        if (tx < L.t3w && ty < L.t3h)
+            reinterpret_cast<float2 *>(map + L.off_t3)[((size_t)k * L.t3h + ty) * L.t3w + tx] = b;
+    }
+}
+
+// One block per (128x128 tile, view): 16x16 threads, one 8x8 tile each.
+__global__ void __launch_bounds__(256) depth_bounds_kernel(char *__restrict__ map, MapLayout L) {
+    __shared__ float2 s[16][16];
+    const int k = blockIdx.z;
+    const int tx = blockIdx.x * 16 + threadIdx.x;
+    const int ty = blockIdx.y * 16 + threadIdx.y;
+    float2 b = make_float2(kInf, -kInf);
+    if (tx < L.t3w && ty < L.t3h) b = reinterpret_cast<const float2 *>(map + L.off_t3)[((size_t)k * L.t3h + ty) * L.t3w + tx];
+    s[threadIdx.y][threadIdx.x] = b;
+    __syncthreads();
+    if ((threadIdx.x & 3) == 0 && (threadIdx.y & 3) == 0) {
+        float2 c = make_float2(kInf, -kInf);
+#pragma unroll
+        for (int dy = 0; dy < 4; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 4; ++dx) {
+                c.x = fminf(c.x, s[threadIdx.y + dy][threadIdx.x + dx].x);
+                c.y = fmaxf(c.y, s[threadIdx.y + dy][threadIdx.x + dx].y);
+            }
+        const int x5 = blockIdx.x * 4 + (threadIdx.x >> 2), y5 = blockIdx.y * 4 + (threadIdx.y >> 2);
+        if (x5 < L.t5w && y5 < L.t5h)
+            reinterpret_cast<float2 *>(map + L.off_t5)[((size_t)k * L.t5h + y5) * L.t5w + x5] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        float2 c = make_float2(kInf, -kInf);
+        for (int i = 0; i < 256; ++i) {
+            c.x = fminf(c.x, s[i >> 4][i & 15].x);
+            c.y = fmaxf(c.y, s[i >> 4][i & 15].y);
+        }
+        reinterpret_cast<float2 *>(map + L.off_t7)[((size_t)k * L.t7h + blockIdx.y) * L.t7w + blockIdx.x] = c;
+        int *g = reinterpret_cast<int *>(map + L.off_g) + 2 * k;
+        if (c.x <= c.y) {  // the tile holds a valid depth
+            atomicMin(&g[0], __float_as_int(c.x));  // positive floats order like their bits
+            atomicMax(&g[1], __float_as_int(c.y));
+        }
+    }
 }
 
 // Nearest integer (ties to even) of the exact real quotient num/den, den > 0.
@@ -85,6 +159,97 @@ __device__ __forceinline__ int nearest_of_quotient(float num, float den, float r
 
 constexpr int FZ_TX = 16;
 constexpr int FZ_TY = 8;
+constexpr int SKIP_LONG = 16;
+constexpr int SKIP_SHORT = 4;
+
+struct Ray {
+    float ax, ay, az;
+};
+
+// True when no sample s in [s0, s1] can end a crossing: for every view, every
+// pixel the samples can project to (their nearest pixels lie within one pixel
+// of the segment joining the end projections) has all valid depths strictly
+// beyond the samples' projected depths (sdf > 0: a positive term) or every
+// valid depth at least 1.0001 mu in front of them (sdf < -1: cut off), or lies
+// outside the image.  Then S_s > 0 whenever W_s > 0 throughout, so no
+// crossing pair ends inside [s0, s1].
+template <int KMAX>
+__device__ __forceinline__ bool segment_is_free(const FuseArgs &a, const Ray (&ray)[KMAX], float z0, float z1) {
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+        if (k >= a.K) break;
+        const float hz0 = __fmaf_rn(z0, ray[k].az, a.xf[k].b[2]);
+        const float hz1 = __fmaf_rn(z1, ray[k].az, a.xf[k].b[2]);
+        const bool f0 = hz0 > 1e-6f, f1 = hz1 > 1e-6f;
+        if (!f0 && !f1) continue;      // behind the camera all along: no contribution
+        if (f0 != f1) return false;    // crosses the camera plane: do not try
+        const float r0 = __fdividef(1.0f, hz0), r1 = __fdividef(1.0f, hz1);
+        const float x0 = __fmaf_rn(z0, ray[k].ax, a.xf[k].b[0]) * r0;
+        const float x1 = __fmaf_rn(z1, ray[k].ax, a.xf[k].b[0]) * r1;
+        const float y0 = __fmaf_rn(z0, ray[k].ay, a.xf[k].b[1]) * r0;
+        const float y1 = __fmaf_rn(z1, ray[k].ay, a.xf[k].b[1]) * r1;
+        const float xlo = fminf(x0, x1) - 1.0f, xhi = fmaxf(x0, x1) + 1.0f;
+        const float ylo = fminf(y0, y1) - 1.0f, yhi = fmaxf(y0, y1) + 1.0f;
+        if (!(xhi >= 0.0f && ylo <= (float)(a.H - 1) && yhi >= 0.0f && xlo <= (float)(a.W - 1))) {
+            if (xhi < 0.0f || yhi < 0.0f || xlo > (float)(a.W - 1) || ylo > (float)(a.H - 1)) continue;  // outside
+            return false;  // NaN
+        }
+        const int bx0 = (int)fmaxf(floorf(xlo), 0.0f), bx1 = (int)fminf(ceilf(xhi), (float)(a.W - 1));
+        const int by0 = (int)fmaxf(floorf(ylo), 0.0f), by1 = (int)fminf(ceilf(yhi), (float)(a.H - 1));
+        const float zlo = fminf(hz0, hz1), zhi = fmaxf(hz0, hz1);
+        const float2 *tl;
+        int sh, tw, th;
+        if ((bx1 >> 3) - (bx0 >> 3) <= 1 && (by1 >> 3) - (by0 >> 3) <= 1) {
+            tl = a.t3; sh = 3; tw = a.t3w; th = a.t3h;
+        } else if ((bx1 >> 5) - (bx0 >> 5) <= 1 && (by1 >> 5) - (by0 >> 5) <= 1) {
+            tl = a.t5; sh = 5; tw = a.t5w; th = a.t5h;
+        } else if ((bx1 >> 7) - (bx0 >> 7) <= 1 && (by1 >> 7) - (by0 >> 7) <= 1) {
+            tl = a.t7; sh = 7; tw = a.t7w; th = a.t7h;
+        } else {
+            const float2 g = __ldg(&a.tg[k]);
+            if (!(zhi < g.x || zlo > g.y + a.behind)) return false;
+            continue;
+        }
+        tl += (size_t)k * tw * th;
+        for (int ty = by0 >> sh; ty <= (by1 >> sh); ++ty)
+            for (int tx = bx0 >> sh; tx <= (bx1 >> sh); ++tx) {
+                const float2 b = __ldg(&tl[ty * tw + tx]);
+                if (!(zhi < b.x || zlo > b.y + a.behind)) return false;
+            }
+    }
+    return true;
+}
+
+// S and W of one sample (Supplement A.1), exactly as the full march computes them.
+template <int KMAX>
+__device__ __forceinline__ void evaluate_sample(const FuseArgs &a, const Ray (&ray)[KMAX], float zs, float &S,
+                                                float &Wsum) {
+    const size_t plane = (size_t)a.W * a.H;
+    S = 0.0f;
+    Wsum = 0.0f;
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+        if (k < a.K) {
+            const float hz = __fmaf_rn(zs, ray[k].az, a.xf[k].b[2]);
+            if (hz > 1e-6f) {
+                const float hx = __fmaf_rn(zs, ray[k].ax, a.xf[k].b[0]);
+                const float hy = __fmaf_rn(zs, ray[k].ay, a.xf[k].b[1]);
+                const float r = __fdividef(1.0f, hz);
+                const int u = nearest_of_quotient(hx, hz, r);
+                const int v = nearest_of_quotient(hy, hz, r);
+                if ((unsigned)u < (unsigned)a.W && (unsigned)v < (unsigned)a.H) {
+                    const float2 p = __ldg(&a.dw[(size_t)k * plane + (size_t)v * a.W + u]);
+                    const float sdf = (p.x - hz) * a.inv_mu;
+                    if (sdf >= -1.0f) {
+                        S = fmaf(p.y, fminf(sdf, 1.0f), S);
+                        Wsum += p.y;
+                    }
+                }
+            }
+        }
+    }
+    if (a.normalize && Wsum > 0.0f) S = S / Wsum;
+}
 
 template <int KMAX>
 __global__ void __launch_bounds__(FZ_TX *FZ_TY) fuse_kernel(const FuseArgs a) {
@@ -92,46 +257,43 @@ __global__ void __launch_bounds__(FZ_TX *FZ_TY) fuse_kernel(const FuseArgs a) {
     const int j = blockIdx.y * FZ_TY + threadIdx.y;
     if (i >= a.Wt || j >= a.Ht) return;
     const float fi = (float)i, fj = (float)j;
-    float ax[KMAX], ay[KMAX], az[KMAX];
+    Ray ray[KMAX];
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) {
         if (k < a.K) {
             const float *M = a.xf[k].M;
-            ax[k] = __fmaf_rn(M[0], fi, __fmaf_rn(M[1], fj, M[2]));
-            ay[k] = __fmaf_rn(M[3], fi, __fmaf_rn(M[4], fj, M[5]));
-            az[k] = __fmaf_rn(M[6], fi, __fmaf_rn(M[7], fj, M[8]));
+            ray[k].ax = __fmaf_rn(M[0], fi, __fmaf_rn(M[1], fj, M[2]));
+            ray[k].ay = __fmaf_rn(M[3], fi, __fmaf_rn(M[4], fj, M[5]));
+            ray[k].az = __fmaf_rn(M[6], fi, __fmaf_rn(M[7], fj, M[8]));
         }
     }
-    const size_t plane = (size_t)a.W * a.H;
     float S_prev = 0.0f, W_prev = 0.0f, z_prev = 0.0f;
+    bool have_prev = false;
     float out = 0.0f;
     int idx = -1;
-    for (int s = 0; s < a.D; ++s) {
-        const float zs = __fmaf_rn((float)s, a.dz, a.zn);
-        float S = 0.0f, Wsum = 0.0f;
-#pragma unroll
-        for (int k = 0; k < KMAX; ++k) {
-            if (k < a.K) {
-                const float hz = __fmaf_rn(zs, az[k], a.xf[k].b[2]);
-                if (hz > 1e-6f) {
-                    const float hx = __fmaf_rn(zs, ax[k], a.xf[k].b[0]);
-                    const float hy = __fmaf_rn(zs, ay[k], a.xf[k].b[1]);
-                    const float r = __fdividef(1.0f, hz);
-                    const int u = nearest_of_quotient(hx, hz, r);
-                    const int v = nearest_of_quotient(hy, hz, r);
-                    if ((unsigned)u < (unsigned)a.W && (unsigned)v < (unsigned)a.H) {
-                        const float2 p = __ldg(&a.dw[(size_t)k * plane + (size_t)v * a.W + u]);
-                        const float sdf = (p.x - hz) * a.inv_mu;
-                        if (sdf >= -1.0f) {
-                            S = fmaf(p.y, fminf(sdf, 1.0f), S);
-                            Wsum += p.y;
-                        }
-                    }
-                }
+    int s = 0;
+    int cool = 0;  // samples to evaluate before trying to skip again
+    while (s < a.D) {
+        if (cool == 0 && s < a.D - 1) {
+            const int Ll = min(SKIP_LONG, a.D - 1 - s);
+            const float z0 = __fmaf_rn((float)s, a.dz, a.zn);
+            if (segment_is_free<KMAX>(a, ray, z0, __fmaf_rn((float)(s + Ll), a.dz, a.zn))) {
+                s += Ll;  // samples s..s+Ll are not crossing ends; s+Ll is evaluated next
+                have_prev = false;
+                continue;
             }
+            const int Ls = min(SKIP_SHORT, a.D - 1 - s);
+            if (Ls < Ll && segment_is_free<KMAX>(a, ray, z0, __fmaf_rn((float)(s + Ls), a.dz, a.zn))) {
+                s += Ls;
+                have_prev = false;
+                continue;
+            }
+            cool = SKIP_SHORT;
         }
-        if (a.normalize && Wsum > 0.0f) S = S / Wsum;
-        if (s > 0 && W_prev > 0.0f && Wsum > 0.0f && S_prev > 0.0f && S <= 0.0f) {
+        const float zs = __fmaf_rn((float)s, a.dz, a.zn);
+        float S, Wsum;
+        evaluate_sample<KMAX>(a, ray, zs, S, Wsum);
+        if (have_prev && W_prev > 0.0f && Wsum > 0.0f && S_prev > 0.0f && S <= 0.0f) {
             out = z_prev + (zs - z_prev) * (S_prev / (S_prev - S));
             idx = s - 1;
             break;
@@ -139,6 +301,9 @@ __global__ void __launch_bounds__(FZ_TX *FZ_TY) fuse_kernel(const FuseArgs a) {
         S_prev = S;
         W_prev = Wsum;
         z_prev = zs;
+        have_prev = true;
+        ++s;
+        if (cool > 0) --cool;
     }
     const size_t o = (size_t)j * a.Wt + i;
     a.fused[o] = out;
@@ -146,30 +311,36 @@ __global__ void __launch_bounds__(FZ_TX *FZ_TY) fuse_kernel(const FuseArgs a) {
 }
 
 template <int R>
-cudaError_t launch_wm(const float *depth, float2 *dw, int K, int W, int H, float mu, float wconst, float inv_w2,
+cudaError_t launch_wm(const float *depth, char *map, const MapLayout &L, float mu, float wconst, float inv_w2,
                       cudaStream_t st) {
-    dim3 grid((W + WM_TX - 1) / WM_TX, (H + WM_TY - 1) / WM_TY, K);
-    weight_map_kernel<R><<<grid, dim3(WM_TX, WM_TY), 0, st>>>(depth, dw, W, H, mu, wconst, inv_w2);
+    dim3 grid((L.W + WM_TX - 1) / WM_TX, (L.H + WM_TY - 1) / WM_TY, L.K);
+    weight_map_kernel<R><<<grid, dim3(WM_TX, WM_TY), 0, st>>>(depth, map, L, mu, wconst, inv_w2);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_weight_map(const float *depth, float2 *dw, int K, int W, int H, float mu, float wconst,
+cudaError_t launch_weight_map(const float *depth, void *map, int K, int W, int H, float mu, float wconst,
                               int window, cudaStream_t st) {
     if (K == 0) return cudaSuccess;
+    const MapLayout L = map_layout(K, W, H);
+    char *m = reinterpret_cast<char *>(map);
     const float inv_w2 = (float)(1.0 / ((double)window * (double)window));
+    cudaError_t e;
     switch (window / 2) {
-        case 0: return launch_wm<0>(depth, dw, K, W, H, mu, wconst, inv_w2, st);
-        case 1: return launch_wm<1>(depth, dw, K, W, H, mu, wconst, inv_w2, st);
-        case 2: return launch_wm<2>(depth, dw, K, W, H, mu, wconst, inv_w2, st);
-        case 3: return launch_wm<3>(depth, dw, K, W, H, mu, wconst, inv_w2, st);
-        case 4: return launch_wm<4>(depth, dw, K, W, H, mu, wconst, inv_w2, st);
-        case 5: return launch_wm<5>(depth, dw, K, W, H, mu, wconst, inv_w2, st);
-        case 6: return launch_wm<6>(depth, dw, K, W, H, mu, wconst, inv_w2, st);
-        case 7: return launch_wm<7>(depth, dw, K, W, H, mu, wconst, inv_w2, st);
+        case 0: e = launch_wm<0>(depth, m, L, mu, wconst, inv_w2, st); break;
+        case 1: e = launch_wm<1>(depth, m, L, mu, wconst, inv_w2, st); break;
+        case 2: e = launch_wm<2>(depth, m, L, mu, wconst, inv_w2, st); break;
+        case 3: e = launch_wm<3>(depth, m, L, mu, wconst, inv_w2, st); break;
+        case 4: e = launch_wm<4>(depth, m, L, mu, wconst, inv_w2, st); break;
+        case 5: e = launch_wm<5>(depth, m, L, mu, wconst, inv_w2, st); break;
+        case 6: e = launch_wm<6>(depth, m, L, mu, wconst, inv_w2, st); break;
+        case 7: e = launch_wm<7>(depth, m, L, mu, wconst, inv_w2, st); break;
         default: return cudaErrorInvalidValue;
     }
+    if (e != cudaSuccess) return e;
+    depth_bounds_kernel<<<dim3(L.t7w, L.t7h, K), dim3(16, 16), 0, st>>>(m, L);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_fuse(const FuseArgs &a, cudaStream_t st) {

@@ -62,8 +62,9 @@ API = {
                                       ctypes.c_void_p]),
     "gvs_weight_map": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                       ctypes.c_float, ctypes.c_float, ctypes.c_int32, ctypes.c_void_p,
-                                      ctypes.c_void_p]),
-    "gvs_fuse_depth_from_map": (ctypes.c_int, [ctypes.POINTER(GvsCamera), ctypes.c_void_p, ctypes.c_int32,
+                                      ctypes.c_size_t, ctypes.c_void_p]),
+    "gvs_fuse_depth_from_map": (ctypes.c_int, [ctypes.POINTER(GvsCamera), ctypes.c_void_p, ctypes.c_size_t,
+                                               ctypes.c_int32,
                                                ctypes.POINTER(GvsCamera), ctypes.POINTER(GvsFuseParams),
                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "gvs_splat_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32] * 3),
@@ -188,15 +189,14 @@ def fuse_depth(in_cams, in_depths, target, num_samples, z_near, z_far, mu, weigh
 
 
 def weight_map(in_depths, mu, weight_const=0.001, window=7, ws=None, stream=None):
-    """Stage 1 of fusion: packed (depth, weight) map [N, H, W] float2, written into `ws` (bytes)."""
+    """Stage 1 of fusion: the map (packed (depth, weight) float2 [N, H, W] first, then depth-bound tiles),
+    written into the uint8 buffer `ws`."""
     lib = load()
     N, H, W = in_depths.shape
     if ws is None:
         ws = workspace(fuse_workspace_bytes(N, W, H), in_depths.device)
-    if ws.numel() * ws.element_size() < N * H * W * 8:
-        raise ValueError("gvs: weight-map buffer too small")
     st = lib.gvs_weight_map(_ptr(in_depths), N, W, H, float(mu), float(weight_const), int(window), _ptr(ws),
-                            _stream(stream))
+                            ws.numel() * ws.element_size(), _stream(stream))
     _check("gvs_weight_map", st)
     return ws
 
@@ -212,7 +212,8 @@ def fuse_depth_from_map(in_cams, dw_map, shape, target, num_samples, z_near, z_f
     if crossing is None and want_crossing:
         crossing = torch.empty((target.height, target.width), dtype=torch.int16, device=dev)
     p = GvsFuseParams(int(num_samples), float(z_near), float(z_far), float(mu), 0.001, 7, int(bool(normalize)))
-    st = lib.gvs_fuse_depth_from_map(camera_array(in_cams), _ptr(dw_map), N, ctypes.byref(camera_struct(target)),
+    st = lib.gvs_fuse_depth_from_map(camera_array(in_cams), _ptr(dw_map), dw_map.numel() * dw_map.element_size(), N,
+                                     ctypes.byref(camera_struct(target)),
                                      ctypes.byref(p), _ptr(fused), _ptr(crossing), _stream(stream))
     _check("gvs_fuse_depth_from_map", st)
     return fused, crossing

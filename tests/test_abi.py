@@ -60,7 +60,7 @@ def test_fuse_rejects_bad_arguments(lib):
     tgt = _cam(gvs)
     good = dict(num_samples=64, z_near=0.5, z_far=5.0, mu=0.05, weight_const=0.001, window=7, normalize=0)
     ws = lib.gvs_fuse_workspace_bytes(2, 64, 48)
-    assert ws == 2 * 64 * 48 * 8
+    assert ws >= 2 * 64 * 48 * 8 and ws % 256 == 0
 
     def call(params=good, cams=cams, n=2, target=tgt, fused=FAKE, wsp=FAKE, wsb=ws, depths=FAKE):
         p = gvs.GvsFuseParams(**params)
