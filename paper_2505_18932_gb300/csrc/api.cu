@@ -187,14 +187,13 @@ gvs::FuseArgs fuse_args(const gvs_camera *in_cams, const void *map, int32_t n_vi
     const char *m = reinterpret_cast<const char *>(map);
     if (n_views > 0) {
         a.dw = reinterpret_cast<const float2 *>(m + L.off_dw);
-        a.t3 = reinterpret_cast<const float2 *>(m + L.off_t3);
-        a.t5 = reinterpret_cast<const float2 *>(m + L.off_t5);
-        a.t7 = reinterpret_cast<const float2 *>(m + L.off_t7);
+        for (int l = 0; l < 3; ++l) a.ob[l] = reinterpret_cast<const float2 *>(m + L.off_O[l]);
         a.tg = reinterpret_cast<const float2 *>(m + L.off_g);
     }
-    a.t3w = L.t3w; a.t3h = L.t3h;
-    a.t5w = L.t5w; a.t5h = L.t5h;
-    a.t7w = L.t7w; a.t7h = L.t7h;
+    for (int l = 0; l < 3; ++l) {
+        a.tw[l] = L.tw[l];
+        a.th[l] = L.th[l];
+    }
     a.K = n_views;
     a.W = W;
     a.H = H;

@@ -7,7 +7,9 @@
 //               signed distance is below -1 so it never contributes.  7x7
 //               stencil over a shared-memory tile with halo.  The same kernel
 //               writes the min/max valid depth of every 8x8 tile.
-// depth_bounds: reduces the 8x8 tiles to 32x32, 128x128 and whole-view bounds.
+// depth_bounds, bounds_overlap: build the per-view bound pyramid (8, 32 and
+//               128 pixel tiles, each also as overlapping 2x2-tile blocks, and
+//               the whole view) from the 8x8 tiles.
 // fuse        : one thread per target pixel marches the D samples in
 //               registers (one 8-byte gather per sample and view) and stops at
 //               the first +/- crossing.  Before evaluating samples it tries to
@@ -94,48 +96,71 @@ __global__ void __launch_bounds__(WM_TX *WM_TY) weight_map_kernel(const float *_
         }
         const int tx = blockIdx.x * (WM_TX / 8) + threadIdx.x;
         const int ty = blockIdx.y;  // WM_TY == 8
-        if (tx < L.t3w && ty < L.t3h)
-            reinterpret_cast<float2 *>(map + L.off_t3)[((size_t)k * L.t3h + ty) * L.t3w + tx] = b;
+        if (tx < L.tw[0] && ty < L.th[0])
+            reinterpret_cast<float2 *>(map + L.off_T[0])[((size_t)k * L.th[0] + ty) * L.tw[0] + tx] = b;
     }
 }
 
-// One block per (128x128 tile, view): 16x16 threads, one 8x8 tile each.
+__device__ __forceinline__ float2 merge(float2 a, float2 b) { return make_float2(fminf(a.x, b.x), fmaxf(a.y, b.y)); }
+
+// One block per (128x128 pixel tile, view), one thread per 8x8 tile: writes
+// O_3 (needs one tile of halo right and below), T_5, T_7 and the view bounds.
 __global__ void __launch_bounds__(256) depth_bounds_kernel(char *__restrict__ map, MapLayout L) {
-    __shared__ float2 s[16][16];
+    __shared__ float2 s[17][17];
     const int k = blockIdx.z;
-    const int tx = blockIdx.x * 16 + threadIdx.x;
-    const int ty = blockIdx.y * 16 + threadIdx.y;
-    float2 b = make_float2(kInf, -kInf);
-    if (tx < L.t3w && ty < L.t3h) b = reinterpret_cast<const float2 *>(map + L.off_t3)[((size_t)k * L.t3h + ty) * L.t3w + tx];
-    s[threadIdx.y][threadIdx.x] = b;
+    const float2 *T3 = reinterpret_cast<const float2 *>(map + L.off_T[0]) + (size_t)k * L.tw[0] * L.th[0];
+    const int tid = threadIdx.y * 16 + threadIdx.x;
+    for (int e = tid; e < 17 * 17; e += 256) {
+        const int ly = e / 17, lx = e - ly * 17;
+        const int tx = blockIdx.x * 16 + lx, ty = blockIdx.y * 16 + ly;
+        s[ly][lx] = (tx < L.tw[0] && ty < L.th[0]) ? T3[(size_t)ty * L.tw[0] + tx] : make_float2(kInf, -kInf);
+    }
     __syncthreads();
-    if ((threadIdx.x & 3) == 0 && (threadIdx.y & 3) == 0) {
+    const int x = threadIdx.x, y = threadIdx.y;
+    const int tx = blockIdx.x * 16 + x, ty = blockIdx.y * 16 + y;
+    if (tx < L.tw[0] && ty < L.th[0]) {
+        const float2 o = merge(merge(s[y][x], s[y][x + 1]), merge(s[y + 1][x], s[y + 1][x + 1]));
+        reinterpret_cast<float2 *>(map + L.off_O[0])[((size_t)k * L.th[0] + ty) * L.tw[0] + tx] = o;
+    }
+    if ((x & 3) == 0 && (y & 3) == 0) {
         float2 c = make_float2(kInf, -kInf);
 #pragma unroll
         for (int dy = 0; dy < 4; ++dy)
 #pragma unroll
-            for (int dx = 0; dx < 4; ++dx) {
-                c.x = fminf(c.x, s[threadIdx.y + dy][threadIdx.x + dx].x);
-                c.y = fmaxf(c.y, s[threadIdx.y + dy][threadIdx.x + dx].y);
-            }
-        const int x5 = blockIdx.x * 4 + (threadIdx.x >> 2), y5 = blockIdx.y * 4 + (threadIdx.y >> 2);
-        if (x5 < L.t5w && y5 < L.t5h)
-            reinterpret_cast<float2 *>(map + L.off_t5)[((size_t)k * L.t5h + y5) * L.t5w + x5] = c;
+            for (int dx = 0; dx < 4; ++dx) c = merge(c, s[y + dy][x + dx]);
+        const int x5 = blockIdx.x * 4 + (x >> 2), y5 = blockIdx.y * 4 + (y >> 2);
+        if (x5 < L.tw[1] && y5 < L.th[1])
+            reinterpret_cast<float2 *>(map + L.off_T[1])[((size_t)k * L.th[1] + y5) * L.tw[1] + x5] = c;
     }
-    __syncthreads();
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
+    if (tid == 0) {
         float2 c = make_float2(kInf, -kInf);
-        for (int i = 0; i < 256; ++i) {
-            c.x = fminf(c.x, s[i >> 4][i & 15].x);
-            c.y = fmaxf(c.y, s[i >> 4][i & 15].y);
-        }
-        reinterpret_cast<float2 *>(map + L.off_t7)[((size_t)k * L.t7h + blockIdx.y) * L.t7w + blockIdx.x] = c;
+        for (int i = 0; i < 256; ++i) c = merge(c, s[i >> 4][i & 15]);
+        reinterpret_cast<float2 *>(map + L.off_T[2])[((size_t)k * L.th[2] + blockIdx.y) * L.tw[2] + blockIdx.x] = c;
         int *g = reinterpret_cast<int *>(map + L.off_g) + 2 * k;
         if (c.x <= c.y) {  // the tile holds a valid depth
             atomicMin(&g[0], __float_as_int(c.x));  // positive floats order like their bits
             atomicMax(&g[1], __float_as_int(c.y));
         }
     }
+}
+
+// O_l from T_l for levels 5 and 7: one thread per (view, tile).
+__global__ void __launch_bounds__(256) bounds_overlap_kernel(char *__restrict__ map, MapLayout L) {
+    const int64_t n5 = (int64_t)L.tw[1] * L.th[1], n7 = (int64_t)L.tw[2] * L.th[2];
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (int64_t)L.K * (n5 + n7)) return;
+    const int k = (int)(q / (n5 + n7));
+    q -= (int64_t)k * (n5 + n7);
+    const int l = q < n5 ? 1 : 2;
+    if (l == 2) q -= n5;
+    const int tw = L.tw[l], th = L.th[l];
+    const int tx = (int)(q % tw), ty = (int)(q / tw);
+    const float2 *T = reinterpret_cast<const float2 *>(map + L.off_T[l]) + (size_t)k * tw * th;
+    float2 o = T[(size_t)ty * tw + tx];
+    if (tx + 1 < tw) o = merge(o, T[(size_t)ty * tw + tx + 1]);
+    if (ty + 1 < th) o = merge(o, T[(size_t)(ty + 1) * tw + tx]);
+    if (tx + 1 < tw && ty + 1 < th) o = merge(o, T[(size_t)(ty + 1) * tw + tx + 1]);
+    reinterpret_cast<float2 *>(map + L.off_O[l])[((size_t)k * th + ty) * tw + tx] = o;
 }
 
 // Nearest integer (ties to even) of the exact real quotient num/den, den > 0.
@@ -172,52 +197,47 @@ struct Ray {
 // beyond the samples' projected depths (sdf > 0: a positive term) or every
 // valid depth at least 1.0001 mu in front of them (sdf < -1: cut off), or lies
 // outside the image.  Then S_s > 0 whenever W_s > 0 throughout, so no
-// crossing pair ends inside [s0, s1].
+// crossing pair ends inside [s0, s1].  Each view needs one bounds load (the
+// finest level whose overlapping 2x2-tile block covers the box, else the
+// whole view), and no load depends on another view's outcome.
 template <int KMAX>
 __device__ __forceinline__ bool segment_is_free(const FuseArgs &a, const Ray (&ray)[KMAX], float z0, float z1) {
+    bool ok = true;
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) {
-        if (k >= a.K) break;
-        const float hz0 = __fmaf_rn(z0, ray[k].az, a.xf[k].b[2]);
-        const float hz1 = __fmaf_rn(z1, ray[k].az, a.xf[k].b[2]);
-        const bool f0 = hz0 > 1e-6f, f1 = hz1 > 1e-6f;
-        if (!f0 && !f1) continue;      // behind the camera all along: no contribution
-        if (f0 != f1) return false;    // crosses the camera plane: do not try
-        const float r0 = __fdividef(1.0f, hz0), r1 = __fdividef(1.0f, hz1);
-        const float x0 = __fmaf_rn(z0, ray[k].ax, a.xf[k].b[0]) * r0;
-        const float x1 = __fmaf_rn(z1, ray[k].ax, a.xf[k].b[0]) * r1;
-        const float y0 = __fmaf_rn(z0, ray[k].ay, a.xf[k].b[1]) * r0;
-        const float y1 = __fmaf_rn(z1, ray[k].ay, a.xf[k].b[1]) * r1;
-        const float xlo = fminf(x0, x1) - 1.0f, xhi = fmaxf(x0, x1) + 1.0f;
-        const float ylo = fminf(y0, y1) - 1.0f, yhi = fmaxf(y0, y1) + 1.0f;
-        if (!(xhi >= 0.0f && ylo <= (float)(a.H - 1) && yhi >= 0.0f && xlo <= (float)(a.W - 1))) {
-            if (xhi < 0.0f || yhi < 0.0f || xlo > (float)(a.W - 1) || ylo > (float)(a.H - 1)) continue;  // outside
-            return false;  // NaN
+        if (k < a.K) {
+            const float hz0 = __fmaf_rn(z0, ray[k].az, a.xf[k].b[2]);
+            const float hz1 = __fmaf_rn(z1, ray[k].az, a.xf[k].b[2]);
+            const bool f0 = hz0 > 1e-6f, f1 = hz1 > 1e-6f;
+            const float r0 = __fdividef(1.0f, hz0), r1 = __fdividef(1.0f, hz1);
+            const float x0 = __fmaf_rn(z0, ray[k].ax, a.xf[k].b[0]) * r0;
+            const float x1 = __fmaf_rn(z1, ray[k].ax, a.xf[k].b[0]) * r1;
+            const float y0 = __fmaf_rn(z0, ray[k].ay, a.xf[k].b[1]) * r0;
+            const float y1 = __fmaf_rn(z1, ray[k].ay, a.xf[k].b[1]) * r1;
+            const float xlo = fminf(x0, x1) - 1.0f, xhi = fmaxf(x0, x1) + 1.0f;
+            const float ylo = fminf(y0, y1) - 1.0f, yhi = fmaxf(y0, y1) + 1.0f;
+            const bool finite = xlo <= xhi && ylo <= yhi;  // false on NaN
+            const bool outside = xhi < 0.0f || yhi < 0.0f || xlo > (float)(a.W - 1) || ylo > (float)(a.H - 1);
+            const int bx0 = min(max(__float2int_rd(xlo), 0), a.W - 1), bx1 = min(max(__float2int_ru(xhi), 0), a.W - 1);
+            const int by0 = min(max(__float2int_rd(ylo), 0), a.H - 1), by1 = min(max(__float2int_ru(yhi), 0), a.H - 1);
+            const float2 *p;
+            if ((bx1 >> 3) - (bx0 >> 3) <= 1 && (by1 >> 3) - (by0 >> 3) <= 1)
+                p = a.ob[0] + ((size_t)k * a.th[0] + (by0 >> 3)) * a.tw[0] + (bx0 >> 3);
+            else if ((bx1 >> 5) - (bx0 >> 5) <= 1 && (by1 >> 5) - (by0 >> 5) <= 1)
+                p = a.ob[1] + ((size_t)k * a.th[1] + (by0 >> 5)) * a.tw[1] + (bx0 >> 5);
+            else if ((bx1 >> 7) - (bx0 >> 7) <= 1 && (by1 >> 7) - (by0 >> 7) <= 1)
+                p = a.ob[2] + ((size_t)k * a.th[2] + (by0 >> 7)) * a.tw[2] + (bx0 >> 7);
+            else
+                p = a.tg + k;
+            const bool none = !f0 && !f1;  // behind the camera all along: no contribution
+            const float2 b = (none || outside) ? make_float2(kInf, -kInf) : __ldg(p);
+            const float zlo = fminf(hz0, hz1), zhi = fmaxf(hz0, hz1);
+            const bool view_free =
+                none || (f0 && f1 && finite && (outside || zhi < b.x || zlo > b.y + a.behind));
+            ok = ok && view_free;
         }
-        const int bx0 = (int)fmaxf(floorf(xlo), 0.0f), bx1 = (int)fminf(ceilf(xhi), (float)(a.W - 1));
-        const int by0 = (int)fmaxf(floorf(ylo), 0.0f), by1 = (int)fminf(ceilf(yhi), (float)(a.H - 1));
-        const float zlo = fminf(hz0, hz1), zhi = fmaxf(hz0, hz1);
-        const float2 *tl;
-        int sh, tw, th;
-        if ((bx1 >> 3) - (bx0 >> 3) <= 1 && (by1 >> 3) - (by0 >> 3) <= 1) {
-            tl = a.t3; sh = 3; tw = a.t3w; th = a.t3h;
-        } else if ((bx1 >> 5) - (bx0 >> 5) <= 1 && (by1 >> 5) - (by0 >> 5) <= 1) {
-            tl = a.t5; sh = 5; tw = a.t5w; th = a.t5h;
-        } else if ((bx1 >> 7) - (bx0 >> 7) <= 1 && (by1 >> 7) - (by0 >> 7) <= 1) {
-            tl = a.t7; sh = 7; tw = a.t7w; th = a.t7h;
-        } else {
-            const float2 g = __ldg(&a.tg[k]);
-            if (!(zhi < g.x || zlo > g.y + a.behind)) return false;
-            continue;
-        }
-        tl += (size_t)k * tw * th;
-        for (int ty = by0 >> sh; ty <= (by1 >> sh); ++ty)
-            for (int tx = bx0 >> sh; tx <= (bx1 >> sh); ++tx) {
-                const float2 b = __ldg(&tl[ty * tw + tx]);
-                if (!(zhi < b.x || zlo > b.y + a.behind)) return false;
-            }
     }
-    return true;
+    return ok;
 }
 
 // S and W of one sample (Supplement A.1), exactly as the full march computes them.
@@ -339,7 +359,9 @@ cudaError_t launch_weight_map(const float *depth, void *map, int K, int W, int H
         default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;
-    depth_bounds_kernel<<<dim3(L.t7w, L.t7h, K), dim3(16, 16), 0, st>>>(m, L);
+    depth_bounds_kernel<<<dim3(L.tw[2], L.th[2], K), dim3(16, 16), 0, st>>>(m, L);
+    const int64_t n = (int64_t)K * ((int64_t)L.tw[1] * L.th[1] + (int64_t)L.tw[2] * L.th[2]);
+    bounds_overlap_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m, L);
     return cudaGetLastError();
 }
 

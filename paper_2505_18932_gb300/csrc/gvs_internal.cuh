@@ -24,35 +24,41 @@ cudaError_t launch_refine(const uint32_t *rgba_t, const uint32_t *rgba_prev, con
 // ---- TSDF fusion -----------------------------------------------------------
 // Byte layout of the fusion workspace ("map"): the packed (depth, weight)
 // float2 per input pixel, then per-view depth bounds (min, max over valid
-// depths; +inf/-inf where a tile has none) over 8x8, 32x32 and 128x128 pixel
-// tiles and over the whole view.  Every section starts 256-byte aligned.
+// depths; +inf/-inf where there is none).  For each tile level l in {3, 5, 7}
+// (tiles of 2^l x 2^l pixels) T_l holds the bounds of each tile and O_l the
+// bounds of the 2x2 block of tiles anchored at it, so that any pixel box
+// spanning at most two tiles per axis at level l is covered by one O_l
+// entry.  G holds the bounds of the whole view.  Sections are 256-byte
+// aligned.
 struct MapLayout {
     int K, W, H;
-    int t3w, t3h, t5w, t5h, t7w, t7h;
-    size_t off_dw, off_t3, off_t5, off_t7, off_g, total;
+    int tw[3], th[3];          // tiles per row / column at levels 3, 5, 7
+    size_t off_dw, off_T[3], off_O[3], off_g, total;
 };
 
 inline MapLayout map_layout(int K, int W, int H) {
     auto up = [](size_t n) { return (n + 255) / 256 * 256; };
     MapLayout m;
     m.K = K; m.W = W; m.H = H;
-    m.t3w = (W + 7) >> 3;    m.t3h = (H + 7) >> 3;
-    m.t5w = (W + 31) >> 5;   m.t5h = (H + 31) >> 5;
-    m.t7w = (W + 127) >> 7;  m.t7h = (H + 127) >> 7;
+    const int shift[3] = {3, 5, 7};
     size_t o = 0;
     m.off_dw = o; o = up(o + (size_t)K * W * H * 8);
-    m.off_t3 = o; o = up(o + (size_t)K * m.t3w * m.t3h * 8);
-    m.off_t5 = o; o = up(o + (size_t)K * m.t5w * m.t5h * 8);
-    m.off_t7 = o; o = up(o + (size_t)K * m.t7w * m.t7h * 8);
-    m.off_g = o;  o = up(o + (size_t)K * 8);
+    for (int l = 0; l < 3; ++l) {
+        m.tw[l] = (W + (1 << shift[l]) - 1) >> shift[l];
+        m.th[l] = (H + (1 << shift[l]) - 1) >> shift[l];
+        m.off_T[l] = o; o = up(o + (size_t)K * m.tw[l] * m.th[l] * 8);
+        m.off_O[l] = o; o = up(o + (size_t)K * m.tw[l] * m.th[l] * 8);
+    }
+    m.off_g = o; o = up(o + (size_t)K * 8);
     m.total = K > 0 ? o : 0;
     return m;
 }
 
 struct FuseArgs {
     const float2 *dw;          // [K][H][W] packed (depth or 0, weight)
-    const float2 *t3, *t5, *t7, *tg;  // depth bounds per tile level and per view
-    int t3w, t3h, t5w, t5h, t7w, t7h;
+    const float2 *ob[3];       // O_l overlapping 2x2-tile bounds, levels 3, 5, 7: [K][th][tw]
+    const float2 *tg;          // whole-view bounds [K]
+    int tw[3], th[3];
     int K, W, H;               // input views and their size
     int Wt, Ht;                // target size
     int D;
