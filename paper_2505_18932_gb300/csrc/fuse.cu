@@ -184,8 +184,19 @@ __device__ __forceinline__ int nearest_of_quotient(float num, float den, float r
 
 constexpr int FZ_TX = 16;
 constexpr int FZ_TY = 8;
-constexpr int SKIP_LONG = 16;
-constexpr int SKIP_SHORT = 4;
+#ifndef GVS_SKIP_LONG
+#define GVS_SKIP_LONG 16   // samples spanned by the first segment test
+#endif
+#ifndef GVS_SKIP_SHORT
+#define GVS_SKIP_SHORT 4   // samples spanned by the second test when the first fails
+#endif
+#ifndef GVS_SKIP_COOL
+#define GVS_SKIP_COOL 4    // samples evaluated after both tests fail, before testing again
+#endif
+constexpr int SKIP_LONG = GVS_SKIP_LONG;
+constexpr int SKIP_SHORT = GVS_SKIP_SHORT;
+constexpr int SKIP_COOL = GVS_SKIP_COOL;
+static_assert(SKIP_LONG >= 1 && SKIP_SHORT >= 1 && SKIP_COOL >= 0, "skip lengths must advance the march");
 
 struct Ray {
     float ax, ay, az;
@@ -308,7 +319,7 @@ __global__ void __launch_bounds__(FZ_TX *FZ_TY) fuse_kernel(const FuseArgs a) {
                 have_prev = false;
                 continue;
             }
-            cool = SKIP_SHORT;
+            cool = SKIP_COOL;
         }
         const float zs = __fmaf_rn((float)s, a.dz, a.zn);
         float S, Wsum;
