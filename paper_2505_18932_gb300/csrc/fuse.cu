@@ -163,23 +163,35 @@ __global__ void __launch_bounds__(256) bounds_overlap_kernel(char *__restrict__ 
     reinterpret_cast<float2 *>(map + L.off_O[l])[((size_t)k * th + ty) * tw + tx] = o;
 }
 
-// Nearest integer (ties to even) of the exact real quotient num/den, den > 0.
-// q = num * r with r ~ 1/den (relative error a few ulp) is within 0.01 of the
-// quotient for any quotient that can land inside an image (|q| < 2^14 + 1);
-// only when q sits within 0.01 of a half-integer is the decision re-taken
-// from the signs of the exact residuals num - (n +/- 0.5) den (one rounding
-// each in the FMA, which never changes a sign).
-__device__ __forceinline__ int nearest_of_quotient(float num, float den, float r) {
-    const float q = num * r;
-    float n = rintf(q);
-    if (fabsf(q - n) > 0.49f && fabsf(n) < 4194304.0f) {
+// Nearest integers (ties to even) of the exact real quotients hx/hz, hy/hz,
+// hz > 0.  q = h * r with r ~ 1/hz (relative error a few ulp) is within 0.01
+// of the quotient for any quotient that can land inside an image
+// (|q| < 2^14 + 1); only when a q sits within 0.01 of a half-integer is the
+// decision re-taken from the signs of the exact residuals h - (n +/- 0.5) hz
+// (one rounding each in the FMA, which never changes a sign).  The fix-up
+// leaves n unchanged when q is not near a half-integer, so it runs for both
+// coordinates under one branch.
+__device__ __forceinline__ float exact_nearest_fixup(float num, float den, float n) {
+    if (fabsf(n) < 4194304.0f) {
         const float hi = __fmaf_rn(-(n + 0.5f), den, num);
         const float lo = __fmaf_rn(-(n - 0.5f), den, num);
         const bool odd = (__float2int_rz(n) & 1) != 0;
         if (hi > 0.0f || (hi == 0.0f && odd)) n += 1.0f;
         else if (lo < 0.0f || (lo == 0.0f && odd)) n -= 1.0f;
     }
-    return __float2int_rz(n);
+    return n;
+}
+
+__device__ __forceinline__ void nearest_pixel(float hx, float hy, float hz, int &u, int &v) {
+    const float r = __fdividef(1.0f, hz);
+    const float qx = hx * r, qy = hy * r;
+    float nx = rintf(qx), ny = rintf(qy);
+    if (fmaxf(fabsf(qx - nx), fabsf(qy - ny)) > 0.49f) {
+        nx = exact_nearest_fixup(hx, hz, nx);
+        ny = exact_nearest_fixup(hy, hz, ny);
+    }
+    u = __float2int_rz(nx);
+    v = __float2int_rz(ny);
 }
 
 constexpr int FZ_TX = 16;
@@ -191,7 +203,7 @@ constexpr int FZ_TY = 8;
 #define GVS_SKIP_SHORT 4   // samples spanned by the second test when the first fails
 #endif
 #ifndef GVS_SKIP_COOL
-#define GVS_SKIP_COOL 4    // samples evaluated after both tests fail, before testing again
+#define GVS_SKIP_COOL 8    // samples evaluated after both tests fail, before testing again
 #endif
 constexpr int SKIP_LONG = GVS_SKIP_LONG;
 constexpr int SKIP_SHORT = GVS_SKIP_SHORT;
@@ -231,12 +243,14 @@ __device__ __forceinline__ bool segment_is_free(const FuseArgs &a, const Ray (&r
             const bool outside = xhi < 0.0f || yhi < 0.0f || xlo > (float)(a.W - 1) || ylo > (float)(a.H - 1);
             const int bx0 = min(max(__float2int_rd(xlo), 0), a.W - 1), bx1 = min(max(__float2int_ru(xhi), 0), a.W - 1);
             const int by0 = min(max(__float2int_rd(ylo), 0), a.H - 1), by1 = min(max(__float2int_ru(yhi), 0), a.H - 1);
+            // a box spanning fewer than 2^l pixels per axis covers at most 2x2 tiles of level l
+            const int span = max(bx1 - bx0, by1 - by0);
             const float2 *p;
-            if ((bx1 >> 3) - (bx0 >> 3) <= 1 && (by1 >> 3) - (by0 >> 3) <= 1)
+            if (span < 8)
                 p = a.ob[0] + ((size_t)k * a.th[0] + (by0 >> 3)) * a.tw[0] + (bx0 >> 3);
-            else if ((bx1 >> 5) - (bx0 >> 5) <= 1 && (by1 >> 5) - (by0 >> 5) <= 1)
+            else if (span < 32)
                 p = a.ob[1] + ((size_t)k * a.th[1] + (by0 >> 5)) * a.tw[1] + (bx0 >> 5);
-            else if ((bx1 >> 7) - (bx0 >> 7) <= 1 && (by1 >> 7) - (by0 >> 7) <= 1)
+            else if (span < 128)
                 p = a.ob[2] + ((size_t)k * a.th[2] + (by0 >> 7)) * a.tw[2] + (bx0 >> 7);
             else
                 p = a.tg + k;
@@ -265,9 +279,8 @@ __device__ __forceinline__ void evaluate_sample(const FuseArgs &a, const Ray (&r
             if (hz > 1e-6f) {
                 const float hx = __fmaf_rn(zs, ray[k].ax, a.xf[k].b[0]);
                 const float hy = __fmaf_rn(zs, ray[k].ay, a.xf[k].b[1]);
-                const float r = __fdividef(1.0f, hz);
-                const int u = nearest_of_quotient(hx, hz, r);
-                const int v = nearest_of_quotient(hy, hz, r);
+                int u, v;
+                nearest_pixel(hx, hy, hz, u, v);
                 if ((unsigned)u < (unsigned)a.W && (unsigned)v < (unsigned)a.H) {
                     const float2 p = __ldg(&a.dw[(size_t)k * plane + (size_t)v * a.W + u]);
                     const float sdf = (p.x - hz) * a.inv_mu;
@@ -303,22 +316,23 @@ __global__ void __launch_bounds__(FZ_TX *FZ_TY) fuse_kernel(const FuseArgs a) {
     float out = 0.0f;
     int idx = -1;
     int s = 0;
-    int cool = 0;  // samples to evaluate before trying to skip again
+    int cool = 0;     // samples to evaluate before trying to skip again
+    bool shorter = false;  // the long test just failed: try the short one
     while (s < a.D) {
         if (cool == 0 && s < a.D - 1) {
-            const int Ll = min(SKIP_LONG, a.D - 1 - s);
-            const float z0 = __fmaf_rn((float)s, a.dz, a.zn);
-            if (segment_is_free<KMAX>(a, ray, z0, __fmaf_rn((float)(s + Ll), a.dz, a.zn))) {
-                s += Ll;  // samples s..s+Ll are not crossing ends; s+Ll is evaluated next
+            const int L = min(shorter ? SKIP_SHORT : SKIP_LONG, a.D - 1 - s);
+            if (segment_is_free<KMAX>(a, ray, __fmaf_rn((float)s, a.dz, a.zn),
+                                      __fmaf_rn((float)(s + L), a.dz, a.zn))) {
+                s += L;  // samples s..s+L are not crossing ends; s+L is evaluated next
                 have_prev = false;
+                shorter = false;
                 continue;
             }
-            const int Ls = min(SKIP_SHORT, a.D - 1 - s);
-            if (Ls < Ll && segment_is_free<KMAX>(a, ray, z0, __fmaf_rn((float)(s + Ls), a.dz, a.zn))) {
-                s += Ls;
-                have_prev = false;
+            if (!shorter && L > SKIP_SHORT) {
+                shorter = true;
                 continue;
             }
+            shorter = false;
             cool = SKIP_COOL;
         }
         const float zs = __fmaf_rn((float)s, a.dz, a.zn);
