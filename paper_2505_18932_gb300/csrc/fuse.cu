@@ -10,13 +10,14 @@
 // depth_bounds, bounds_overlap: build the per-view bound pyramid (8, 32 and
 //               128 pixel tiles, each also as overlapping 2x2-tile blocks, and
 //               the whole view) from the 8x8 tiles.
-// fuse        : one thread per target pixel marches the D samples in
-//               registers (one 8-byte gather per sample and view) and stops at
-//               the first +/- crossing.  Before evaluating samples it tries to
-//               prove that a run of them holds no crossing end (see
-//               segment_is_free); such runs are skipped.  A skipped sample
-//               provably has S > 0 or W = 0, so the first crossing, its index
-//               and its interpolated depth are exactly those of the full march.
+// fuse        : one warp per 8x4 bundle of target pixels, one thread per ray,
+//               marching the D samples in registers (one 8-byte gather per
+//               sample and view) to the first +/- crossing.  Before evaluating
+//               samples the warp tries to prove that a run of them holds no
+//               crossing end for any ray of the bundle (see slab_view_free);
+//               such runs are skipped.  A skipped sample provably has S > 0 or
+//               W = 0, so the first crossing, its index and its interpolated
+//               depth are exactly those of the full uniform march.
 #include <math.h>
 
 #include "gvs_internal.cuh"
@@ -194,16 +195,17 @@ __device__ __forceinline__ void nearest_pixel(float hx, float hy, float hz, int 
     v = __float2int_rz(ny);
 }
 
-constexpr int FZ_TX = 16;
-constexpr int FZ_TY = 8;
+constexpr int BX = 8;   // a warp marches a bundle of BX x BY target pixels
+constexpr int BY = 4;
+constexpr int FZ_WARPS = 4;
 #ifndef GVS_SKIP_LONG
-#define GVS_SKIP_LONG 16   // samples spanned by the first segment test
+#define GVS_SKIP_LONG 8    // samples per segment in the first test
 #endif
 #ifndef GVS_SKIP_SHORT
-#define GVS_SKIP_SHORT 4   // samples spanned by the second test when the first fails
+#define GVS_SKIP_SHORT 2   // samples per segment in the second test when the first fails
 #endif
 #ifndef GVS_SKIP_COOL
-#define GVS_SKIP_COOL 8    // samples evaluated after both tests fail, before testing again
+#define GVS_SKIP_COOL 4    // samples evaluated after both tests fail, before testing again
 #endif
 constexpr int SKIP_LONG = GVS_SKIP_LONG;
 constexpr int SKIP_SHORT = GVS_SKIP_SHORT;
@@ -214,55 +216,60 @@ struct Ray {
     float ax, ay, az;
 };
 
-// True when no sample s in [s0, s1] can end a crossing: for every view, every
-// pixel the samples can project to (their nearest pixels lie within one pixel
-// of the segment joining the end projections) has all valid depths strictly
-// beyond the samples' projected depths (sdf > 0: a positive term) or every
-// valid depth at least 1.0001 mu in front of them (sdf < -1: cut off), or lies
-// outside the image.  Then S_s > 0 whenever W_s > 0 throughout, so no
-// crossing pair ends inside [s0, s1].  Each view needs one bounds load (the
-// finest level whose overlapping 2x2-tile block covers the box, else the
-// whole view), and no load depends on another view's outcome.
-template <int KMAX>
-__device__ __forceinline__ bool segment_is_free(const FuseArgs &a, const Ray (&ray)[KMAX], float z0, float z1) {
-    bool ok = true;
+// The bundle's rays between depths z0 and z1 fill a truncated pyramid (convex,
+// 8 vertices: its 4 corner rays at z0 and z1).  In view k its points project
+// inside the hull of the 8 vertex projections and their projected depths lie
+// between the vertices' extremes (both statements exact for an affine depth
+// and a projective map on a convex body in front of the camera; FP32 rounding
+// of the samples is covered by a 1 pixel and 1e-6 relative margin).  The view
+// is free over the slab when every valid depth in the pixel box around that
+// hull is strictly beyond the largest projected depth (sdf > 0: a positive
+// term) or at least 1.0001 mu in front of the smallest (sdf < -1: cut off), or
+// the box is outside the image, or the slab is behind the camera.  One bounds
+// load: the finest tile level whose overlapping 2x2 block covers the box, else
+// the whole view.  When every view is free over the slab, no sample of it can
+// end a crossing (S > 0 wherever W > 0).
+__device__ __forceinline__ bool slab_view_free(const FuseArgs &a, int k, const Ray (&corner)[4], float z0,
+                                               float z1) {
+    const float b0 = a.xf[k].b[0], b1 = a.xf[k].b[1], b2 = a.xf[k].b[2];
+    float xlo = kInf, xhi = -kInf, ylo = kInf, yhi = -kInf, zlo = kInf, zhi = -kInf;
+    bool any_front = false, any_back = false;
 #pragma unroll
-    for (int k = 0; k < KMAX; ++k) {
-        if (k < a.K) {
-            const float hz0 = __fmaf_rn(z0, ray[k].az, a.xf[k].b[2]);
-            const float hz1 = __fmaf_rn(z1, ray[k].az, a.xf[k].b[2]);
-            const bool f0 = hz0 > 1e-6f, f1 = hz1 > 1e-6f;
-            const float r0 = __fdividef(1.0f, hz0), r1 = __fdividef(1.0f, hz1);
-            const float x0 = __fmaf_rn(z0, ray[k].ax, a.xf[k].b[0]) * r0;
-            const float x1 = __fmaf_rn(z1, ray[k].ax, a.xf[k].b[0]) * r1;
-            const float y0 = __fmaf_rn(z0, ray[k].ay, a.xf[k].b[1]) * r0;
-            const float y1 = __fmaf_rn(z1, ray[k].ay, a.xf[k].b[1]) * r1;
-            const float xlo = fminf(x0, x1) - 1.0f, xhi = fmaxf(x0, x1) + 1.0f;
-            const float ylo = fminf(y0, y1) - 1.0f, yhi = fmaxf(y0, y1) + 1.0f;
-            const bool finite = xlo <= xhi && ylo <= yhi;  // false on NaN
-            const bool outside = xhi < 0.0f || yhi < 0.0f || xlo > (float)(a.W - 1) || ylo > (float)(a.H - 1);
-            const int bx0 = min(max(__float2int_rd(xlo), 0), a.W - 1), bx1 = min(max(__float2int_ru(xhi), 0), a.W - 1);
-            const int by0 = min(max(__float2int_rd(ylo), 0), a.H - 1), by1 = min(max(__float2int_ru(yhi), 0), a.H - 1);
-            // a box spanning fewer than 2^l pixels per axis covers at most 2x2 tiles of level l
-            const int span = max(bx1 - bx0, by1 - by0);
-            const float2 *p;
-            if (span < 8)
-                p = a.ob[0] + ((size_t)k * a.th[0] + (by0 >> 3)) * a.tw[0] + (bx0 >> 3);
-            else if (span < 32)
-                p = a.ob[1] + ((size_t)k * a.th[1] + (by0 >> 5)) * a.tw[1] + (bx0 >> 5);
-            else if (span < 128)
-                p = a.ob[2] + ((size_t)k * a.th[2] + (by0 >> 7)) * a.tw[2] + (bx0 >> 7);
-            else
-                p = a.tg + k;
-            const bool none = !f0 && !f1;  // behind the camera all along: no contribution
-            const float2 b = (none || outside) ? make_float2(kInf, -kInf) : __ldg(p);
-            const float zlo = fminf(hz0, hz1), zhi = fmaxf(hz0, hz1);
-            const bool view_free =
-                none || (f0 && f1 && finite && (outside || zhi < b.x || zlo > b.y + a.behind));
-            ok = ok && view_free;
-        }
+    for (int c = 0; c < 8; ++c) {
+        const float z = (c & 1) ? z1 : z0;
+        const Ray &r = corner[c >> 1];
+        const float hz = __fmaf_rn(z, r.az, b2);
+        const float q = __fdividef(1.0f, hz);
+        const float x = __fmaf_rn(z, r.ax, b0) * q;
+        const float y = __fmaf_rn(z, r.ay, b1) * q;
+        any_front |= hz > 1e-6f;
+        any_back |= !(hz > 1e-6f);
+        xlo = fminf(xlo, x); xhi = fmaxf(xhi, x);
+        ylo = fminf(ylo, y); yhi = fmaxf(yhi, y);
+        zlo = fminf(zlo, hz); zhi = fmaxf(zhi, hz);
     }
-    return ok;
+    zhi += 1e-6f * fabsf(zhi);
+    zlo -= 1e-6f * fabsf(zlo);
+    if (!any_front && zhi <= 1e-6f) return true;  // behind the camera throughout
+    if (any_back) return false;                   // crosses the camera plane: do not try
+    xlo -= 1.0f; xhi += 1.0f; ylo -= 1.0f; yhi += 1.0f;
+    if (!(xlo <= xhi && ylo <= yhi)) return false;  // NaN
+    if (xhi < 0.0f || yhi < 0.0f || xlo > (float)(a.W - 1) || ylo > (float)(a.H - 1)) return true;  // outside
+    const int bx0 = min(max(__float2int_rd(xlo), 0), a.W - 1), bx1 = min(max(__float2int_ru(xhi), 0), a.W - 1);
+    const int by0 = min(max(__float2int_rd(ylo), 0), a.H - 1), by1 = min(max(__float2int_ru(yhi), 0), a.H - 1);
+    // a box spanning fewer than 2^l pixels per axis covers at most 2x2 tiles of level l
+    const int span = max(bx1 - bx0, by1 - by0);
+    const float2 *p;
+    if (span < 8)
+        p = a.ob[0] + ((size_t)k * a.th[0] + (by0 >> 3)) * a.tw[0] + (bx0 >> 3);
+    else if (span < 32)
+        p = a.ob[1] + ((size_t)k * a.th[1] + (by0 >> 5)) * a.tw[1] + (bx0 >> 5);
+    else if (span < 128)
+        p = a.ob[2] + ((size_t)k * a.th[2] + (by0 >> 7)) * a.tw[2] + (bx0 >> 7);
+    else
+        p = a.tg + k;
+    const float2 b = __ldg(p);
+    return zhi < b.x || zlo > b.y + a.behind;
 }
 
 // S and W of one sample (Supplement A.1), exactly as the full march computes them.
@@ -295,12 +302,26 @@ __device__ __forceinline__ void evaluate_sample(const FuseArgs &a, const Ray (&r
     if (a.normalize && Wsum > 0.0f) S = S / Wsum;
 }
 
+// One warp per bundle of BX x BY target pixels.  The warp marches one sample
+// index s for all its rays: cooperative slab tests (lane = view x segment,
+// 32 / KMAX consecutive segments at once) skip runs of samples that hold no
+// crossing end for any ray of the bundle; otherwise every ray still marching
+// evaluates sample s (all KMAX views unrolled, one 8-byte gather each) and
+// checks its own crossing.  The result equals the full uniform march.
 template <int KMAX>
-__global__ void __launch_bounds__(FZ_TX *FZ_TY) fuse_kernel(const FuseArgs a) {
-    const int i = blockIdx.x * FZ_TX + threadIdx.x;
-    const int j = blockIdx.y * FZ_TY + threadIdx.y;
-    if (i >= a.Wt || j >= a.Ht) return;
-    const float fi = (float)i, fj = (float)j;
+__global__ void __launch_bounds__(32 * FZ_WARPS) fuse_kernel(const FuseArgs a) {
+    constexpr int NSEG = 32 / KMAX;
+    constexpr unsigned SEGMASK = KMAX == 32 ? 0xffffffffu : ((1u << KMAX) - 1u);
+    const int lane = threadIdx.x & 31;
+    const int nbx = (a.Wt + BX - 1) / BX;
+    const int nbundles = nbx * ((a.Ht + BY - 1) / BY);
+    const int bundle = blockIdx.x * FZ_WARPS + (threadIdx.x >> 5);
+    if (bundle >= nbundles) return;  // the whole warp leaves together
+    const int i0 = (bundle % nbx) * BX, j0 = (bundle / nbx) * BY;
+    const int i1 = min(i0 + BX - 1, a.Wt - 1), j1 = min(j0 + BY - 1, a.Ht - 1);
+    const int i = i0 + (lane % BX), j = j0 + (lane / BX);
+    const bool inside = i < a.Wt && j < a.Ht;
+    const float fi = (float)min(i, a.Wt - 1), fj = (float)min(j, a.Ht - 1);
     Ray ray[KMAX];
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) {
@@ -311,24 +332,53 @@ __global__ void __launch_bounds__(FZ_TX *FZ_TY) fuse_kernel(const FuseArgs a) {
             ray[k].az = __fmaf_rn(M[6], fi, __fmaf_rn(M[7], fj, M[8]));
         }
     }
+    // this lane's role in the slab tests: view tk of segment tseg
+    const int tk = lane % KMAX, tseg = lane / KMAX;
+    const bool tview = tk < a.K;
+    Ray corner[4];
+    {
+        const int kk = tview ? tk : 0;
+        const float *M = a.xf[kk].M;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float ci = (float)((c & 1) ? i1 : i0), cj = (float)((c & 2) ? j1 : j0);
+            corner[c].ax = __fmaf_rn(M[0], ci, __fmaf_rn(M[1], cj, M[2]));
+            corner[c].ay = __fmaf_rn(M[3], ci, __fmaf_rn(M[4], cj, M[5]));
+            corner[c].az = __fmaf_rn(M[6], ci, __fmaf_rn(M[7], cj, M[8]));
+        }
+    }
     float S_prev = 0.0f, W_prev = 0.0f, z_prev = 0.0f;
-    bool have_prev = false;
+    bool have_prev = false;  // sample s-1 was evaluated (uniform across the warp)
+    bool done = !inside;
     float out = 0.0f;
     int idx = -1;
     int s = 0;
-    int cool = 0;     // samples to evaluate before trying to skip again
-    bool shorter = false;  // the long test just failed: try the short one
+    int cool = 0;
+    bool shorter = false;
     while (s < a.D) {
+        if (__all_sync(0xffffffffu, done)) break;
         if (cool == 0 && s < a.D - 1) {
-            const int L = min(shorter ? SKIP_SHORT : SKIP_LONG, a.D - 1 - s);
-            if (segment_is_free<KMAX>(a, ray, __fmaf_rn((float)s, a.dz, a.zn),
-                                      __fmaf_rn((float)(s + L), a.dz, a.zn))) {
-                s += L;  // samples s..s+L are not crossing ends; s+L is evaluated next
+            const int L = shorter ? SKIP_SHORT : SKIP_LONG;
+            const int sa = s + tseg * L;
+            bool f = false;
+            if (sa < a.D - 1) {
+                const int sb = min(sa + L, a.D - 1);
+                f = !tview || slab_view_free(a, tk, corner, __fmaf_rn((float)sa, a.dz, a.zn),
+                                             __fmaf_rn((float)sb, a.dz, a.zn));
+            }
+            const unsigned ball = __ballot_sync(0xffffffffu, f);
+            int nfree = 0;
+#pragma unroll
+            for (int g = 0; g < NSEG; ++g) {
+                if (nfree == g && ((ball >> (g * KMAX)) & SEGMASK) == SEGMASK) ++nfree;
+            }
+            if (nfree > 0) {
+                s = min(s + nfree * L, a.D - 1);  // samples up to s are not crossing ends; s is evaluated next
                 have_prev = false;
                 shorter = false;
                 continue;
             }
-            if (!shorter && L > SKIP_SHORT) {
+            if (!shorter && SKIP_SHORT < SKIP_LONG) {
                 shorter = true;
                 continue;
             }
@@ -336,23 +386,27 @@ __global__ void __launch_bounds__(FZ_TX *FZ_TY) fuse_kernel(const FuseArgs a) {
             cool = SKIP_COOL;
         }
         const float zs = __fmaf_rn((float)s, a.dz, a.zn);
-        float S, Wsum;
-        evaluate_sample<KMAX>(a, ray, zs, S, Wsum);
-        if (have_prev && W_prev > 0.0f && Wsum > 0.0f && S_prev > 0.0f && S <= 0.0f) {
-            out = z_prev + (zs - z_prev) * (S_prev / (S_prev - S));
-            idx = s - 1;
-            break;
+        if (!done) {
+            float S, Wsum;
+            evaluate_sample<KMAX>(a, ray, zs, S, Wsum);
+            if (have_prev && W_prev > 0.0f && Wsum > 0.0f && S_prev > 0.0f && S <= 0.0f) {
+                out = z_prev + (zs - z_prev) * (S_prev / (S_prev - S));
+                idx = s - 1;
+                done = true;
+            }
+            S_prev = S;
+            W_prev = Wsum;
+            z_prev = zs;
         }
-        S_prev = S;
-        W_prev = Wsum;
-        z_prev = zs;
         have_prev = true;
         ++s;
         if (cool > 0) --cool;
     }
-    const size_t o = (size_t)j * a.Wt + i;
-    a.fused[o] = out;
-    if (a.crossing) a.crossing[o] = (int16_t)idx;
+    if (inside) {
+        const size_t o = (size_t)j * a.Wt + i;
+        a.fused[o] = out;
+        if (a.crossing) a.crossing[o] = (int16_t)idx;
+    }
 }
 
 template <int R>
@@ -391,8 +445,9 @@ cudaError_t launch_weight_map(const float *depth, void *map, int K, int W, int H
 }
 
 cudaError_t launch_fuse(const FuseArgs &a, cudaStream_t st) {
-    dim3 grid((a.Wt + FZ_TX - 1) / FZ_TX, (a.Ht + FZ_TY - 1) / FZ_TY);
-    dim3 block(FZ_TX, FZ_TY);
+    const int64_t nb = (int64_t)((a.Wt + BX - 1) / BX) * ((a.Ht + BY - 1) / BY);
+    const unsigned grid = (unsigned)((nb + FZ_WARPS - 1) / FZ_WARPS);
+    const dim3 block(32 * FZ_WARPS);
     if (a.K <= 4) fuse_kernel<4><<<grid, block, 0, st>>>(a);
     else if (a.K <= 8) fuse_kernel<8><<<grid, block, 0, st>>>(a);
     else if (a.K <= 16) fuse_kernel<16><<<grid, block, 0, st>>>(a);
