@@ -169,11 +169,12 @@ class Pipeline:
             events[3].record()
 
     def launches_per_step(self):
-        # refine (vec4 kernel), weight map, fuse, splat clear + scatter/resolve per group of views
+        # refine (vector kernel + tail), weight map + two bound-pyramid kernels, fuse,
+        # splat clear + scatter/resolve per group of views
         slots = max(1, min(self.N, self.ws_splat.numel() // (self.Ht * self.Wt * 8)))
         groups = (self.N + slots - 1) // slots
         n_refine = 1 + (1 if (self.N * self.H * self.W) % 4 else 0)
-        return n_refine + 2 + 1 + 2 * groups
+        return n_refine + 3 + 1 + 1 + 2 * groups
 
 
 def algorithmic_fuse(cross_np, D, K):

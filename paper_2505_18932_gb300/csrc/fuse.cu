@@ -25,21 +25,24 @@
 namespace gvs {
 namespace {
 
-constexpr int WM_TX = 32;
-constexpr int WM_TY = 8;
+constexpr int WM_TX = 32;   // block of 32 x 32 output pixels: 32 x 8 threads,
+constexpr int WM_TY = 32;   // each thread a column of WM_P pixels
+constexpr int WM_P = 4;
 #define kInf __int_as_float(0x7f800000)
 
 __device__ __forceinline__ bool valid_depth(float d) { return isfinite(d) && d > 0.0f; }
 
-// R = window / 2.  Tile of WM_TX x WM_TY outputs; halo replicated at borders.
+// R = window / 2.  The shared tile holds the block's depths plus an R-pixel
+// halo replicated at the image borders (invalid depths as NaN).  A thread
+// reads each of the (WM_P + 2R) x (2R + 1) shared values its column needs once
+// and reuses it for every output whose window contains it.
 template <int R>
-__global__ void __launch_bounds__(WM_TX *WM_TY) weight_map_kernel(const float *__restrict__ depth,
-                                                                  char *__restrict__ map, MapLayout L, float mu,
-                                                                  float wconst, float inv_w2) {
+__global__ void __launch_bounds__(256) weight_map_kernel(const float *__restrict__ depth, char *__restrict__ map,
+                                                         MapLayout L, float mu, float wconst, float inv_w2) {
     constexpr int SW = WM_TX + 2 * R;
     constexpr int SH = WM_TY + 2 * R;
     __shared__ float tile[SH][SW];
-    __shared__ float2 red[WM_TY][WM_TX / 8];
+    __shared__ float2 red[WM_TY / WM_P][WM_TX / 8];
     const int W = L.W, H = L.H;
     const int k = blockIdx.z;
     const float *dep = depth + (size_t)k * W * H;
@@ -50,7 +53,7 @@ __global__ void __launch_bounds__(WM_TX *WM_TY) weight_map_kernel(const float *_
         // whole-view bounds, reduced into by depth_bounds with integer atomics on the float bits
         reinterpret_cast<int2 *>(map + L.off_g)[k] = make_int2(0x7f800000, (int)0xff800000u);
     }
-    for (int e = tid; e < SW * SH; e += WM_TX * WM_TY) {
+    for (int e = tid; e < SW * SH; e += 256) {
         const int sy = e / SW, sx = e - sy * SW;
         const int gx = min(max(x0 + sx, 0), W - 1);
         const int gy = min(max(y0 + sy, 0), H - 1);
@@ -58,47 +61,63 @@ __global__ void __launch_bounds__(WM_TX *WM_TY) weight_map_kernel(const float *_
         tile[sy][sx] = valid_depth(d) ? d : __int_as_float(0x7fc00000);  // NaN marks invalid
     }
     __syncthreads();
-    const int x = blockIdx.x * WM_TX + threadIdx.x;
-    const int y = blockIdx.y * WM_TY + threadIdx.y;
-    const bool inside = x < W && y < H;
-    const float dc = tile[threadIdx.y + R][threadIdx.x + R];
-    const bool valid = inside && (dc == dc);
-    if (valid) {
-        float nu = 0.0f;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int x = blockIdx.x * WM_TX + tx;
+    const int yb = blockIdx.y * WM_TY + ty * WM_P;
+    float dc[WM_P], nu[WM_P];
 #pragma unroll
-        for (int dy = 0; dy <= 2 * R; ++dy) {
+    for (int p = 0; p < WM_P; ++p) {
+        dc[p] = tile[ty * WM_P + p + R][tx + R];
+        nu[p] = 0.0f;
+    }
 #pragma unroll
-            for (int dx = 0; dx <= 2 * R; ++dx) {
-                // fminf returns mu for a NaN (invalid) neighbour: it counts mu^2
-                const float t = fminf(fabsf(dc - tile[threadIdx.y + dy][threadIdx.x + dx]), mu);
-                nu = fmaf(t, t, nu);
+    for (int r = 0; r < WM_P + 2 * R; ++r) {
+        float row[2 * R + 1];
+#pragma unroll
+        for (int dx = 0; dx <= 2 * R; ++dx) row[dx] = tile[ty * WM_P + r][tx + dx];
+#pragma unroll
+        for (int p = 0; p < WM_P; ++p) {
+            if (r - p >= 0 && r - p <= 2 * R) {
+#pragma unroll
+                for (int dx = 0; dx <= 2 * R; ++dx) {
+                    // fminf returns mu for a NaN (invalid) neighbour: it counts mu^2
+                    const float t = fminf(fabsf(dc[p] - row[dx]), mu);
+                    nu[p] = fmaf(t, t, nu[p]);
+                }
             }
         }
-        const float w = nu > 0.0f ? fminf(wconst * rsqrtf(nu * inv_w2), 1.0f) : 1.0f;
-        reinterpret_cast<float2 *>(map + L.off_dw)[(size_t)k * W * H + (size_t)y * W + x] = make_float2(dc, w);
-    } else if (inside) {
-        reinterpret_cast<float2 *>(map + L.off_dw)[(size_t)k * W * H + (size_t)y * W + x] = make_float2(0.0f, 0.0f);
     }
-    // 8x8 tile bounds: reduce over the 8 lanes of a tile row, then over the 8 rows
-    float lo = valid ? dc : kInf, hi = valid ? dc : -kInf;
+    float lo = kInf, hi = -kInf;
+    float2 *dw = reinterpret_cast<float2 *>(map + L.off_dw) + (size_t)k * W * H;
+#pragma unroll
+    for (int p = 0; p < WM_P; ++p) {
+        const int y = yb + p;
+        if (x < W && y < H) {
+            float2 out = make_float2(0.0f, 0.0f);
+            if (dc[p] == dc[p]) {  // valid centre
+                const float w = nu[p] > 0.0f ? fminf(wconst * rsqrtf(nu[p] * inv_w2), 1.0f) : 1.0f;
+                out = make_float2(dc[p], w);
+                lo = fminf(lo, dc[p]);
+                hi = fmaxf(hi, dc[p]);
+            }
+            dw[(size_t)y * W + x] = out;
+        }
+    }
+    // 8x8 tile bounds: over the 8 lanes of a tile column group, then the two thread rows of a tile
 #pragma unroll
     for (int m = 1; m < 8; m <<= 1) {
         lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, m));
         hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, m));
     }
-    if ((threadIdx.x & 7) == 0) red[threadIdx.y][threadIdx.x >> 3] = make_float2(lo, hi);
+    if ((tx & 7) == 0) red[ty][tx >> 3] = make_float2(lo, hi);
     __syncthreads();
-    if (threadIdx.y == 0 && threadIdx.x < WM_TX / 8) {
-        float2 b = red[0][threadIdx.x];
-#pragma unroll
-        for (int r = 1; r < WM_TY; ++r) {
-            b.x = fminf(b.x, red[r][threadIdx.x].x);
-            b.y = fmaxf(b.y, red[r][threadIdx.x].y);
-        }
-        const int tx = blockIdx.x * (WM_TX / 8) + threadIdx.x;
-        const int ty = blockIdx.y;  // WM_TY == 8
-        if (tx < L.tw[0] && ty < L.th[0])
-            reinterpret_cast<float2 *>(map + L.off_T[0])[((size_t)k * L.th[0] + ty) * L.tw[0] + tx] = b;
+    if (tid < (WM_TY / 8) * (WM_TX / 8)) {
+        const int tc = tid % (WM_TX / 8), tr = tid / (WM_TX / 8);
+        const float2 a = red[2 * tr][tc], b = red[2 * tr + 1][tc];
+        const int gx = blockIdx.x * (WM_TX / 8) + tc, gy = blockIdx.y * (WM_TY / 8) + tr;
+        if (gx < L.tw[0] && gy < L.th[0])
+            reinterpret_cast<float2 *>(map + L.off_T[0])[((size_t)k * L.th[0] + gy) * L.tw[0] + gx] =
+                make_float2(fminf(a.x, b.x), fmaxf(a.y, b.y));
     }
 }
 
@@ -198,6 +217,9 @@ __device__ __forceinline__ void nearest_pixel(float hx, float hy, float hz, int 
 constexpr int BX = 8;   // a warp marches a bundle of BX x BY target pixels
 constexpr int BY = 4;
 constexpr int FZ_WARPS = 4;
+#ifndef GVS_FUSE_MIN_BLOCKS
+#define GVS_FUSE_MIN_BLOCKS 8   // resident blocks per SM requested from the register allocator (64 registers)
+#endif
 #ifndef GVS_SKIP_LONG
 #define GVS_SKIP_LONG 8    // samples per segment in the first test
 #endif
@@ -309,7 +331,7 @@ __device__ __forceinline__ void evaluate_sample(const FuseArgs &a, const Ray (&r
 // evaluates sample s (all KMAX views unrolled, one 8-byte gather each) and
 // checks its own crossing.  The result equals the full uniform march.
 template <int KMAX>
-__global__ void __launch_bounds__(32 * FZ_WARPS) fuse_kernel(const FuseArgs a) {
+__global__ void __launch_bounds__(32 * FZ_WARPS, GVS_FUSE_MIN_BLOCKS) fuse_kernel(const FuseArgs a) {
     constexpr int NSEG = 32 / KMAX;
     constexpr unsigned SEGMASK = KMAX == 32 ? 0xffffffffu : ((1u << KMAX) - 1u);
     const int lane = threadIdx.x & 31;
@@ -413,7 +435,7 @@ template <int R>
 cudaError_t launch_wm(const float *depth, char *map, const MapLayout &L, float mu, float wconst, float inv_w2,
                       cudaStream_t st) {
     dim3 grid((L.W + WM_TX - 1) / WM_TX, (L.H + WM_TY - 1) / WM_TY, L.K);
-    weight_map_kernel<R><<<grid, dim3(WM_TX, WM_TY), 0, st>>>(depth, map, L, mu, wconst, inv_w2);
+    weight_map_kernel<R><<<grid, dim3(WM_TX, WM_TY / WM_P), 0, st>>>(depth, map, L, mu, wconst, inv_w2);
     return cudaGetLastError();
 }
 

@@ -80,6 +80,13 @@ __global__ void __launch_bounds__(256) splat_scatter(const SplatArgs a, int k0, 
         for (int ii = i0; ii <= i1; ++ii) atomicMin(&slot[(size_t)jj * a.Wt + ii], key);
 }
 
+__device__ __forceinline__ void decode(unsigned long long key, bool &has, int32_t &w, float &z) {
+    has = key != ~0ull;
+    w = has ? (int32_t)(uint32_t)(key & 0xffffffffull) : -1;
+    z = has ? __uint_as_float((uint32_t)(key >> 32)) : 0.0f;
+}
+
+// One thread per target pixel and view (any size).
 __global__ void __launch_bounds__(256) splat_resolve(const SplatArgs a, int k0, int kn) {
     const int64_t HWt = (int64_t)a.Wt * a.Ht;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -90,15 +97,62 @@ __global__ void __launch_bounds__(256) splat_resolve(const SplatArgs a, int k0, 
     unsigned long long *slot = a.keys + (size_t)kk * HWt;
     const unsigned long long key = slot[t];
     slot[t] = ~0ull;  // ready for the next group of views
-    const bool has = key != ~0ull;
-    const int32_t w = has ? (int32_t)(uint32_t)(key & 0xffffffffull) : -1;
-    const float z = has ? __uint_as_float((uint32_t)(key >> 32)) : 0.0f;
+    bool has;
+    int32_t w;
+    float z;
+    decode(key, has, w, z);
     const size_t o = (size_t)k * HWt + t;
     a.winner[o] = w;
     if (a.warped_rgba) a.warped_rgba[o] = has ? __ldg(&a.rgba[(size_t)k * a.W * a.H + w]) : 0u;
     if (a.warped_depth) a.warped_depth[o] = z;
     if (a.alpha) a.alpha[o] = (uint8_t)has;
     if (a.guided) a.guided[o] = (uint8_t)(has && fabsf(z - __ldg(&a.fused[t])) <= a.mu_guide);
+}
+
+// Four consecutive target pixels per thread, every access a 16-byte (or, for
+// the byte maps, 4-byte) vector; needs Wt * Ht divisible by 4.  The four
+// colour gathers are independent, so each thread keeps four in flight.
+__global__ void __launch_bounds__(256) splat_resolve4(const SplatArgs a, int k0, int kn) {
+    const int64_t HWt = (int64_t)a.Wt * a.Ht;
+    const int64_t q4 = HWt / 4;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (int64_t)kn * q4) return;
+    const int kk = (int)(q / q4);
+    const int k = k0 + kk;
+    const int64_t t4 = q - (int64_t)kk * q4;
+    ulonglong2 *slot = reinterpret_cast<ulonglong2 *>(a.keys + (size_t)kk * HWt) + 2 * t4;
+    const ulonglong2 k01 = slot[0], k23 = slot[1];
+    const ulonglong2 ones = make_ulonglong2(~0ull, ~0ull);
+    slot[0] = ones;  // ready for the next group of views
+    slot[1] = ones;
+    bool h0, h1, h2, h3;
+    int4 w;
+    float4 z;
+    decode(k01.x, h0, w.x, z.x);
+    decode(k01.y, h1, w.y, z.y);
+    decode(k23.x, h2, w.z, z.z);
+    decode(k23.y, h3, w.w, z.w);
+    const size_t o4 = (size_t)k * q4 + t4;
+    __stcs(reinterpret_cast<int4 *>(a.winner) + o4, w);
+    if (a.warped_rgba) {
+        const uint32_t *src = a.rgba + (size_t)k * a.W * a.H;
+        uint4 c;
+        c.x = h0 ? __ldg(&src[w.x]) : 0u;
+        c.y = h1 ? __ldg(&src[w.y]) : 0u;
+        c.z = h2 ? __ldg(&src[w.z]) : 0u;
+        c.w = h3 ? __ldg(&src[w.w]) : 0u;
+        __stcs(reinterpret_cast<uint4 *>(a.warped_rgba) + o4, c);
+    }
+    if (a.warped_depth) __stcs(reinterpret_cast<float4 *>(a.warped_depth) + o4, z);
+    if (a.alpha)
+        __stcs(reinterpret_cast<unsigned int *>(a.alpha) + o4,
+               (unsigned)h0 | ((unsigned)h1 << 8) | ((unsigned)h2 << 16) | ((unsigned)h3 << 24));
+    if (a.guided) {
+        const float4 f = __ldg(reinterpret_cast<const float4 *>(a.fused) + t4);
+        const unsigned g0 = h0 && fabsf(z.x - f.x) <= a.mu_guide, g1 = h1 && fabsf(z.y - f.y) <= a.mu_guide;
+        const unsigned g2 = h2 && fabsf(z.z - f.z) <= a.mu_guide, g3 = h3 && fabsf(z.w - f.w) <= a.mu_guide;
+        __stcs(reinterpret_cast<unsigned int *>(a.guided) + o4, g0 | (g1 << 8) | (g2 << 16) | (g3 << 24));
+    }
 }
 
 }  // namespace
@@ -120,8 +174,13 @@ cudaError_t launch_splat(const SplatArgs &a, int K, cudaStream_t st) {
         const int kn = (K - k0) < slots ? (K - k0) : slots;
         const int64_t ns = (int64_t)kn * HW;
         splat_scatter<<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(a, k0, kn);
-        const int64_t nt = (int64_t)kn * HWt;
-        splat_resolve<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(a, k0, kn);
+        if (HWt % 4 == 0) {
+            const int64_t nt = (int64_t)kn * (HWt / 4);
+            splat_resolve4<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(a, k0, kn);
+        } else {
+            const int64_t nt = (int64_t)kn * HWt;
+            splat_resolve<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(a, k0, kn);
+        }
     }
     return cudaGetLastError();
 }
