@@ -227,6 +227,31 @@ GVS_API gvs_status gvs_forward_splat(const gvs_camera *in_cams, const float *in_
                              float *warped_depth, uint8_t *alpha, uint8_t *guided, void *workspace,
                              size_t workspace_bytes, void *stream);
 
+/*
+ * gvs_forward_splat_noalloc -- gvs_forward_splat for callers that cannot
+ * allocate device memory.  The paper has no counterpart; this is a service of
+ * the library.  A plugin living inside a host application that owns all device
+ * allocations, code recorded into a CUDA graph, or a real-time loop that must
+ * not block on the allocator cannot create the splat workspace; this call
+ * needs none.  Its z-buffer is a file-scope device array of 2^21 64-bit keys
+ * (16 MiB) that every GPU loading the library holds until the process exits.
+ *   - Arguments, outputs and errors are those of gvs_forward_splat without the
+ *     workspace.  Targets of more than 2,097,152 pixels (e.g. larger than
+ *     1920 x 1080) are rejected with GVS_ERR_INVALID_ARG before anything runs.
+ *   - The first call on a device looks up the array's device address with
+ *     cudaGetSymbolAddress (with that device current); make that first call
+ *     before any stream capture.
+ *   - It calls no cudaMalloc, cudaFree or allocating library routine.
+ *   - Every call shares the one array and clears it before use.  Calls whose
+ *     work overlaps on the GPU (other streams, other host threads) race on it:
+ *     order them on one stream.
+ */
+GVS_API gvs_status gvs_forward_splat_noalloc(const gvs_camera *in_cams, const float *in_depths,
+                                             const uint32_t *in_rgba, int32_t n_views, const gvs_camera *target,
+                                             const gvs_splat_params *params, const float *fused_depth,
+                                             int32_t *winner, uint32_t *warped_rgba, float *warped_depth,
+                                             uint8_t *alpha, uint8_t *guided, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

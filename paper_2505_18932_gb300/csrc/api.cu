@@ -334,3 +334,70 @@ gvs_status gvs_forward_splat(const gvs_camera *in_cams, const float *in_depths, 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Forward splat without any device allocation.
+//
+// Some callers cannot hand the library a workspace: a plugin inside a host
+// application that owns every device allocation through its own allocator,
+// code recorded into a CUDA graph where a cudaMalloc would break the capture,
+// or a real-time loop that must not block on the allocator (cudaMalloc and
+// cudaFree can synchronize the device).  For them the z-buffer lives in a
+// file-scope device array, loaded with the library and held by every GPU that
+// loads it until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocKeys = size_t(1) << 21;  // 16 MiB of 64-bit keys: targets up to 2,097,152 pixels
+static __device__ __align__(256) unsigned long long g_noalloc_keys[kNoAllocKeys];
+
+// Device address of g_noalloc_keys on the current device, looked up once per
+// device.  In host code the symbol is only a host-side handle, never a device
+// address, so it must not be passed to a kernel directly.
+unsigned long long *noalloc_keys_on_current_device(gvs_status *st) {
+    static std::mutex mu;
+    static unsigned long long *addr[64] = {nullptr};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        *st = fail(GVS_ERR_DEVICE, "splat (no-alloc): cudaGetDevice: %s", cudaGetErrorString(e));
+        return nullptr;
+    }
+    if (dev < 0 || dev >= 64) {
+        *st = fail(GVS_ERR_DEVICE, "splat (no-alloc): device index %d out of range", dev);
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_keys);
+        if (e != cudaSuccess || !p) {
+            *st = fail(GVS_ERR_CUDA, "splat (no-alloc): cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+            return nullptr;
+        }
+        addr[dev] = reinterpret_cast<unsigned long long *>(p);
+    }
+    *st = GVS_OK;
+    return addr[dev];
+}
+
+}  // namespace
+
+extern "C" gvs_status gvs_forward_splat_noalloc(const gvs_camera *in_cams, const float *in_depths,
+                                                const uint32_t *in_rgba, int32_t n_views, const gvs_camera *target,
+                                                const gvs_splat_params *params, const float *fused_depth,
+                                                int32_t *winner, uint32_t *warped_rgba, float *warped_depth,
+                                                uint8_t *alpha, uint8_t *guided, void *stream) {
+    if (!target) return fail(GVS_ERR_INVALID_ARG, "splat (no-alloc): target camera is NULL");
+    const int64_t pixels = (int64_t)target->width * (int64_t)target->height;
+    if (pixels > (int64_t)kNoAllocKeys)
+        return fail(GVS_ERR_INVALID_ARG,
+                    "splat (no-alloc): target has %lld pixels; this entry point holds a z-buffer for at most %zu",
+                    (long long)pixels, kNoAllocKeys);
+    gvs_status st = GVS_OK;
+    unsigned long long *keys = noalloc_keys_on_current_device(&st);
+    if (!keys) return st;
+    return gvs_forward_splat(in_cams, in_depths, in_rgba, n_views, target, params, fused_depth, winner,
+                             warped_rgba, warped_depth, alpha, guided, keys, kNoAllocKeys * sizeof(unsigned long long),
+                             stream);
+}

@@ -73,6 +73,11 @@ API = {
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                          ctypes.c_void_p]),
+    "gvs_forward_splat_noalloc": (ctypes.c_int, [ctypes.POINTER(GvsCamera), ctypes.c_void_p, ctypes.c_void_p,
+                                                 ctypes.c_int32, ctypes.POINTER(GvsCamera),
+                                                 ctypes.POINTER(GvsSplatParams), ctypes.c_void_p, ctypes.c_void_p,
+                                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                 ctypes.c_void_p]),
 }
 
 
