@@ -77,6 +77,14 @@ typedef enum {
     GVS_ERR_DEVICE = 5         /* no usable CUDA device */
 } gvs_status;
 
+/* Storage type of depth inputs and of the fusion map.  Arithmetic is FP32
+ * whatever the storage: FP16 halves the bytes moved and gathered. */
+typedef enum {
+    GVS_F32 = 0,               /* float */
+    GVS_F16 = 1,               /* IEEE half */
+    GVS_BF16 = 2               /* bfloat16 (colour of the soft splat only) */
+} gvs_dtype;
+
 typedef struct {
     int32_t width, height;
     double fx, fy, cx, cy;     /* pinhole intrinsics, pixels */
@@ -87,6 +95,7 @@ typedef struct {
 /* Temporal refinement (Sec. 3.2, Eq. 1-2), binary mask form. */
 typedef struct {
     float tau;                 /* colour threshold in [0,1]; integer T = floor(255 * tau) */
+    int32_t depth_dtype;       /* GVS_F32 or GVS_F16: element type of depth_t and depth_state */
 } gvs_refine_params;
 
 /* TSDF fusion (Supplement A.1, Eq. 3). */
@@ -97,6 +106,8 @@ typedef struct {
     float weight_const;        /* 0.001 in the paper */
     int32_t window;            /* w, odd, 1..GVS_MAX_WINDOW; 7 in the paper */
     int32_t normalize;         /* 0: S = sum w*clamp (paper); 1: S / W */
+    int32_t depth_dtype;       /* GVS_F32 or GVS_F16: element type of in_depths */
+    int32_t map_dtype;         /* GVS_F32: (d, omega) as float2; GVS_F16: as half2 (omega rounded to half) */
 } gvs_fuse_params;
 
 /* Forward splat (Sec. 3.1, Supplement A.3). */
@@ -104,6 +115,7 @@ typedef struct {
     int32_t footprint;         /* 1: pixel-sized footprint; 0: single nearest pixel */
     float max_half_width;      /* footprint half-width cap in target pixels (>= 0.5), e.g. 2 */
     float mu_guide;            /* guided mask: |warped depth - fused depth| <= mu_guide */
+    int32_t depth_dtype;       /* GVS_F32 or GVS_F16: element type of in_depths */
 } gvs_splat_params;
 
 /* Library identification and diagnostics. */
@@ -120,13 +132,13 @@ GVS_API const char *gvs_last_error(void);
  *   depth_state = m ? depth_t : depth_state       (in place, bit-exact copy)
  * rgba_prev == NULL marks the first frame: m = 1 everywhere.
  *   rgba_t, rgba_prev : uint32 [n_views][height][width]
- *   depth_t           : float  [n_views][height][width]
- *   depth_state       : float  [n_views][height][width], in: previous filtered
+ *   depth_t           : [n_views][height][width] of params->depth_dtype
+ *   depth_state       : same type and shape, in: previous filtered
  *                       depth (ignored when rgba_prev == NULL), out: new one
  *   mask              : uint8  [n_views][height][width] or NULL
  */
-GVS_API gvs_status gvs_refine_depth(const uint32_t *rgba_t, const uint32_t *rgba_prev, const float *depth_t,
-                            float *depth_state, uint8_t *mask, int32_t n_views, int32_t width,
+GVS_API gvs_status gvs_refine_depth(const uint32_t *rgba_t, const uint32_t *rgba_prev, const void *depth_t,
+                            void *depth_state, uint8_t *mask, int32_t n_views, int32_t width,
                             int32_t height, const gvs_refine_params *params, void *stream);
 
 /* Workspace bytes for gvs_fuse_depth (the "map" of gvs_weight_map): the packed
@@ -158,12 +170,14 @@ GVS_API size_t gvs_fuse_workspace_bytes(int32_t n_views, int32_t width, int32_t 
  * fused_depth(i, j) = z_s + (z_{s+1} - z_s) S_s / (S_s - S_{s+1}) at the first
  *   s with W_s > 0, W_{s+1} > 0, S_s > 0, S_{s+1} <= 0; 0 if there is none.
  *   in_cams   : n_views cameras, all of one size (width x height)
- *   in_depths : float [n_views][height][width]
+ *   in_depths : [n_views][height][width] of params->depth_dtype (values are
+ *               widened to FP32; with map_dtype GVS_F16 the weight is stored
+ *               as half, every sum and the interpolation stay FP32)
  *   fused_depth : float [target.height][target.width]
  *   crossing  : int16 [target.height][target.width] (s, or -1) or NULL
  *   workspace : >= gvs_fuse_workspace_bytes(n_views, width, height) bytes
  */
-GVS_API gvs_status gvs_fuse_depth(const gvs_camera *in_cams, const float *in_depths, int32_t n_views,
+GVS_API gvs_status gvs_fuse_depth(const gvs_camera *in_cams, const void *in_depths, int32_t n_views,
                           const gvs_camera *target, const gvs_fuse_params *params, float *fused_depth,
                           int16_t *crossing, void *workspace, size_t workspace_bytes, void *stream);
 
@@ -175,13 +189,15 @@ GVS_API gvs_status gvs_fuse_depth(const gvs_camera *in_cams, const float *in_dep
  * depth as (d, omega), (0, 0) where d is invalid; with it go the min and max
  * valid depth of every 8, 32 and 128 pixel tile and of each whole view,
  * which let the march skip runs of samples that provably hold no crossing.
- *   in_depths : float [n_views][height][width]
+ *   in_depths : [n_views][height][width] of depth_dtype (GVS_F32 or GVS_F16)
+ *   map_dtype : GVS_F32 or GVS_F16 storage of (d, omega); the map must be read
+ *               back with the same map_dtype in gvs_fuse_params
  *   map       : >= gvs_fuse_workspace_bytes(n_views, width, height) bytes,
  *               256-byte aligned; its layout is private to the library
  */
-GVS_API gvs_status gvs_weight_map(const float *in_depths, int32_t n_views, int32_t width, int32_t height,
-                                  float mu, float weight_const, int32_t window, void *map, size_t map_bytes,
-                                  void *stream);
+GVS_API gvs_status gvs_weight_map(const void *in_depths, int32_t depth_dtype, int32_t n_views, int32_t width,
+                                  int32_t height, float mu, float weight_const, int32_t window, int32_t map_dtype,
+                                  void *map, size_t map_bytes, void *stream);
 
 /*
  * gvs_fuse_depth_from_map -- stage 2: the TSDF march and zero crossing of
@@ -212,6 +228,7 @@ GVS_API size_t gvs_splat_workspace_bytes(int32_t n_views, int32_t target_width, 
  *   point    : covers (rint(x), rint(y))
  *   key = (float bits of h.z) << 32 | (v * width + u); per target pixel the
  *   smallest key wins: the nearest surface, ties to the lower source index.
+ * in_depths is [n_views][height][width] of params->depth_dtype (widened to FP32).
  * Outputs, each [n_views][target.height][target.width] (NULL to skip, except winner):
  *   winner       int32  source pixel index v*width+u, or -1
  *   warped_rgba  uint32 source colour of the winner (0 if none)
@@ -221,7 +238,7 @@ GVS_API size_t gvs_splat_workspace_bytes(int32_t n_views, int32_t target_width, 
  *                needs fused_depth [target.height][target.width]
  *   workspace : >= gvs_splat_workspace_bytes(...) bytes
  */
-GVS_API gvs_status gvs_forward_splat(const gvs_camera *in_cams, const float *in_depths, const uint32_t *in_rgba,
+GVS_API gvs_status gvs_forward_splat(const gvs_camera *in_cams, const void *in_depths, const uint32_t *in_rgba,
                              int32_t n_views, const gvs_camera *target, const gvs_splat_params *params,
                              const float *fused_depth, int32_t *winner, uint32_t *warped_rgba,
                              float *warped_depth, uint8_t *alpha, uint8_t *guided, void *workspace,
@@ -246,7 +263,7 @@ GVS_API gvs_status gvs_forward_splat(const gvs_camera *in_cams, const float *in_
  *     work overlaps on the GPU (other streams, other host threads) race on it:
  *     order them on one stream.
  */
-GVS_API gvs_status gvs_forward_splat_noalloc(const gvs_camera *in_cams, const float *in_depths,
+GVS_API gvs_status gvs_forward_splat_noalloc(const gvs_camera *in_cams, const void *in_depths,
                                              const uint32_t *in_rgba, int32_t n_views, const gvs_camera *target,
                                              const gvs_splat_params *params, const float *fused_depth,
                                              int32_t *winner, uint32_t *warped_rgba, float *warped_depth,

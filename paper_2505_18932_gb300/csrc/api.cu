@@ -121,14 +121,16 @@ const char *gvs_status_string(gvs_status s) {
 
 const char *gvs_last_error(void) { return g_err; }
 
-gvs_status gvs_refine_depth(const uint32_t *rgba_t, const uint32_t *rgba_prev, const float *depth_t,
-                            float *depth_state, uint8_t *mask, int32_t n_views, int32_t width, int32_t height,
+gvs_status gvs_refine_depth(const uint32_t *rgba_t, const uint32_t *rgba_prev, const void *depth_t,
+                            void *depth_state, uint8_t *mask, int32_t n_views, int32_t width, int32_t height,
                             const gvs_refine_params *params, void *stream) {
     if (!params) return fail(GVS_ERR_INVALID_ARG, "refine: params is NULL");
     if (n_views < 0 || n_views > GVS_MAX_VIEWS) return fail(GVS_ERR_INVALID_ARG, "refine: n_views out of range");
     if (width < 1 || height < 1 || width > GVS_MAX_DIM || height > GVS_MAX_DIM)
         return fail(GVS_ERR_INVALID_ARG, "refine: image size out of range");
     if (!(params->tau >= 0.0f && params->tau <= 1.0f)) return fail(GVS_ERR_INVALID_ARG, "refine: tau not in [0,1]");
+    if (params->depth_dtype != GVS_F32 && params->depth_dtype != GVS_F16)
+        return fail(GVS_ERR_UNSUPPORTED, "refine: depth_dtype must be GVS_F32 or GVS_F16");
     if (n_views == 0) return GVS_OK;
     if (!rgba_t || !depth_t || !depth_state) return fail(GVS_ERR_INVALID_ARG, "refine: NULL array");
     if (!aligned(rgba_t, 16) || !aligned(depth_t, 16) || !aligned(depth_state, 16) ||
@@ -137,7 +139,7 @@ gvs_status gvs_refine_depth(const uint32_t *rgba_t, const uint32_t *rgba_prev, c
     const int threshold = (int)floor(255.0 * (double)params->tau);
     const int64_t n = (int64_t)n_views * width * height;
     cudaError_t e = gvs::launch_refine(rgba_t, rgba_prev, depth_t, depth_state, mask, n, threshold,
-                                       (cudaStream_t)stream);
+                                       params->depth_dtype, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "refine launch");
     return GVS_OK;
 }
@@ -164,6 +166,10 @@ gvs_status check_fuse_common(const gvs_camera *in_cams, int32_t n_views, const g
         return fail(GVS_ERR_INVALID_ARG, "fuse: need 0 < z_near < z_far");
     if (!(isfinite(p.mu) && p.mu > 0.0f)) return fail(GVS_ERR_INVALID_ARG, "fuse: mu must be > 0");
     if (p.normalize != 0 && p.normalize != 1) return fail(GVS_ERR_INVALID_ARG, "fuse: normalize must be 0 or 1");
+    if (p.depth_dtype != GVS_F32 && p.depth_dtype != GVS_F16)
+        return fail(GVS_ERR_UNSUPPORTED, "fuse: depth_dtype must be GVS_F32 or GVS_F16");
+    if (p.map_dtype != GVS_F32 && p.map_dtype != GVS_F16)
+        return fail(GVS_ERR_UNSUPPORTED, "fuse: map_dtype must be GVS_F32 or GVS_F16");
     if (!fused_depth) return fail(GVS_ERR_INVALID_ARG, "fuse: fused_depth is NULL");
     if (!aligned(fused_depth, 16) || (crossing && !aligned(crossing, 16)))
         return fail(GVS_ERR_INVALID_ARG, "fuse: arrays must be 16-byte aligned");
@@ -186,7 +192,7 @@ gvs::FuseArgs fuse_args(const gvs_camera *in_cams, const void *map, int32_t n_vi
     const gvs::MapLayout L = gvs::map_layout(n_views, W, H);
     const char *m = reinterpret_cast<const char *>(map);
     if (n_views > 0) {
-        a.dw = reinterpret_cast<const float2 *>(m + L.off_dw);
+        a.dw = m + L.off_dw;
         for (int l = 0; l < 3; ++l) a.ob[l] = reinterpret_cast<const float2 *>(m + L.off_O[l]);
         a.tg = reinterpret_cast<const float2 *>(m + L.off_g);
     }
@@ -205,6 +211,7 @@ gvs::FuseArgs fuse_args(const gvs_camera *in_cams, const void *map, int32_t n_vi
     a.inv_mu = (float)(1.0 / (double)p.mu);
     a.behind = (float)(1.0001 * (double)p.mu);
     a.normalize = p.normalize;
+    a.map_dtype = p.map_dtype;
     a.fused = fused;
     a.crossing = crossing;
     for (int k = 0; k < n_views; ++k) a.xf[k] = compose(in_cams[k], *target);
@@ -215,20 +222,25 @@ gvs::FuseArgs fuse_args(const gvs_camera *in_cams, const void *map, int32_t n_vi
 
 extern "C" {
 
-gvs_status gvs_weight_map(const float *in_depths, int32_t n_views, int32_t width, int32_t height, float mu,
-                          float weight_const, int32_t window, void *map, size_t map_bytes, void *stream) {
+gvs_status gvs_weight_map(const void *in_depths, int32_t depth_dtype, int32_t n_views, int32_t width,
+                          int32_t height, float mu, float weight_const, int32_t window, int32_t map_dtype, void *map,
+                          size_t map_bytes, void *stream) {
     if (n_views < 0 || n_views > GVS_MAX_VIEWS) return fail(GVS_ERR_INVALID_ARG, "weight map: n_views out of range");
     if (width < 1 || height < 1 || width > GVS_MAX_DIM || height > GVS_MAX_DIM)
         return fail(GVS_ERR_INVALID_ARG, "weight map: image size out of range");
     gvs_status s = check_weight_params(mu, weight_const, window);
     if (s != GVS_OK) return s;
+    if (depth_dtype != GVS_F32 && depth_dtype != GVS_F16)
+        return fail(GVS_ERR_UNSUPPORTED, "weight map: depth_dtype must be GVS_F32 or GVS_F16");
+    if (map_dtype != GVS_F32 && map_dtype != GVS_F16)
+        return fail(GVS_ERR_UNSUPPORTED, "weight map: map_dtype must be GVS_F32 or GVS_F16");
     if (n_views == 0) return GVS_OK;
     if (!in_depths || !aligned(in_depths, 16)) return fail(GVS_ERR_INVALID_ARG, "weight map: in_depths is NULL or misaligned");
     const size_t need = gvs_fuse_workspace_bytes(n_views, width, height);
     if (!map || map_bytes < need || !aligned(map, 256))
         return fail(GVS_ERR_WORKSPACE, "weight map: map needs %zu bytes, 256-byte aligned", need);
-    cudaError_t e = gvs::launch_weight_map(in_depths, map, n_views, width, height, mu, weight_const, window,
-                                           (cudaStream_t)stream);
+    cudaError_t e = gvs::launch_weight_map(in_depths, depth_dtype, map, map_dtype, n_views, width, height, mu,
+                                           weight_const, window, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "weight map launch");
     return GVS_OK;
 }
@@ -248,7 +260,7 @@ gvs_status gvs_fuse_depth_from_map(const gvs_camera *in_cams, const void *map, s
     return GVS_OK;
 }
 
-gvs_status gvs_fuse_depth(const gvs_camera *in_cams, const float *in_depths, int32_t n_views,
+gvs_status gvs_fuse_depth(const gvs_camera *in_cams, const void *in_depths, int32_t n_views,
                           const gvs_camera *target, const gvs_fuse_params *params, float *fused_depth,
                           int16_t *crossing, void *workspace, size_t workspace_bytes, void *stream) {
     int32_t W = 0, H = 0;
@@ -262,8 +274,8 @@ gvs_status gvs_fuse_depth(const gvs_camera *in_cams, const float *in_depths, int
     if (need > 0 && (!workspace || workspace_bytes < need || !aligned(workspace, 256)))
         return fail(GVS_ERR_WORKSPACE, "fuse: workspace needs %zu bytes, 256-byte aligned", need);
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = gvs::launch_weight_map(in_depths, workspace, n_views, W, H, params->mu, params->weight_const,
-                                           params->window, st);
+    cudaError_t e = gvs::launch_weight_map(in_depths, params->depth_dtype, workspace, params->map_dtype, n_views, W,
+                                           H, params->mu, params->weight_const, params->window, st);
     if (e != cudaSuccess) return cuda_fail(e, "fuse: weight map launch");
     gvs::FuseArgs a = fuse_args(in_cams, workspace, n_views, W, H, target, *params, fused_depth, crossing);
     e = gvs::launch_fuse(a, st);
@@ -277,7 +289,7 @@ size_t gvs_splat_workspace_bytes(int32_t n_views, int32_t target_width, int32_t 
     return align_up((size_t)target_width * (size_t)target_height * sizeof(unsigned long long), 256);
 }
 
-gvs_status gvs_forward_splat(const gvs_camera *in_cams, const float *in_depths, const uint32_t *in_rgba,
+gvs_status gvs_forward_splat(const gvs_camera *in_cams, const void *in_depths, const uint32_t *in_rgba,
                              int32_t n_views, const gvs_camera *target, const gvs_splat_params *params,
                              const float *fused_depth, int32_t *winner, uint32_t *warped_rgba, float *warped_depth,
                              uint8_t *alpha, uint8_t *guided, void *workspace, size_t workspace_bytes,
@@ -289,6 +301,8 @@ gvs_status gvs_forward_splat(const gvs_camera *in_cams, const float *in_depths, 
     if (!camera_ok(target)) return fail(GVS_ERR_INVALID_ARG, "splat: target camera invalid");
     const gvs_splat_params &p = *params;
     if (p.footprint != 0 && p.footprint != 1) return fail(GVS_ERR_INVALID_ARG, "splat: footprint must be 0 or 1");
+    if (p.depth_dtype != GVS_F32 && p.depth_dtype != GVS_F16)
+        return fail(GVS_ERR_UNSUPPORTED, "splat: depth_dtype must be GVS_F32 or GVS_F16");
     if (!(isfinite(p.max_half_width) && p.max_half_width >= 0.5f && p.max_half_width <= 64.0f))
         return fail(GVS_ERR_INVALID_ARG, "splat: max_half_width must be in [0.5, 64]");
     if (guided && !(isfinite(p.mu_guide) && p.mu_guide >= 0.0f))
@@ -306,6 +320,7 @@ gvs_status gvs_forward_splat(const gvs_camera *in_cams, const float *in_depths, 
     gvs::SplatArgs a;
     memset(&a, 0, sizeof(a));
     a.depth = in_depths;
+    a.depth_dtype = p.depth_dtype;
     a.rgba = in_rgba;
     a.W = W;
     a.H = H;
@@ -383,7 +398,7 @@ unsigned long long *noalloc_keys_on_current_device(gvs_status *st) {
 
 }  // namespace
 
-extern "C" gvs_status gvs_forward_splat_noalloc(const gvs_camera *in_cams, const float *in_depths,
+extern "C" gvs_status gvs_forward_splat_noalloc(const gvs_camera *in_cams, const void *in_depths,
                                                 const uint32_t *in_rgba, int32_t n_views, const gvs_camera *target,
                                                 const gvs_splat_params *params, const float *fused_depth,
                                                 int32_t *winner, uint32_t *warped_rgba, float *warped_depth,

@@ -18,6 +18,7 @@
 //               such runs are skipped.  A skipped sample provably has S > 0 or
 //               W = 0, so the first crossing, its index and its interpolated
 //               depth are exactly those of the full uniform march.
+#include <cuda_fp16.h>
 #include <math.h>
 
 #include "gvs_internal.cuh"
@@ -32,12 +33,27 @@ constexpr int WM_P = 4;
 
 __device__ __forceinline__ bool valid_depth(float d) { return isfinite(d) && d > 0.0f; }
 
-// R = window / 2.  The shared tile holds the block's depths plus an R-pixel
-// halo replicated at the image borders (invalid depths as NaN).  A thread
-// reads each of the (WM_P + 2R) x (2R + 1) shared values its column needs once
-// and reuses it for every output whose window contains it.
-template <int R>
-__global__ void __launch_bounds__(256) weight_map_kernel(const float *__restrict__ depth, char *__restrict__ map,
+// Depth element load (FP32 or FP16) widened to FP32.
+__device__ __forceinline__ float load_depth(const float *p) { return __ldg(p); }
+__device__ __forceinline__ float load_depth(const __half *p) { return __half2float(__ldg(p)); }
+
+// The depth as the map stores it: exact for float2, rounded to half for half2.
+__device__ __forceinline__ float as_stored(float d, float2 *) { return d; }
+__device__ __forceinline__ float as_stored(float d, __half2 *) { return __half2float(__float2half_rn(d)); }
+
+__device__ __forceinline__ void store_map(float2 *p, float d, float w) { *p = make_float2(d, w); }
+__device__ __forceinline__ void store_map(__half2 *p, float d, float w) { *p = __floats2half2_rn(d, w); }
+
+__device__ __forceinline__ float2 load_map(const float2 *p) { return __ldg(p); }
+__device__ __forceinline__ float2 load_map(const __half2 *p) { return __half22float2(__ldg(p)); }
+
+// R = window / 2.  The shared tile holds the block's depths, as the map will
+// store them, plus an R-pixel halo replicated at the image borders (invalid
+// depths as NaN).  A thread reads each of the (WM_P + 2R) x (2R + 1) shared
+// values its column needs once and reuses it for every output whose window
+// contains it.  DT: float or __half input; MT: float2 or __half2 map.
+template <int R, typename DT, typename MT>
+__global__ void __launch_bounds__(256) weight_map_kernel(const DT *__restrict__ depth, char *__restrict__ map,
                                                          MapLayout L, float mu, float wconst, float inv_w2) {
     constexpr int SW = WM_TX + 2 * R;
     constexpr int SH = WM_TY + 2 * R;
@@ -45,7 +61,7 @@ __global__ void __launch_bounds__(256) weight_map_kernel(const float *__restrict
     __shared__ float2 red[WM_TY / WM_P][WM_TX / 8];
     const int W = L.W, H = L.H;
     const int k = blockIdx.z;
-    const float *dep = depth + (size_t)k * W * H;
+    const DT *dep = depth + (size_t)k * W * H;
     const int x0 = blockIdx.x * WM_TX - R;
     const int y0 = blockIdx.y * WM_TY - R;
     const int tid = threadIdx.y * WM_TX + threadIdx.x;
@@ -57,7 +73,7 @@ __global__ void __launch_bounds__(256) weight_map_kernel(const float *__restrict
         const int sy = e / SW, sx = e - sy * SW;
         const int gx = min(max(x0 + sx, 0), W - 1);
         const int gy = min(max(y0 + sy, 0), H - 1);
-        const float d = __ldg(&dep[(size_t)gy * W + gx]);
+        const float d = as_stored(load_depth(&dep[(size_t)gy * W + gx]), (MT *)nullptr);
         tile[sy][sx] = valid_depth(d) ? d : __int_as_float(0x7fc00000);  // NaN marks invalid
     }
     __syncthreads();
@@ -88,19 +104,19 @@ __global__ void __launch_bounds__(256) weight_map_kernel(const float *__restrict
         }
     }
     float lo = kInf, hi = -kInf;
-    float2 *dw = reinterpret_cast<float2 *>(map + L.off_dw) + (size_t)k * W * H;
+    MT *dw = reinterpret_cast<MT *>(map + L.off_dw) + (size_t)k * W * H;
 #pragma unroll
     for (int p = 0; p < WM_P; ++p) {
         const int y = yb + p;
         if (x < W && y < H) {
-            float2 out = make_float2(0.0f, 0.0f);
+            float d = 0.0f, w = 0.0f;
             if (dc[p] == dc[p]) {  // valid centre
-                const float w = nu[p] > 0.0f ? fminf(wconst * rsqrtf(nu[p] * inv_w2), 1.0f) : 1.0f;
-                out = make_float2(dc[p], w);
-                lo = fminf(lo, dc[p]);
-                hi = fmaxf(hi, dc[p]);
+                w = nu[p] > 0.0f ? fminf(wconst * rsqrtf(nu[p] * inv_w2), 1.0f) : 1.0f;
+                d = dc[p];
+                lo = fminf(lo, d);
+                hi = fmaxf(hi, d);
             }
-            dw[(size_t)y * W + x] = out;
+            store_map(&dw[(size_t)y * W + x], d, w);
         }
     }
     // 8x8 tile bounds: over the 8 lanes of a tile column group, then the two thread rows of a tile
@@ -295,9 +311,10 @@ __device__ __forceinline__ bool slab_view_free(const FuseArgs &a, int k, const R
 }
 
 // S and W of one sample (Supplement A.1), exactly as the full march computes them.
-template <int KMAX>
+template <int KMAX, typename MT>
 __device__ __forceinline__ void evaluate_sample(const FuseArgs &a, const Ray (&ray)[KMAX], float zs, float &S,
                                                 float &Wsum) {
+    const MT *map = reinterpret_cast<const MT *>(a.dw);
     const size_t plane = (size_t)a.W * a.H;
     S = 0.0f;
     Wsum = 0.0f;
@@ -311,7 +328,7 @@ __device__ __forceinline__ void evaluate_sample(const FuseArgs &a, const Ray (&r
                 int u, v;
                 nearest_pixel(hx, hy, hz, u, v);
                 if ((unsigned)u < (unsigned)a.W && (unsigned)v < (unsigned)a.H) {
-                    const float2 p = __ldg(&a.dw[(size_t)k * plane + (size_t)v * a.W + u]);
+                    const float2 p = load_map(&map[(size_t)k * plane + (size_t)v * a.W + u]);
                     const float sdf = (p.x - hz) * a.inv_mu;
                     if (sdf >= -1.0f) {
                         S = fmaf(p.y, fminf(sdf, 1.0f), S);
@@ -330,7 +347,7 @@ __device__ __forceinline__ void evaluate_sample(const FuseArgs &a, const Ray (&r
 // crossing end for any ray of the bundle; otherwise every ray still marching
 // evaluates sample s (all KMAX views unrolled, one 8-byte gather each) and
 // checks its own crossing.  The result equals the full uniform march.
-template <int KMAX>
+template <int KMAX, typename MT>
 __global__ void __launch_bounds__(32 * FZ_WARPS, GVS_FUSE_MIN_BLOCKS) fuse_kernel(const FuseArgs a) {
     constexpr int NSEG = 32 / KMAX;
     constexpr unsigned SEGMASK = KMAX == 32 ? 0xffffffffu : ((1u << KMAX) - 1u);
@@ -410,7 +427,7 @@ __global__ void __launch_bounds__(32 * FZ_WARPS, GVS_FUSE_MIN_BLOCKS) fuse_kerne
         const float zs = __fmaf_rn((float)s, a.dz, a.zn);
         if (!done) {
             float S, Wsum;
-            evaluate_sample<KMAX>(a, ray, zs, S, Wsum);
+            evaluate_sample<KMAX, MT>(a, ray, zs, S, Wsum);
             if (have_prev && W_prev > 0.0f && Wsum > 0.0f && S_prev > 0.0f && S <= 0.0f) {
                 out = z_prev + (zs - z_prev) * (S_prev / (S_prev - S));
                 idx = s - 1;
@@ -431,33 +448,46 @@ __global__ void __launch_bounds__(32 * FZ_WARPS, GVS_FUSE_MIN_BLOCKS) fuse_kerne
     }
 }
 
-template <int R>
-cudaError_t launch_wm(const float *depth, char *map, const MapLayout &L, float mu, float wconst, float inv_w2,
+template <int R, typename DT, typename MT>
+cudaError_t launch_wm(const void *depth, char *map, const MapLayout &L, float mu, float wconst, float inv_w2,
                       cudaStream_t st) {
     dim3 grid((L.W + WM_TX - 1) / WM_TX, (L.H + WM_TY - 1) / WM_TY, L.K);
-    weight_map_kernel<R><<<grid, dim3(WM_TX, WM_TY / WM_P), 0, st>>>(depth, map, L, mu, wconst, inv_w2);
+    weight_map_kernel<R, DT, MT><<<grid, dim3(WM_TX, WM_TY / WM_P), 0, st>>>(reinterpret_cast<const DT *>(depth), map,
+                                                                          L, mu, wconst, inv_w2);
     return cudaGetLastError();
+}
+
+template <typename DT, typename MT>
+cudaError_t launch_wm_window(const void *depth, char *map, const MapLayout &L, float mu, float wconst, int window,
+                             cudaStream_t st) {
+    const float inv_w2 = (float)(1.0 / ((double)window * (double)window));
+    switch (window / 2) {
+        case 0: return launch_wm<0, DT, MT>(depth, map, L, mu, wconst, inv_w2, st);
+        case 1: return launch_wm<1, DT, MT>(depth, map, L, mu, wconst, inv_w2, st);
+        case 2: return launch_wm<2, DT, MT>(depth, map, L, mu, wconst, inv_w2, st);
+        case 3: return launch_wm<3, DT, MT>(depth, map, L, mu, wconst, inv_w2, st);
+        case 4: return launch_wm<4, DT, MT>(depth, map, L, mu, wconst, inv_w2, st);
+        case 5: return launch_wm<5, DT, MT>(depth, map, L, mu, wconst, inv_w2, st);
+        case 6: return launch_wm<6, DT, MT>(depth, map, L, mu, wconst, inv_w2, st);
+        case 7: return launch_wm<7, DT, MT>(depth, map, L, mu, wconst, inv_w2, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace
 
-cudaError_t launch_weight_map(const float *depth, void *map, int K, int W, int H, float mu, float wconst,
-                              int window, cudaStream_t st) {
+cudaError_t launch_weight_map(const void *depth, int depth_dtype, void *map, int map_dtype, int K, int W, int H,
+                              float mu, float wconst, int window, cudaStream_t st) {
     if (K == 0) return cudaSuccess;
     const MapLayout L = map_layout(K, W, H);
     char *m = reinterpret_cast<char *>(map);
-    const float inv_w2 = (float)(1.0 / ((double)window * (double)window));
     cudaError_t e;
-    switch (window / 2) {
-        case 0: e = launch_wm<0>(depth, m, L, mu, wconst, inv_w2, st); break;
-        case 1: e = launch_wm<1>(depth, m, L, mu, wconst, inv_w2, st); break;
-        case 2: e = launch_wm<2>(depth, m, L, mu, wconst, inv_w2, st); break;
-        case 3: e = launch_wm<3>(depth, m, L, mu, wconst, inv_w2, st); break;
-        case 4: e = launch_wm<4>(depth, m, L, mu, wconst, inv_w2, st); break;
-        case 5: e = launch_wm<5>(depth, m, L, mu, wconst, inv_w2, st); break;
-        case 6: e = launch_wm<6>(depth, m, L, mu, wconst, inv_w2, st); break;
-        case 7: e = launch_wm<7>(depth, m, L, mu, wconst, inv_w2, st); break;
-        default: return cudaErrorInvalidValue;
+    if (depth_dtype == GVS_F16) {
+        e = map_dtype == GVS_F16 ? launch_wm_window<__half, __half2>(depth, m, L, mu, wconst, window, st)
+                                 : launch_wm_window<__half, float2>(depth, m, L, mu, wconst, window, st);
+    } else {
+        e = map_dtype == GVS_F16 ? launch_wm_window<float, __half2>(depth, m, L, mu, wconst, window, st)
+                                 : launch_wm_window<float, float2>(depth, m, L, mu, wconst, window, st);
     }
     if (e != cudaSuccess) return e;
     depth_bounds_kernel<<<dim3(L.tw[2], L.th[2], K), dim3(16, 16), 0, st>>>(m, L);
@@ -470,10 +500,17 @@ cudaError_t launch_fuse(const FuseArgs &a, cudaStream_t st) {
     const int64_t nb = (int64_t)((a.Wt + BX - 1) / BX) * ((a.Ht + BY - 1) / BY);
     const unsigned grid = (unsigned)((nb + FZ_WARPS - 1) / FZ_WARPS);
     const dim3 block(32 * FZ_WARPS);
-    if (a.K <= 4) fuse_kernel<4><<<grid, block, 0, st>>>(a);
-    else if (a.K <= 8) fuse_kernel<8><<<grid, block, 0, st>>>(a);
-    else if (a.K <= 16) fuse_kernel<16><<<grid, block, 0, st>>>(a);
-    else fuse_kernel<32><<<grid, block, 0, st>>>(a);
+    if (a.map_dtype == GVS_F16) {
+        if (a.K <= 4) fuse_kernel<4, __half2><<<grid, block, 0, st>>>(a);
+        else if (a.K <= 8) fuse_kernel<8, __half2><<<grid, block, 0, st>>>(a);
+        else if (a.K <= 16) fuse_kernel<16, __half2><<<grid, block, 0, st>>>(a);
+        else fuse_kernel<32, __half2><<<grid, block, 0, st>>>(a);
+    } else {
+        if (a.K <= 4) fuse_kernel<4, float2><<<grid, block, 0, st>>>(a);
+        else if (a.K <= 8) fuse_kernel<8, float2><<<grid, block, 0, st>>>(a);
+        else if (a.K <= 16) fuse_kernel<16, float2><<<grid, block, 0, st>>>(a);
+        else fuse_kernel<32, float2><<<grid, block, 0, st>>>(a);
+    }
     return cudaGetLastError();
 }
 

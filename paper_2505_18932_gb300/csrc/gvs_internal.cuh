@@ -18,8 +18,9 @@ struct ViewXform {
 };
 
 // ---- temporal refinement -------------------------------------------------
-cudaError_t launch_refine(const uint32_t *rgba_t, const uint32_t *rgba_prev, const float *depth_t,
-                          float *state, uint8_t *mask, int64_t n, int threshold, cudaStream_t st);
+// depth_dtype: GVS_F32 or GVS_F16 (depth_t and state share it)
+cudaError_t launch_refine(const uint32_t *rgba_t, const uint32_t *rgba_prev, const void *depth_t, void *state,
+                          uint8_t *mask, int64_t n, int threshold, int depth_dtype, cudaStream_t st);
 
 // ---- TSDF fusion -----------------------------------------------------------
 // Byte layout of the fusion workspace ("map"): the packed (depth, weight)
@@ -55,7 +56,8 @@ inline MapLayout map_layout(int K, int W, int H) {
 }
 
 struct FuseArgs {
-    const float2 *dw;          // [K][H][W] packed (depth or 0, weight)
+    const void *dw;            // [K][H][W] packed (depth or 0, weight): float2 or half2 (map_dtype)
+    int map_dtype;
     const float2 *ob[3];       // O_l overlapping 2x2-tile bounds, levels 3, 5, 7: [K][th][tw]
     const float2 *tg;          // whole-view bounds [K]
     int tw[3], th[3];
@@ -70,8 +72,8 @@ struct FuseArgs {
     ViewXform xf[GVS_MAX_VIEWS];
 };
 
-cudaError_t launch_weight_map(const float *depth, void *map, int K, int W, int H, float mu, float wconst,
-                              int window, cudaStream_t st);
+cudaError_t launch_weight_map(const void *depth, int depth_dtype, void *map, int map_dtype, int K, int W, int H,
+                              float mu, float wconst, int window, cudaStream_t st);
 cudaError_t launch_fuse(const FuseArgs &a, cudaStream_t st);
 
 // ---- forward splat ---------------------------------------------------------
@@ -81,7 +83,8 @@ struct SplatView {
 };
 
 struct SplatArgs {
-    const float *depth;        // [K][H][W]
+    const void *depth;         // [K][H][W] of depth_dtype
+    int depth_dtype;
     const uint32_t *rgba;      // [K][H][W]
     int W, H, Wt, Ht;
     int footprint;

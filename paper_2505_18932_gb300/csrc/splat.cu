@@ -13,6 +13,7 @@
 //   resolve : one thread per target pixel and view: decode the key, gather
 //             the winner's colour, write the outputs and reset the key to ~0
 //             for the next group.
+#include <cuda_fp16.h>
 #include <math.h>
 
 #include "gvs_internal.cuh"
@@ -32,6 +33,11 @@ __global__ void __launch_bounds__(256) clear_keys(unsigned long long *__restrict
     if (first == 0 && (n & 1)) keys[n - 1] = ~0ull;
 }
 
+__device__ __forceinline__ float load_depth(const float *p) { return __ldg(p); }
+__device__ __forceinline__ float load_depth(const __half *p) { return __half2float(__ldg(p)); }
+
+// DT: float or __half depth storage, widened to FP32 before the contract.
+template <typename DT>
 __global__ void __launch_bounds__(256) splat_scatter(const SplatArgs a, int k0, int kn) {
     const int64_t HW = (int64_t)a.W * a.H;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -41,7 +47,7 @@ __global__ void __launch_bounds__(256) splat_scatter(const SplatArgs a, int k0, 
     const int src = (int)(p - (int64_t)kk * HW);
     const int v = src / a.W;
     const int u = src - v * a.W;
-    const float d = __ldg(&a.depth[(size_t)k * HW + src]);
+    const float d = load_depth(reinterpret_cast<const DT *>(a.depth) + (size_t)k * HW + src);
     if (!valid_depth(d)) return;
     const float *A = a.v[k].xf.M;
     const float *c = a.v[k].xf.b;
@@ -173,7 +179,10 @@ cudaError_t launch_splat(const SplatArgs &a, int K, cudaStream_t st) {
     for (int k0 = 0; k0 < K; k0 += slots) {
         const int kn = (K - k0) < slots ? (K - k0) : slots;
         const int64_t ns = (int64_t)kn * HW;
-        splat_scatter<<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(a, k0, kn);
+        if (a.depth_dtype == GVS_F16)
+            splat_scatter<__half><<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(a, k0, kn);
+        else
+            splat_scatter<float><<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(a, k0, kn);
         if (HWt % 4 == 0) {
             const int64_t nt = (int64_t)kn * (HWt / 4);
             splat_resolve4<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(a, k0, kn);

@@ -34,18 +34,22 @@ class GvsCamera(ctypes.Structure):
                 ("R", ctypes.c_double * 9), ("t", ctypes.c_double * 3)]
 
 
+GVS_F32, GVS_F16, GVS_BF16 = 0, 1, 2
+
+
 class GvsRefineParams(ctypes.Structure):
-    _fields_ = [("tau", ctypes.c_float)]
+    _fields_ = [("tau", ctypes.c_float), ("depth_dtype", ctypes.c_int32)]
 
 
 class GvsFuseParams(ctypes.Structure):
     _fields_ = [("num_samples", ctypes.c_int32), ("z_near", ctypes.c_float), ("z_far", ctypes.c_float),
                 ("mu", ctypes.c_float), ("weight_const", ctypes.c_float), ("window", ctypes.c_int32),
-                ("normalize", ctypes.c_int32)]
+                ("normalize", ctypes.c_int32), ("depth_dtype", ctypes.c_int32), ("map_dtype", ctypes.c_int32)]
 
 
 class GvsSplatParams(ctypes.Structure):
-    _fields_ = [("footprint", ctypes.c_int32), ("max_half_width", ctypes.c_float), ("mu_guide", ctypes.c_float)]
+    _fields_ = [("footprint", ctypes.c_int32), ("max_half_width", ctypes.c_float), ("mu_guide", ctypes.c_float),
+                ("depth_dtype", ctypes.c_int32)]
 
 
 API = {
@@ -61,8 +65,8 @@ API = {
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                       ctypes.c_void_p]),
     "gvs_weight_map": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
-                                      ctypes.c_float, ctypes.c_float, ctypes.c_int32, ctypes.c_void_p,
-                                      ctypes.c_size_t, ctypes.c_void_p]),
+                                      ctypes.c_int32, ctypes.c_float, ctypes.c_float, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "gvs_fuse_depth_from_map": (ctypes.c_int, [ctypes.POINTER(GvsCamera), ctypes.c_void_p, ctypes.c_size_t,
                                                ctypes.c_int32,
                                                ctypes.POINTER(GvsCamera), ctypes.POINTER(GvsFuseParams),
@@ -140,6 +144,15 @@ def _stream(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+def depth_dtype_of(t) -> int:
+    """gvs_dtype of a depth tensor (float32 or float16)."""
+    if t.dtype == torch.float32:
+        return GVS_F32
+    if t.dtype == torch.float16:
+        return GVS_F16
+    raise ValueError(f"gvs: depth must be float32 or float16, got {t.dtype}")
+
+
 def _want(t, dtype, shape, name):
     if t.dtype != dtype or tuple(t.shape) != tuple(shape):
         raise ValueError(f"gvs: {name} must be {dtype} of shape {tuple(shape)}, got {t.dtype} {tuple(t.shape)}")
@@ -150,7 +163,9 @@ def refine_depth(rgba_t, rgba_prev, depth_t, depth_state, mask=None, tau: float 
     depth_t, depth_state float32 [N, H, W] (depth_state updated in place); mask uint8 [N, H, W] or None."""
     lib = load()
     N, H, W = depth_t.shape
-    p = GvsRefineParams(float(tau))
+    if depth_state.dtype != depth_t.dtype:
+        raise ValueError("gvs: depth_t and depth_state must share a dtype")
+    p = GvsRefineParams(float(tau), depth_dtype_of(depth_t))
     st = lib.gvs_refine_depth(_ptr(rgba_t), _ptr(rgba_prev), _ptr(depth_t), _ptr(depth_state), _ptr(mask),
                               N, W, H, ctypes.byref(p), _stream(stream))
     _check("gvs_refine_depth", st)
@@ -171,7 +186,7 @@ def workspace(nbytes: int, device=None) -> torch.Tensor:
 
 
 def fuse_depth(in_cams, in_depths, target, num_samples, z_near, z_far, mu, weight_const=0.001, window=7,
-               normalize=False, fused=None, crossing=None, ws=None, want_crossing=True, stream=None):
+               normalize=False, fused=None, crossing=None, ws=None, want_crossing=True, map_half=False, stream=None):
     """Supplement A.1 / Eq. 3.  in_depths float32 [N, H, W] on the GPU.
     Returns (fused float32 [Ht, Wt], crossing int16 [Ht, Wt] or None)."""
     lib = load()
@@ -186,28 +201,30 @@ def fuse_depth(in_cams, in_depths, target, num_samples, z_near, z_far, mu, weigh
     if ws is None:
         ws = workspace(need, dev)
     p = GvsFuseParams(int(num_samples), float(z_near), float(z_far), float(mu), float(weight_const), int(window),
-                      int(bool(normalize)))
+                      int(bool(normalize)), depth_dtype_of(in_depths) if N else GVS_F32,
+                      GVS_F16 if map_half else GVS_F32)
     st = lib.gvs_fuse_depth(camera_array(in_cams), _ptr(in_depths), N, ctypes.byref(camera_struct(target)),
                             ctypes.byref(p), _ptr(fused), _ptr(crossing), _ptr(ws), ws.numel(), _stream(stream))
     _check("gvs_fuse_depth", st)
     return fused, crossing
 
 
-def weight_map(in_depths, mu, weight_const=0.001, window=7, ws=None, stream=None):
+def weight_map(in_depths, mu, weight_const=0.001, window=7, ws=None, map_half=False, stream=None):
     """Stage 1 of fusion: the map (packed (depth, weight) float2 [N, H, W] first, then depth-bound tiles),
     written into the uint8 buffer `ws`."""
     lib = load()
     N, H, W = in_depths.shape
     if ws is None:
         ws = workspace(fuse_workspace_bytes(N, W, H), in_depths.device)
-    st = lib.gvs_weight_map(_ptr(in_depths), N, W, H, float(mu), float(weight_const), int(window), _ptr(ws),
-                            ws.numel() * ws.element_size(), _stream(stream))
+    st = lib.gvs_weight_map(_ptr(in_depths), depth_dtype_of(in_depths), N, W, H, float(mu), float(weight_const),
+                            int(window), GVS_F16 if map_half else GVS_F32, _ptr(ws), ws.numel() * ws.element_size(),
+                            _stream(stream))
     _check("gvs_weight_map", st)
     return ws
 
 
 def fuse_depth_from_map(in_cams, dw_map, shape, target, num_samples, z_near, z_far, mu, normalize=False,
-                        fused=None, crossing=None, want_crossing=True, stream=None):
+                        fused=None, crossing=None, want_crossing=True, map_half=False, stream=None):
     """Stage 2 of fusion reading a map from weight_map(); `shape` = (N, H, W) of the inputs."""
     lib = load()
     N = len(in_cams)
@@ -216,7 +233,8 @@ def fuse_depth_from_map(in_cams, dw_map, shape, target, num_samples, z_near, z_f
         fused = torch.empty((target.height, target.width), dtype=torch.float32, device=dev)
     if crossing is None and want_crossing:
         crossing = torch.empty((target.height, target.width), dtype=torch.int16, device=dev)
-    p = GvsFuseParams(int(num_samples), float(z_near), float(z_far), float(mu), 0.001, 7, int(bool(normalize)))
+    p = GvsFuseParams(int(num_samples), float(z_near), float(z_far), float(mu), 0.001, 7, int(bool(normalize)),
+                      GVS_F32, GVS_F16 if map_half else GVS_F32)
     st = lib.gvs_fuse_depth_from_map(camera_array(in_cams), _ptr(dw_map), dw_map.numel() * dw_map.element_size(), N,
                                      ctypes.byref(camera_struct(target)),
                                      ctypes.byref(p), _ptr(fused), _ptr(crossing), _stream(stream))
@@ -243,7 +261,8 @@ def forward_splat(in_cams, in_depths, in_rgba, target, fused=None, footprint=Tru
             out[n] = torch.empty(shape, dtype=dtypes[n], device=dev)
     if ws is None:
         ws = workspace(splat_workspace_bytes(N, target.width, target.height), dev)
-    p = GvsSplatParams(int(bool(footprint)), float(max_half_width), float(mu_guide))
+    p = GvsSplatParams(int(bool(footprint)), float(max_half_width), float(mu_guide),
+                       depth_dtype_of(in_depths) if N else GVS_F32)
     st = lib.gvs_forward_splat(camera_array(in_cams), _ptr(in_depths), _ptr(in_rgba), N,
                                ctypes.byref(camera_struct(target)), ctypes.byref(p), _ptr(fused),
                                _ptr(out["winner"]), _ptr(out.get("warped_rgba")), _ptr(out.get("warped_depth")),

@@ -58,7 +58,8 @@ def test_fuse_rejects_bad_arguments(lib):
     from paper_2505_18932_gb300 import gvs
     cams = (gvs.GvsCamera * 2)(_cam(gvs), _cam(gvs))
     tgt = _cam(gvs)
-    good = dict(num_samples=64, z_near=0.5, z_far=5.0, mu=0.05, weight_const=0.001, window=7, normalize=0)
+    good = dict(num_samples=64, z_near=0.5, z_far=5.0, mu=0.05, weight_const=0.001, window=7, normalize=0,
+                depth_dtype=0, map_dtype=0)
     ws = lib.gvs_fuse_workspace_bytes(2, 64, 48)
     assert ws >= 2 * 64 * 48 * 8 and ws % 256 == 0
 
@@ -74,6 +75,8 @@ def test_fuse_rejects_bad_arguments(lib):
         assert lib.gvs_last_error()
     assert call(n=33) == 1
     assert call(n=-1) == 1
+    assert call(params={**good, "depth_dtype": 2}) == 2     # bf16 depth is not a storage this path offers
+    assert call(params={**good, "map_dtype": 7}) == 2
     assert call(fused=None) == 1
     assert call(fused=FAKE + 4) == 1           # misaligned
     assert call(depths=None) == 1
@@ -102,6 +105,9 @@ def test_splat_rejects_bad_arguments(lib):
                                      None, None, None, guided, FAKE, wsb, None)
 
     assert call(fp=2) == 1
+    p_bad = gvs.GvsSplatParams(1, 2.0, 0.04, 2)
+    assert lib.gvs_forward_splat(cams, FAKE, FAKE, 1, ctypes.byref(tgt), ctypes.byref(p_bad), FAKE, FAKE,
+                                 None, None, None, FAKE, FAKE, ws, None) == 2
     assert call(mhw=0.25) == 1
     assert call(mug=-1.0) == 1
     assert call(fused=None) == 1       # guided mask without the fused depth
@@ -117,6 +123,8 @@ def test_refine_rejects_bad_arguments(lib):
         p = gvs.GvsRefineParams(tau)
         return lib.gvs_refine_depth(rgba, FAKE, depth, state, None, n, W, H, ctypes.byref(p), None)
 
+    assert lib.gvs_refine_depth(FAKE, FAKE, FAKE, FAKE, None, 1, 4, 4, ctypes.byref(gvs.GvsRefineParams(0.03, 2)),
+                                None) == 2
     assert call(tau=-0.1) == 1
     assert call(tau=1.5) == 1
     assert call(tau=float("nan")) == 1
