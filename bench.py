@@ -126,17 +126,18 @@ def render_frames(w, frames):
 class Pipeline:
     """Device buffers and the per-frame call sequence through the C ABI."""
 
-    def __init__(self, w, frames_np, device):
+    def __init__(self, w, frames_np, device, half=False):
         import torch
         from paper_2505_18932_gb300 import gvs
-        self.torch, self.gvs, self.w = torch, gvs, w
+        self.torch, self.gvs, self.w, self.half = torch, gvs, w, half
         self.tgt = w.targets[0]
         N = len(w.inputs)
         H, W = w.inputs[0].height, w.inputs[0].width
         Ht, Wt = self.tgt.height, self.tgt.width
         self.N, self.H, self.W, self.Ht, self.Wt = N, H, W, Ht, Wt
         self.rgba = [torch.from_numpy(c.view(np.int32)).to(device) for c, _ in frames_np]
-        self.depth = [torch.from_numpy(d).to(device) for _, d in frames_np]
+        dt = torch.float16 if half else torch.float32
+        self.depth = [torch.from_numpy(d).to(device).to(dt) for _, d in frames_np]
         self.state = self.depth[0].clone()
         self.mask = torch.empty((N, H, W), dtype=torch.uint8, device=device)
         self.fused = torch.empty((Ht, Wt), dtype=torch.float32, device=device)
@@ -160,7 +161,7 @@ class Pipeline:
         if events:
             events[1].record()
         gvs.fuse_depth(w.inputs, self.state, self.tgt, w.num_samples, w.z_near, w.z_far, w.mu,
-                       fused=self.fused, crossing=self.cross, ws=self.ws_fuse)
+                       fused=self.fused, crossing=self.cross, ws=self.ws_fuse, map_half=self.half)
         if events:
             events[2].record()
         gvs.forward_splat(w.inputs, self.state, self.rgba[cur], self.tgt, fused=self.fused, mu_guide=w.mu,
@@ -255,6 +256,7 @@ def run_gvs(args, rank, local_rank, world):
     holes = statistics.mean(float((c < 0).mean()) for c in crosses)
 
     e2e = run_e2e(pipe, frames_np, args.e2e_steps) if args.e2e_steps > 0 else None
+    forms = {"f16_storage": time_form(Pipeline(w, frames_np, device, half=True), steps=min(K, 100))}
 
     if rank != 0:
         return
@@ -286,6 +288,8 @@ def run_gvs(args, rank, local_rank, world):
                      "kernel_ms": round(fuse_kernel_ms, 4), "hole_fraction": round(holes, 4),
                      "peak_source": "152 SMs x 128 FP32 lanes x max SM clock"},
         "e2e": e2e,
+        "forms": {name: {**f, "value": round(pipe.Ht * pipe.Wt / (f["ms_per_step"] * 1e-3) / 1e6, 3)}
+                  for name, f in forms.items()},
         "gpu_launches": pipe.launches_per_step() * K,
         "clocks": clk,
         "wall_s": round(wall, 3),
@@ -293,6 +297,22 @@ def run_gvs(args, rank, local_rank, world):
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(w, frames_np, budget_s=15.0)
     print(json.dumps(line), flush=True)
+
+
+def time_form(pipe, steps):
+    """ms per step of another form of the same workload (events around `steps` steps)."""
+    import torch
+    for i in range(3):
+        pipe.step(i)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for i in range(steps):
+        pipe.step(i + 1)
+    b.record()
+    torch.cuda.synchronize()
+    return {"ms_per_step": round(a.elapsed_time(b) / steps, 4), "steps": steps,
+            "storage": "depth f16, (d, w) map half2, FP32 arithmetic" if pipe.half else "f32"}
 
 
 def device_sms():
