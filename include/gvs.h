@@ -210,6 +210,35 @@ GVS_API gvs_status gvs_fuse_depth_from_map(const gvs_camera *in_cams, const void
                                            const gvs_fuse_params *params, float *fused_depth, int16_t *crossing,
                                            void *stream);
 
+/* Workspace bytes for gvs_fuse_depth_backward: one float2 accumulator per input pixel. */
+GVS_API size_t gvs_fuse_backward_workspace_bytes(int32_t n_views, int32_t width, int32_t height);
+
+/*
+ * gvs_fuse_depth_backward -- adjoint of gvs_fuse_depth (normalize = 0):
+ * grad_depths = d(sum_p grad_fused(p) D(p)) / d in_depths, written (not
+ * accumulated).  D = z_s + dz S_s / (S_s - S_{s+1}) (Eq. 3 with linear
+ * interpolation) is differentiated through S_s and S_{s+1} only, each
+ * S = sum_k omega_k clamp(sdf_k, -1, 1) (Supplement A.1) through the clamped
+ * signed distance (slope 1/mu strictly inside the band) and through the
+ * confidence weight (d omega / d nu = -omega / (2 nu) unless saturated, nu
+ * through every (d_c - d_n)^2 strictly below mu^2).  The nearest-pixel
+ * choice, the cut-off, the crossing index and saturation are piecewise
+ * constant and carry no gradient.  The two bracketing samples are recomputed;
+ * nothing of size D x H x W is stored.
+ *   in_depths, params : as passed to the forward (params->normalize must be 0)
+ *   map       : the forward's map (gvs_weight_map / gvs_fuse_depth workspace)
+ *   crossing  : the forward's int16 crossing index [Ht][Wt]
+ *   grad_fused: float [Ht][Wt];  grad_depths: float [n_views][height][width]
+ *   workspace : >= gvs_fuse_backward_workspace_bytes() bytes, 256-byte aligned
+ * Gradient sums use float atomics: the order, hence the last bits, can vary
+ * from run to run.
+ */
+GVS_API gvs_status gvs_fuse_depth_backward(const gvs_camera *in_cams, const void *in_depths, int32_t n_views,
+                                           const gvs_camera *target, const gvs_fuse_params *params,
+                                           const void *map, size_t map_bytes, const int16_t *crossing,
+                                           const float *grad_fused, float *grad_depths, void *workspace,
+                                           size_t workspace_bytes, void *stream);
+
 /* Workspace bytes for gvs_forward_splat: one 64-bit z-buffer of the target size.
  * A workspace holding several such buffers lets several views splat in one pass. */
 GVS_API size_t gvs_splat_workspace_bytes(int32_t n_views, int32_t target_width, int32_t target_height);

@@ -80,6 +80,7 @@ def _load():
                                            vp, vp, vp, vp, i32]
             lib.orc_forward_splat.argtypes = [cp, vp, vp, i32, cp, i32, flt, flt, vp, vp, vp, vp, vp, vp, vp, vp]
             lib.orc_splat_bruteforce.argtypes = [cp, vp, i32, cp, i32, flt, vp]
+            lib.orc_fuse_depth_grad.argtypes = [cp, vp, i32, cp, i32, dbl, dbl, dbl, dbl, i32, vp, vp]
             _lib = lib
     return _lib
 
@@ -150,6 +151,21 @@ def fuse_depth(in_cams, depths, target, num_samples, z_near, z_far, mu,
         raise ValueError("orc_fuse_depth rejected its arguments")
     return {"depth": out_d.reshape(shape), "index": out_i.reshape(shape), "ambiguous": out_a.reshape(shape),
             "fp64_mismatch": int(mism.value)}
+
+
+def fuse_depth_grad(in_cams, depths, target, num_samples, z_near, z_far, mu, grad_fused,
+                    weight_const=DEFAULT_WEIGHT_CONST, window=DEFAULT_WINDOW):
+    """Adjoint of fuse_depth (normalize off): d(sum grad_fused * D) / d depths, float64 [N, H, W]."""
+    lib = _load()
+    depths = np.ascontiguousarray(depths, np.float32)
+    g = np.ascontiguousarray(grad_fused, np.float64)
+    out = np.zeros(depths.shape, np.float64)
+    rc = lib.orc_fuse_depth_grad(_cams(in_cams), _ptr(depths), len(in_cams), ctypes.byref(_cam(target)),
+                                 int(num_samples), float(np.float32(z_near)), float(np.float32(z_far)),
+                                 float(np.float32(mu)), float(weight_const), int(window), _ptr(g), _ptr(out))
+    if rc != 0:
+        raise ValueError("orc_fuse_depth_grad rejected its arguments")
+    return out
 
 
 def forward_splat(in_cams, depths, rgba_u32, target, footprint=True, max_half_width=2.0, mu_guide=0.04,

@@ -477,3 +477,142 @@ int orc_splat_bruteforce(const orc_camera *in_cams, const float *depths, int n_v
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Adjoint of the fused depth with respect to the input depths              */
+/* (Supplement A.1 and Eq. 3 differentiated; normalize = 0).                */
+/*                                                                          */
+/* D = z_s + (z_{s+1} - z_s) S_s / (S_s - S_{s+1}) depends on the inputs    */
+/* only through S_s and S_{s+1}.  For each view contributing at either      */
+/* bracketing sample, with c = clamp(sdf, -1, 1) and omega the weight at the */
+/* sampled pixel, S = sum omega c gives                                      */
+/*   dS/dD(centre) = omega [ -1 < sdf < 1 ] / mu + c domega/dD(centre)       */
+/*   dS/dD(n)      = c domega/dD(n)   for every window entry n               */
+/* with domega/dnu = -0.5 weight_const w nu^(-3/2) when omega < 1 (0 when    */
+/* saturated), dnu/dD(centre) = sum 2 (D_c - D_n) [ (D_c - D_n)^2 < mu^2 ]   */
+/* and dnu/dD(n) = -2 (D_c - D_n) [ ... ] per entry (invalid neighbours add  */
+/* the constant mu^2).  Clamp, cut-off, crossing index and the nearest-pixel */
+/* choice are piecewise constant: no gradient (subgradient 0 at the kinks).  */
+/* The scatter below is written per window entry, literally.                */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int contributes;
+    int u, v;
+    double sdf, c, w;
+} orc_view_sample;
+
+static void sample_detail(const fuse_job *jb, int i, int j, int s, orc_view_sample *vs, double *S_out) {
+    const float zn = (float)jb->z_near;
+    const float dz = (float)((jb->z_far - jb->z_near) / (double)(jb->D - 1));
+    float zs = fmaf((float)s, dz, zn);
+    double S = 0.0;
+    for (int k = 0; k < jb->n_views; ++k) {
+        const orc_camera *vc = &jb->in_cams[k];
+        const float *M = jb->M[k];
+        const float *b = jb->b[k];
+        vs[k].contributes = 0;
+        float a0 = fmaf(M[0], (float)i, fmaf(M[1], (float)j, M[2]));
+        float a1 = fmaf(M[3], (float)i, fmaf(M[4], (float)j, M[5]));
+        float a2 = fmaf(M[6], (float)i, fmaf(M[7], (float)j, M[8]));
+        float h0 = fmaf(zs, a0, b[0]), h1 = fmaf(zs, a1, b[1]), h2 = fmaf(zs, a2, b[2]);
+        if (!(h2 > 1e-6f)) continue;
+        double u = nearest_of_quotient(h0, h2), v = nearest_of_quotient(h1, h2);
+        if (u < 0 || v < 0 || u > vc->width - 1 || v > vc->height - 1) continue;
+        const float *dep = jb->depths + (size_t)k * vc->width * vc->height;
+        float d = dep[(size_t)v * vc->width + (size_t)u];
+        if (!depth_valid(d)) continue;
+        double sdf = ((double)d - (double)h2) / jb->mu;
+        if (sdf < -1.0) continue;
+        vs[k].contributes = 1;
+        vs[k].u = (int)u;
+        vs[k].v = (int)v;
+        vs[k].sdf = sdf;
+        vs[k].c = sdf > 1.0 ? 1.0 : sdf;
+        vs[k].w = orc_weight(dep, vc->height, vc->width, (int)u, (int)v, jb->mu, jb->wconst, jb->window);
+        S += vs[k].w * vs[k].c;
+    }
+    *S_out = S;
+}
+
+/* d omega / d D for one view's sampled pixel, scattered into grad (scaled by g). */
+static void scatter_weight_grad(const float *dep, int H, int W, int u, int v, double mu, double wconst, int window,
+                                double g, double *grad) {
+    float dc = dep[(size_t)v * W + u];
+    if (!depth_valid(dc)) return;
+    int r = window / 2;
+    double nu = 0.0;
+    for (int dy = -r; dy <= r; ++dy)
+        for (int dx = -r; dx <= r; ++dx) {
+            int q = v + dy, p = u + dx;
+            q = q < 0 ? 0 : (q >= H ? H - 1 : q);
+            p = p < 0 ? 0 : (p >= W ? W - 1 : p);
+            float dn = dep[(size_t)q * W + p];
+            if (!depth_valid(dn)) { nu += mu * mu; continue; }
+            double diff = (double)dc - (double)dn;
+            nu += diff * diff < mu * mu ? diff * diff : mu * mu;
+        }
+    if (nu == 0.0) return;
+    double unclamped = wconst * pow(nu / (double)(window * window), -0.5);
+    if (unclamped >= 1.0) return; /* saturated weight: no gradient */
+    double dw_dnu = -0.5 * unclamped / nu;
+    for (int dy = -r; dy <= r; ++dy)
+        for (int dx = -r; dx <= r; ++dx) {
+            int q = v + dy, p = u + dx;
+            q = q < 0 ? 0 : (q >= H ? H - 1 : q);
+            p = p < 0 ? 0 : (p >= W ? W - 1 : p);
+            float dn = dep[(size_t)q * W + p];
+            if (!depth_valid(dn)) continue;
+            double diff = (double)dc - (double)dn;
+            if (!(diff * diff < mu * mu)) continue;
+            grad[(size_t)v * W + u] += g * dw_dnu * 2.0 * diff;
+            grad[(size_t)q * W + p] -= g * dw_dnu * 2.0 * diff;
+        }
+}
+
+int orc_fuse_depth_grad(const orc_camera *in_cams, const float *depths, int n_views, const orc_camera *target,
+                        int num_samples, double z_near, double z_far, double mu, double weight_const, int window,
+                        const double *grad_fused, double *grad_depths) {
+    if (!in_cams || !depths || n_views <= 0 || n_views > 256 || !target || num_samples < 2 || !(z_near < z_far) ||
+        !(mu > 0) || window < 1 || !grad_fused || !grad_depths)
+        return -1;
+    float (*M)[9] = malloc(sizeof(float[9]) * n_views);
+    float (*b)[3] = malloc(sizeof(float[3]) * n_views);
+    for (int k = 0; k < n_views; ++k) compose(&in_cams[k], target, M[k], b[k]);
+    fuse_job jb = {in_cams, depths, n_views, target, num_samples, z_near, z_far, mu, weight_const, window,
+                   0, NULL, 0, NULL, NULL, NULL, NULL, M, b, 0, 0};
+    const int W = in_cams[0].width, H = in_cams[0].height;
+    const size_t plane = (size_t)W * H;
+    for (size_t q = 0; q < plane * n_views; ++q) grad_depths[q] = 0.0;
+    orc_view_sample vs0[256], vs1[256];
+    const float zn = (float)z_near;
+    const float dz = (float)((z_far - z_near) / (double)(num_samples - 1));
+    for (int j = 0; j < target->height; ++j)
+        for (int i = 0; i < target->width; ++i) {
+            double G = grad_fused[(size_t)j * target->width + i];
+            if (G == 0.0) continue;
+            double d_out;
+            int32_t s;
+            uint8_t amb;
+            fuse_pixel(&jb, i, j, &d_out, &s, &amb, NULL);
+            if (s < 0) continue;
+            double S0, S1;
+            sample_detail(&jb, i, j, s, vs0, &S0);
+            sample_detail(&jb, i, j, s + 1, vs1, &S1);
+            double z0 = (double)fmaf((float)s, dz, zn), z1 = (double)fmaf((float)(s + 1), dz, zn);
+            double den = (S0 - S1) * (S0 - S1);
+            double gS[2] = {G * (z1 - z0) * (-S1) / den, G * (z1 - z0) * S0 / den};
+            for (int t = 0; t < 2; ++t) {
+                orc_view_sample *vs = t ? vs1 : vs0;
+                for (int k = 0; k < n_views; ++k) {
+                    if (!vs[k].contributes) continue;
+                    const float *dep = depths + (size_t)k * plane;
+                    double *gk = grad_depths + (size_t)k * plane;
+                    if (vs[k].sdf > -1.0 && vs[k].sdf < 1.0) gk[(size_t)vs[k].v * W + vs[k].u] += gS[t] * vs[k].w / mu;
+                    scatter_weight_grad(dep, H, W, vs[k].u, vs[k].v, mu, weight_const, window, gS[t] * vs[k].c, gk);
+                }
+            }
+        }
+    free(M);
+    free(b);
+    return 0;
+}

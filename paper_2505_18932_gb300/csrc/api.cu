@@ -283,6 +283,41 @@ gvs_status gvs_fuse_depth(const gvs_camera *in_cams, const void *in_depths, int3
     return GVS_OK;
 }
 
+size_t gvs_fuse_backward_workspace_bytes(int32_t n_views, int32_t width, int32_t height) {
+    if (n_views < 0 || width < 0 || height < 0) return 0;
+    return align_up((size_t)n_views * (size_t)width * (size_t)height * sizeof(float2), 256);
+}
+
+gvs_status gvs_fuse_depth_backward(const gvs_camera *in_cams, const void *in_depths, int32_t n_views,
+                                   const gvs_camera *target, const gvs_fuse_params *params, const void *map,
+                                   size_t map_bytes, const int16_t *crossing, const float *grad_fused,
+                                   float *grad_depths, void *workspace, size_t workspace_bytes, void *stream) {
+    int32_t W = 0, H = 0;
+    // the checks of the forward, with the fused-depth output replaced by its gradient
+    gvs_status s = check_fuse_common(in_cams, n_views, target, params, grad_fused, crossing, &W, &H);
+    if (s != GVS_OK) return s;
+    s = check_weight_params(params->mu, params->weight_const, params->window);
+    if (s != GVS_OK) return s;
+    if (params->normalize != 0)
+        return fail(GVS_ERR_UNSUPPORTED, "fuse backward: only the unnormalised sum (normalize = 0) is differentiated");
+    if (!crossing) return fail(GVS_ERR_INVALID_ARG, "fuse backward: crossing (from the forward) is NULL");
+    if (n_views == 0) return GVS_OK;
+    if (!in_depths || !aligned(in_depths, 16) || !grad_depths || !aligned(grad_depths, 16))
+        return fail(GVS_ERR_INVALID_ARG, "fuse backward: in_depths / grad_depths NULL or not 16-byte aligned");
+    const size_t need_map = gvs_fuse_workspace_bytes(n_views, W, H);
+    if (!map || map_bytes < need_map || !aligned(map, 256))
+        return fail(GVS_ERR_WORKSPACE, "fuse backward: map needs %zu bytes, 256-byte aligned", need_map);
+    const size_t need = gvs_fuse_backward_workspace_bytes(n_views, W, H);
+    if (!workspace || workspace_bytes < need || !aligned(workspace, 256))
+        return fail(GVS_ERR_WORKSPACE, "fuse backward: workspace needs %zu bytes, 256-byte aligned", need);
+    gvs::FuseArgs a = fuse_args(in_cams, map, n_views, W, H, target, *params, grad_depths, nullptr);
+    cudaError_t e = gvs::launch_fuse_backward(a, in_depths, params->depth_dtype, crossing, grad_fused, grad_depths,
+                                              reinterpret_cast<float2 *>(workspace), params->mu,
+                                              params->weight_const, params->window, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "fuse backward: launch");
+    return GVS_OK;
+}
+
 size_t gvs_splat_workspace_bytes(int32_t n_views, int32_t target_width, int32_t target_height) {
     (void)n_views;
     if (target_width < 0 || target_height < 0) return 0;

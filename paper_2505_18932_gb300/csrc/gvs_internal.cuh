@@ -75,6 +75,10 @@ struct FuseArgs {
 cudaError_t launch_weight_map(const void *depth, int depth_dtype, void *map, int map_dtype, int K, int W, int H,
                               float mu, float wconst, int window, cudaStream_t st);
 cudaError_t launch_fuse(const FuseArgs &a, cudaStream_t st);
+// acc: [K][H][W] float2 scratch; grad_depths written (not accumulated)
+cudaError_t launch_fuse_backward(const FuseArgs &a, const void *depth, int depth_dtype, const int16_t *crossing,
+                                 const float *grad_fused, float *grad_depths, float2 *acc, float mu, float wconst,
+                                 int window, cudaStream_t st);
 
 // ---- forward splat ---------------------------------------------------------
 struct SplatView {

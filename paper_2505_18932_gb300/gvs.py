@@ -71,6 +71,11 @@ API = {
                                                ctypes.c_int32,
                                                ctypes.POINTER(GvsCamera), ctypes.POINTER(GvsFuseParams),
                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "gvs_fuse_backward_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32] * 3),
+    "gvs_fuse_depth_backward": (ctypes.c_int, [ctypes.POINTER(GvsCamera), ctypes.c_void_p, ctypes.c_int32,
+                                               ctypes.POINTER(GvsCamera), ctypes.POINTER(GvsFuseParams),
+                                               ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "gvs_splat_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32] * 3),
     "gvs_forward_splat": (ctypes.c_int, [ctypes.POINTER(GvsCamera), ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_int32, ctypes.POINTER(GvsCamera), ctypes.POINTER(GvsSplatParams),
@@ -207,6 +212,56 @@ def fuse_depth(in_cams, in_depths, target, num_samples, z_near, z_far, mu, weigh
                             ctypes.byref(p), _ptr(fused), _ptr(crossing), _ptr(ws), ws.numel(), _stream(stream))
     _check("gvs_fuse_depth", st)
     return fused, crossing
+
+
+def fuse_depth_backward(in_cams, in_depths, target, num_samples, z_near, z_far, mu, ws, crossing, grad_fused,
+                        weight_const=0.001, window=7, map_half=False, grad_depths=None, bwd_ws=None, stream=None):
+    """Adjoint of fuse_depth: gradient w.r.t. in_depths (float32 [N, H, W]).  `ws` is the forward's map."""
+    lib = load()
+    N = len(in_cams)
+    H, W = (in_depths.shape[1], in_depths.shape[2]) if N else (0, 0)
+    if grad_depths is None:
+        grad_depths = torch.empty(in_depths.shape, dtype=torch.float32, device=in_depths.device)
+    if bwd_ws is None:
+        bwd_ws = workspace(int(lib.gvs_fuse_backward_workspace_bytes(N, W, H)), in_depths.device)
+    grad_fused = grad_fused.contiguous().to(torch.float32)
+    p = GvsFuseParams(int(num_samples), float(z_near), float(z_far), float(mu), float(weight_const), int(window), 0,
+                      depth_dtype_of(in_depths) if N else GVS_F32, GVS_F16 if map_half else GVS_F32)
+    st = lib.gvs_fuse_depth_backward(camera_array(in_cams), _ptr(in_depths), N, ctypes.byref(camera_struct(target)),
+                                     ctypes.byref(p), _ptr(ws), ws.numel() * ws.element_size(), _ptr(crossing),
+                                     _ptr(grad_fused), _ptr(grad_depths), _ptr(bwd_ws),
+                                     bwd_ws.numel() * bwd_ws.element_size(), _stream(stream))
+    _check("gvs_fuse_depth_backward", st)
+    return grad_depths
+
+
+class FuseDepth(torch.autograd.Function):
+    """Differentiable image-based TSDF fusion: fused = FuseDepth.apply(in_depths, cams, target, cfg).
+
+    cfg: dict(num_samples, z_near, z_far, mu[, weight_const, window]).  The backward
+    is gvs_fuse_depth_backward (through the clamped signed distances and the
+    confidence weights; the crossing index itself is piecewise constant)."""
+
+    @staticmethod
+    def forward(ctx, in_depths, in_cams, target, cfg):
+        wc, win = cfg.get("weight_const", 0.001), cfg.get("window", 7)
+        N, H, W = in_depths.shape
+        ws = workspace(fuse_workspace_bytes(N, W, H), in_depths.device)
+        fused, crossing = fuse_depth(in_cams, in_depths, target, cfg["num_samples"], cfg["z_near"], cfg["z_far"],
+                                     cfg["mu"], weight_const=wc, window=win, ws=ws)
+        ctx.save_for_backward(in_depths, ws, crossing)
+        ctx.cams, ctx.target, ctx.cfg = in_cams, target, cfg
+        ctx.mark_non_differentiable(crossing)
+        return fused, crossing
+
+    @staticmethod
+    def backward(ctx, grad_fused, grad_crossing):
+        in_depths, ws, crossing = ctx.saved_tensors
+        cfg = ctx.cfg
+        g = fuse_depth_backward(ctx.cams, in_depths, ctx.target, cfg["num_samples"], cfg["z_near"], cfg["z_far"],
+                                cfg["mu"], ws, crossing, grad_fused, weight_const=cfg.get("weight_const", 0.001),
+                                window=cfg.get("window", 7))
+        return g, None, None, None
 
 
 def weight_map(in_depths, mu, weight_const=0.001, window=7, ws=None, map_half=False, stream=None):
