@@ -118,6 +118,14 @@ typedef struct {
     int32_t depth_dtype;       /* GVS_F32 or GVS_F16: element type of in_depths */
 } gvs_splat_params;
 
+/* Differentiable colour splat (Sec. 3.1 / Supplement A.3, pixel-sized Gaussians as weights). */
+typedef struct {
+    float max_half_width;      /* footprint half-width cap (>= 0.5), as gvs_splat_params */
+    float mu_band;             /* front band: sources with z <= z_winner + mu_band are blended */
+    int32_t depth_dtype;       /* GVS_F32 or GVS_F16 */
+    int32_t color_dtype;       /* GVS_F32 (float RGBA) or GVS_BF16 (bfloat16 RGBA) */
+} gvs_soft_splat_params;
+
 /* Library identification and diagnostics. */
 GVS_API const char *gvs_version(void);
 GVS_API const char *gvs_status_string(gvs_status s);
@@ -238,6 +246,50 @@ GVS_API gvs_status gvs_fuse_depth_backward(const gvs_camera *in_cams, const void
                                            const void *map, size_t map_bytes, const int16_t *crossing,
                                            const float *grad_fused, float *grad_depths, void *workspace,
                                            size_t workspace_bytes, void *stream);
+
+/* Workspace bytes for gvs_soft_splat: a 64-bit key and a float4 accumulator per
+ * target pixel (one view at a time; a larger workspace holds several views). */
+GVS_API size_t gvs_soft_splat_workspace_bytes(int32_t n_views, int32_t target_width, int32_t target_height);
+
+/*
+ * gvs_soft_splat -- differentiable forward rendering of each input view's
+ * colour into the target (Sec. 3.1, Supplement A.3: pixel-sized Gaussians,
+ * each view rendered separately, occlusion by depth).  The winner, warped depth
+ * and alpha are exactly those of gvs_forward_splat in footprint mode (same
+ * contract).  The colour blends every covering source q within the front band
+ * z_q <= z_winner + mu_band (FP32 sum and test) with weights
+ *   g_q = exp(-|(x_q, y_q) - p|^2 / (2 sigma_q^2)),  sigma_q = hw_q / 2:
+ *   colour(p) = sum g_q c_q / sum g_q   (RGB; the 4th channel is written 0).
+ *   in_color    : [n_views][height][width][4] of color_dtype, values in [0, 1]
+ *   winner      : int32 [n_views][Ht][Wt];  warped_color: float [n_views][Ht][Wt][4]
+ *   warped_depth: float [n_views][Ht][Wt] (NULL allowed); alpha: uint8 (NULL allowed)
+ *   weight_sum  : float [n_views][Ht][Wt], sum g (kept for the backward)
+ */
+GVS_API gvs_status gvs_soft_splat(const gvs_camera *in_cams, const void *in_depths, const void *in_color,
+                                  int32_t n_views, const gvs_camera *target, const gvs_soft_splat_params *params,
+                                  int32_t *winner, float *warped_color, float *warped_depth, float *weight_sum,
+                                  uint8_t *alpha, void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * gvs_soft_splat_backward -- adjoint of gvs_soft_splat.  From the upstream
+ * gradients of the warped colour (grad_color [n_views][Ht][Wt][4], 4th channel
+ * ignored) and, optionally, of the warped depth (grad_depth [n_views][Ht][Wt]),
+ * writes the gradients of the source depths (grad_in_depth float [n_views][H][W])
+ * and colours (grad_in_color float [n_views][H][W][4], 4th channel 0):
+ *   d colour / d c_q = g_q / sum g,   d colour / d g_q = (c_q - colour) / sum g,
+ *   g_q through (x_q, y_q) and sigma_q as functions of d_q (sigma only where the
+ *   half-width is not clamped), and the warped depth through dz/dd of the
+ *   winner.  Band membership, coverage and the winner are piecewise constant.
+ * Needs the forward's winner, warped_color, warped_depth and weight_sum.  One
+ * thread per source pixel gathers over its own footprint: no atomics, so the
+ * result is deterministic.
+ */
+GVS_API gvs_status gvs_soft_splat_backward(const gvs_camera *in_cams, const void *in_depths, const void *in_color,
+                                           int32_t n_views, const gvs_camera *target,
+                                           const gvs_soft_splat_params *params, const int32_t *winner,
+                                           const float *warped_color, const float *warped_depth,
+                                           const float *weight_sum, const float *grad_color, const float *grad_depth,
+                                           float *grad_in_depth, float *grad_in_color, void *stream);
 
 /* Workspace bytes for gvs_forward_splat: one 64-bit z-buffer of the target size.
  * A workspace holding several such buffers lets several views splat in one pass. */

@@ -81,6 +81,8 @@ def _load():
             lib.orc_forward_splat.argtypes = [cp, vp, vp, i32, cp, i32, flt, flt, vp, vp, vp, vp, vp, vp, vp, vp]
             lib.orc_splat_bruteforce.argtypes = [cp, vp, i32, cp, i32, flt, vp]
             lib.orc_fuse_depth_grad.argtypes = [cp, vp, i32, cp, i32, dbl, dbl, dbl, dbl, i32, vp, vp]
+            lib.orc_soft_splat.argtypes = [cp, vp, vp, i32, cp, flt, flt, vp, vp, vp, vp, vp]
+            lib.orc_soft_splat_grad.argtypes = [cp, vp, vp, i32, cp, flt, flt, vp, vp, vp, vp]
             _lib = lib
     return _lib
 
@@ -195,6 +197,45 @@ def forward_splat(in_cams, depths, rgba_u32, target, footprint=True, max_half_wi
         raise ValueError("orc_forward_splat rejected its arguments")
     return {"winner": win, "warped_rgba": wr, "warped_depth": wd, "alpha": al, "guided": gu,
             "guided_ambiguous": ga, "fp64_mismatch": int(mism.value)}
+
+
+def soft_splat(in_cams, depths, colors, target, max_half_width=2.0, mu_band=0.04):
+    """Differentiable colour splat (footprint mode).  colors float [N, H, W, 4] in [0, 1].
+
+    Returns dict(winner int32, color float64 [N, Ht, Wt, 4], depth float32, wsum float64, alpha uint8)."""
+    lib = _load()
+    depths = np.ascontiguousarray(depths, np.float32)
+    colors = np.ascontiguousarray(colors, np.float64)
+    N = len(in_cams)
+    shape = (N, target.height, target.width)
+    win = np.empty(shape, np.int32)
+    col = np.empty(shape + (4,), np.float64)
+    dep = np.empty(shape, np.float32)
+    wsum = np.empty(shape, np.float64)
+    al = np.empty(shape, np.uint8)
+    rc = lib.orc_soft_splat(_cams(in_cams), _ptr(depths), _ptr(colors), N, ctypes.byref(_cam(target)),
+                            ctypes.c_float(max_half_width), ctypes.c_float(mu_band), _ptr(win), _ptr(col), _ptr(dep),
+                            _ptr(wsum), _ptr(al))
+    if rc != 0:
+        raise ValueError("orc_soft_splat rejected its arguments")
+    return {"winner": win, "color": col, "depth": dep, "wsum": wsum, "alpha": al}
+
+
+def soft_splat_grad(in_cams, depths, colors, target, grad_color, grad_depth=None, max_half_width=2.0, mu_band=0.04):
+    """Adjoint of soft_splat: (grad w.r.t. depths float64 [N, H, W], w.r.t. colors float64 [N, H, W, 4])."""
+    lib = _load()
+    depths = np.ascontiguousarray(depths, np.float32)
+    colors = np.ascontiguousarray(colors, np.float64)
+    gc = np.ascontiguousarray(grad_color, np.float64)
+    gd = None if grad_depth is None else np.ascontiguousarray(grad_depth, np.float64)
+    out_d = np.zeros(depths.shape, np.float64)
+    out_c = np.zeros(colors.shape, np.float64)
+    rc = lib.orc_soft_splat_grad(_cams(in_cams), _ptr(depths), _ptr(colors), len(in_cams), ctypes.byref(_cam(target)),
+                                 ctypes.c_float(max_half_width), ctypes.c_float(mu_band), _ptr(gc), _ptr(gd),
+                                 _ptr(out_d), _ptr(out_c))
+    if rc != 0:
+        raise ValueError("orc_soft_splat_grad rejected its arguments")
+    return out_d, out_c
 
 
 def splat_bruteforce(in_cams, depths, target, footprint=True, max_half_width=2.0):

@@ -616,3 +616,174 @@ int orc_fuse_depth_grad(const orc_camera *in_cams, const float *depths, int n_vi
     free(b);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Differentiable colour splat (reading of Sec. 3.1 / Supplement A.3 with   */
+/* the pixel-sized Gaussians kept as weights).  Per view and target pixel p: */
+/* z_w = depth of the z-buffer winner (as in orc_forward_splat); the front  */
+/* band S(p) = { covering sources q : z_q <= z_w + mu_band } (FP32 test, as  */
+/* the kernel takes it); g_q = exp(-|(x_q, y_q) - p|^2 / (2 sigma_q^2)),      */
+/* sigma_q = hw_q / 2 (the footprint half-width); colour                     */
+/* I(p) = sum_S g_q c_q / sum_S g_q; warped depth z_w.  Colours are          */
+/* [N][H][W][4] (the 4th channel is carried, not splatted).                  */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int ok;
+    float x, y, z, hw;
+    int i0, i1, j0, j1;
+    float m2;
+} soft_geo;
+
+static soft_geo soft_contract(const float A[9], const float c[3], float f_ratio, float max_hw, int u, int v, float d,
+                              int Wt, int Ht) {
+    soft_geo s;
+    memset(&s, 0, sizeof(s));
+    splat_geo g = splat_contract(A, c, f_ratio, 1, max_hw, u, v, d, Wt, Ht);
+    if (!g.ok) return s;
+    s.ok = 1;
+    s.x = g.x; s.y = g.y; s.z = g.z;
+    s.i0 = g.i0; s.i1 = g.i1; s.j0 = g.j0; s.j1 = g.j1;
+    float rho = f_ratio * (d / g.z);
+    float hw = 0.5f * rho;
+    hw = hw > 0.5f ? hw : 0.5f;
+    hw = hw < max_hw ? hw : max_hw;
+    s.hw = hw;
+    s.m2 = fmaf(A[6], (float)u, fmaf(A[7], (float)v, A[8]));
+    return s;
+}
+
+/* Forward; also returns per target pixel the winner, z_w and sum g for reuse. */
+int orc_soft_splat(const orc_camera *in_cams, const float *depths, const double *colors, int n_views,
+                   const orc_camera *target, float max_hw, float mu_band, int32_t *winner, double *out_color,
+                   float *out_depth, double *out_wsum, uint8_t *out_alpha) {
+    if (!in_cams || !depths || !colors || n_views <= 0 || !target || !winner || !out_color) return -1;
+    int Wt = target->width, Ht = target->height;
+    size_t np = (size_t)Wt * Ht;
+    uint64_t *key = malloc(sizeof(uint64_t) * np);
+    double *acc = malloc(sizeof(double) * 4 * np);
+    size_t in_off = 0;
+    for (int k = 0; k < n_views; ++k) {
+        const orc_camera *vc = &in_cams[k];
+        int W = vc->width, H = vc->height;
+        float A[9], c[3];
+        compose(target, vc, A, c);
+        float f_ratio = (float)(target->fx / vc->fx);
+        for (size_t p = 0; p < np; ++p) key[p] = ~(uint64_t)0;
+        for (size_t p = 0; p < 4 * np; ++p) acc[p] = 0.0;
+        for (int v = 0; v < H; ++v)
+            for (int u = 0; u < W; ++u) {
+                float d = depths[in_off + (size_t)v * W + u];
+                soft_geo g = soft_contract(A, c, f_ratio, max_hw, u, v, d, Wt, Ht);
+                if (!g.ok) continue;
+                uint64_t kk = make_key(g.z, (uint32_t)(v * W + u));
+                for (int jj = g.j0; jj <= g.j1; ++jj)
+                    for (int ii = g.i0; ii <= g.i1; ++ii)
+                        if (kk < key[(size_t)jj * Wt + ii]) key[(size_t)jj * Wt + ii] = kk;
+            }
+        for (int v = 0; v < H; ++v)
+            for (int u = 0; u < W; ++u) {
+                float d = depths[in_off + (size_t)v * W + u];
+                soft_geo g = soft_contract(A, c, f_ratio, max_hw, u, v, d, Wt, Ht);
+                if (!g.ok) continue;
+                double sig = 0.5 * (double)g.hw;
+                const double *col = colors + 4 * (in_off + (size_t)v * W + u);
+                for (int jj = g.j0; jj <= g.j1; ++jj)
+                    for (int ii = g.i0; ii <= g.i1; ++ii) {
+                        size_t p = (size_t)jj * Wt + ii;
+                        uint32_t zb = (uint32_t)(key[p] >> 32);
+                        float zw;
+                        memcpy(&zw, &zb, 4);
+                        float lim = zw + mu_band; /* FP32 sum, as the kernel forms it */
+                        if (!(g.z <= lim)) continue;
+                        double dx = (double)g.x - ii, dy = (double)g.y - jj;
+                        double w = exp(-(dx * dx + dy * dy) / (2.0 * sig * sig));
+                        for (int ch = 0; ch < 3; ++ch) acc[4 * p + ch] += w * col[ch];
+                        acc[4 * p + 3] += w;
+                    }
+            }
+        for (size_t p = 0; p < np; ++p) {
+            size_t o = (size_t)k * np + p;
+            int has = key[p] != ~(uint64_t)0;
+            uint32_t zb = (uint32_t)(key[p] >> 32);
+            float zw;
+            memcpy(&zw, &zb, 4);
+            winner[o] = has ? (int32_t)(uint32_t)(key[p] & 0xffffffffu) : -1;
+            if (out_depth) out_depth[o] = has ? zw : 0.0f;
+            if (out_alpha) out_alpha[o] = (uint8_t)has;
+            if (out_wsum) out_wsum[o] = acc[4 * p + 3];
+            for (int ch = 0; ch < 4; ++ch)
+                out_color[4 * o + ch] = (has && ch < 3 && acc[4 * p + 3] > 0.0) ? acc[4 * p + ch] / acc[4 * p + 3] : 0.0;
+        }
+        in_off += (size_t)W * H;
+    }
+    free(key);
+    free(acc);
+    return 0;
+}
+
+/* Adjoint: grad_color [N][Ht][Wt][4] (4th ignored), grad_depth [N][Ht][Wt] or NULL.
+ * d I / d c_q = g_q / sum g;  d I / d g_q = (c_q - I) / sum g;
+ * g_q depends on d_q through (x_q, y_q) and sigma_q (when hw is not clamped);
+ * the warped depth z_w depends on the winner's depth through dz/dd = m_2.
+ * Band membership, coverage and the winner are piecewise constant. */
+int orc_soft_splat_grad(const orc_camera *in_cams, const float *depths, const double *colors, int n_views,
+                        const orc_camera *target, float max_hw, float mu_band, const double *grad_color,
+                        const double *grad_depth, double *grad_in_depth, double *grad_in_color) {
+    int Wt = target->width, Ht = target->height;
+    size_t np = (size_t)Wt * Ht;
+    size_t nin = 0;
+    for (int k = 0; k < n_views; ++k) nin += (size_t)in_cams[k].width * in_cams[k].height;
+    int32_t *win = malloc(sizeof(int32_t) * np * n_views);
+    double *col = malloc(sizeof(double) * 4 * np * n_views);
+    float *zd = malloc(sizeof(float) * np * n_views);
+    double *ws = malloc(sizeof(double) * np * n_views);
+    int rc = orc_soft_splat(in_cams, depths, colors, n_views, target, max_hw, mu_band, win, col, zd, ws, NULL);
+    if (rc) return rc;
+    for (size_t q = 0; q < nin; ++q) grad_in_depth[q] = 0.0;
+    for (size_t q = 0; q < 4 * nin; ++q) grad_in_color[q] = 0.0;
+    size_t in_off = 0;
+    for (int k = 0; k < n_views; ++k) {
+        const orc_camera *vc = &in_cams[k];
+        int W = vc->width, H = vc->height;
+        float A[9], c[3];
+        compose(target, vc, A, c);
+        float f_ratio = (float)(target->fx / vc->fx);
+        for (int v = 0; v < H; ++v)
+            for (int u = 0; u < W; ++u) {
+                size_t qi = in_off + (size_t)v * W + u;
+                float d = depths[qi];
+                soft_geo g = soft_contract(A, c, f_ratio, max_hw, u, v, d, Wt, Ht);
+                if (!g.ok) continue;
+                /* derivatives of the contract geometry with respect to d (FP64) */
+                float m0 = fmaf(A[0], (float)u, fmaf(A[1], (float)v, A[2]));
+                float m1 = fmaf(A[3], (float)u, fmaf(A[4], (float)v, A[5]));
+                double h2 = (double)g.z;
+                double dx_dd = ((double)m0 - (double)g.x * g.m2) / h2;
+                double dy_dd = ((double)m1 - (double)g.y * g.m2) / h2;
+                double rho = (double)f_ratio * ((double)d / h2);
+                double dhw_dd = (0.5 * rho > 0.5 && 0.5 * rho < (double)max_hw)
+                                    ? 0.5 * (double)f_ratio * (double)c[2] / (h2 * h2) : 0.0;
+                double sig = 0.5 * (double)g.hw, dsig_dd = 0.5 * dhw_dd;
+                for (int jj = g.j0; jj <= g.j1; ++jj)
+                    for (int ii = g.i0; ii <= g.i1; ++ii) {
+                        size_t o = (size_t)k * np + (size_t)jj * Wt + ii;
+                        float lim = zd[o] + mu_band;
+                        if (!(g.z <= lim)) continue;
+                        double ex = (double)g.x - ii, ey = (double)g.y - jj;
+                        double r2 = ex * ex + ey * ey;
+                        double w = exp(-r2 / (2.0 * sig * sig));
+                        double dw_dd = w * (-(ex * dx_dd + ey * dy_dd) / (sig * sig) + r2 * dsig_dd / (sig * sig * sig));
+                        double sw = ws[o];
+                        for (int ch = 0; ch < 3; ++ch) {
+                            double G = grad_color[4 * o + ch];
+                            grad_in_color[4 * qi + ch] += G * w / sw;
+                            grad_in_depth[qi] += G * (colors[4 * qi + ch] - col[4 * o + ch]) / sw * dw_dd;
+                        }
+                        if (grad_depth && win[o] == (int32_t)(v * W + u)) grad_in_depth[qi] += grad_depth[o] * (double)g.m2;
+                    }
+            }
+        in_off += (size_t)W * H;
+    }
+    free(win); free(col); free(zd); free(ws);
+    return 0;
+}

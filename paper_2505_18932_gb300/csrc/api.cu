@@ -385,6 +385,126 @@ gvs_status gvs_forward_splat(const gvs_camera *in_cams, const void *in_depths, c
 
 }  // extern "C"
 
+namespace {
+
+// Slots of (keys, accumulators) that fit a soft-splat workspace: keys for all
+// slots first, then the float4 accumulators from the next 256-byte boundary.
+int soft_slots(size_t ws_bytes, int64_t HWt, int K) {
+    int slots = 0;
+    for (int s = 1; s <= K; ++s) {
+        const size_t need = align_up((size_t)s * HWt * 8, 256) + (size_t)s * HWt * 16;
+        if (need > ws_bytes) break;
+        slots = s;
+    }
+    return slots;
+}
+
+gvs_status soft_common(const gvs_camera *in_cams, const void *in_depths, const void *in_color, int32_t n_views,
+                       const gvs_camera *target, const gvs_soft_splat_params *params, gvs::SplatArgs *a) {
+    int32_t W = 0, H = 0;
+    if (!params) return fail(GVS_ERR_INVALID_ARG, "soft splat: params is NULL");
+    if (!views_ok(in_cams, n_views, &W, &H))
+        return fail(GVS_ERR_INVALID_ARG, "soft splat: input cameras invalid, of different sizes, or n_views out of range");
+    if (!camera_ok(target)) return fail(GVS_ERR_INVALID_ARG, "soft splat: target camera invalid");
+    const gvs_soft_splat_params &p = *params;
+    if (!(isfinite(p.max_half_width) && p.max_half_width >= 0.5f && p.max_half_width <= 64.0f))
+        return fail(GVS_ERR_INVALID_ARG, "soft splat: max_half_width must be in [0.5, 64]");
+    if (!(isfinite(p.mu_band) && p.mu_band >= 0.0f)) return fail(GVS_ERR_INVALID_ARG, "soft splat: mu_band must be >= 0");
+    if (p.depth_dtype != GVS_F32 && p.depth_dtype != GVS_F16)
+        return fail(GVS_ERR_UNSUPPORTED, "soft splat: depth_dtype must be GVS_F32 or GVS_F16");
+    if (p.color_dtype != GVS_F32 && p.color_dtype != GVS_BF16)
+        return fail(GVS_ERR_UNSUPPORTED, "soft splat: color_dtype must be GVS_F32 or GVS_BF16");
+    if (n_views > 0 && (!in_depths || !in_color || !aligned(in_depths, 16) || !aligned(in_color, 16)))
+        return fail(GVS_ERR_INVALID_ARG, "soft splat: inputs NULL or not 16-byte aligned");
+    memset(a, 0, sizeof(*a));
+    a->depth = in_depths;
+    a->depth_dtype = p.depth_dtype;
+    a->color = in_color;
+    a->color_dtype = p.color_dtype;
+    a->W = W;
+    a->H = H;
+    a->Wt = target->width;
+    a->Ht = target->height;
+    a->footprint = 1;
+    a->max_hw = p.max_half_width;
+    a->mu_band = p.mu_band;
+    for (int k = 0; k < n_views; ++k) {
+        a->v[k].xf = compose(*target, in_cams[k]);
+        a->v[k].f_ratio = (float)(target->fx / in_cams[k].fx);
+    }
+    return GVS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t gvs_soft_splat_workspace_bytes(int32_t n_views, int32_t target_width, int32_t target_height) {
+    (void)n_views;
+    if (target_width < 0 || target_height < 0) return 0;
+    const size_t HWt = (size_t)target_width * target_height;
+    return align_up(align_up(HWt * 8, 256) + HWt * 16, 256);
+}
+
+gvs_status gvs_soft_splat(const gvs_camera *in_cams, const void *in_depths, const void *in_color, int32_t n_views,
+                          const gvs_camera *target, const gvs_soft_splat_params *params, int32_t *winner,
+                          float *warped_color, float *warped_depth, float *weight_sum, uint8_t *alpha,
+                          void *workspace, size_t workspace_bytes, void *stream) {
+    gvs::SplatArgs a;
+    gvs_status s = soft_common(in_cams, in_depths, in_color, n_views, target, params, &a);
+    if (s != GVS_OK) return s;
+    if (n_views == 0) return GVS_OK;
+    const void *outs[] = {winner, warped_color, weight_sum};
+    for (const void *q : outs)
+        if (!q || !aligned(q, 16)) return fail(GVS_ERR_INVALID_ARG, "soft splat: winner, warped_color and weight_sum are required, 16-byte aligned");
+    if ((warped_depth && !aligned(warped_depth, 16)) || (alpha && !aligned(alpha, 16)))
+        return fail(GVS_ERR_INVALID_ARG, "soft splat: outputs must be 16-byte aligned");
+    const int64_t HWt = (int64_t)target->width * target->height;
+    const int slots = soft_slots(workspace_bytes, HWt, n_views);
+    if (!workspace || !aligned(workspace, 256) || slots < 1)
+        return fail(GVS_ERR_WORKSPACE, "soft splat: workspace needs %zu bytes, 256-byte aligned",
+                    gvs_soft_splat_workspace_bytes(n_views, target->width, target->height));
+    a.keys = reinterpret_cast<unsigned long long *>(workspace);
+    a.acc = reinterpret_cast<float4 *>(reinterpret_cast<char *>(workspace) + align_up((size_t)slots * HWt * 8, 256));
+    a.slots = slots;
+    a.winner = winner;
+    a.out_color = reinterpret_cast<float4 *>(warped_color);
+    a.warped_depth = warped_depth;
+    a.wsum = weight_sum;
+    a.alpha = alpha;
+    cudaError_t e = gvs::launch_soft_splat(a, n_views, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "soft splat: launch");
+    return GVS_OK;
+}
+
+gvs_status gvs_soft_splat_backward(const gvs_camera *in_cams, const void *in_depths, const void *in_color,
+                                   int32_t n_views, const gvs_camera *target, const gvs_soft_splat_params *params,
+                                   const int32_t *winner, const float *warped_color, const float *warped_depth,
+                                   const float *weight_sum, const float *grad_color, const float *grad_depth,
+                                   float *grad_in_depth, float *grad_in_color, void *stream) {
+    gvs::SplatArgs a;
+    gvs_status s = soft_common(in_cams, in_depths, in_color, n_views, target, params, &a);
+    if (s != GVS_OK) return s;
+    if (n_views == 0) return GVS_OK;
+    const void *req[] = {winner, warped_color, warped_depth, weight_sum, grad_color, grad_in_depth, grad_in_color};
+    for (const void *q : req)
+        if (!q || !aligned(q, 16)) return fail(GVS_ERR_INVALID_ARG, "soft splat backward: NULL or misaligned array");
+    if (grad_depth && !aligned(grad_depth, 16)) return fail(GVS_ERR_INVALID_ARG, "soft splat backward: grad_depth misaligned");
+    a.winner = const_cast<int32_t *>(winner);
+    a.out_color = const_cast<float4 *>(reinterpret_cast<const float4 *>(warped_color));
+    a.warped_depth = const_cast<float *>(warped_depth);
+    a.wsum = const_cast<float *>(weight_sum);
+    a.grad_color = reinterpret_cast<const float4 *>(grad_color);
+    a.grad_depth = grad_depth;
+    a.grad_in_depth = grad_in_depth;
+    a.grad_in_color = reinterpret_cast<float4 *>(grad_in_color);
+    cudaError_t e = gvs::launch_soft_splat_backward(a, n_views, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "soft splat backward: launch");
+    return GVS_OK;
+}
+
+}  // extern "C"
+
 // ---------------------------------------------------------------------------
 // Forward splat without any device allocation.
 //

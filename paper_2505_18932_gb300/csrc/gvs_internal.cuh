@@ -101,9 +101,22 @@ struct SplatArgs {
     uint8_t *guided;
     unsigned long long *keys;  // [slots][Ht][Wt]
     int slots;
+    // differentiable colour splat (soft): colour [K][H][W][4] of color_dtype (F32 or BF16)
+    const void *color;
+    int color_dtype;
+    float mu_band;
+    float4 *acc;               // [slots][Ht][Wt] running (sum g c, sum g)
+    float4 *out_color;         // [K][Ht][Wt] RGBA (A = 0)
+    float *wsum;               // [K][Ht][Wt] sum g
+    const float4 *grad_color;  // backward inputs [K][Ht][Wt]
+    const float *grad_depth;   // [K][Ht][Wt] or null
+    float *grad_in_depth;      // backward outputs [K][H][W]
+    float4 *grad_in_color;     // [K][H][W]
     SplatView v[GVS_MAX_VIEWS];
 };
 
 cudaError_t launch_splat(const SplatArgs &a, int K, cudaStream_t st);
+cudaError_t launch_soft_splat(const SplatArgs &a, int K, cudaStream_t st);
+cudaError_t launch_soft_splat_backward(const SplatArgs &a, int K, cudaStream_t st);
 
 }  // namespace gvs

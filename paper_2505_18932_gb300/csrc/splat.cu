@@ -36,6 +36,55 @@ __global__ void __launch_bounds__(256) clear_keys(unsigned long long *__restrict
 __device__ __forceinline__ float load_depth(const float *p) { return __ldg(p); }
 __device__ __forceinline__ float load_depth(const __half *p) { return __half2float(__ldg(p)); }
 
+// The FP32 address contract of one source pixel (see gvs.h): projected
+// position, depth, footprint half-width and the covered target pixels.
+struct Geo {
+    bool ok;
+    float x, y, z, hw, m0, m1, m2;
+    int i0, i1, j0, j1;
+};
+
+__device__ __forceinline__ Geo contract(const SplatView &sv, int u, int v, float d, int Wt, int Ht, int footprint,
+                                        float max_hw) {
+    Geo g;
+    g.ok = false;
+    if (!valid_depth(d)) return g;
+    const float *A = sv.xf.M;
+    const float *c = sv.xf.b;
+    const float fu = (float)u, fv = (float)v;
+    g.m0 = __fmaf_rn(A[0], fu, __fmaf_rn(A[1], fv, A[2]));
+    g.m1 = __fmaf_rn(A[3], fu, __fmaf_rn(A[4], fv, A[5]));
+    g.m2 = __fmaf_rn(A[6], fu, __fmaf_rn(A[7], fv, A[8]));
+    const float h0 = __fmaf_rn(d, g.m0, c[0]);
+    const float h1 = __fmaf_rn(d, g.m1, c[1]);
+    const float h2 = __fmaf_rn(d, g.m2, c[2]);
+    if (!(h2 > 1e-6f)) return g;
+    const float x = __fdiv_rn(h0, h2);
+    const float y = __fdiv_rn(h1, h2);
+    float lox, hix, loy, hiy, hw = 0.5f;
+    if (footprint) {
+        const float rho = __fmul_rn(sv.f_ratio, __fdiv_rn(d, h2));
+        hw = fminf(fmaxf(__fmul_rn(0.5f, rho), 0.5f), max_hw);
+        lox = ceilf(__fsub_rn(x, hw));
+        hix = floorf(__fadd_rn(x, hw));
+        loy = ceilf(__fsub_rn(y, hw));
+        hiy = floorf(__fadd_rn(y, hw));
+    } else {
+        lox = hix = rintf(x);
+        loy = hiy = rintf(y);
+    }
+    // clip with plain comparisons so that a NaN bound (overflowed geometry) skips the pixel
+    if (lox < 0.0f) lox = 0.0f;
+    if (loy < 0.0f) loy = 0.0f;
+    if (hix > (float)(Wt - 1)) hix = (float)(Wt - 1);
+    if (hiy > (float)(Ht - 1)) hiy = (float)(Ht - 1);
+    if (!(lox <= hix) || !(loy <= hiy)) return g;
+    g.ok = true;
+    g.x = x; g.y = y; g.z = h2; g.hw = hw;
+    g.i0 = (int)lox; g.i1 = (int)hix; g.j0 = (int)loy; g.j1 = (int)hiy;
+    return g;
+}
+
 // DT: float or __half depth storage, widened to FP32 before the contract.
 template <typename DT>
 __global__ void __launch_bounds__(256) splat_scatter(const SplatArgs a, int k0, int kn) {
@@ -48,42 +97,12 @@ __global__ void __launch_bounds__(256) splat_scatter(const SplatArgs a, int k0, 
     const int v = src / a.W;
     const int u = src - v * a.W;
     const float d = load_depth(reinterpret_cast<const DT *>(a.depth) + (size_t)k * HW + src);
-    if (!valid_depth(d)) return;
-    const float *A = a.v[k].xf.M;
-    const float *c = a.v[k].xf.b;
-    const float fu = (float)u, fv = (float)v;
-    const float m0 = __fmaf_rn(A[0], fu, __fmaf_rn(A[1], fv, A[2]));
-    const float m1 = __fmaf_rn(A[3], fu, __fmaf_rn(A[4], fv, A[5]));
-    const float m2 = __fmaf_rn(A[6], fu, __fmaf_rn(A[7], fv, A[8]));
-    const float h0 = __fmaf_rn(d, m0, c[0]);
-    const float h1 = __fmaf_rn(d, m1, c[1]);
-    const float h2 = __fmaf_rn(d, m2, c[2]);
-    if (!(h2 > 1e-6f)) return;
-    const float x = __fdiv_rn(h0, h2);
-    const float y = __fdiv_rn(h1, h2);
-    float lox, hix, loy, hiy;
-    if (a.footprint) {
-        const float rho = __fmul_rn(a.v[k].f_ratio, __fdiv_rn(d, h2));
-        const float hw = fminf(fmaxf(__fmul_rn(0.5f, rho), 0.5f), a.max_hw);
-        lox = ceilf(__fsub_rn(x, hw));
-        hix = floorf(__fadd_rn(x, hw));
-        loy = ceilf(__fsub_rn(y, hw));
-        hiy = floorf(__fadd_rn(y, hw));
-    } else {
-        lox = hix = rintf(x);
-        loy = hiy = rintf(y);
-    }
-    // clip with plain comparisons so that a NaN bound (overflowed geometry) skips the pixel
-    if (lox < 0.0f) lox = 0.0f;
-    if (loy < 0.0f) loy = 0.0f;
-    if (hix > (float)(a.Wt - 1)) hix = (float)(a.Wt - 1);
-    if (hiy > (float)(a.Ht - 1)) hiy = (float)(a.Ht - 1);
-    if (!(lox <= hix) || !(loy <= hiy)) return;
-    const unsigned long long key = ((unsigned long long)__float_as_uint(h2) << 32) | (unsigned)src;
+    const Geo g = contract(a.v[k], u, v, d, a.Wt, a.Ht, a.footprint, a.max_hw);
+    if (!g.ok) return;
+    const unsigned long long key = ((unsigned long long)__float_as_uint(g.z) << 32) | (unsigned)src;
     unsigned long long *slot = a.keys + (size_t)kk * a.Wt * a.Ht;
-    const int i0 = (int)lox, i1 = (int)hix, j0 = (int)loy, j1 = (int)hiy;
-    for (int jj = j0; jj <= j1; ++jj)
-        for (int ii = i0; ii <= i1; ++ii) atomicMin(&slot[(size_t)jj * a.Wt + ii], key);
+    for (int jj = g.j0; jj <= g.j1; ++jj)
+        for (int ii = g.i0; ii <= g.i1; ++ii) atomicMin(&slot[(size_t)jj * a.Wt + ii], key);
 }
 
 __device__ __forceinline__ void decode(unsigned long long key, bool &has, int32_t &w, float &z) {
@@ -161,6 +180,131 @@ __global__ void __launch_bounds__(256) splat_resolve4(const SplatArgs a, int k0,
     }
 }
 
+// ---------------------------------------------------------------------------
+// Differentiable colour splat.  The hard z-buffer (scatter above) fixes the
+// winner's depth z_w per target pixel; every covering source q inside the
+// front band z_q <= z_w + mu_band adds a Gaussian weight
+// g = exp(-|(x_q, y_q) - p|^2 / (2 sigma^2)), sigma = hw / 2 (a pixel-sized
+// Gaussian, Sec. 3.1 / Supplement A.3), and the colour is sum g c / sum g.
+// The adjoint gathers from the source side (one thread per source pixel
+// walking its own footprint), so it needs no atomics.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float4 load_color(const float4 *p) { return __ldg(p); }
+__device__ __forceinline__ float4 load_color(const uint2 *p) {  // four bfloat16
+    const uint2 r = __ldg(p);
+    return make_float4(__uint_as_float(r.x << 16), __uint_as_float(r.x & 0xffff0000u), __uint_as_float(r.y << 16),
+                       __uint_as_float(r.y & 0xffff0000u));
+}
+
+template <typename DT, typename CT>
+__global__ void __launch_bounds__(256) soft_accum(const SplatArgs a, int k0, int kn) {
+    const int64_t HW = (int64_t)a.W * a.H;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= (int64_t)kn * HW) return;
+    const int kk = (int)(p / HW);
+    const int k = k0 + kk;
+    const int src = (int)(p - (int64_t)kk * HW);
+    const int v = src / a.W, u = src - v * a.W;
+    const float d = load_depth(reinterpret_cast<const DT *>(a.depth) + (size_t)k * HW + src);
+    const Geo g = contract(a.v[k], u, v, d, a.Wt, a.Ht, 1, a.max_hw);
+    if (!g.ok) return;
+    const float4 c = load_color(reinterpret_cast<const CT *>(a.color) + (size_t)k * HW + src);
+    const float inv2s2 = 2.0f / (g.hw * g.hw);  // 1 / (2 sigma^2), sigma = hw / 2
+    const unsigned long long *keys = a.keys + (size_t)kk * a.Wt * a.Ht;
+    float4 *acc = a.acc + (size_t)kk * a.Wt * a.Ht;
+    for (int jj = g.j0; jj <= g.j1; ++jj)
+        for (int ii = g.i0; ii <= g.i1; ++ii) {
+            const size_t t = (size_t)jj * a.Wt + ii;
+            const float zw = __uint_as_float((uint32_t)(keys[t] >> 32));
+            if (!(g.z <= __fadd_rn(zw, a.mu_band))) continue;
+            const float ex = g.x - (float)ii, ey = g.y - (float)jj;
+            const float w = expf(-(ex * ex + ey * ey) * inv2s2);
+            atomicAdd(&acc[t], make_float4(w * c.x, w * c.y, w * c.z, w));
+        }
+}
+
+__global__ void __launch_bounds__(256) soft_resolve(const SplatArgs a, int k0, int kn) {
+    const int64_t HWt = (int64_t)a.Wt * a.Ht;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= (int64_t)kn * HWt) return;
+    const int kk = (int)(p / HWt);
+    const int k = k0 + kk;
+    const int64_t t = p - (int64_t)kk * HWt;
+    unsigned long long *slot = a.keys + (size_t)kk * HWt;
+    float4 *acc = a.acc + (size_t)kk * HWt;
+    const unsigned long long key = slot[t];
+    const float4 s = acc[t];
+    slot[t] = ~0ull;  // ready for the next group of views
+    acc[t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    bool has;
+    int32_t w;
+    float z;
+    decode(key, has, w, z);
+    const size_t o = (size_t)k * HWt + t;
+    a.winner[o] = w;
+    if (a.warped_depth) a.warped_depth[o] = z;
+    if (a.alpha) a.alpha[o] = (uint8_t)has;
+    a.wsum[o] = s.w;
+    const float r = (has && s.w > 0.0f) ? 1.0f / s.w : 0.0f;
+    a.out_color[o] = make_float4(s.x * r, s.y * r, s.z * r, 0.0f);
+}
+
+template <typename DT, typename CT>
+__global__ void __launch_bounds__(256) soft_bwd(const SplatArgs a, int K) {
+    const int64_t HW = (int64_t)a.W * a.H, HWt = (int64_t)a.Wt * a.Ht;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= (int64_t)K * HW) return;
+    const int k = (int)(p / HW);
+    const int src = (int)(p - (int64_t)k * HW);
+    const int v = src / a.W, u = src - v * a.W;
+    const float d = load_depth(reinterpret_cast<const DT *>(a.depth) + (size_t)k * HW + src);
+    const Geo g = contract(a.v[k], u, v, d, a.Wt, a.Ht, 1, a.max_hw);
+    float gd = 0.0f;
+    float3 gc = make_float3(0.0f, 0.0f, 0.0f);
+    if (g.ok) {
+        const float4 c = load_color(reinterpret_cast<const CT *>(a.color) + (size_t)k * HW + src);
+        const float z = g.z;
+        const float dx_dd = (g.m0 - g.x * g.m2) / z, dy_dd = (g.m1 - g.y * g.m2) / z;
+        const float rho = a.v[k].f_ratio * (d / z);
+        const float dhw_dd = (0.5f * rho > 0.5f && 0.5f * rho < a.max_hw)
+                                 ? 0.5f * a.v[k].f_ratio * a.v[k].xf.b[2] / (z * z) : 0.0f;
+        const float sig = 0.5f * g.hw, dsig_dd = 0.5f * dhw_dd;
+        const float inv_s2 = 1.0f / (sig * sig);
+        for (int jj = g.j0; jj <= g.j1; ++jj)
+            for (int ii = g.i0; ii <= g.i1; ++ii) {
+                const size_t o = (size_t)k * HWt + (size_t)jj * a.Wt + ii;
+                if (a.grad_depth && a.winner[o] == src) gd += a.grad_depth[o] * g.m2;
+                if (!(z <= __fadd_rn(a.warped_depth[o], a.mu_band))) continue;
+                const float ex = g.x - (float)ii, ey = g.y - (float)jj;
+                const float r2 = ex * ex + ey * ey;
+                const float w = expf(-0.5f * r2 * inv_s2);
+                const float dw_dd = w * (-(ex * dx_dd + ey * dy_dd) * inv_s2 + r2 * dsig_dd * inv_s2 / sig);
+                const float inv_sw = 1.0f / a.wsum[o];
+                const float4 G = a.grad_color[o];
+                const float4 I = a.out_color[o];
+                gc.x += G.x * w * inv_sw;
+                gc.y += G.y * w * inv_sw;
+                gc.z += G.z * w * inv_sw;
+                gd += (G.x * (c.x - I.x) + G.y * (c.y - I.y) + G.z * (c.z - I.z)) * inv_sw * dw_dd;
+            }
+    }
+    a.grad_in_depth[(size_t)k * HW + src] = gd;
+    a.grad_in_color[(size_t)k * HW + src] = make_float4(gc.x, gc.y, gc.z, 0.0f);
+}
+
+template <typename DT, typename CT>
+void soft_groups(const SplatArgs &a, int K, cudaStream_t st) {
+    const int64_t HWt = (int64_t)a.Wt * a.Ht, HW = (int64_t)a.W * a.H;
+    const int slots = a.slots < K ? a.slots : K;
+    for (int k0 = 0; k0 < K; k0 += slots) {
+        const int kn = (K - k0) < slots ? (K - k0) : slots;
+        const int64_t ns = (int64_t)kn * HW, nt = (int64_t)kn * HWt;
+        splat_scatter<DT><<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(a, k0, kn);
+        soft_accum<DT, CT><<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(a, k0, kn);
+        soft_resolve<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(a, k0, kn);
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_splat(const SplatArgs &a, int K, cudaStream_t st) {
@@ -190,6 +334,44 @@ cudaError_t launch_splat(const SplatArgs &a, int K, cudaStream_t st) {
             const int64_t nt = (int64_t)kn * HWt;
             splat_resolve<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(a, k0, kn);
         }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_soft_splat(const SplatArgs &a, int K, cudaStream_t st) {
+    if (K == 0) return cudaSuccess;
+    const int64_t HWt = (int64_t)a.Wt * a.Ht;
+    const int slots = a.slots < K ? a.slots : K;
+    {
+        const int64_t n = HWt * slots;
+        int64_t blocks = (n / 2 + 255) / 256;
+        const int64_t cap = (int64_t)device_sm_count() * 8;
+        if (blocks > cap) blocks = cap;
+        if (blocks < 1) blocks = 1;
+        clear_keys<<<(unsigned)blocks, 256, 0, st>>>(a.keys, n);
+        cudaError_t e = cudaMemsetAsync(a.acc, 0, (size_t)n * sizeof(float4), st);
+        if (e != cudaSuccess) return e;
+    }
+    if (a.depth_dtype == GVS_F16) {
+        if (a.color_dtype == GVS_BF16) soft_groups<__half, uint2>(a, K, st);
+        else soft_groups<__half, float4>(a, K, st);
+    } else {
+        if (a.color_dtype == GVS_BF16) soft_groups<float, uint2>(a, K, st);
+        else soft_groups<float, float4>(a, K, st);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_soft_splat_backward(const SplatArgs &a, int K, cudaStream_t st) {
+    if (K == 0) return cudaSuccess;
+    const int64_t n = (int64_t)K * a.W * a.H;
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    if (a.depth_dtype == GVS_F16) {
+        if (a.color_dtype == GVS_BF16) soft_bwd<__half, uint2><<<grid, 256, 0, st>>>(a, K);
+        else soft_bwd<__half, float4><<<grid, 256, 0, st>>>(a, K);
+    } else {
+        if (a.color_dtype == GVS_BF16) soft_bwd<float, uint2><<<grid, 256, 0, st>>>(a, K);
+        else soft_bwd<float, float4><<<grid, 256, 0, st>>>(a, K);
     }
     return cudaGetLastError();
 }

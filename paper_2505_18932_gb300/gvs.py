@@ -52,6 +52,11 @@ class GvsSplatParams(ctypes.Structure):
                 ("depth_dtype", ctypes.c_int32)]
 
 
+class GvsSoftSplatParams(ctypes.Structure):
+    _fields_ = [("max_half_width", ctypes.c_float), ("mu_band", ctypes.c_float), ("depth_dtype", ctypes.c_int32),
+                ("color_dtype", ctypes.c_int32)]
+
+
 API = {
     # name: (restype, argtypes)
     "gvs_version": (ctypes.c_char_p, []),
@@ -77,6 +82,13 @@ API = {
                                                ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p,
                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "gvs_splat_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32] * 3),
+    "gvs_soft_splat_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32] * 3),
+    "gvs_soft_splat": (ctypes.c_int, [ctypes.POINTER(GvsCamera), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                      ctypes.POINTER(GvsCamera), ctypes.POINTER(GvsSoftSplatParams)] +
+                       [ctypes.c_void_p] * 6 + [ctypes.c_size_t, ctypes.c_void_p]),
+    "gvs_soft_splat_backward": (ctypes.c_int, [ctypes.POINTER(GvsCamera), ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_int32, ctypes.POINTER(GvsCamera),
+                                               ctypes.POINTER(GvsSoftSplatParams)] + [ctypes.c_void_p] * 9),
     "gvs_forward_splat": (ctypes.c_int, [ctypes.POINTER(GvsCamera), ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_int32, ctypes.POINTER(GvsCamera), ctypes.POINTER(GvsSplatParams),
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -325,3 +337,79 @@ def forward_splat(in_cams, in_depths, in_rgba, target, fused=None, footprint=Tru
                                _stream(stream))
     _check("gvs_forward_splat", st)
     return out
+
+
+def _color_dtype_of(t) -> int:
+    if t.dtype == torch.float32:
+        return GVS_F32
+    if t.dtype == torch.bfloat16:
+        return GVS_BF16
+    raise ValueError(f"gvs: soft-splat colour must be float32 or bfloat16, got {t.dtype}")
+
+
+def soft_splat(in_cams, in_depths, in_color, target, max_half_width=2.0, mu_band=0.04, outputs=None, ws=None,
+               stream=None):
+    """Differentiable colour splat.  in_color [N, H, W, 4] float32 or bfloat16 in [0, 1].
+    Returns dict: winner int32, color float32 [N, Ht, Wt, 4], depth float32, wsum float32, alpha uint8."""
+    lib = load()
+    N = len(in_cams)
+    dev = in_depths.device
+    shape = (N, target.height, target.width)
+    out = dict(outputs or {})
+    spec = {"winner": (shape, torch.int32), "color": (shape + (4,), torch.float32), "depth": (shape, torch.float32),
+            "wsum": (shape, torch.float32), "alpha": (shape, torch.uint8)}
+    for n, (sh, dt) in spec.items():
+        if n not in out:
+            out[n] = torch.empty(sh, dtype=dt, device=dev)
+    if ws is None:
+        ws = workspace(int(lib.gvs_soft_splat_workspace_bytes(N, target.width, target.height)), dev)
+    p = GvsSoftSplatParams(float(max_half_width), float(mu_band), depth_dtype_of(in_depths) if N else GVS_F32,
+                           _color_dtype_of(in_color) if N else GVS_F32)
+    st = lib.gvs_soft_splat(camera_array(in_cams), _ptr(in_depths), _ptr(in_color), N,
+                            ctypes.byref(camera_struct(target)), ctypes.byref(p), _ptr(out["winner"]),
+                            _ptr(out["color"]), _ptr(out["depth"]), _ptr(out["wsum"]), _ptr(out["alpha"]), _ptr(ws),
+                            ws.numel() * ws.element_size(), _stream(stream))
+    _check("gvs_soft_splat", st)
+    return out
+
+
+def soft_splat_backward(in_cams, in_depths, in_color, target, fwd, grad_color, grad_depth=None, max_half_width=2.0,
+                        mu_band=0.04, stream=None):
+    """Adjoint of soft_splat: (grad w.r.t. in_depths float32 [N, H, W], w.r.t. in_color float32 [N, H, W, 4])."""
+    lib = load()
+    N = len(in_cams)
+    gd = torch.empty(in_depths.shape, dtype=torch.float32, device=in_depths.device)
+    gc = torch.empty(tuple(in_color.shape[:3]) + (4,), dtype=torch.float32, device=in_depths.device)
+    grad_color = grad_color.contiguous().to(torch.float32)
+    if grad_depth is not None:
+        grad_depth = grad_depth.contiguous().to(torch.float32)
+    p = GvsSoftSplatParams(float(max_half_width), float(mu_band), depth_dtype_of(in_depths) if N else GVS_F32,
+                           _color_dtype_of(in_color) if N else GVS_F32)
+    st = lib.gvs_soft_splat_backward(camera_array(in_cams), _ptr(in_depths), _ptr(in_color), N,
+                                     ctypes.byref(camera_struct(target)), ctypes.byref(p), _ptr(fwd["winner"]),
+                                     _ptr(fwd["color"]), _ptr(fwd["depth"]), _ptr(fwd["wsum"]), _ptr(grad_color),
+                                     _ptr(grad_depth), _ptr(gd), _ptr(gc), _stream(stream))
+    _check("gvs_soft_splat_backward", st)
+    return gd, gc
+
+
+class SoftSplat(torch.autograd.Function):
+    """color, depth, alpha = SoftSplat.apply(in_depths, in_color, cams, target, cfg);
+    cfg: dict(max_half_width=2.0, mu_band).  Gradients flow to in_depths and in_color."""
+
+    @staticmethod
+    def forward(ctx, in_depths, in_color, in_cams, target, cfg):
+        fwd = soft_splat(in_cams, in_depths, in_color, target, cfg.get("max_half_width", 2.0), cfg["mu_band"])
+        ctx.save_for_backward(in_depths, in_color, fwd["winner"], fwd["color"], fwd["depth"], fwd["wsum"])
+        ctx.cams, ctx.target, ctx.cfg = in_cams, target, cfg
+        ctx.mark_non_differentiable(fwd["alpha"])
+        return fwd["color"], fwd["depth"], fwd["alpha"]
+
+    @staticmethod
+    def backward(ctx, g_color, g_depth, g_alpha):
+        in_depths, in_color, winner, color, depth, wsum = ctx.saved_tensors
+        fwd = {"winner": winner, "color": color, "depth": depth, "wsum": wsum}
+        gd, gc = soft_splat_backward(ctx.cams, in_depths, in_color, ctx.target, fwd,
+                                     g_color if g_color is not None else torch.zeros_like(color), g_depth,
+                                     ctx.cfg.get("max_half_width", 2.0), ctx.cfg["mu_band"])
+        return gd, gc.to(in_color.dtype), None, None, None
