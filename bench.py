@@ -256,7 +256,15 @@ def run_gvs(args, rank, local_rank, world):
     holes = statistics.mean(float((c < 0).mean()) for c in crosses)
 
     e2e = run_e2e(pipe, frames_np, args.e2e_steps) if args.e2e_steps > 0 else None
-    forms = {"f16_storage": time_form(Pipeline(w, frames_np, device, half=True), steps=min(K, 100))}
+    forms = {"f16_storage": form_line("f16_storage", w, time_form(Pipeline(w, frames_np, device, half=True),
+                                                                  steps=min(K, 100)),
+                                      "refine + weight map + fuse + splat with FP16 depth and half2 map")}
+    forms["fwd_bwd"] = form_line("fwd_bwd", w, time_form(FwdBwd(w, frames_np[:2], device), steps=min(K, 30)),
+                                 "fuse + differentiable splat forward, 0.8 L1 + 0.1 L_Depth, both adjoints")
+    wd = configs.diff_640x360()
+    forms["fwd_bwd_640x360"] = form_line("fwd_bwd_640x360", wd,
+                                         time_form(FwdBwd(wd, render_frames(wd, [0, 1]), device), steps=min(K, 50)),
+                                         "the differentiable workload: 4 x 640x360, D = 96, forward + backward")
 
     if rank != 0:
         return
@@ -294,8 +302,7 @@ def run_gvs(args, rank, local_rank, world):
                               "(all D where none), 20 FP32 instructions each; the kernel proves most of them "
                               "crossing-free without evaluating them, so frac can exceed 1")},
         "e2e": e2e,
-        "forms": {name: {**f, "value": round(pipe.Ht * pipe.Wt / (f["ms_per_step"] * 1e-3) / 1e6, 3)}
-                  for name, f in forms.items()},
+        "forms": forms,
         "gpu_launches": pipe.launches_per_step() * K,
         "clocks": clk,
         "wall_s": round(wall, 3),
@@ -303,6 +310,47 @@ def run_gvs(args, rank, local_rank, world):
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(w, frames_np, budget_s=15.0)
     print(json.dumps(line), flush=True)
+
+
+class FwdBwd:
+    """One training-style step on a frame: fused depth and differentiable splat forward,
+    the loss 0.8 L1(blend, ground truth) + 0.1 L_Depth (Sec. 3.3, uniform blend weights),
+    and both adjoints back to the input depths and colours."""
+
+    def __init__(self, w, frames_np, device):
+        import torch
+        from paper_2505_18932_gb300 import gvs
+        self.torch, self.gvs, self.w = torch, gvs, w
+        self.tgt = w.targets[0]
+        self.depth = [torch.from_numpy(d).to(device) for _, d in frames_np]
+        self.color = [torch.from_numpy(np.ascontiguousarray(c).view(np.uint8).reshape(c.shape + (4,))).to(device)
+                      .float().div_(255.0) for c, _ in frames_np]
+        gts = []
+        for t in range(len(frames_np)):
+            rgb, _ = w.render_target_gt(self.tgt, t)
+            gts.append(torch.from_numpy(np.ascontiguousarray(rgb[..., :3], np.float32)).to(device) / 255.0)
+        self.gt = gts
+        self.cfg = dict(num_samples=w.num_samples, z_near=w.z_near, z_far=w.z_far, mu=w.mu)
+        self.half = False
+
+    def step(self, i, events=None):
+        torch, gvs, w = self.torch, self.gvs, self.w
+        cur = i % len(self.depth)
+        d = self.depth[cur].detach().requires_grad_(True)
+        c = self.color[cur].detach().requires_grad_(True)
+        fused, _ = gvs.FuseDepth.apply(d, w.inputs, self.tgt, self.cfg)
+        color, wdepth, alpha = gvs.SoftSplat.apply(d, c, w.inputs, self.tgt, {"mu_band": w.mu})
+        a = alpha.to(torch.float32).unsqueeze(-1)
+        asum = a.sum(0)
+        valid = asum > 0
+        blend = (color[..., :3] * a).sum(0) / asum.clamp_min(1.0)
+        l1 = ((blend - self.gt[cur]).abs() * valid).sum() / (3.0 * valid.sum().clamp_min(1))
+        dblend = (wdepth * alpha).sum(0) / asum[..., 0].clamp_min(1.0)
+        dvalid = valid[..., 0] & (fused > 0)
+        ldepth = ((fused - dblend).abs() * dvalid).sum() / (len(w.inputs) * dvalid.numel())
+        loss = 0.8 * l1 + 0.1 * ldepth
+        loss.backward()
+        self.last = (d.grad, c.grad, loss.detach())
 
 
 def time_form(pipe, steps):
@@ -319,6 +367,12 @@ def time_form(pipe, steps):
     torch.cuda.synchronize()
     return {"ms_per_step": round(a.elapsed_time(b) / steps, 4), "steps": steps,
             "storage": "depth f16, (d, w) map half2, FP32 arithmetic" if pipe.half else "f32"}
+
+
+def form_line(name, w, f, note):
+    tpx = w.targets[0].width * w.targets[0].height
+    return {**f, "value": round(tpx / (f["ms_per_step"] * 1e-3) / 1e6, 3), "unit": "target Mpix/s",
+            "workload": w.name, "note": note}
 
 
 def recorded_traffic(kernel_file="fuse_kernel_traffic.txt"):
