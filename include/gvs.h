@@ -67,6 +67,7 @@ extern "C" {
 #define GVS_MAX_DIM 16384       /* width and height limit of every image */
 #define GVS_MAX_SAMPLES 32767   /* samples per ray (crossing index is int16) */
 #define GVS_MAX_WINDOW 15       /* confidence window side (odd) */
+#define GVS_MAX_BATCH_ITEMS 1024 /* (frame, target) items of one batched fusion */
 
 typedef enum {
     GVS_OK = 0,
@@ -108,6 +109,8 @@ typedef struct {
     int32_t normalize;         /* 0: S = sum w*clamp (paper); 1: S / W */
     int32_t depth_dtype;       /* GVS_F32 or GVS_F16: element type of in_depths */
     int32_t map_dtype;         /* GVS_F32: (d, omega) as float2; GVS_F16: as half2 (omega rounded to half) */
+    int32_t variant;           /* 0..3: bundle shape and slab-test lengths of the march; every variant gives
+                                  the same result, the autotuner picks the fastest (0 = default) */
 } gvs_fuse_params;
 
 /* Forward splat (Sec. 3.1, Supplement A.3). */
@@ -290,6 +293,42 @@ GVS_API gvs_status gvs_soft_splat_backward(const gvs_camera *in_cams, const void
                                            const float *warped_color, const float *warped_depth,
                                            const float *weight_sum, const float *grad_color, const float *grad_depth,
                                            float *grad_in_depth, float *grad_in_color, void *stream);
+
+/*
+ * Batched fusion: many (frame, target) items in one persistent launch.  Each
+ * item fuses the map of one frame (gvs_weight_map) into one target camera,
+ * exactly as gvs_fuse_depth_from_map would; targets may differ in size.  The
+ * launch keeps every SM busy with one grid that takes bundles of target pixels
+ * from a global counter until all items are done (no block waits on another),
+ * and is a plain kernel launch plus a 4-byte reset, so it can be captured in a
+ * CUDA graph.
+ */
+typedef struct {
+    const void *map;           /* the frame's map, as from gvs_weight_map */
+    size_t map_bytes;
+    const gvs_camera *target;  /* host, read during gvs_fuse_batch_create */
+    float *fused_depth;        /* device [target.height][target.width] */
+    int16_t *crossing;         /* device, or NULL */
+} gvs_fuse_item;
+
+typedef struct gvs_fuse_batch gvs_fuse_batch;  /* opaque host object */
+
+/* Device table bytes for n_items items. */
+GVS_API size_t gvs_fuse_batch_bytes(int32_t n_items);
+
+/* Validates the items (all with the same input views and params), writes their
+ * descriptors into `table` (device, caller-owned, >= gvs_fuse_batch_bytes)
+ * with a synchronous copy -- call it outside any stream capture -- and returns
+ * a host handle.  The maps, outputs and table must outlive the handle. */
+GVS_API gvs_status gvs_fuse_batch_create(const gvs_camera *in_cams, int32_t n_views, const gvs_fuse_item *items,
+                                         int32_t n_items, const gvs_fuse_params *params, void *table,
+                                         size_t table_bytes, gvs_fuse_batch **out);
+
+/* Enqueues the batched fusion on `stream`.  Launches that share a table must
+ * not overlap. */
+GVS_API gvs_status gvs_fuse_batch_launch(const gvs_fuse_batch *batch, void *stream);
+
+GVS_API void gvs_fuse_batch_destroy(gvs_fuse_batch *batch);
 
 /* Workspace bytes for gvs_forward_splat: one 64-bit z-buffer of the target size.
  * A workspace holding several such buffers lets several views splat in one pass. */

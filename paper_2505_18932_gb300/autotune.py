@@ -1,0 +1,81 @@
+"""Autotuner for the fusion march: picks the bundle shape / slab-test lengths
+(gvs_fuse_params.variant) that runs fastest on a given workload.
+
+Every variant computes the same fused depth bit for bit; only the time
+differs.  Each candidate is timed with CUDA events on the caller's stream
+after a warm-up, and the winner is cached in a JSON file keyed by the device
+(name, SM count) and a hash of the workload's shape, so a later process with
+the same workload reuses it without timing.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+import threading
+
+import torch
+
+CACHE_PATH = os.environ.get("GVS_AUTOTUNE_CACHE",
+                            os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json"))
+VARIANTS = (0, 1, 2, 3)
+_lock = threading.Lock()
+
+
+def device_key() -> str:
+    p = torch.cuda.get_device_properties(torch.cuda.current_device())
+    return f"{p.name}|{p.multi_processor_count}"
+
+
+def workload_key(**shape) -> str:
+    blob = json.dumps(shape, sort_keys=True, default=str).encode()
+    return hashlib.sha256(blob).hexdigest()[:16]
+
+
+def _load_cache() -> dict:
+    try:
+        with open(CACHE_PATH) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(key: str, entry: dict) -> None:
+    with _lock:
+        cache = _load_cache()
+        cache[key] = entry
+        os.makedirs(os.path.dirname(CACHE_PATH), exist_ok=True)
+        tmp = CACHE_PATH + f".tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(cache, f, indent=1, sort_keys=True)
+        os.replace(tmp, CACHE_PATH)
+
+
+def time_ms(fn, warmup: int = 2, reps: int = 5) -> float:
+    """Median time of fn() on the current stream, CUDA events around each call."""
+    for _ in range(warmup):
+        fn()
+    times = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    times.sort()
+    return times[len(times) // 2]
+
+
+def choose(shape: dict, make_runner, candidates=VARIANTS, use_cache: bool = True):
+    """Return (best variant, {variant: ms}).  make_runner(variant) -> zero-argument callable
+    that enqueues one run of the workload with that variant."""
+    key = device_key() + "|" + workload_key(**shape)
+    if use_cache:
+        hit = _load_cache().get(key)
+        if hit is not None and hit.get("variant") in candidates:
+            return hit["variant"], {int(k): v for k, v in hit.get("ms", {}).items()}
+    timings = {v: time_ms(make_runner(v)) for v in candidates}
+    best = min(timings, key=timings.get)
+    _store(key, {"variant": best, "ms": timings, "shape": shape})
+    return best, timings

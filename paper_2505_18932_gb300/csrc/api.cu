@@ -8,6 +8,8 @@
 #include <string.h>
 
 #include <mutex>
+#include <new>
+#include <vector>
 
 #include "gvs_internal.cuh"
 
@@ -170,6 +172,7 @@ gvs_status check_fuse_common(const gvs_camera *in_cams, int32_t n_views, const g
         return fail(GVS_ERR_UNSUPPORTED, "fuse: depth_dtype must be GVS_F32 or GVS_F16");
     if (p.map_dtype != GVS_F32 && p.map_dtype != GVS_F16)
         return fail(GVS_ERR_UNSUPPORTED, "fuse: map_dtype must be GVS_F32 or GVS_F16");
+    if (p.variant < 0 || p.variant > 3) return fail(GVS_ERR_INVALID_ARG, "fuse: variant must be in [0, 3]");
     if (!fused_depth) return fail(GVS_ERR_INVALID_ARG, "fuse: fused_depth is NULL");
     if (!aligned(fused_depth, 16) || (crossing && !aligned(crossing, 16)))
         return fail(GVS_ERR_INVALID_ARG, "fuse: arrays must be 16-byte aligned");
@@ -212,6 +215,7 @@ gvs::FuseArgs fuse_args(const gvs_camera *in_cams, const void *map, int32_t n_vi
     a.behind = (float)(1.0001 * (double)p.mu);
     a.normalize = p.normalize;
     a.map_dtype = p.map_dtype;
+    a.variant = p.variant;
     a.fused = fused;
     a.crossing = crossing;
     for (int k = 0; k < n_views; ++k) a.xf[k] = compose(in_cams[k], *target);
@@ -571,3 +575,73 @@ extern "C" gvs_status gvs_forward_splat_noalloc(const gvs_camera *in_cams, const
                              warped_rgba, warped_depth, alpha, guided, keys, kNoAllocKeys * sizeof(unsigned long long),
                              stream);
 }
+
+// ---------------------------------------------------------------------------
+// Batched fusion: many (frame, target) items, one persistent launch.
+// ---------------------------------------------------------------------------
+struct gvs_fuse_batch {
+    int K, map_dtype, variant, n_items, total;
+    gvs::BatchItem *d_items;
+    unsigned *d_counter;
+};
+
+extern "C" {
+
+size_t gvs_fuse_batch_bytes(int32_t n_items) {
+    if (n_items < 0) return 0;
+    return align_up((size_t)n_items * sizeof(gvs::BatchItem), 256) + 256;
+}
+
+gvs_status gvs_fuse_batch_create(const gvs_camera *in_cams, int32_t n_views, const gvs_fuse_item *items,
+                                 int32_t n_items, const gvs_fuse_params *params, void *table, size_t table_bytes,
+                                 gvs_fuse_batch **out) {
+    if (!out) return fail(GVS_ERR_INVALID_ARG, "fuse batch: out is NULL");
+    *out = nullptr;
+    if (n_items < 1 || n_items > GVS_MAX_BATCH_ITEMS || !items)
+        return fail(GVS_ERR_INVALID_ARG, "fuse batch: n_items must be in [1, %d]", GVS_MAX_BATCH_ITEMS);
+    if (n_views < 1) return fail(GVS_ERR_INVALID_ARG, "fuse batch: needs at least one input view");
+    const size_t need = gvs_fuse_batch_bytes(n_items);
+    if (!table || table_bytes < need || !aligned(table, 256))
+        return fail(GVS_ERR_WORKSPACE, "fuse batch: table needs %zu bytes, 256-byte aligned", need);
+    std::vector<gvs::BatchItem> host((size_t)n_items);
+    int64_t total = 0;
+    int32_t W = 0, H = 0;
+    for (int i = 0; i < n_items; ++i) {
+        const gvs_fuse_item &it = items[i];
+        gvs_status s = check_fuse_common(in_cams, n_views, it.target, params, it.fused_depth, it.crossing, &W, &H);
+        if (s != GVS_OK) return s;
+        const size_t need_map = gvs_fuse_workspace_bytes(n_views, W, H);
+        if (!it.map || it.map_bytes < need_map || !aligned(it.map, 256))
+            return fail(GVS_ERR_WORKSPACE, "fuse batch: item %d map needs %zu bytes, 256-byte aligned", i, need_map);
+        host[i].args = fuse_args(in_cams, it.map, n_views, W, H, it.target, *params, it.fused_depth, it.crossing);
+        host[i].bundle_begin = (int)total;
+        total += gvs::bundle_count(it.target->width, it.target->height, n_views, params->variant);
+        if (total > INT32_MAX / 2) return fail(GVS_ERR_UNSUPPORTED, "fuse batch: too many target pixels");
+    }
+    cudaError_t e = cudaMemcpy(table, host.data(), host.size() * sizeof(gvs::BatchItem), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "fuse batch: copying the item table");
+    gvs_fuse_batch *b = new (std::nothrow) gvs_fuse_batch;
+    if (!b) return fail(GVS_ERR_INVALID_ARG, "fuse batch: out of host memory");
+    b->K = n_views;
+    b->map_dtype = params->map_dtype;
+    b->variant = params->variant;
+    b->n_items = n_items;
+    b->total = (int)total;
+    b->d_items = reinterpret_cast<gvs::BatchItem *>(table);
+    b->d_counter = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(table) +
+                                                align_up((size_t)n_items * sizeof(gvs::BatchItem), 256));
+    *out = b;
+    return GVS_OK;
+}
+
+gvs_status gvs_fuse_batch_launch(const gvs_fuse_batch *b, void *stream) {
+    if (!b) return fail(GVS_ERR_INVALID_ARG, "fuse batch: NULL batch");
+    cudaError_t e = gvs::launch_fuse_batch(b->d_items, b->n_items, b->total, b->d_counter, b->K, b->map_dtype,
+                                           b->variant, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "fuse batch: launch");
+    return GVS_OK;
+}
+
+void gvs_fuse_batch_destroy(gvs_fuse_batch *b) { delete b; }
+
+}  // extern "C"

@@ -1,0 +1,59 @@
+// Batched fusion: many (frame, target) items in one persistent launch.
+#include "fuse_march.cuh"
+
+namespace gvs {
+namespace {
+
+// Many (frame, target) items in one persistent launch: each warp takes the
+// next bundle index from a global counter until every item's bundles are
+// taken, and marches it with that item's arguments.  No warp ever waits on
+// another; the counter is reset before each launch.
+template <int KMAX, typename MT, typename T>
+__global__ void __launch_bounds__(32 * FZ_WARPS, GVS_FUSE_MIN_BLOCKS)
+    fuse_batch_kernel(const BatchItem *__restrict__ items, int n_items, int total, unsigned *__restrict__ counter) {
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int b = 0;
+        if (lane == 0) b = (int)atomicAdd(counter, 1u);
+        b = __shfl_sync(0xffffffffu, b, 0);
+        if (b >= total) break;
+        int lo = 0, hi = n_items - 1;  // last item whose first bundle is <= b
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (items[mid].bundle_begin <= b) lo = mid; else hi = mid - 1;
+        }
+        march_bundle<KMAX, MT, T>(items[lo].args, b - items[lo].bundle_begin, lane);
+    }
+}
+
+template <int KMAX, typename MT, typename T>
+void launch_batch_t(const BatchItem *items, int n_items, int total, unsigned *counter, cudaStream_t st) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fuse_batch_kernel<KMAX, MT, T>, 32 * FZ_WARPS, 0) !=
+            cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    const int64_t want = ((int64_t)total + FZ_WARPS - 1) / FZ_WARPS;
+    int64_t grid = (int64_t)per_sm * device_sm_count();
+    if (grid > want) grid = want;
+    if (grid < 1) grid = 1;
+    fuse_batch_kernel<KMAX, MT, T><<<(unsigned)grid, 32 * FZ_WARPS, 0, st>>>(items, n_items, total, counter);
+}
+
+template <int KMAX, typename MT, typename T>
+struct BatchLaunch {
+    static void run(const BatchItem *items, int n, int total, unsigned *counter, cudaStream_t st) {
+        launch_batch_t<KMAX, MT, T>(items, n, total, counter, st);
+    }
+};
+
+}  // namespace
+
+cudaError_t launch_fuse_batch(const BatchItem *items, int n_items, int total, unsigned *counter, int K, int map_dtype,
+                              int variant, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    by_kmax<BatchLaunch>(K, map_dtype, variant, items, n_items, total, counter, st);
+    return cudaGetLastError();
+}
+}  // namespace gvs

@@ -1,0 +1,226 @@
+// Adjoint of the image-based TSDF fusion (Supplement A.1, Eq. 3 differentiated).
+#include "fuse_march.cuh"
+
+namespace gvs {
+namespace {
+
+// ---------------------------------------------------------------------------
+// Adjoint of the fused depth (normalize = 0), in two passes.
+//
+// D = z_s + dz S_s / (S_s - S_{s+1}) depends on the inputs only through the
+// two bracketing samples.  For a view contributing at one of them with
+// clamped distance c, weight omega and signed distance sdf at input pixel q:
+//   dD/dd(q) += g_S omega [-1 < sdf < 1] / mu                 (the clamp)
+//   dD/dd(n) += g_S c domega(q)/dd(n)   for q's window entries n (the weight)
+// with g_S = dD/dS of that sample.  The weight's derivative is linear in
+// g_S c, so pass 1 (one thread per target pixel) accumulates, per sampled
+// input pixel q, A(q) = sum g_S c and B(q) = sum g_S omega [...] / mu with one
+// float2 atomic per (sample, view); pass 2 (one thread per input pixel x)
+// applies domega/dnu and the window:
+//   grad(x) = B(x) + P(x) sum_{entries n of x} 2 (d_x - d_n) [|d_x - d_n| < mu]
+//           + sum_{c whose window holds x, with multiplicity}
+//                 P(c) (-2) (d_c - d_x) [|d_c - d_x| < mu]
+// where P(c) = A(c) domega/dnu(c) (0 when the weight is saturated or c is
+// invalid).  Nothing of size D x H x W is stored; the bracketing samples are
+// recomputed by the forward's own code, so they are bit-identical to it.
+// ---------------------------------------------------------------------------
+
+template <int KMAX, typename MT>
+__global__ void __launch_bounds__(128) fuse_bwd_scatter(const FuseArgs a, const int16_t *__restrict__ crossing,
+                                                        const float *__restrict__ grad_fused, float2 *__restrict__ acc) {
+    const int i = blockIdx.x * 16 + threadIdx.x;
+    const int j = blockIdx.y * 8 + threadIdx.y;
+    if (i >= a.Wt || j >= a.Ht) return;
+    const size_t o = (size_t)j * a.Wt + i;
+    const int s = crossing[o];
+    const float G = grad_fused[o];
+    if (s < 0 || s + 1 >= a.D || G == 0.0f) return;
+    const float fi = (float)i, fj = (float)j;
+    Ray ray[KMAX];
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+        if (k < a.K) {
+            const float *M = a.xf[k].M;
+            ray[k].ax = __fmaf_rn(M[0], fi, __fmaf_rn(M[1], fj, M[2]));
+            ray[k].ay = __fmaf_rn(M[3], fi, __fmaf_rn(M[4], fj, M[5]));
+            ray[k].az = __fmaf_rn(M[6], fi, __fmaf_rn(M[7], fj, M[8]));
+        }
+    }
+    const float z0 = __fmaf_rn((float)s, a.dz, a.zn), z1 = __fmaf_rn((float)(s + 1), a.dz, a.zn);
+    float S0, S1, W0, W1;
+    evaluate_sample<KMAX, MT>(a, ray, z0, S0, W0);
+    evaluate_sample<KMAX, MT>(a, ray, z1, S1, W1);
+    const float den = (S0 - S1) * (S0 - S1);
+    const float gS[2] = {G * (z1 - z0) * (-S1) / den, G * (z1 - z0) * S0 / den};
+    const MT *map = reinterpret_cast<const MT *>(a.dw);
+    const size_t plane = (size_t)a.W * a.H;
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        const float zs = t ? z1 : z0;
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k) {
+            if (k < a.K) {
+                const float hz = __fmaf_rn(zs, ray[k].az, a.xf[k].b[2]);
+                if (hz > 1e-6f) {
+                    const float hx = __fmaf_rn(zs, ray[k].ax, a.xf[k].b[0]);
+                    const float hy = __fmaf_rn(zs, ray[k].ay, a.xf[k].b[1]);
+                    int u, v;
+                    nearest_pixel(hx, hy, hz, u, v);
+                    if ((unsigned)u < (unsigned)a.W && (unsigned)v < (unsigned)a.H) {
+                        const size_t q = (size_t)k * plane + (size_t)v * a.W + u;
+                        const float2 p = load_map(&map[q]);
+                        const float sdf = (p.x - hz) * a.inv_mu;
+                        if (sdf >= -1.0f && p.y > 0.0f) {
+                            const float c = fminf(sdf, 1.0f);
+                            const float inband = (sdf > -1.0f && sdf < 1.0f) ? a.inv_mu : 0.0f;
+                            atomicAdd(&acc[q], make_float2(gS[t] * c, gS[t] * p.y * inband));
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Entries e in [-R, R] of a clamp-to-edge window centred at c that land on x
+// (one axis, image extent n).
+__device__ __forceinline__ int window_multiplicity(int c, int x, int n, int R) {
+    if (c < 0 || c >= n) return 0;
+    if (n == 1) return 2 * R + 1;
+    if (x == 0) return max(0, R - c + 1);
+    if (x == n - 1) return max(0, c - (n - 1) + R + 1);
+    return abs(c - x) <= R ? 1 : 0;
+}
+
+constexpr int GB_TX = 32;
+constexpr int GB_TY = 8;
+
+template <int R, typename DT>
+__global__ void __launch_bounds__(GB_TX *GB_TY) fuse_bwd_gather(const DT *__restrict__ depth,
+                                                                const float2 *__restrict__ acc,
+                                                                float *__restrict__ grad, int W, int H, float mu,
+                                                                float wconst, float inv_w2) {
+    constexpr int DW = GB_TX + 4 * R, DH = GB_TY + 4 * R;   // depths: outputs + 2R halo
+    constexpr int PW = GB_TX + 2 * R, PH = GB_TY + 2 * R;   // P(c): outputs + R halo
+    __shared__ float dt[DH][DW];
+    __shared__ float pt[PH][PW];
+    const int k = blockIdx.z;
+    const DT *dep = depth + (size_t)k * W * H;
+    const float2 *ak = acc + (size_t)k * W * H;
+    const int bx = blockIdx.x * GB_TX, by = blockIdx.y * GB_TY;
+    const int tid = threadIdx.y * GB_TX + threadIdx.x;
+    for (int e = tid; e < DW * DH; e += GB_TX * GB_TY) {
+        const int sy = e / DW, sx = e - sy * DW;
+        const int gx = min(max(bx - 2 * R + sx, 0), W - 1), gy = min(max(by - 2 * R + sy, 0), H - 1);
+        const float d = load_depth(&dep[(size_t)gy * W + gx]);
+        dt[sy][sx] = valid_depth(d) ? d : __int_as_float(0x7fc00000);
+    }
+    __syncthreads();
+    // P(c) = A(c) domega/dnu(c) on the outputs and an R halo
+    for (int e = tid; e < PW * PH; e += GB_TX * GB_TY) {
+        const int py = e / PW, px = e - py * PW;
+        const int cx = bx - R + px, cy = by - R + py;
+        float P = 0.0f;
+        if (cx >= 0 && cx < W && cy >= 0 && cy < H) {
+            const float A = ak[(size_t)cy * W + cx].x;
+            const float dc = dt[py + R][px + R];
+            if (A != 0.0f && dc == dc) {
+                float nu = 0.0f;
+                for (int dy = 0; dy <= 2 * R; ++dy)
+                    for (int dx = 0; dx <= 2 * R; ++dx) {
+                        const float t = fminf(fabsf(dc - dt[py + dy][px + dx]), mu);
+                        nu = fmaf(t, t, nu);
+                    }
+                const float unclamped = nu > 0.0f ? wconst * rsqrtf(nu * inv_w2) : 2.0f;
+                if (unclamped < 1.0f) P = A * (-0.5f * unclamped / nu);
+            }
+        }
+        pt[py][px] = P;
+    }
+    __syncthreads();
+    const int x = bx + threadIdx.x, y = by + threadIdx.y;
+    if (x >= W || y >= H) return;
+    const float dx0 = dt[threadIdx.y + 2 * R][threadIdx.x + 2 * R];
+    float g = ak[(size_t)y * W + x].y;  // B(x)
+    if (dx0 == dx0) {
+        const float Px = pt[threadIdx.y + R][threadIdx.x + R];
+        if (Px != 0.0f) {
+            float sum = 0.0f;
+            for (int ey = -R; ey <= R; ++ey)
+                for (int ex = -R; ex <= R; ++ex) {
+                    const float dn = dt[threadIdx.y + 2 * R + ey][threadIdx.x + 2 * R + ex];
+                    const float diff = dx0 - dn;
+                    if (fabsf(diff) < mu) sum += 2.0f * diff;  // false for a NaN (invalid) neighbour
+                }
+            g += Px * sum;
+        }
+        for (int cyo = -R; cyo <= R; ++cyo) {
+            const int my = window_multiplicity(y + cyo, y, H, R);
+            if (my == 0) continue;
+            for (int cxo = -R; cxo <= R; ++cxo) {
+                const int mx = window_multiplicity(x + cxo, x, W, R);
+                if (mx == 0) continue;
+                const float Pc = pt[threadIdx.y + R + cyo][threadIdx.x + R + cxo];
+                if (Pc == 0.0f) continue;
+                const float diff = dt[threadIdx.y + 2 * R + cyo][threadIdx.x + 2 * R + cxo] - dx0;
+                if (fabsf(diff) < mu) g += (float)(mx * my) * Pc * (-2.0f) * diff;
+            }
+        }
+    }
+    grad[(size_t)k * W * H + (size_t)y * W + x] = g;
+}
+
+template <int R, typename DT>
+cudaError_t launch_bwd_gather_r(const void *depth, const float2 *acc, float *grad, int K, int W, int H, float mu,
+                                float wconst, float inv_w2, cudaStream_t st) {
+    dim3 grid((W + GB_TX - 1) / GB_TX, (H + GB_TY - 1) / GB_TY, K);
+    fuse_bwd_gather<R, DT><<<grid, dim3(GB_TX, GB_TY), 0, st>>>(reinterpret_cast<const DT *>(depth), acc, grad, W, H,
+                                                                mu, wconst, inv_w2);
+    return cudaGetLastError();
+}
+
+template <typename DT>
+cudaError_t launch_bwd_gather(const void *depth, const float2 *acc, float *grad, int K, int W, int H, float mu,
+                              float wconst, int window, cudaStream_t st) {
+    const float inv_w2 = (float)(1.0 / ((double)window * (double)window));
+    switch (window / 2) {
+        case 0: return launch_bwd_gather_r<0, DT>(depth, acc, grad, K, W, H, mu, wconst, inv_w2, st);
+        case 1: return launch_bwd_gather_r<1, DT>(depth, acc, grad, K, W, H, mu, wconst, inv_w2, st);
+        case 2: return launch_bwd_gather_r<2, DT>(depth, acc, grad, K, W, H, mu, wconst, inv_w2, st);
+        case 3: return launch_bwd_gather_r<3, DT>(depth, acc, grad, K, W, H, mu, wconst, inv_w2, st);
+        case 4: return launch_bwd_gather_r<4, DT>(depth, acc, grad, K, W, H, mu, wconst, inv_w2, st);
+        case 5: return launch_bwd_gather_r<5, DT>(depth, acc, grad, K, W, H, mu, wconst, inv_w2, st);
+        case 6: return launch_bwd_gather_r<6, DT>(depth, acc, grad, K, W, H, mu, wconst, inv_w2, st);
+        case 7: return launch_bwd_gather_r<7, DT>(depth, acc, grad, K, W, H, mu, wconst, inv_w2, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_fuse_backward(const FuseArgs &a, const void *depth, int depth_dtype, const int16_t *crossing,
+                                 const float *grad_fused, float *grad_depths, float2 *acc, float mu, float wconst,
+                                 int window, cudaStream_t st) {
+    if (a.K == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(acc, 0, (size_t)a.K * a.W * a.H * sizeof(float2), st);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((a.Wt + 15) / 16, (a.Ht + 7) / 8), block(16, 8);
+    if (a.map_dtype == GVS_F16) {
+        if (a.K <= 4) fuse_bwd_scatter<4, __half2><<<grid, block, 0, st>>>(a, crossing, grad_fused, acc);
+        else if (a.K <= 8) fuse_bwd_scatter<8, __half2><<<grid, block, 0, st>>>(a, crossing, grad_fused, acc);
+        else if (a.K <= 16) fuse_bwd_scatter<16, __half2><<<grid, block, 0, st>>>(a, crossing, grad_fused, acc);
+        else fuse_bwd_scatter<32, __half2><<<grid, block, 0, st>>>(a, crossing, grad_fused, acc);
+    } else {
+        if (a.K <= 4) fuse_bwd_scatter<4, float2><<<grid, block, 0, st>>>(a, crossing, grad_fused, acc);
+        else if (a.K <= 8) fuse_bwd_scatter<8, float2><<<grid, block, 0, st>>>(a, crossing, grad_fused, acc);
+        else if (a.K <= 16) fuse_bwd_scatter<16, float2><<<grid, block, 0, st>>>(a, crossing, grad_fused, acc);
+        else fuse_bwd_scatter<32, float2><<<grid, block, 0, st>>>(a, crossing, grad_fused, acc);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return depth_dtype == GVS_F16
+               ? launch_bwd_gather<__half>(depth, acc, grad_depths, a.K, a.W, a.H, mu, wconst, window, st)
+               : launch_bwd_gather<float>(depth, acc, grad_depths, a.K, a.W, a.H, mu, wconst, window, st);
+}
+
+}  // namespace gvs

@@ -1,0 +1,311 @@
+// Device code shared by the fusion kernels (forward, batched, backward):
+// map and depth loads, the nearest-pixel contract, the per-sample TSDF sum,
+// the warp-bundle march with its slab tests, and the kernel-variant dispatch.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <math.h>
+
+#include "gvs_internal.cuh"
+
+namespace gvs {
+namespace {
+
+#define kInf __int_as_float(0x7f800000)
+
+__device__ __forceinline__ bool valid_depth(float d) { return isfinite(d) && d > 0.0f; }
+
+// Depth element load (FP32 or FP16) widened to FP32.
+__device__ __forceinline__ float load_depth(const float *p) { return __ldg(p); }
+__device__ __forceinline__ float load_depth(const __half *p) { return __half2float(__ldg(p)); }
+
+// The depth as the map stores it: exact for float2, rounded to half for half2.
+__device__ __forceinline__ float as_stored(float d, float2 *) { return d; }
+__device__ __forceinline__ float as_stored(float d, __half2 *) { return __half2float(__float2half_rn(d)); }
+
+__device__ __forceinline__ void store_map(float2 *p, float d, float w) { *p = make_float2(d, w); }
+__device__ __forceinline__ void store_map(__half2 *p, float d, float w) { *p = __floats2half2_rn(d, w); }
+
+__device__ __forceinline__ float2 load_map(const float2 *p) { return __ldg(p); }
+__device__ __forceinline__ float2 load_map(const __half2 *p) { return __half22float2(__ldg(p)); }
+
+// Nearest integers (ties to even) of the exact real quotients hx/hz, hy/hz,
+// hz > 0.  q = h * r with r ~ 1/hz (relative error a few ulp) is within 0.01
+// of the quotient for any quotient that can land inside an image
+// (|q| < 2^14 + 1); only when a q sits within 0.01 of a half-integer is the
+// decision re-taken from the signs of the exact residuals h - (n +/- 0.5) hz
+// (one rounding each in the FMA, which never changes a sign).  The fix-up
+// leaves n unchanged when q is not near a half-integer, so it runs for both
+// coordinates under one branch.
+__device__ __forceinline__ float exact_nearest_fixup(float num, float den, float n) {
+    if (fabsf(n) < 4194304.0f) {
+        const float hi = __fmaf_rn(-(n + 0.5f), den, num);
+        const float lo = __fmaf_rn(-(n - 0.5f), den, num);
+        const bool odd = (__float2int_rz(n) & 1) != 0;
+        if (hi > 0.0f || (hi == 0.0f && odd)) n += 1.0f;
+        else if (lo < 0.0f || (lo == 0.0f && odd)) n -= 1.0f;
+    }
+    return n;
+}
+
+__device__ __forceinline__ void nearest_pixel(float hx, float hy, float hz, int &u, int &v) {
+    const float r = __fdividef(1.0f, hz);
+    const float qx = hx * r, qy = hy * r;
+    float nx = rintf(qx), ny = rintf(qy);
+    if (fmaxf(fabsf(qx - nx), fabsf(qy - ny)) > 0.49f) {
+        nx = exact_nearest_fixup(hx, hz, nx);
+        ny = exact_nearest_fixup(hy, hz, ny);
+    }
+    u = __float2int_rz(nx);
+    v = __float2int_rz(ny);
+}
+constexpr int FZ_WARPS = 4;
+#ifndef GVS_FUSE_MIN_BLOCKS
+#define GVS_FUSE_MIN_BLOCKS 8   // resident blocks per SM requested from the register allocator (64 registers)
+#endif
+constexpr int SKIP_COOL = 4;    // samples evaluated after both slab tests fail, before testing again
+
+// Bundle shape and slab-test lengths of the march.  Every variant computes the
+// same result; they differ only in speed, and the autotuner picks one per
+// workload (gvs_fuse_params.variant).
+//   bx x by : target pixels one warp marches together (bx * by = 32)
+//   llong   : samples per segment in the first slab test
+//   lshort  : samples per segment in the second test when the first fails
+template <int BX_, int BY_, int LLONG_, int LSHORT_>
+struct Tile {
+    static constexpr int bx = BX_, by = BY_, llong = LLONG_, lshort = LSHORT_;
+    static_assert(bx * by == 32, "a bundle is one warp");
+    static_assert(llong >= 1 && lshort >= 1, "skip lengths must advance the march");
+};
+using Tile0 = Tile<8, 4, 8, 2>;
+using Tile1 = Tile<8, 4, 16, 4>;
+using Tile2 = Tile<16, 2, 8, 2>;
+using Tile3 = Tile<4, 8, 8, 2>;
+
+struct Ray {
+    float ax, ay, az;
+};
+
+// The bundle's rays between depths z0 and z1 fill a truncated pyramid (convex,
+// 8 vertices: its 4 corner rays at z0 and z1).  In view k its points project
+// inside the hull of the 8 vertex projections and their projected depths lie
+// between the vertices' extremes (both statements exact for an affine depth
+// and a projective map on a convex body in front of the camera; FP32 rounding
+// of the samples is covered by a 1 pixel and 1e-6 relative margin).  The view
+// is free over the slab when every valid depth in the pixel box around that
+// hull is strictly beyond the largest projected depth (sdf > 0: a positive
+// term) or at least 1.0001 mu in front of the smallest (sdf < -1: cut off), or
+// the box is outside the image, or the slab is behind the camera.  One bounds
+// load: the finest tile level whose overlapping 2x2 block covers the box, else
+// the whole view.  When every view is free over the slab, no sample of it can
+// end a crossing (S > 0 wherever W > 0).
+__device__ __forceinline__ bool slab_view_free(const FuseArgs &a, int k, const Ray (&corner)[4], float z0,
+                                               float z1) {
+    const float b0 = a.xf[k].b[0], b1 = a.xf[k].b[1], b2 = a.xf[k].b[2];
+    float xlo = kInf, xhi = -kInf, ylo = kInf, yhi = -kInf, zlo = kInf, zhi = -kInf;
+    bool any_front = false, any_back = false;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const float z = (c & 1) ? z1 : z0;
+        const Ray &r = corner[c >> 1];
+        const float hz = __fmaf_rn(z, r.az, b2);
+        const float q = __fdividef(1.0f, hz);
+        const float x = __fmaf_rn(z, r.ax, b0) * q;
+        const float y = __fmaf_rn(z, r.ay, b1) * q;
+        any_front |= hz > 1e-6f;
+        any_back |= !(hz > 1e-6f);
+        xlo = fminf(xlo, x); xhi = fmaxf(xhi, x);
+        ylo = fminf(ylo, y); yhi = fmaxf(yhi, y);
+        zlo = fminf(zlo, hz); zhi = fmaxf(zhi, hz);
+    }
+    zhi += 1e-6f * fabsf(zhi);
+    zlo -= 1e-6f * fabsf(zlo);
+    if (!any_front && zhi <= 1e-6f) return true;  // behind the camera throughout
+    if (any_back) return false;                   // crosses the camera plane: do not try
+    xlo -= 1.0f; xhi += 1.0f; ylo -= 1.0f; yhi += 1.0f;
+    if (!(xlo <= xhi && ylo <= yhi)) return false;  // NaN
+    if (xhi < 0.0f || yhi < 0.0f || xlo > (float)(a.W - 1) || ylo > (float)(a.H - 1)) return true;  // outside
+    const int bx0 = min(max(__float2int_rd(xlo), 0), a.W - 1), bx1 = min(max(__float2int_ru(xhi), 0), a.W - 1);
+    const int by0 = min(max(__float2int_rd(ylo), 0), a.H - 1), by1 = min(max(__float2int_ru(yhi), 0), a.H - 1);
+    // a box spanning fewer than 2^l pixels per axis covers at most 2x2 tiles of level l
+    const int span = max(bx1 - bx0, by1 - by0);
+    const float2 *p;
+    if (span < 8)
+        p = a.ob[0] + ((size_t)k * a.th[0] + (by0 >> 3)) * a.tw[0] + (bx0 >> 3);
+    else if (span < 32)
+        p = a.ob[1] + ((size_t)k * a.th[1] + (by0 >> 5)) * a.tw[1] + (bx0 >> 5);
+    else if (span < 128)
+        p = a.ob[2] + ((size_t)k * a.th[2] + (by0 >> 7)) * a.tw[2] + (bx0 >> 7);
+    else
+        p = a.tg + k;
+    const float2 b = __ldg(p);
+    return zhi < b.x || zlo > b.y + a.behind;
+}
+
+// S and W of one sample (Supplement A.1), exactly as the full march computes them.
+template <int KMAX, typename MT>
+__device__ __forceinline__ void evaluate_sample(const FuseArgs &a, const Ray (&ray)[KMAX], float zs, float &S,
+                                                float &Wsum) {
+    const MT *map = reinterpret_cast<const MT *>(a.dw);
+    const size_t plane = (size_t)a.W * a.H;
+    S = 0.0f;
+    Wsum = 0.0f;
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+        if (k < a.K) {
+            const float hz = __fmaf_rn(zs, ray[k].az, a.xf[k].b[2]);
+            if (hz > 1e-6f) {
+                const float hx = __fmaf_rn(zs, ray[k].ax, a.xf[k].b[0]);
+                const float hy = __fmaf_rn(zs, ray[k].ay, a.xf[k].b[1]);
+                int u, v;
+                nearest_pixel(hx, hy, hz, u, v);
+                if ((unsigned)u < (unsigned)a.W && (unsigned)v < (unsigned)a.H) {
+                    const float2 p = load_map(&map[(size_t)k * plane + (size_t)v * a.W + u]);
+                    const float sdf = (p.x - hz) * a.inv_mu;
+                    if (sdf >= -1.0f) {
+                        S = fmaf(p.y, fminf(sdf, 1.0f), S);
+                        Wsum += p.y;
+                    }
+                }
+            }
+        }
+    }
+    if (a.normalize && Wsum > 0.0f) S = S / Wsum;
+}
+
+// One warp per bundle of BX x BY target pixels.  The warp marches one sample
+// index s for all its rays: cooperative slab tests (lane = view x segment,
+// 32 / KMAX consecutive segments at once) skip runs of samples that hold no
+// crossing end for any ray of the bundle; otherwise every ray still marching
+// evaluates sample s (all KMAX views unrolled, one 8-byte gather each) and
+// checks its own crossing.  The result equals the full uniform march.
+template <int KMAX, typename MT, typename T>
+__device__ __forceinline__ void march_bundle(const FuseArgs &a, int bundle, int lane) {
+    constexpr int BX = T::bx, BY = T::by, SKIP_LONG = T::llong, SKIP_SHORT = T::lshort;
+    constexpr int NSEG = 32 / KMAX;
+    constexpr unsigned SEGMASK = KMAX == 32 ? 0xffffffffu : ((1u << KMAX) - 1u);
+    const int nbx = (a.Wt + BX - 1) / BX;
+    const int i0 = (bundle % nbx) * BX, j0 = (bundle / nbx) * BY;
+    const int i1 = min(i0 + BX - 1, a.Wt - 1), j1 = min(j0 + BY - 1, a.Ht - 1);
+    const int i = i0 + (lane % BX), j = j0 + (lane / BX);
+    const bool inside = i < a.Wt && j < a.Ht;
+    const float fi = (float)min(i, a.Wt - 1), fj = (float)min(j, a.Ht - 1);
+    Ray ray[KMAX];
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+        if (k < a.K) {
+            const float *M = a.xf[k].M;
+            ray[k].ax = __fmaf_rn(M[0], fi, __fmaf_rn(M[1], fj, M[2]));
+            ray[k].ay = __fmaf_rn(M[3], fi, __fmaf_rn(M[4], fj, M[5]));
+            ray[k].az = __fmaf_rn(M[6], fi, __fmaf_rn(M[7], fj, M[8]));
+        }
+    }
+    // this lane's role in the slab tests: view tk of segment tseg
+    const int tk = lane % KMAX, tseg = lane / KMAX;
+    const bool tview = tk < a.K;
+    Ray corner[4];
+    {
+        const int kk = tview ? tk : 0;
+        const float *M = a.xf[kk].M;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float ci = (float)((c & 1) ? i1 : i0), cj = (float)((c & 2) ? j1 : j0);
+            corner[c].ax = __fmaf_rn(M[0], ci, __fmaf_rn(M[1], cj, M[2]));
+            corner[c].ay = __fmaf_rn(M[3], ci, __fmaf_rn(M[4], cj, M[5]));
+            corner[c].az = __fmaf_rn(M[6], ci, __fmaf_rn(M[7], cj, M[8]));
+        }
+    }
+    float S_prev = 0.0f, W_prev = 0.0f, z_prev = 0.0f;
+    bool have_prev = false;  // sample s-1 was evaluated (uniform across the warp)
+    bool done = !inside;
+    float out = 0.0f;
+    int idx = -1;
+    int s = 0;
+    int cool = 0;
+    bool shorter = false;
+    while (s < a.D) {
+        if (__all_sync(0xffffffffu, done)) break;
+        if (cool == 0 && s < a.D - 1) {
+            const int L = shorter ? SKIP_SHORT : SKIP_LONG;
+            const int sa = s + tseg * L;
+            bool f = false;
+            if (sa < a.D - 1) {
+                const int sb = min(sa + L, a.D - 1);
+                f = !tview || slab_view_free(a, tk, corner, __fmaf_rn((float)sa, a.dz, a.zn),
+                                             __fmaf_rn((float)sb, a.dz, a.zn));
+            }
+            const unsigned ball = __ballot_sync(0xffffffffu, f);
+            int nfree = 0;
+#pragma unroll
+            for (int g = 0; g < NSEG; ++g) {
+                if (nfree == g && ((ball >> (g * KMAX)) & SEGMASK) == SEGMASK) ++nfree;
+            }
+            if (nfree > 0) {
+                s = min(s + nfree * L, a.D - 1);  // samples up to s are not crossing ends; s is evaluated next
+                have_prev = false;
+                shorter = false;
+                continue;
+            }
+            if (!shorter && SKIP_SHORT < SKIP_LONG) {
+                shorter = true;
+                continue;
+            }
+            shorter = false;
+            cool = SKIP_COOL;
+        }
+        const float zs = __fmaf_rn((float)s, a.dz, a.zn);
+        if (!done) {
+            float S, Wsum;
+            evaluate_sample<KMAX, MT>(a, ray, zs, S, Wsum);
+            if (have_prev && W_prev > 0.0f && Wsum > 0.0f && S_prev > 0.0f && S <= 0.0f) {
+                out = z_prev + (zs - z_prev) * (S_prev / (S_prev - S));
+                idx = s - 1;
+                done = true;
+            }
+            S_prev = S;
+            W_prev = Wsum;
+            z_prev = zs;
+        }
+        have_prev = true;
+        ++s;
+        if (cool > 0) --cool;
+    }
+    if (inside) {
+        const size_t o = (size_t)j * a.Wt + i;
+        a.fused[o] = out;
+        if (a.crossing) a.crossing[o] = (int16_t)idx;
+    }
+}
+
+// Calls F<Tile_i>::run(...) for the variant; views counts other than 8 and 16
+// use the default tile only (fewer instantiations to build).
+template <int KMAX, typename MT, template <int, typename, typename> class F, typename... Args>
+void by_variant(int variant, Args... args) {
+    if (KMAX == 8 || KMAX == 16) {
+        switch (variant) {
+            case 1: F<KMAX, MT, Tile1>::run(args...); return;
+            case 2: F<KMAX, MT, Tile2>::run(args...); return;
+            case 3: F<KMAX, MT, Tile3>::run(args...); return;
+            default: break;
+        }
+    }
+    F<KMAX, MT, Tile0>::run(args...);
+}
+
+template <template <int, typename, typename> class F, typename... Args>
+void by_kmax(int K, int map_dtype, int variant, Args... args) {
+    if (map_dtype == GVS_F16) {
+        if (K <= 4) by_variant<4, __half2, F>(variant, args...);
+        else if (K <= 8) by_variant<8, __half2, F>(variant, args...);
+        else if (K <= 16) by_variant<16, __half2, F>(variant, args...);
+        else by_variant<32, __half2, F>(variant, args...);
+    } else {
+        if (K <= 4) by_variant<4, float2, F>(variant, args...);
+        else if (K <= 8) by_variant<8, float2, F>(variant, args...);
+        else if (K <= 16) by_variant<16, float2, F>(variant, args...);
+        else by_variant<32, float2, F>(variant, args...);
+    }
+}
+
+}  // namespace
+}  // namespace gvs

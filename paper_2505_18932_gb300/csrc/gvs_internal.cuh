@@ -67,6 +67,7 @@ struct FuseArgs {
     float zn, dz, inv_mu;
     float behind;              // a sample is surely cut off where z > d_max + behind (= 1.0001 mu)
     int normalize;
+    int variant;               // bundle shape / slab-test lengths (same result, different speed)
     float *fused;
     int16_t *crossing;
     ViewXform xf[GVS_MAX_VIEWS];
@@ -75,6 +76,16 @@ struct FuseArgs {
 cudaError_t launch_weight_map(const void *depth, int depth_dtype, void *map, int map_dtype, int K, int W, int H,
                               float mu, float wconst, int window, cudaStream_t st);
 cudaError_t launch_fuse(const FuseArgs &a, cudaStream_t st);
+
+// One (frame, target) item of a batched fusion: its arguments and the index
+// of its first bundle in the batch's bundle numbering.
+struct BatchItem {
+    FuseArgs args;
+    int bundle_begin;
+};
+int bundle_count(int Wt, int Ht, int K, int variant);
+cudaError_t launch_fuse_batch(const BatchItem *items, int n_items, int total, unsigned *counter, int K, int map_dtype,
+                              int variant, cudaStream_t st);
 // acc: [K][H][W] float2 scratch; grad_depths written (not accumulated)
 cudaError_t launch_fuse_backward(const FuseArgs &a, const void *depth, int depth_dtype, const int16_t *crossing,
                                  const float *grad_fused, float *grad_depths, float2 *acc, float mu, float wconst,

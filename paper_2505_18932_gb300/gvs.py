@@ -44,7 +44,13 @@ class GvsRefineParams(ctypes.Structure):
 class GvsFuseParams(ctypes.Structure):
     _fields_ = [("num_samples", ctypes.c_int32), ("z_near", ctypes.c_float), ("z_far", ctypes.c_float),
                 ("mu", ctypes.c_float), ("weight_const", ctypes.c_float), ("window", ctypes.c_int32),
-                ("normalize", ctypes.c_int32), ("depth_dtype", ctypes.c_int32), ("map_dtype", ctypes.c_int32)]
+                ("normalize", ctypes.c_int32), ("depth_dtype", ctypes.c_int32), ("map_dtype", ctypes.c_int32),
+                ("variant", ctypes.c_int32)]
+
+
+class GvsFuseItem(ctypes.Structure):
+    _fields_ = [("map", ctypes.c_void_p), ("map_bytes", ctypes.c_size_t), ("target", ctypes.POINTER(GvsCamera)),
+                ("fused_depth", ctypes.c_void_p), ("crossing", ctypes.c_void_p)]
 
 
 class GvsSplatParams(ctypes.Structure):
@@ -82,6 +88,12 @@ API = {
                                                ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p,
                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "gvs_splat_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32] * 3),
+    "gvs_fuse_batch_bytes": (ctypes.c_size_t, [ctypes.c_int32]),
+    "gvs_fuse_batch_create": (ctypes.c_int, [ctypes.POINTER(GvsCamera), ctypes.c_int32, ctypes.POINTER(GvsFuseItem),
+                                             ctypes.c_int32, ctypes.POINTER(GvsFuseParams), ctypes.c_void_p,
+                                             ctypes.c_size_t, ctypes.POINTER(ctypes.c_void_p)]),
+    "gvs_fuse_batch_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "gvs_fuse_batch_destroy": (None, [ctypes.c_void_p]),
     "gvs_soft_splat_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32] * 3),
     "gvs_soft_splat": (ctypes.c_int, [ctypes.POINTER(GvsCamera), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                       ctypes.POINTER(GvsCamera), ctypes.POINTER(GvsSoftSplatParams)] +
@@ -203,7 +215,8 @@ def workspace(nbytes: int, device=None) -> torch.Tensor:
 
 
 def fuse_depth(in_cams, in_depths, target, num_samples, z_near, z_far, mu, weight_const=0.001, window=7,
-               normalize=False, fused=None, crossing=None, ws=None, want_crossing=True, map_half=False, stream=None):
+               normalize=False, fused=None, crossing=None, ws=None, want_crossing=True, map_half=False, variant=0,
+               stream=None):
     """Supplement A.1 / Eq. 3.  in_depths float32 [N, H, W] on the GPU.
     Returns (fused float32 [Ht, Wt], crossing int16 [Ht, Wt] or None)."""
     lib = load()
@@ -219,7 +232,7 @@ def fuse_depth(in_cams, in_depths, target, num_samples, z_near, z_far, mu, weigh
         ws = workspace(need, dev)
     p = GvsFuseParams(int(num_samples), float(z_near), float(z_far), float(mu), float(weight_const), int(window),
                       int(bool(normalize)), depth_dtype_of(in_depths) if N else GVS_F32,
-                      GVS_F16 if map_half else GVS_F32)
+                      GVS_F16 if map_half else GVS_F32, int(variant))
     st = lib.gvs_fuse_depth(camera_array(in_cams), _ptr(in_depths), N, ctypes.byref(camera_struct(target)),
                             ctypes.byref(p), _ptr(fused), _ptr(crossing), _ptr(ws), ws.numel(), _stream(stream))
     _check("gvs_fuse_depth", st)
@@ -291,7 +304,7 @@ def weight_map(in_depths, mu, weight_const=0.001, window=7, ws=None, map_half=Fa
 
 
 def fuse_depth_from_map(in_cams, dw_map, shape, target, num_samples, z_near, z_far, mu, normalize=False,
-                        fused=None, crossing=None, want_crossing=True, map_half=False, stream=None):
+                        fused=None, crossing=None, want_crossing=True, map_half=False, variant=0, stream=None):
     """Stage 2 of fusion reading a map from weight_map(); `shape` = (N, H, W) of the inputs."""
     lib = load()
     N = len(in_cams)
@@ -301,7 +314,7 @@ def fuse_depth_from_map(in_cams, dw_map, shape, target, num_samples, z_near, z_f
     if crossing is None and want_crossing:
         crossing = torch.empty((target.height, target.width), dtype=torch.int16, device=dev)
     p = GvsFuseParams(int(num_samples), float(z_near), float(z_far), float(mu), 0.001, 7, int(bool(normalize)),
-                      GVS_F32, GVS_F16 if map_half else GVS_F32)
+                      GVS_F32, GVS_F16 if map_half else GVS_F32, int(variant))
     st = lib.gvs_fuse_depth_from_map(camera_array(in_cams), _ptr(dw_map), dw_map.numel() * dw_map.element_size(), N,
                                      ctypes.byref(camera_struct(target)),
                                      ctypes.byref(p), _ptr(fused), _ptr(crossing), _stream(stream))
@@ -413,3 +426,43 @@ class SoftSplat(torch.autograd.Function):
                                      g_color if g_color is not None else torch.zeros_like(color), g_depth,
                                      ctx.cfg.get("max_half_width", 2.0), ctx.cfg["mu_band"])
         return gd, gc.to(in_color.dtype), None, None, None
+
+
+class FuseBatch:
+    """Batched fusion of many (map, target) items in one persistent launch (gvs_fuse_batch_*).
+
+    items: list of (map_tensor, target_camera, fused_out [Ht, Wt] float32, crossing_out int16 or None).
+    Create outside any stream capture (it copies the item table); launch() may be captured."""
+
+    def __init__(self, in_cams, items, num_samples, z_near, z_far, mu, normalize=False, map_half=False, variant=0):
+        lib = load()
+        self.lib = lib
+        self._keep = items  # the tensors must outlive the batch
+        self._targets = [camera_struct(t) for _, t, _, _ in items]
+        arr = (GvsFuseItem * len(items))()
+        for n, (m, t, f, c) in enumerate(items):
+            arr[n] = GvsFuseItem(_ptr(m), m.numel() * m.element_size(), ctypes.pointer(self._targets[n]), _ptr(f),
+                                 _ptr(c))
+        p = GvsFuseParams(int(num_samples), float(z_near), float(z_far), float(mu), 0.001, 7, int(bool(normalize)),
+                          GVS_F32, GVS_F16 if map_half else GVS_F32, int(variant))
+        dev = items[0][0].device
+        self.table = workspace(int(lib.gvs_fuse_batch_bytes(len(items))), dev)
+        h = ctypes.c_void_p()
+        st = lib.gvs_fuse_batch_create(camera_array(in_cams), len(in_cams), arr, len(items), ctypes.byref(p),
+                                       _ptr(self.table), self.table.numel(), ctypes.byref(h))
+        _check("gvs_fuse_batch_create", st)
+        self.handle = h
+
+    def launch(self, stream=None):
+        _check("gvs_fuse_batch_launch", self.lib.gvs_fuse_batch_launch(self.handle, _stream(stream)))
+
+    def close(self):
+        if self.handle:
+            self.lib.gvs_fuse_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
