@@ -261,6 +261,7 @@ def run_gvs(args, rank, local_rank, world):
                                       "refine + weight map + fuse + splat with FP16 depth and half2 map")}
     forms["fwd_bwd"] = form_line("fwd_bwd", w, time_form(FwdBwd(w, frames_np[:2], device), steps=min(K, 30)),
                                  "fuse + differentiable splat forward, 0.8 L1 + 0.1 L_Depth, both adjoints")
+    forms.update(time_batched(device, steps=min(K, 20)))
     wd = configs.diff_640x360()
     forms["fwd_bwd_640x360"] = form_line("fwd_bwd_640x360", wd,
                                          time_form(FwdBwd(wd, render_frames(wd, [0, 1]), device), steps=min(K, 50)),
@@ -367,6 +368,56 @@ def time_form(pipe, steps):
     torch.cuda.synchronize()
     return {"ms_per_step": round(a.elapsed_time(b) / steps, 4), "steps": steps,
             "storage": "depth f16, (d, w) map half2, FP32 arithmetic" if pipe.half else "f32"}
+
+
+def time_batched(device, steps):
+    """The serving-style workload (8 x 1280x720 inputs, 16 targets of four sizes, 2 frames):
+    the CUDA-graph BatchPlan (one persistent fusion launch, autotuned variant) against the
+    same work through the single-view API, launched eagerly item by item."""
+    import torch
+    from paper_2505_18932_gb300 import batch, gvs
+    from synth import configs
+    w = configs.batched_16_targets()
+    fr = render_frames(w, [0, 1, 2])
+    rgba = [torch.from_numpy(c.view(np.int32)).to(device) for c, _ in fr]
+    dep = [torch.from_numpy(d).to(device) for _, d in fr]
+    plan = batch.BatchPlan(w.inputs, w.targets, rgba[1:], dep[1:], w.num_samples, w.z_near, w.z_far, w.mu,
+                           tau=w.tau, rgba_prev=rgba[0], state0=dep[0], variant=None, graph=True)
+    graph_ms = _event_ms(plan.run, steps)
+
+    def eager():
+        for f in range(plan.F):
+            for n, t in enumerate(plan.targets):
+                gvs.fuse_depth_from_map(w.inputs, plan.maps[f], plan.shape, t, w.num_samples, w.z_near, w.z_far,
+                                        w.mu, fused=plan.fused[f][n], crossing=plan.cross[f][n])
+                gvs.forward_splat(w.inputs, plan.states[f], plan.rgba[f], t, fused=plan.fused[f][n], mu_guide=w.mu,
+                                  outputs=plan.splat[f][n], ws=plan.ws_splat)
+    eager_ms = _event_ms(eager, steps)   # refine and maps excluded: this side only pays fusion + splats
+    px = plan.target_pixels()
+    return {"batched_graph": {"ms_per_step": round(graph_ms, 4), "steps": steps, "workload": w.name,
+                              "value": round(px / (graph_ms * 1e-3) / 1e6, 3), "unit": "target Mpix/s",
+                              "variant": plan.variant, "autotune_ms": plan.timings,
+                              "launches_per_step": plan.launches_per_run(),
+                              "note": "2 frames x 16 targets (640x360 .. 1920x1080): refine + maps + one persistent "
+                                      "fusion + 32 splats, replayed as one CUDA graph"},
+            "batched_eager_per_item": {"ms_per_step": round(eager_ms, 4), "steps": steps, "workload": w.name,
+                                       "value": round(px / (eager_ms * 1e-3) / 1e6, 3), "unit": "target Mpix/s",
+                                       "note": "same fusion + splats through the single-view API, one call per "
+                                               "item, no graph (refine and maps not counted)"}}
+
+
+def _event_ms(fn, steps):
+    import torch
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
 
 
 def form_line(name, w, f, note):
