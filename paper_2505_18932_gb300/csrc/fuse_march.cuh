@@ -30,13 +30,14 @@ __device__ __forceinline__ float2 load_map(const float2 *p) { return __ldg(p); }
 __device__ __forceinline__ float2 load_map(const __half2 *p) { return __half22float2(__ldg(p)); }
 
 // Nearest integers (ties to even) of the exact real quotients hx/hz, hy/hz,
-// hz > 0.  q = h * r with r ~ 1/hz (relative error a few ulp) is within 0.01
-// of the quotient for any quotient that can land inside an image
-// (|q| < 2^14 + 1); only when a q sits within 0.01 of a half-integer is the
-// decision re-taken from the signs of the exact residuals h - (n +/- 0.5) hz
-// (one rounding each in the FMA, which never changes a sign).  The fix-up
-// leaves n unchanged when q is not near a half-integer, so it runs for both
-// coordinates under one branch.
+// hz > 0.  q = h * r with r = __fdividef(1, hz) (documented maximum error
+// 2 ulp for 2^-126 <= hz <= 2^126) and one rounded product is within
+// 3e-7 |q| of the quotient, so n = rint(q) is the answer whenever
+// |q - n| + 4e-7 |q| <= 0.5.  Otherwise (rare: within a few 1e-4 pixel of a
+// half-integer) the decision is re-taken from the signs of the exact
+// residuals h - (n +/- 0.5) hz (one rounding each in the FMA, which never
+// changes a sign).  The fix-up leaves n unchanged when q is not near a
+// half-integer, so it runs for both coordinates under one branch.
 __device__ __forceinline__ float exact_nearest_fixup(float num, float den, float n) {
     if (fabsf(n) < 4194304.0f) {
         const float hi = __fmaf_rn(-(n + 0.5f), den, num);
@@ -52,13 +53,16 @@ __device__ __forceinline__ void nearest_pixel(float hx, float hy, float hz, int 
     const float r = __fdividef(1.0f, hz);
     const float qx = hx * r, qy = hy * r;
     float nx = rintf(qx), ny = rintf(qy);
-    if (fmaxf(fabsf(qx - nx), fabsf(qy - ny)) > 0.49f) {
+    const float mx = fmaf(fabsf(qx), 4e-7f, fabsf(qx - nx));
+    const float my = fmaf(fabsf(qy), 4e-7f, fabsf(qy - ny));
+    if (fmaxf(mx, my) > 0.5f) {
         nx = exact_nearest_fixup(hx, hz, nx);
         ny = exact_nearest_fixup(hy, hz, ny);
     }
     u = __float2int_rz(nx);
     v = __float2int_rz(ny);
 }
+
 constexpr int FZ_WARPS = 4;
 #ifndef GVS_FUSE_MIN_BLOCKS
 #define GVS_FUSE_MIN_BLOCKS 8   // resident blocks per SM requested from the register allocator (64 registers)
@@ -99,9 +103,10 @@ struct Ray {
 // load: the finest tile level whose overlapping 2x2 block covers the box, else
 // the whole view.  When every view is free over the slab, no sample of it can
 // end a crossing (S > 0 wherever W > 0).
-__device__ __forceinline__ bool slab_view_free(const FuseArgs &a, int k, const Ray (&corner)[4], float z0,
-                                               float z1) {
-    const float b0 = a.xf[k].b[0], b1 = a.xf[k].b[1], b2 = a.xf[k].b[2];
+// k is this lane's view; (b0, b1, b2) its offset b_k, held in registers so the
+// lanes of a warp (testing different views) do not serialize on constant loads.
+__device__ __forceinline__ bool slab_view_free(const FuseArgs &a, int k, const Ray (&corner)[4], float b0, float b1,
+                                               float b2, float z0, float z1) {
     float xlo = kInf, xhi = -kInf, ylo = kInf, yhi = -kInf, zlo = kInf, zhi = -kInf;
     bool any_front = false, any_back = false;
 #pragma unroll
@@ -204,9 +209,13 @@ __device__ __forceinline__ void march_bundle(const FuseArgs &a, int bundle, int 
     const int tk = lane % KMAX, tseg = lane / KMAX;
     const bool tview = tk < a.K;
     Ray corner[4];
+    float tb0, tb1, tb2;
     {
         const int kk = tview ? tk : 0;
         const float *M = a.xf[kk].M;
+        tb0 = a.xf[kk].b[0];
+        tb1 = a.xf[kk].b[1];
+        tb2 = a.xf[kk].b[2];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const float ci = (float)((c & 1) ? i1 : i0), cj = (float)((c & 2) ? j1 : j0);
@@ -231,7 +240,7 @@ __device__ __forceinline__ void march_bundle(const FuseArgs &a, int bundle, int 
             bool f = false;
             if (sa < a.D - 1) {
                 const int sb = min(sa + L, a.D - 1);
-                f = !tview || slab_view_free(a, tk, corner, __fmaf_rn((float)sa, a.dz, a.zn),
+                f = !tview || slab_view_free(a, tk, corner, tb0, tb1, tb2, __fmaf_rn((float)sa, a.dz, a.zn),
                                              __fmaf_rn((float)sb, a.dz, a.zn));
             }
             const unsigned ball = __ballot_sync(0xffffffffu, f);
