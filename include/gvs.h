@@ -99,6 +99,13 @@ typedef struct {
     int32_t depth_dtype;       /* GVS_F32 or GVS_F16: element type of depth_t and depth_state */
 } gvs_refine_params;
 
+/* Temporal refinement, the paper's soft mask (Sec. 3.2, Eq. 1-2 as printed). */
+typedef struct {
+    float beta;                /* 0.6 in the paper: the mask's floor */
+    float lambda_t;            /* 0.7 in the paper: colour-difference scale */
+    int32_t depth_dtype;       /* GVS_F32 or GVS_F16 */
+} gvs_refine_soft_params;
+
 /* TSDF fusion (Supplement A.1, Eq. 3). */
 typedef struct {
     int32_t num_samples;       /* D >= 2 uniform samples of target z-depth in [z_near, z_far] */
@@ -151,6 +158,39 @@ GVS_API const char *gvs_last_error(void);
 GVS_API gvs_status gvs_refine_depth(const uint32_t *rgba_t, const uint32_t *rgba_prev, const void *depth_t,
                             void *depth_state, uint8_t *mask, int32_t n_views, int32_t width,
                             int32_t height, const gvs_refine_params *params, void *stream);
+
+/* Workspace bytes for gvs_refine_depth_soft: two quarter-resolution float grids per view. */
+GVS_API size_t gvs_refine_soft_workspace_bytes(int32_t n_views, int32_t width, int32_t height);
+
+/*
+ * gvs_refine_depth_soft -- temporal depth refinement with the soft difference
+ * mask exactly as Sec. 3.2 prints it:
+ *   M = min(|I^t - I^{t-1}| / lambda_t + beta, 1)               (Eq. 1)
+ *   depth_state = M depth_t + (1 - M) depth_state               (Eq. 2)
+ * with M computed at quarter resolution, 3x3 max-pooled and bilinearly
+ * upsampled.  Readings: the per-pixel difference is the largest of the R, G,
+ * B differences in [0, 1]; a quarter cell is the mean over its 4x4 pixels
+ * (fewer at the right and bottom edges); pooling clamps at the borders; the
+ * upsample samples the quarter grid at ((x + 0.5) / 4 - 0.5, (y + 0.5) / 4 -
+ * 0.5), clamped to the grid.  Where the previous depth is invalid the new one
+ * is taken; where the new one is invalid the previous one is kept.
+ *   rgba_t, rgba_prev : uint32 [n_views][height][width] (both required)
+ *   depth_t, depth_state : [n_views][height][width] of params->depth_dtype
+ *   mask      : float [n_views][height][width] (M), or NULL
+ *   workspace : >= gvs_refine_soft_workspace_bytes() bytes, 256-byte aligned
+ */
+GVS_API gvs_status gvs_refine_depth_soft(const uint32_t *rgba_t, const uint32_t *rgba_prev, const void *depth_t,
+                                         void *depth_state, float *mask, int32_t n_views, int32_t width,
+                                         int32_t height, const gvs_refine_soft_params *params, void *workspace,
+                                         size_t workspace_bytes, void *stream);
+
+/*
+ * gvs_select_views -- the K input views closest to the target (Sec. 3.1; the
+ * evaluation uses K = 4 or 2): ranked by the distance between camera centres
+ * C = -R^T t, ties to the lower index.  Host only; writes k indices.
+ */
+GVS_API gvs_status gvs_select_views(const gvs_camera *cams, int32_t n, const gvs_camera *target, int32_t k,
+                                    int32_t *out_idx);
 
 /* Workspace bytes for gvs_fuse_depth (the "map" of gvs_weight_map): the packed
  * (depth, weight) float2 of every input pixel followed by per-view depth

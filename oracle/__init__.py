@@ -81,6 +81,7 @@ def _load():
             lib.orc_forward_splat.argtypes = [cp, vp, vp, i32, cp, i32, flt, flt, vp, vp, vp, vp, vp, vp, vp, vp]
             lib.orc_splat_bruteforce.argtypes = [cp, vp, i32, cp, i32, flt, vp]
             lib.orc_fuse_depth_grad.argtypes = [cp, vp, i32, cp, i32, dbl, dbl, dbl, dbl, i32, vp, vp]
+            lib.orc_refine_depth_soft.argtypes = [i32, i32, i32, vp, vp, vp, vp, dbl, dbl, vp, vp]
             lib.orc_soft_splat.argtypes = [cp, vp, vp, i32, cp, flt, flt, vp, vp, vp, vp, vp]
             lib.orc_soft_splat_grad.argtypes = [cp, vp, vp, i32, cp, flt, flt, vp, vp, vp, vp]
             _lib = lib
@@ -111,6 +112,25 @@ def refine_depth(rgba_t, rgba_prev, depth_t, state_prev, tau: float = 0.03):
                               _ptr(out), _ptr(mask))
     if rc != 0:
         raise ValueError("orc_refine_depth rejected its arguments")
+    return out, mask
+
+
+def refine_depth_soft(rgba_t, rgba_prev, depth_t, state_prev, beta=0.6, lambda_t=0.7):
+    """Eq. 1-2 in the paper's soft form (quarter resolution, 3x3 max-pool, bilinear upsample).
+
+    Returns (state_out float64 [N, H, W], mask float64 [N, H, W])."""
+    lib = _load()
+    rgba_t = np.ascontiguousarray(rgba_t, np.uint8)
+    rgba_prev = np.ascontiguousarray(rgba_prev, np.uint8)
+    N, H, W = rgba_t.shape[:3]
+    d = np.ascontiguousarray(depth_t, np.float32)
+    sp = np.ascontiguousarray(state_prev, np.float32)
+    out = np.empty((N, H, W), np.float64)
+    mask = np.empty((N, H, W), np.float64)
+    rc = lib.orc_refine_depth_soft(N, H, W, _ptr(rgba_t), _ptr(rgba_prev), _ptr(d), _ptr(sp), float(beta),
+                                   float(lambda_t), _ptr(out), _ptr(mask))
+    if rc != 0:
+        raise ValueError("orc_refine_depth_soft rejected its arguments")
     return out, mask
 
 

@@ -787,3 +787,78 @@ int orc_soft_splat_grad(const orc_camera *in_cams, const float *depths, const do
     free(win); free(col); free(zd); free(ws);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Eq. 1 and Eq. 2 in the paper's soft form (Sec. 3.2):                      */
+/*   M = min(|I^t - I^{t-1}| / lambda_t + beta, 1)  (beta 0.6, lambda_t 0.7) */
+/* computed at quarter resolution, 3x3 max-pooled and bilinearly upsampled,  */
+/*   D'^t = M D^t + (1 - M) D'^{t-1}.                                        */
+/* Readings: |I^t - I^{t-1}| per pixel is the largest of the three channel   */
+/* differences in [0, 1] (value / 255); the quarter-resolution value is the  */
+/* mean over the 4x4 block (partial blocks at the right/bottom edge average  */
+/* the pixels they have); the pooling window is clamped at the borders; the  */
+/* upsampling samples the quarter grid at ((x + 0.5) / 4 - 0.5, ...) with    */
+/* clamp-to-edge.  An invalid previous depth takes the new depth; an invalid */
+/* new depth keeps the previous one.                                         */
+/* ------------------------------------------------------------------------ */
+int orc_refine_depth_soft(int n_views, int H, int W, const uint8_t *rgba_t, const uint8_t *rgba_prev,
+                          const float *depth_t, const float *state_prev, double beta, double lambda_t,
+                          double *state_out, double *mask_out) {
+    if (n_views <= 0 || H <= 0 || W <= 0 || !rgba_t || !rgba_prev || !depth_t || !state_prev || !state_out) return -1;
+    int Hq = (H + 3) / 4, Wq = (W + 3) / 4;
+    double *mq = malloc(sizeof(double) * Hq * Wq);
+    double *pq = malloc(sizeof(double) * Hq * Wq);
+    for (int k = 0; k < n_views; ++k) {
+        size_t off = (size_t)k * H * W;
+        for (int qy = 0; qy < Hq; ++qy)
+            for (int qx = 0; qx < Wq; ++qx) {
+                double sum = 0.0;
+                int cnt = 0;
+                for (int y = 4 * qy; y < 4 * qy + 4 && y < H; ++y)
+                    for (int x = 4 * qx; x < 4 * qx + 4 && x < W; ++x) {
+                        size_t p = off + (size_t)y * W + x;
+                        int dmax = 0;
+                        for (int c = 0; c < 3; ++c) {
+                            int d = abs((int)rgba_t[4 * p + c] - (int)rgba_prev[4 * p + c]);
+                            if (d > dmax) dmax = d;
+                        }
+                        sum += dmax / 255.0;
+                        ++cnt;
+                    }
+                double m = (sum / cnt) / lambda_t + beta;
+                mq[qy * Wq + qx] = m < 1.0 ? m : 1.0;
+            }
+        for (int qy = 0; qy < Hq; ++qy)
+            for (int qx = 0; qx < Wq; ++qx) {
+                double best = -1.0;
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        int yy = qy + dy, xx = qx + dx;
+                        yy = yy < 0 ? 0 : (yy >= Hq ? Hq - 1 : yy);
+                        xx = xx < 0 ? 0 : (xx >= Wq ? Wq - 1 : xx);
+                        if (mq[yy * Wq + xx] > best) best = mq[yy * Wq + xx];
+                    }
+                pq[qy * Wq + qx] = best;
+            }
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                double sx = (x + 0.5) / 4.0 - 0.5, sy = (y + 0.5) / 4.0 - 0.5;
+                sx = sx < 0 ? 0 : (sx > Wq - 1 ? Wq - 1 : sx);
+                sy = sy < 0 ? 0 : (sy > Hq - 1 ? Hq - 1 : sy);
+                int x0 = (int)floor(sx), y0 = (int)floor(sy);
+                int x1 = x0 + 1 < Wq ? x0 + 1 : x0, y1 = y0 + 1 < Hq ? y0 + 1 : y0;
+                double fx = sx - x0, fy = sy - y0;
+                double m = (1 - fy) * ((1 - fx) * pq[y0 * Wq + x0] + fx * pq[y0 * Wq + x1]) +
+                           fy * ((1 - fx) * pq[y1 * Wq + x0] + fx * pq[y1 * Wq + x1]);
+                size_t p = off + (size_t)y * W + x;
+                if (mask_out) mask_out[p] = m;
+                float dn = depth_t[p], dp = state_prev[p];
+                if (!depth_valid(dp)) state_out[p] = dn;
+                else if (!depth_valid(dn)) state_out[p] = dp;
+                else state_out[p] = m * (double)dn + (1.0 - m) * (double)dp;
+            }
+    }
+    free(mq);
+    free(pq);
+    return 0;
+}

@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <mutex>
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -143,6 +144,67 @@ gvs_status gvs_refine_depth(const uint32_t *rgba_t, const uint32_t *rgba_prev, c
     cudaError_t e = gvs::launch_refine(rgba_t, rgba_prev, depth_t, depth_state, mask, n, threshold,
                                        params->depth_dtype, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "refine launch");
+    return GVS_OK;
+}
+
+size_t gvs_refine_soft_workspace_bytes(int32_t n_views, int32_t width, int32_t height) {
+    if (n_views < 0 || width < 0 || height < 0) return 0;
+    return align_up(2 * (size_t)n_views * (size_t)((width + 3) / 4) * (size_t)((height + 3) / 4) * sizeof(float), 256);
+}
+
+gvs_status gvs_refine_depth_soft(const uint32_t *rgba_t, const uint32_t *rgba_prev, const void *depth_t,
+                                 void *depth_state, float *mask, int32_t n_views, int32_t width, int32_t height,
+                                 const gvs_refine_soft_params *params, void *workspace, size_t workspace_bytes,
+                                 void *stream) {
+    if (!params) return fail(GVS_ERR_INVALID_ARG, "soft refine: params is NULL");
+    if (n_views < 0 || n_views > GVS_MAX_VIEWS) return fail(GVS_ERR_INVALID_ARG, "soft refine: n_views out of range");
+    if (width < 1 || height < 1 || width > GVS_MAX_DIM || height > GVS_MAX_DIM)
+        return fail(GVS_ERR_INVALID_ARG, "soft refine: image size out of range");
+    if (!(isfinite(params->beta) && params->beta >= 0.0f && params->beta <= 1.0f))
+        return fail(GVS_ERR_INVALID_ARG, "soft refine: beta must be in [0, 1]");
+    if (!(isfinite(params->lambda_t) && params->lambda_t > 0.0f))
+        return fail(GVS_ERR_INVALID_ARG, "soft refine: lambda_t must be > 0");
+    if (params->depth_dtype != GVS_F32 && params->depth_dtype != GVS_F16)
+        return fail(GVS_ERR_UNSUPPORTED, "soft refine: depth_dtype must be GVS_F32 or GVS_F16");
+    if (n_views == 0) return GVS_OK;
+    if (!rgba_t || !rgba_prev || !depth_t || !depth_state)
+        return fail(GVS_ERR_INVALID_ARG, "soft refine: rgba_t, rgba_prev, depth_t and depth_state are required");
+    const void *arrs[] = {rgba_t, rgba_prev, depth_t, depth_state, mask};
+    for (const void *q : arrs)
+        if (q && !aligned(q, 16)) return fail(GVS_ERR_INVALID_ARG, "soft refine: arrays must be 16-byte aligned");
+    const size_t need = gvs_refine_soft_workspace_bytes(n_views, width, height);
+    if (!workspace || workspace_bytes < need || !aligned(workspace, 256))
+        return fail(GVS_ERR_WORKSPACE, "soft refine: workspace needs %zu bytes, 256-byte aligned", need);
+    cudaError_t e = gvs::launch_refine_soft(rgba_t, rgba_prev, depth_t, depth_state, mask, n_views, width, height,
+                                            params->beta, params->lambda_t, params->depth_dtype,
+                                            reinterpret_cast<float *>(workspace), (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "soft refine: launch");
+    return GVS_OK;
+}
+
+gvs_status gvs_select_views(const gvs_camera *cams, int32_t n, const gvs_camera *target, int32_t k,
+                            int32_t *out_idx) {
+    if (!cams || !target || !out_idx || n < 1 || k < 1 || k > n)
+        return fail(GVS_ERR_INVALID_ARG, "select views: need cameras, a target, out_idx and 1 <= k <= n");
+    for (int i = 0; i < n; ++i)
+        if (!camera_ok(&cams[i])) return fail(GVS_ERR_INVALID_ARG, "select views: camera %d invalid", i);
+    if (!camera_ok(target)) return fail(GVS_ERR_INVALID_ARG, "select views: target camera invalid");
+    auto centre = [](const gvs_camera &c, double C[3]) {  // C = -R^T t
+        for (int a = 0; a < 3; ++a) C[a] = -(c.R[0 * 3 + a] * c.t[0] + c.R[1 * 3 + a] * c.t[1] + c.R[2 * 3 + a] * c.t[2]);
+    };
+    double Ct[3];
+    centre(*target, Ct);
+    std::vector<std::pair<double, int>> d((size_t)n);
+    for (int i = 0; i < n; ++i) {
+        double C[3];
+        centre(cams[i], C);
+        const double dx = C[0] - Ct[0], dy = C[1] - Ct[1], dz = C[2] - Ct[2];
+        d[(size_t)i] = {dx * dx + dy * dy + dz * dz, i};
+    }
+    std::stable_sort(d.begin(), d.end(), [](const std::pair<double, int> &a, const std::pair<double, int> &b) {
+        return a.first < b.first;
+    });
+    for (int i = 0; i < k; ++i) out_idx[i] = d[(size_t)i].second;
     return GVS_OK;
 }
 

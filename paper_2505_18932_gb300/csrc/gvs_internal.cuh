@@ -22,6 +22,11 @@ struct ViewXform {
 cudaError_t launch_refine(const uint32_t *rgba_t, const uint32_t *rgba_prev, const void *depth_t, void *state,
                           uint8_t *mask, int64_t n, int threshold, int depth_dtype, cudaStream_t st);
 
+// ws: 2 * K * ceil(W/4) * ceil(H/4) floats
+cudaError_t launch_refine_soft(const uint32_t *rgba_t, const uint32_t *rgba_prev, const void *depth_t, void *state,
+                               float *mask, int K, int W, int H, float beta, float lambda_t, int depth_dtype,
+                               float *ws, cudaStream_t st);
+
 // ---- TSDF fusion -----------------------------------------------------------
 // Byte layout of the fusion workspace ("map"): the packed (depth, weight)
 // float2 per input pixel, then per-view depth bounds (min, max over valid

@@ -5,6 +5,8 @@
 // and writes the filtered depth and the mask byte (5 B or 3 B).  Four pixels
 // per thread so that every access is a vector; a scalar tail covers n % 4.
 // Depths are moved as raw bits, so the copy is exact in either format.
+#include <cuda_fp16.h>
+
 #include "gvs_internal.cuh"
 
 namespace gvs {
@@ -82,6 +84,102 @@ void launch_typed(const uint32_t *rgba_t, const uint32_t *rgba_prev, const void 
                                          reinterpret_cast<T *>(state), mask, 4 * n4, n, T4);
 }
 
+// ---------------------------------------------------------------------------
+// The paper's soft difference mask (Sec. 3.2, Eq. 1 and Eq. 2):
+//   M = min(|I^t - I^{t-1}| / lambda_t + beta, 1) at quarter resolution,
+//   3x3 max-pool, bilinear upsample,  D' = M D + (1 - M) D'_prev.
+// Three small passes: quarter cells (4x4 block means of the per-pixel largest
+// channel difference), the pooled quarter grid, then the full-resolution
+// upsample and blend.  Quarter grids live in the workspace.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) soft_quarter(const uint32_t *__restrict__ rgba_t,
+                                                    const uint32_t *__restrict__ rgba_prev, float *__restrict__ mq,
+                                                    int W, int H, int Wq, int Hq, int K, float inv_lambda,
+                                                    float beta) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (int64_t)K * Wq * Hq) return;
+    const int k = (int)(q / ((int64_t)Wq * Hq));
+    const int r = (int)(q - (int64_t)k * Wq * Hq);
+    const int qy = r / Wq, qx = r - qy * Wq;
+    const size_t off = (size_t)k * W * H;
+    float sum = 0.0f;
+    int cnt = 0;
+    for (int y = 4 * qy; y < min(4 * qy + 4, H); ++y)
+        for (int x = 4 * qx; x < min(4 * qx + 4, W); ++x) {
+            const size_t p = off + (size_t)y * W + x;
+            const uint32_t d = __vabsdiffu4(__ldg(&rgba_t[p]), __ldg(&rgba_prev[p]));
+            const uint32_t m = max(max(d & 0xffu, (d >> 8) & 0xffu), (d >> 16) & 0xffu);
+            sum += (float)m;
+            ++cnt;
+        }
+    const float mean = sum / (255.0f * (float)cnt);
+    mq[q] = fminf(fmaf(mean, inv_lambda, beta), 1.0f);
+}
+
+__global__ void __launch_bounds__(256) soft_pool(const float *__restrict__ mq, float *__restrict__ pq, int Wq,
+                                                 int Hq, int K) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (int64_t)K * Wq * Hq) return;
+    const int k = (int)(q / ((int64_t)Wq * Hq));
+    const int r = (int)(q - (int64_t)k * Wq * Hq);
+    const int qy = r / Wq, qx = r - qy * Wq;
+    const float *m = mq + (size_t)k * Wq * Hq;
+    float best = -1.0f;
+    for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+            const int yy = min(max(qy + dy, 0), Hq - 1), xx = min(max(qx + dx, 0), Wq - 1);
+            best = fmaxf(best, m[yy * Wq + xx]);
+        }
+    pq[q] = best;
+}
+
+__device__ __forceinline__ float ld_depth(const float *p) { return *p; }
+__device__ __forceinline__ float ld_depth(const __half *p) { return __half2float(*p); }
+__device__ __forceinline__ void st_depth(float *p, float v) { *p = v; }
+__device__ __forceinline__ void st_depth(__half *p, float v) { *p = __float2half_rn(v); }
+__device__ __forceinline__ bool valid_d(float d) { return isfinite(d) && d > 0.0f; }
+
+template <typename T>
+__global__ void __launch_bounds__(256) soft_blend(const float *__restrict__ pq, const T *__restrict__ depth_t,
+                                                  T *__restrict__ state, float *__restrict__ mask, int W, int H,
+                                                  int Wq, int Hq, int K) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= (int64_t)K * W * H) return;
+    const int k = (int)(p / ((int64_t)W * H));
+    const int r = (int)(p - (int64_t)k * W * H);
+    const int y = r / W, x = r - y * W;
+    const float *m = pq + (size_t)k * Wq * Hq;
+    const float sx = fminf(fmaxf((x + 0.5f) * 0.25f - 0.5f, 0.0f), (float)(Wq - 1));
+    const float sy = fminf(fmaxf((y + 0.5f) * 0.25f - 0.5f, 0.0f), (float)(Hq - 1));
+    const int x0 = (int)sx, y0 = (int)sy;
+    const int x1 = min(x0 + 1, Wq - 1), y1 = min(y0 + 1, Hq - 1);
+    const float fx = sx - (float)x0, fy = sy - (float)y0;
+    const float M = (1.0f - fy) * ((1.0f - fx) * m[y0 * Wq + x0] + fx * m[y0 * Wq + x1]) +
+                    fy * ((1.0f - fx) * m[y1 * Wq + x0] + fx * m[y1 * Wq + x1]);
+    if (mask) mask[p] = M;
+    const float dn = ld_depth(&depth_t[p]), dp = ld_depth(&state[p]);
+    float out;
+    if (!valid_d(dp)) out = dn;
+    else if (!valid_d(dn)) out = dp;
+    else out = fmaf(M, dn - dp, dp);  // M dn + (1 - M) dp
+    st_depth(&state[p], out);
+}
+
+template <typename T>
+cudaError_t launch_soft_typed(const uint32_t *rgba_t, const uint32_t *rgba_prev, const void *depth_t, void *state,
+                              float *mask, int K, int W, int H, float beta, float lambda_t, float *ws,
+                              cudaStream_t st) {
+    const int Wq = (W + 3) / 4, Hq = (H + 3) / 4;
+    const int64_t nq = (int64_t)K * Wq * Hq, n = (int64_t)K * W * H;
+    float *mq = ws, *pq = ws + nq;
+    soft_quarter<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(rgba_t, rgba_prev, mq, W, H, Wq, Hq, K,
+                                                              1.0f / lambda_t, beta);
+    soft_pool<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(mq, pq, Wq, Hq, K);
+    soft_blend<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(pq, reinterpret_cast<const T *>(depth_t),
+                                                               reinterpret_cast<T *>(state), mask, W, H, Wq, Hq, K);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_refine(const uint32_t *rgba_t, const uint32_t *rgba_prev, const void *depth_t, void *state,
@@ -93,6 +191,14 @@ cudaError_t launch_refine(const uint32_t *rgba_t, const uint32_t *rgba_prev, con
     else
         launch_typed<uint4, uint32_t>(rgba_t, rgba_prev, depth_t, state, mask, n, T4, st);
     return cudaGetLastError();
+}
+
+cudaError_t launch_refine_soft(const uint32_t *rgba_t, const uint32_t *rgba_prev, const void *depth_t, void *state,
+                               float *mask, int K, int W, int H, float beta, float lambda_t, int depth_dtype,
+                               float *ws, cudaStream_t st) {
+    return depth_dtype == GVS_F16
+               ? launch_soft_typed<__half>(rgba_t, rgba_prev, depth_t, state, mask, K, W, H, beta, lambda_t, ws, st)
+               : launch_soft_typed<float>(rgba_t, rgba_prev, depth_t, state, mask, K, W, H, beta, lambda_t, ws, st);
 }
 
 }  // namespace gvs

@@ -41,6 +41,10 @@ class GvsRefineParams(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_float), ("depth_dtype", ctypes.c_int32)]
 
 
+class GvsRefineSoftParams(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_float), ("lambda_t", ctypes.c_float), ("depth_dtype", ctypes.c_int32)]
+
+
 class GvsFuseParams(ctypes.Structure):
     _fields_ = [("num_samples", ctypes.c_int32), ("z_near", ctypes.c_float), ("z_far", ctypes.c_float),
                 ("mu", ctypes.c_float), ("weight_const", ctypes.c_float), ("window", ctypes.c_int32),
@@ -70,6 +74,12 @@ API = {
     "gvs_last_error": (ctypes.c_char_p, []),
     "gvs_refine_depth": (ctypes.c_int, [ctypes.c_void_p] * 5 + [ctypes.c_int32] * 3 +
                          [ctypes.POINTER(GvsRefineParams), ctypes.c_void_p]),
+    "gvs_refine_soft_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32] * 3),
+    "gvs_refine_depth_soft": (ctypes.c_int, [ctypes.c_void_p] * 5 + [ctypes.c_int32] * 3 +
+                              [ctypes.POINTER(GvsRefineSoftParams), ctypes.c_void_p, ctypes.c_size_t,
+                               ctypes.c_void_p]),
+    "gvs_select_views": (ctypes.c_int, [ctypes.POINTER(GvsCamera), ctypes.c_int32, ctypes.POINTER(GvsCamera),
+                                        ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "gvs_fuse_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32] * 3),
     "gvs_fuse_depth": (ctypes.c_int, [ctypes.POINTER(GvsCamera), ctypes.c_void_p, ctypes.c_int32,
                                       ctypes.POINTER(GvsCamera), ctypes.POINTER(GvsFuseParams),
@@ -199,6 +209,30 @@ def refine_depth(rgba_t, rgba_prev, depth_t, depth_state, mask=None, tau: float 
                               N, W, H, ctypes.byref(p), _stream(stream))
     _check("gvs_refine_depth", st)
     return depth_state, mask
+
+
+def refine_depth_soft(rgba_t, rgba_prev, depth_t, depth_state, mask=None, beta=0.6, lambda_t=0.7, ws=None,
+                      stream=None):
+    """Sec. 3.2 Eq. 1-2 as printed (soft mask at quarter resolution, max-pool, bilinear).
+    depth_state (float32/float16 [N, H, W]) is updated in place; mask: float32 [N, H, W] or None."""
+    lib = load()
+    N, H, W = depth_t.shape
+    if ws is None:
+        ws = workspace(int(lib.gvs_refine_soft_workspace_bytes(N, W, H)), depth_t.device)
+    p = GvsRefineSoftParams(float(beta), float(lambda_t), depth_dtype_of(depth_t))
+    st = lib.gvs_refine_depth_soft(_ptr(rgba_t), _ptr(rgba_prev), _ptr(depth_t), _ptr(depth_state), _ptr(mask),
+                                   N, W, H, ctypes.byref(p), _ptr(ws), ws.numel(), _stream(stream))
+    _check("gvs_refine_depth_soft", st)
+    return depth_state, mask
+
+
+def select_views(in_cams, target, k):
+    """Indices of the k input cameras closest to the target (host only)."""
+    lib = load()
+    out = (ctypes.c_int32 * int(k))()
+    st = lib.gvs_select_views(camera_array(in_cams), len(in_cams), ctypes.byref(camera_struct(target)), int(k), out)
+    _check("gvs_select_views", st)
+    return list(out)
 
 
 def fuse_workspace_bytes(n_views, width, height) -> int:

@@ -148,3 +148,23 @@ def test_binding_refuses_cpu_tensors():
     from paper_2505_18932_gb300 import gvs
     with pytest.raises(ValueError):
         gvs._ptr(torch.zeros(4))
+
+
+def test_select_views_host_only(lib):
+    """K-closest selection is host code: checked here without a GPU against distances
+    computed independently."""
+    import numpy as np
+    from paper_2505_18932_gb300 import gvs
+    from synth import camera_at, look_at
+    rng = np.random.default_rng(0)
+    centres = rng.uniform(-1, 1, (9, 3))
+    cams = [look_at(64, 48, c, (0.0, 0.0, 3.0)) if i % 2 else camera_at(64, 48, c) for i, c in enumerate(centres)]
+    tgt = camera_at(64, 48, (0.1, -0.2, 0.05))
+    for k in (1, 4, 9):
+        got = gvs.select_views(cams, tgt, k)
+        d = np.linalg.norm(centres - np.array([0.1, -0.2, 0.05]), axis=1)
+        assert got == list(np.argsort(d, kind="stable")[:k])
+    twins = [camera_at(64, 48, (1.0, 0, 0)), camera_at(64, 48, (-1.0, 0, 0)), camera_at(64, 48, (0, 0.5, 0))]
+    assert gvs.select_views(twins, camera_at(64, 48, (0, 0, 0)), 3) == [2, 0, 1]   # tie -> lower index
+    with pytest.raises(gvs.GvsError):
+        gvs.select_views(twins, camera_at(64, 48, (0, 0, 0)), 4)
