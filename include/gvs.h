@@ -83,7 +83,8 @@ typedef enum {
 typedef enum {
     GVS_F32 = 0,               /* float */
     GVS_F16 = 1,               /* IEEE half */
-    GVS_BF16 = 2               /* bfloat16 (colour of the soft splat only) */
+    GVS_BF16 = 2,              /* bfloat16 (colour of the soft splat only) */
+    GVS_U8 = 3                 /* uint8 (binary difference masks) */
 } gvs_dtype;
 
 typedef struct {
@@ -369,6 +370,48 @@ GVS_API gvs_status gvs_fuse_batch_create(const gvs_camera *in_cams, int32_t n_vi
 GVS_API gvs_status gvs_fuse_batch_launch(const gvs_fuse_batch *batch, void *stream);
 
 GVS_API void gvs_fuse_batch_destroy(gvs_fuse_batch *batch);
+
+/*
+ * The temporal term of Sec. 3.2 / Supplement A.2, for a novel viewpoint that
+ * stays fixed from frame to frame (or whose state the caller reprojects):
+ *
+ * gvs_temporal_weight -- the target-view difference mask M(p) = max over views
+ * of each view's mask at its z-buffer winner (the forward splat of the masks
+ * with a channel-wise maximum; 1 where no view covers p), and the temporal
+ * fusion weight
+ *   w_tmp(p) = min(beta_t (w_tmp_prev(p) + w_view_prev(p)) max(1 - M(p), 0), eta)
+ * where w_view_prev is the views' weight at the previous frame's crossing
+ * (view_weight of gvs_fuse_depth_temporal).  eta = 15 in the paper; beta_t is
+ * not given there (1 is this library's default).
+ *   masks       : [n_views][height][width], float (soft masks) or uint8 (binary)
+ *   winner      : int32 [n_views][target_height][target_width] (gvs_forward_splat)
+ *   w_tmp_prev, w_view_prev, w_tmp, target_mask (or NULL): float [Ht][Wt]
+ */
+GVS_API gvs_status gvs_temporal_weight(const void *masks, int32_t mask_dtype, const int32_t *winner,
+                                       int32_t n_views, int32_t width, int32_t height, int32_t target_width,
+                                       int32_t target_height, const float *w_tmp_prev, const float *w_view_prev,
+                                       float beta_t, float eta, float *w_tmp, float *target_mask, void *stream);
+
+/*
+ * gvs_fuse_depth_temporal -- gvs_fuse_depth_from_map with the previous output
+ * depth prev_depth(p) as one more TSDF input at the ray's own pixel, weighted
+ * w_tmp(p) (zero or an invalid depth: absent):
+ *   S_s += w_tmp clamp((prev_depth - z_s) / mu, -1, 1), W_s += w_tmp,
+ * both only where (prev_depth - z_s) / mu >= -1, as for the views.
+ *   view_weight : float [Ht][Wt] (or NULL): the views' weight sum at the
+ *                 crossing, interpolated like the depth (0 without a crossing)
+ */
+GVS_API gvs_status gvs_fuse_depth_temporal(const gvs_camera *in_cams, const void *map, size_t map_bytes,
+                                           int32_t n_views, const gvs_camera *target, const gvs_fuse_params *params,
+                                           const float *prev_depth, const float *w_tmp, float *fused_depth,
+                                           int16_t *crossing, float *view_weight, void *stream);
+
+/* gvs_guided_mask -- the guided mask of gvs_forward_splat computed afterwards:
+ * guided = alpha && |warped_depth - fused_depth| <= mu_guide, all [n_views][Ht][Wt]
+ * except fused_depth [Ht][Wt]. */
+GVS_API gvs_status gvs_guided_mask(const float *warped_depth, const uint8_t *alpha, const float *fused_depth,
+                                   int32_t n_views, int32_t target_width, int32_t target_height, float mu_guide,
+                                   uint8_t *guided, void *stream);
 
 /* Workspace bytes for gvs_forward_splat: one 64-bit z-buffer of the target size.
  * A workspace holding several such buffers lets several views splat in one pass. */

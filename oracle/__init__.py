@@ -82,6 +82,9 @@ def _load():
             lib.orc_splat_bruteforce.argtypes = [cp, vp, i32, cp, i32, flt, vp]
             lib.orc_fuse_depth_grad.argtypes = [cp, vp, i32, cp, i32, dbl, dbl, dbl, dbl, i32, vp, vp]
             lib.orc_refine_depth_soft.argtypes = [i32, i32, i32, vp, vp, vp, vp, dbl, dbl, vp, vp]
+            lib.orc_temporal_weight.argtypes = [vp, vp, i32, i32, i32, i32, i32, vp, vp, dbl, dbl, vp, vp]
+            lib.orc_fuse_depth_temporal.argtypes = [cp, vp, i32, cp, i32, dbl, dbl, dbl, dbl, i32, vp, vp, vp, vp,
+                                                    vp, vp]
             lib.orc_soft_splat.argtypes = [cp, vp, vp, i32, cp, flt, flt, vp, vp, vp, vp, vp]
             lib.orc_soft_splat_grad.argtypes = [cp, vp, vp, i32, cp, flt, flt, vp, vp, vp, vp]
             _lib = lib
@@ -173,6 +176,48 @@ def fuse_depth(in_cams, depths, target, num_samples, z_near, z_far, mu,
         raise ValueError("orc_fuse_depth rejected its arguments")
     return {"depth": out_d.reshape(shape), "index": out_i.reshape(shape), "ambiguous": out_a.reshape(shape),
             "fp64_mismatch": int(mism.value)}
+
+
+def temporal_weight(masks, winner, w_tmp_prev, w_view_prev, beta_t=1.0, eta=15.0):
+    """Supplement A.2: target-view difference mask (max over views at the z-buffer winners)
+    and the temporal fusion weight.  masks float [N, H, W]; winner int32 [N, Ht, Wt].
+    Returns (w_tmp float64 [Ht, Wt], mask float64 [Ht, Wt])."""
+    lib = _load()
+    masks = np.ascontiguousarray(masks, np.float32)
+    winner = np.ascontiguousarray(winner, np.int32)
+    N, H, W = masks.shape
+    Ht, Wt = winner.shape[1:]
+    wp = np.ascontiguousarray(w_tmp_prev, np.float32)
+    wv = np.ascontiguousarray(w_view_prev, np.float32)
+    out = np.empty((Ht, Wt), np.float64)
+    m = np.empty((Ht, Wt), np.float64)
+    rc = lib.orc_temporal_weight(_ptr(masks), _ptr(winner), N, W, H, Wt, Ht, _ptr(wp), _ptr(wv), float(beta_t),
+                                 float(eta), _ptr(out), _ptr(m))
+    if rc != 0:
+        raise ValueError("orc_temporal_weight rejected its arguments")
+    return out, m
+
+
+def fuse_depth_temporal(in_cams, depths, target, num_samples, z_near, z_far, mu, tmp_depth, tmp_weight,
+                        weight_const=DEFAULT_WEIGHT_CONST, window=DEFAULT_WINDOW):
+    """fuse_depth with the previous output depth as one more input at the same pixel (weight tmp_weight).
+    Returns dict(depth, index, ambiguous, wview) with wview = sum of the views' weights at the crossing."""
+    lib = _load()
+    depths = np.ascontiguousarray(depths, np.float32)
+    td = np.ascontiguousarray(tmp_depth, np.float32)
+    tw = np.ascontiguousarray(tmp_weight, np.float32)
+    shape = (target.height, target.width)
+    out_d = np.empty(shape, np.float64)
+    out_i = np.empty(shape, np.int32)
+    out_a = np.empty(shape, np.uint8)
+    out_w = np.empty(shape, np.float64)
+    rc = lib.orc_fuse_depth_temporal(_cams(in_cams), _ptr(depths), len(in_cams), ctypes.byref(_cam(target)),
+                                     int(num_samples), float(np.float32(z_near)), float(np.float32(z_far)),
+                                     float(np.float32(mu)), float(weight_const), int(window), _ptr(td), _ptr(tw),
+                                     _ptr(out_d), _ptr(out_i), _ptr(out_a), _ptr(out_w))
+    if rc != 0:
+        raise ValueError("orc_fuse_depth_temporal rejected its arguments")
+    return {"depth": out_d, "index": out_i, "ambiguous": out_a, "wview": out_w}
 
 
 def fuse_depth_grad(in_cams, depths, target, num_samples, z_near, z_far, mu, grad_fused,

@@ -178,6 +178,9 @@ typedef struct {
     int64_t *addr_fp64_mismatch;
     float (*M)[9]; float (*b)[3];
     int64_t p0, p1;
+    /* temporal term (Supplement A.2), per target pixel, or NULL */
+    const float *tmp_depth, *tmp_weight;
+    double *out_wview;
 } fuse_job;
 
 /* One target pixel: Supplement A.1 + Eq. 3 with D uniform samples. */
@@ -189,7 +192,16 @@ static void fuse_pixel(const fuse_job *jb, int i, int j, double *out_d, int32_t 
     const float dz = (float)((jb->z_far - jb->z_near) / (double)(D - 1));
     const double mu = jb->mu;
     int amb = 0;
-    double S_prev = 0.0, W_prev = 0.0, z_prev = 0.0;
+    double S_prev = 0.0, W_prev = 0.0, z_prev = 0.0, Wv_prev = 0.0;
+    double td = 0.0, tw = 0.0;
+    if (jb->tmp_depth) {
+        size_t tp = (size_t)j * jb->target->width + i;
+        if (depth_valid(jb->tmp_depth[tp]) && jb->tmp_weight[tp] > 0.0f) {
+            td = jb->tmp_depth[tp];
+            tw = jb->tmp_weight[tp];
+        }
+    }
+    if (jb->out_wview) jb->out_wview[(size_t)j * jb->target->width + i] = 0.0;
     *out_d = 0.0;
     *out_s = -1;
     for (int s = 0; s < D; ++s) {
@@ -225,6 +237,16 @@ static void fuse_pixel(const fuse_job *jb, int i, int j, double *out_d, int32_t 
             S += w * c;
             Wt += w;
         }
+        double Wv = Wt; /* the input views' weight, before the temporal term */
+        if (tw > 0.0) {
+            /* Supplement A.2: the previous output depth as one more TSDF input, at the same pixel */
+            double sdf = (td - (double)zs) / mu;
+            if (fabs(sdf + 1.0) < 1e-5) amb = 1;
+            if (sdf >= -1.0) {
+                S += tw * (sdf > 1.0 ? 1.0 : sdf);
+                Wt += tw;
+            }
+        }
         if (jb->normalize && Wt > 0.0) S /= Wt;
         double scale = jb->normalize ? 1.0 : Wt;
         if (Wt > 0.0 && fabs(S) <= 1e-5 * scale) amb = 1;
@@ -235,10 +257,12 @@ static void fuse_pixel(const fuse_job *jb, int i, int j, double *out_d, int32_t 
             /* conditioning of the interpolation against FP32 rounding of S */
             double sens = ((double)zs - z_prev) * 1e-5 * (jb->normalize ? 2.0 : (W_prev + Wt)) / (S_prev - S);
             if (sens > 0.25e-4 * fabs(*out_d)) amb = 1;
+            if (jb->out_wview) jb->out_wview[(size_t)j * jb->target->width + i] = Wv_prev + t * (Wv - Wv_prev);
             break;
         }
         S_prev = S;
         W_prev = Wt;
+        Wv_prev = Wv;
         z_prev = (double)zs;
     }
     *out_a = (uint8_t)amb;
@@ -280,7 +304,7 @@ int orc_fuse_depth(const orc_camera *in_cams, const float *depths, int n_views, 
         fuse_job jb = {in_cams, depths, n_views, target, num_samples, z_near, z_far, mu, weight_const, window,
                        normalize, pixels, n_pixels, out_depth, out_index, out_amb,
                        addr_fp64_mismatch ? &mism[t] : NULL, M, b,
-                       n_pixels * t / n_threads, n_pixels * (t + 1) / n_threads};
+                       n_pixels * t / n_threads, n_pixels * (t + 1) / n_threads, NULL, NULL, NULL};
         jobs[t] = jb;
     }
     int started = 0;
@@ -579,7 +603,7 @@ int orc_fuse_depth_grad(const orc_camera *in_cams, const float *depths, int n_vi
     float (*b)[3] = malloc(sizeof(float[3]) * n_views);
     for (int k = 0; k < n_views; ++k) compose(&in_cams[k], target, M[k], b[k]);
     fuse_job jb = {in_cams, depths, n_views, target, num_samples, z_near, z_far, mu, weight_const, window,
-                   0, NULL, 0, NULL, NULL, NULL, NULL, M, b, 0, 0};
+                   0, NULL, 0, NULL, NULL, NULL, NULL, M, b, 0, 0, NULL, NULL, NULL};
     const int W = in_cams[0].width, H = in_cams[0].height;
     const size_t plane = (size_t)W * H;
     for (size_t q = 0; q < plane * n_views; ++q) grad_depths[q] = 0.0;
@@ -860,5 +884,59 @@ int orc_refine_depth_soft(int n_views, int H, int W, const uint8_t *rgba_t, cons
     }
     free(mq);
     free(pq);
+    return 0;
+}
+
+
+/* ------------------------------------------------------------------------ */
+/* Supplement A.2: the temporal term.                                       */
+/* M(p) = max over views of the difference mask at the view's z-buffer       */
+/* winner (the splat of every view's mask, channel-wise max); 1 where no     */
+/* view covers p (reading: unknown = dynamic).                               */
+/* w_tmp(p) = min(beta_t * (w_tmp_prev(p) + w_view_prev(p)) * max(1 - M, 0), */
+/*            eta)                                                           */
+/* with w_view_prev = sum_k omega_k at the previous frame's crossing.        */
+/* The fused depth with the temporal term is orc_fuse_depth with the        */
+/* previous output depth and w_tmp as one more input at the same pixel.     */
+/* ------------------------------------------------------------------------ */
+int orc_temporal_weight(const float *masks, const int32_t *winner, int n_views, int W, int H, int Wt, int Ht,
+                        const float *w_tmp_prev, const float *w_view_prev, double beta_t, double eta,
+                        double *w_tmp_out, double *mask_out) {
+    if (!masks || !winner || n_views <= 0 || !w_tmp_prev || !w_view_prev || !w_tmp_out) return -1;
+    size_t np = (size_t)Wt * Ht;
+    for (size_t p = 0; p < np; ++p) {
+        double M = -1.0;
+        for (int k = 0; k < n_views; ++k) {
+            int32_t w = winner[(size_t)k * np + p];
+            if (w < 0) continue;
+            double m = masks[(size_t)k * W * H + (size_t)w];
+            if (m > M) M = m;
+        }
+        if (M < 0.0) M = 1.0;
+        if (mask_out) mask_out[p] = M;
+        double keep = 1.0 - M;
+        keep = keep > 0.0 ? keep : 0.0;
+        double w = beta_t * ((double)w_tmp_prev[p] + (double)w_view_prev[p]) * keep;
+        w_tmp_out[p] = w < eta ? w : eta;
+    }
+    return 0;
+}
+
+int orc_fuse_depth_temporal(const orc_camera *in_cams, const float *depths, int n_views, const orc_camera *target,
+                            int num_samples, double z_near, double z_far, double mu, double weight_const, int window,
+                            const float *tmp_depth, const float *tmp_weight, double *out_depth, int32_t *out_index,
+                            uint8_t *out_amb, double *out_wview) {
+    if (!in_cams || !depths || n_views <= 0 || !target || num_samples < 2 || !(z_near < z_far) || !(mu > 0) ||
+        !out_depth || !out_index)
+        return -1;
+    float (*M)[9] = malloc(sizeof(float[9]) * n_views);
+    float (*b)[3] = malloc(sizeof(float[3]) * n_views);
+    for (int k = 0; k < n_views; ++k) compose(&in_cams[k], target, M[k], b[k]);
+    int64_t n = (int64_t)target->width * target->height;
+    fuse_job jb = {in_cams, depths, n_views, target, num_samples, z_near, z_far, mu, weight_const, window,
+                   0, NULL, n, out_depth, out_index, out_amb, NULL, M, b, 0, n, tmp_depth, tmp_weight, out_wview};
+    fuse_worker(&jb);
+    free(M);
+    free(b);
     return 0;
 }

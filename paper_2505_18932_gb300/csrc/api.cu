@@ -326,6 +326,63 @@ gvs_status gvs_fuse_depth_from_map(const gvs_camera *in_cams, const void *map, s
     return GVS_OK;
 }
 
+gvs_status gvs_fuse_depth_temporal(const gvs_camera *in_cams, const void *map, size_t map_bytes, int32_t n_views,
+                                   const gvs_camera *target, const gvs_fuse_params *params, const float *prev_depth,
+                                   const float *w_tmp, float *fused_depth, int16_t *crossing, float *view_weight,
+                                   void *stream) {
+    int32_t W = 0, H = 0;
+    gvs_status s = check_fuse_common(in_cams, n_views, target, params, fused_depth, crossing, &W, &H);
+    if (s != GVS_OK) return s;
+    if (!prev_depth || !w_tmp || !aligned(prev_depth, 16) || !aligned(w_tmp, 16) ||
+        (view_weight && !aligned(view_weight, 16)))
+        return fail(GVS_ERR_INVALID_ARG, "fuse temporal: prev_depth and w_tmp required, 16-byte aligned");
+    const size_t need = gvs_fuse_workspace_bytes(n_views, W, H);
+    if (n_views > 0 && (!map || map_bytes < need || !aligned(map, 256)))
+        return fail(GVS_ERR_WORKSPACE, "fuse temporal: map needs %zu bytes, 256-byte aligned", need);
+    gvs::FuseArgs a = fuse_args(in_cams, map, n_views, W, H, target, *params, fused_depth, crossing);
+    a.tmp_depth = prev_depth;
+    a.tmp_weight = w_tmp;
+    a.wview = view_weight;
+    cudaError_t e = gvs::launch_fuse(a, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "fuse temporal: launch");
+    return GVS_OK;
+}
+
+gvs_status gvs_temporal_weight(const void *masks, int32_t mask_dtype, const int32_t *winner, int32_t n_views,
+                               int32_t width, int32_t height, int32_t target_width, int32_t target_height,
+                               const float *w_tmp_prev, const float *w_view_prev, float beta_t, float eta,
+                               float *w_tmp, float *target_mask, void *stream) {
+    if (n_views < 0 || n_views > GVS_MAX_VIEWS || width < 1 || height < 1 || target_width < 1 || target_height < 1 ||
+        width > GVS_MAX_DIM || height > GVS_MAX_DIM || target_width > GVS_MAX_DIM || target_height > GVS_MAX_DIM)
+        return fail(GVS_ERR_INVALID_ARG, "temporal weight: sizes out of range");
+    if (mask_dtype != GVS_F32 && mask_dtype != GVS_U8)
+        return fail(GVS_ERR_UNSUPPORTED, "temporal weight: mask_dtype must be GVS_F32 or GVS_U8");
+    if (!(isfinite(beta_t) && beta_t >= 0.0f) || !(isfinite(eta) && eta >= 0.0f))
+        return fail(GVS_ERR_INVALID_ARG, "temporal weight: beta_t and eta must be finite and >= 0");
+    if ((n_views > 0 && (!masks || !winner)) || !w_tmp_prev || !w_view_prev || !w_tmp)
+        return fail(GVS_ERR_INVALID_ARG, "temporal weight: NULL array");
+    cudaError_t e = gvs::launch_temporal_weight(masks, mask_dtype, winner, n_views, (int64_t)width * height,
+                                                (int64_t)target_width * target_height, w_tmp_prev, w_view_prev,
+                                                beta_t, eta, w_tmp, target_mask, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "temporal weight: launch");
+    return GVS_OK;
+}
+
+gvs_status gvs_guided_mask(const float *warped_depth, const uint8_t *alpha, const float *fused_depth,
+                           int32_t n_views, int32_t target_width, int32_t target_height, float mu_guide,
+                           uint8_t *guided, void *stream) {
+    if (n_views < 0 || n_views > GVS_MAX_VIEWS || target_width < 1 || target_height < 1)
+        return fail(GVS_ERR_INVALID_ARG, "guided mask: sizes out of range");
+    if (!(isfinite(mu_guide) && mu_guide >= 0.0f)) return fail(GVS_ERR_INVALID_ARG, "guided mask: mu_guide must be >= 0");
+    if (n_views == 0) return GVS_OK;
+    if (!warped_depth || !alpha || !fused_depth || !guided) return fail(GVS_ERR_INVALID_ARG, "guided mask: NULL array");
+    cudaError_t e = gvs::launch_guided_mask(warped_depth, alpha, fused_depth, n_views,
+                                            (int64_t)target_width * target_height, mu_guide, guided,
+                                            (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "guided mask: launch");
+    return GVS_OK;
+}
+
 gvs_status gvs_fuse_depth(const gvs_camera *in_cams, const void *in_depths, int32_t n_views,
                           const gvs_camera *target, const gvs_fuse_params *params, float *fused_depth,
                           int16_t *crossing, void *workspace, size_t workspace_bytes, void *stream) {

@@ -147,7 +147,8 @@ __device__ __forceinline__ bool slab_view_free(const FuseArgs &a, int k, const R
     return zhi < b.x || zlo > b.y + a.behind;
 }
 
-// S and W of one sample (Supplement A.1), exactly as the full march computes them.
+// S and W of one sample over the input views (Supplement A.1), before the
+// temporal term and the optional normalisation, exactly as the march computes them.
 template <int KMAX, typename MT>
 __device__ __forceinline__ void evaluate_sample(const FuseArgs &a, const Ray (&ray)[KMAX], float zs, float &S,
                                                 float &Wsum) {
@@ -175,7 +176,6 @@ __device__ __forceinline__ void evaluate_sample(const FuseArgs &a, const Ray (&r
             }
         }
     }
-    if (a.normalize && Wsum > 0.0f) S = S / Wsum;
 }
 
 // One warp per bundle of BX x BY target pixels.  The warp marches one sample
@@ -224,7 +224,24 @@ __device__ __forceinline__ void march_bundle(const FuseArgs &a, int bundle, int 
             corner[c].az = __fmaf_rn(M[6], ci, __fmaf_rn(M[7], cj, M[8]));
         }
     }
-    float S_prev = 0.0f, W_prev = 0.0f, z_prev = 0.0f;
+    // temporal input at this ray's pixel, and its depth range over the bundle's rays
+    float td = 0.0f, tw = 0.0f;
+    if (a.tmp_depth && inside) {
+        const size_t o = (size_t)j * a.Wt + i;
+        const float d = a.tmp_depth[o], w = a.tmp_weight[o];
+        if (valid_depth(d) && w > 0.0f) {
+            td = d;
+            tw = w;
+        }
+    }
+    float tlo = tw > 0.0f ? td : kInf, thi = tw > 0.0f ? td : -kInf;
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+        tlo = fminf(tlo, __shfl_xor_sync(0xffffffffu, tlo, m));
+        thi = fmaxf(thi, __shfl_xor_sync(0xffffffffu, thi, m));
+    }
+    float S_prev = 0.0f, W_prev = 0.0f, z_prev = 0.0f, Wv_prev = 0.0f;
+    float wview = 0.0f;
     bool have_prev = false;  // sample s-1 was evaluated (uniform across the warp)
     bool done = !inside;
     float out = 0.0f;
@@ -240,8 +257,10 @@ __device__ __forceinline__ void march_bundle(const FuseArgs &a, int bundle, int 
             bool f = false;
             if (sa < a.D - 1) {
                 const int sb = min(sa + L, a.D - 1);
-                f = !tview || slab_view_free(a, tk, corner, tb0, tb1, tb2, __fmaf_rn((float)sa, a.dz, a.zn),
-                                             __fmaf_rn((float)sb, a.dz, a.zn));
+                const float z0 = __fmaf_rn((float)sa, a.dz, a.zn), z1 = __fmaf_rn((float)sb, a.dz, a.zn);
+                f = !tview || slab_view_free(a, tk, corner, tb0, tb1, tb2, z0, z1);
+                // the temporal input sits at the ray's own pixel: its projected depth is the sample depth
+                f = f && (z1 < tlo || z0 > thi + a.behind);
             }
             const unsigned ball = __ballot_sync(0xffffffffu, f);
             int nfree = 0;
@@ -266,13 +285,25 @@ __device__ __forceinline__ void march_bundle(const FuseArgs &a, int bundle, int 
         if (!done) {
             float S, Wsum;
             evaluate_sample<KMAX, MT>(a, ray, zs, S, Wsum);
+            const float Wv = Wsum;
+            if (tw > 0.0f) {
+                const float sdf = (td - zs) * a.inv_mu;
+                if (sdf >= -1.0f) {
+                    S = fmaf(tw, fminf(sdf, 1.0f), S);
+                    Wsum += tw;
+                }
+            }
+            if (a.normalize && Wsum > 0.0f) S = S / Wsum;
             if (have_prev && W_prev > 0.0f && Wsum > 0.0f && S_prev > 0.0f && S <= 0.0f) {
-                out = z_prev + (zs - z_prev) * (S_prev / (S_prev - S));
+                const float t = S_prev / (S_prev - S);
+                out = z_prev + (zs - z_prev) * t;
+                wview = Wv_prev + t * (Wv - Wv_prev);
                 idx = s - 1;
                 done = true;
             }
             S_prev = S;
             W_prev = Wsum;
+            Wv_prev = Wv;
             z_prev = zs;
         }
         have_prev = true;
@@ -283,6 +314,7 @@ __device__ __forceinline__ void march_bundle(const FuseArgs &a, int bundle, int 
         const size_t o = (size_t)j * a.Wt + i;
         a.fused[o] = out;
         if (a.crossing) a.crossing[o] = (int16_t)idx;
+        if (a.wview) a.wview[o] = wview;
     }
 }
 

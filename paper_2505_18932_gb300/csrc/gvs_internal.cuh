@@ -73,6 +73,11 @@ struct FuseArgs {
     float behind;              // a sample is surely cut off where z > d_max + behind (= 1.0001 mu)
     int normalize;
     int variant;               // bundle shape / slab-test lengths (same result, different speed)
+    // temporal term (Supplement A.2): per target pixel the previous output depth and its
+    // weight, added as one more input at the ray's own pixel; null when absent
+    const float *tmp_depth;
+    const float *tmp_weight;
+    float *wview;              // out: the input views' weight at the crossing (or null)
     float *fused;
     int16_t *crossing;
     ViewXform xf[GVS_MAX_VIEWS];
@@ -133,6 +138,11 @@ struct SplatArgs {
 
 cudaError_t launch_splat(const SplatArgs &a, int K, cudaStream_t st);
 cudaError_t launch_soft_splat(const SplatArgs &a, int K, cudaStream_t st);
+cudaError_t launch_temporal_weight(const void *masks, int mask_dtype, const int32_t *winner, int K, int64_t HW,
+                                   int64_t HWt, const float *w_tmp_prev, const float *w_view_prev, float beta_t,
+                                   float eta, float *w_tmp, float *target_mask, cudaStream_t st);
+cudaError_t launch_guided_mask(const float *warped_depth, const uint8_t *alpha, const float *fused, int K,
+                               int64_t HWt, float mu_guide, uint8_t *guided, cudaStream_t st);
 cudaError_t launch_soft_splat_backward(const SplatArgs &a, int K, cudaStream_t st);
 
 }  // namespace gvs

@@ -376,4 +376,64 @@ cudaError_t launch_soft_splat_backward(const SplatArgs &a, int K, cudaStream_t s
     return cudaGetLastError();
 }
 
+namespace {
+
+// Supplement A.2: the target-view difference mask is the largest of the
+// views' masks at their z-buffer winners (1 where no view covers the pixel),
+// and w_tmp = min(beta_t (w_tmp_prev + w_view_prev) max(1 - M, 0), eta).
+template <typename MK>
+__global__ void __launch_bounds__(256) temporal_weight_kernel(const MK *__restrict__ masks, const int32_t *__restrict__ winner,
+                                                              int K, int64_t HW, int64_t HWt,
+                                                              const float *__restrict__ w_tmp_prev,
+                                                              const float *__restrict__ w_view_prev, float beta_t,
+                                                              float eta, float *__restrict__ w_tmp,
+                                                              float *__restrict__ target_mask) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= HWt) return;
+    float M = -1.0f;
+    for (int k = 0; k < K; ++k) {
+        const int32_t w = winner[(size_t)k * HWt + p];
+        if (w >= 0) M = fmaxf(M, (float)masks[(size_t)k * HW + w]);
+    }
+    if (M < 0.0f) M = 1.0f;
+    if (target_mask) target_mask[p] = M;
+    const float keep = fmaxf(1.0f - M, 0.0f);
+    w_tmp[p] = fminf(beta_t * (w_tmp_prev[p] + w_view_prev[p]) * keep, eta);
+}
+
+__global__ void __launch_bounds__(256) guided_mask_kernel(const float *__restrict__ warped_depth,
+                                                          const uint8_t *__restrict__ alpha,
+                                                          const float *__restrict__ fused, int K, int64_t HWt,
+                                                          float mu_guide, uint8_t *__restrict__ guided) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= (int64_t)K * HWt) return;
+    const int64_t t = p % HWt;
+    guided[p] = (uint8_t)(alpha[p] && fabsf(warped_depth[p] - fused[t]) <= mu_guide);
+}
+
+}  // namespace
+
+cudaError_t launch_temporal_weight(const void *masks, int mask_dtype, const int32_t *winner, int K, int64_t HW,
+                                   int64_t HWt, const float *w_tmp_prev, const float *w_view_prev, float beta_t,
+                                   float eta, float *w_tmp, float *target_mask, cudaStream_t st) {
+    const unsigned grid = (unsigned)((HWt + 255) / 256);
+    if (mask_dtype == GVS_U8)
+        temporal_weight_kernel<uint8_t><<<grid, 256, 0, st>>>(reinterpret_cast<const uint8_t *>(masks), winner, K,
+                                                             HW, HWt, w_tmp_prev, w_view_prev, beta_t, eta, w_tmp,
+                                                             target_mask);
+    else
+        temporal_weight_kernel<float><<<grid, 256, 0, st>>>(reinterpret_cast<const float *>(masks), winner, K, HW,
+                                                           HWt, w_tmp_prev, w_view_prev, beta_t, eta, w_tmp,
+                                                           target_mask);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_guided_mask(const float *warped_depth, const uint8_t *alpha, const float *fused, int K,
+                               int64_t HWt, float mu_guide, uint8_t *guided, cudaStream_t st) {
+    const int64_t n = (int64_t)K * HWt;
+    guided_mask_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(warped_depth, alpha, fused, K, HWt, mu_guide,
+                                                                    guided);
+    return cudaGetLastError();
+}
+
 }  // namespace gvs

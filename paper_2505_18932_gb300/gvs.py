@@ -34,7 +34,7 @@ class GvsCamera(ctypes.Structure):
                 ("R", ctypes.c_double * 9), ("t", ctypes.c_double * 3)]
 
 
-GVS_F32, GVS_F16, GVS_BF16 = 0, 1, 2
+GVS_F32, GVS_F16, GVS_BF16, GVS_U8 = 0, 1, 2, 3
 
 
 class GvsRefineParams(ctypes.Structure):
@@ -98,6 +98,14 @@ API = {
                                                ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p,
                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "gvs_splat_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32] * 3),
+    "gvs_temporal_weight": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p] + [ctypes.c_int32] * 5 +
+                            [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float, ctypes.c_float, ctypes.c_void_p,
+                             ctypes.c_void_p, ctypes.c_void_p]),
+    "gvs_fuse_depth_temporal": (ctypes.c_int, [ctypes.POINTER(GvsCamera), ctypes.c_void_p, ctypes.c_size_t,
+                                               ctypes.c_int32, ctypes.POINTER(GvsCamera),
+                                               ctypes.POINTER(GvsFuseParams)] + [ctypes.c_void_p] * 6),
+    "gvs_guided_mask": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_int32] * 3 +
+                        [ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]),
     "gvs_fuse_batch_bytes": (ctypes.c_size_t, [ctypes.c_int32]),
     "gvs_fuse_batch_create": (ctypes.c_int, [ctypes.POINTER(GvsCamera), ctypes.c_int32, ctypes.POINTER(GvsFuseItem),
                                              ctypes.c_int32, ctypes.POINTER(GvsFuseParams), ctypes.c_void_p,
@@ -500,3 +508,77 @@ class FuseBatch:
             self.close()
         except Exception:
             pass
+
+
+def temporal_weight(masks, winner, w_tmp_prev, w_view_prev, beta_t=1.0, eta=15.0, w_tmp=None, target_mask=None,
+                    stream=None):
+    """Supplement A.2 temporal fusion weight (see gvs_temporal_weight).  masks float32 or uint8 [N, H, W]."""
+    lib = load()
+    N, H, W = masks.shape
+    Ht, Wt = winner.shape[1:]
+    if w_tmp is None:
+        w_tmp = torch.empty((Ht, Wt), dtype=torch.float32, device=masks.device)
+    md = GVS_U8 if masks.dtype == torch.uint8 else GVS_F32
+    st = lib.gvs_temporal_weight(_ptr(masks), md, _ptr(winner), N, W, H, Wt, Ht, _ptr(w_tmp_prev), _ptr(w_view_prev),
+                                 float(beta_t), float(eta), _ptr(w_tmp), _ptr(target_mask), _stream(stream))
+    _check("gvs_temporal_weight", st)
+    return w_tmp
+
+
+def fuse_depth_temporal(in_cams, dw_map, target, num_samples, z_near, z_far, mu, prev_depth, w_tmp, fused=None,
+                        crossing=None, view_weight=None, stream=None):
+    """fuse_depth_from_map with the previous output depth as one more input (Supplement A.2)."""
+    lib = load()
+    N = len(in_cams)
+    dev = dw_map.device
+    shape = (target.height, target.width)
+    if fused is None:
+        fused = torch.empty(shape, dtype=torch.float32, device=dev)
+    if crossing is None:
+        crossing = torch.empty(shape, dtype=torch.int16, device=dev)
+    if view_weight is None:
+        view_weight = torch.empty(shape, dtype=torch.float32, device=dev)
+    p = GvsFuseParams(int(num_samples), float(z_near), float(z_far), float(mu), 0.001, 7, 0, GVS_F32, GVS_F32, 0)
+    st = lib.gvs_fuse_depth_temporal(camera_array(in_cams), _ptr(dw_map), dw_map.numel(), N,
+                                     ctypes.byref(camera_struct(target)), ctypes.byref(p), _ptr(prev_depth),
+                                     _ptr(w_tmp), _ptr(fused), _ptr(crossing), _ptr(view_weight), _stream(stream))
+    _check("gvs_fuse_depth_temporal", st)
+    return fused, crossing, view_weight
+
+
+def guided_mask(warped_depth, alpha, fused, mu_guide, guided=None, stream=None):
+    lib = load()
+    N, Ht, Wt = warped_depth.shape
+    if guided is None:
+        guided = torch.empty((N, Ht, Wt), dtype=torch.uint8, device=warped_depth.device)
+    st = lib.gvs_guided_mask(_ptr(warped_depth), _ptr(alpha), _ptr(fused), N, Wt, Ht, float(mu_guide), _ptr(guided),
+                             _stream(stream))
+    _check("gvs_guided_mask", st)
+    return guided
+
+
+class TemporalFusion:
+    """Online fused depth with the temporal term (Sec. 3.2, Supplement A.2) for a fixed
+    novel viewpoint.  Per frame: splat the views (winners), the temporal weight from the
+    splatted difference masks and the previous frame's state, the fusion with the previous
+    output as one more input, then the guided mask.  State per target pixel: previous
+    fused depth, temporal weight, views' weight at the crossing (all start at 0)."""
+
+    def __init__(self, in_cams, target, num_samples, z_near, z_far, mu, beta_t=1.0, eta=15.0, device="cuda"):
+        self.cams, self.target = in_cams, target
+        self.cfg = dict(num_samples=num_samples, z_near=z_near, z_far=z_far, mu=mu, beta_t=beta_t, eta=eta)
+        shape = (target.height, target.width)
+        self.prev = torch.zeros(shape, dtype=torch.float32, device=device)
+        self.w_tmp_prev = torch.zeros(shape, dtype=torch.float32, device=device)
+        self.w_view_prev = torch.zeros(shape, dtype=torch.float32, device=device)
+
+    def step(self, depths, rgba, masks, ws_map=None):
+        c = self.cfg
+        m = weight_map(depths, c["mu"], ws=ws_map)
+        sp = forward_splat(self.cams, depths, rgba, self.target, fused=None, mu_guide=c["mu"])
+        w_tmp = temporal_weight(masks, sp["winner"], self.w_tmp_prev, self.w_view_prev, c["beta_t"], c["eta"])
+        fused, crossing, wview = fuse_depth_temporal(self.cams, m, self.target, c["num_samples"], c["z_near"],
+                                                     c["z_far"], c["mu"], self.prev, w_tmp)
+        sp["guided"] = guided_mask(sp["warped_depth"], sp["alpha"], fused, c["mu"])
+        self.prev, self.w_tmp_prev, self.w_view_prev = fused, w_tmp, wview
+        return fused, crossing, sp, w_tmp
