@@ -70,32 +70,33 @@ def test_fuse_temporal_plane_weighted_mean(gvs):
 
 
 def test_online_sequence_matches_oracle(gvs, oracle_mod):
-    """Three frames of a moving sphere seen from a fixed novel viewpoint: soft masks,
-    temporal weights and temporally fused depths against the oracle frame by frame
-    (each frame's oracle inputs are its own previous outputs, never the GPU's)."""
+    """Three frames of a moving sphere seen from a fixed novel viewpoint: binary
+    difference masks (bit-exact refined depths on both sides), temporal weights and
+    temporally fused depths against the oracle frame by frame (each frame's oracle
+    inputs are its own previous outputs, never the GPU's)."""
     from synth import configs
     w = configs.tiny(64, 48, 4, 96)
     tgt = w.targets[0]
     frames = [w.render_inputs(f) for f in range(4)]
     tf = gvs.TemporalFusion(w.inputs, tgt, w.num_samples, w.z_near, w.z_far, w.mu)
     state_g = to_dev(frames[0][1])
-    o_state = frames[0][1].astype(np.float64)
+    o_state = frames[0][1]
     o_prev = np.zeros((tgt.height, tgt.width), np.float32)
     o_wtmp = np.zeros_like(o_prev)
     o_wview = np.zeros_like(o_prev)
     for f in range(1, 4):
         rgb_p, rgb_c = frames[f - 1][0], frames[f][0]
-        mask_g = torch.empty(state_g.shape, device="cuda")
-        gvs.refine_depth_soft(to_dev(u32(rgb_c)), to_dev(u32(rgb_p)), to_dev(frames[f][1]), state_g, mask_g)
+        mask_g = torch.empty(state_g.shape, dtype=torch.uint8, device="cuda")
+        gvs.refine_depth(to_dev(u32(rgb_c)), to_dev(u32(rgb_p)), to_dev(frames[f][1]), state_g, mask_g, tau=w.tau)
         fused, cross, sp, w_tmp = tf.step(state_g, to_dev(u32(rgb_c)), mask_g)
         torch.cuda.synchronize()
-        o_state, o_mask = oracle_mod.refine_depth_soft(rgb_c, rgb_p, frames[f][1], o_state.astype(np.float32))
-        st32 = o_state.astype(np.float32)
-        hs = oracle_mod.forward_splat(w.inputs, st32, u32(rgb_c), tgt)
+        o_state, o_mask = oracle_mod.refine_depth(rgb_c, rgb_p, frames[f][1], o_state, w.tau)
+        hs = oracle_mod.forward_splat(w.inputs, o_state, u32(rgb_c), tgt)
+        assert np.array_equal(sp["winner"].cpu().numpy(), hs["winner"])
         o_w, _ = oracle_mod.temporal_weight(o_mask.astype(np.float32), hs["winner"], o_wtmp, o_wview)
-        ref = oracle_mod.fuse_depth_temporal(w.inputs, st32, tgt, w.num_samples, w.z_near, w.z_far, w.mu, o_prev,
+        ref = oracle_mod.fuse_depth_temporal(w.inputs, o_state, tgt, w.num_samples, w.z_near, w.z_far, w.mu, o_prev,
                                              o_w.astype(np.float32))
-        np.testing.assert_allclose(w_tmp.cpu().numpy(), o_w, rtol=1e-5, atol=1e-5)
+        np.testing.assert_allclose(w_tmp.cpu().numpy(), o_w, rtol=1e-5, atol=1e-4)
         compare_fused(fused, cross, ref)
         o_prev = ref["depth"].astype(np.float32)
         o_wtmp = o_w.astype(np.float32)
