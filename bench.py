@@ -274,6 +274,10 @@ def run_gvs(args, rank, local_rank, world):
                                       "refine + weight map + fuse + splat with FP16 depth and half2 map")}
     forms["fwd_bwd"] = form_line("fwd_bwd", w, time_form(FwdBwd(w, frames_np[:2], device), steps=min(K, 30)),
                                  "fuse + differentiable splat forward, 0.8 L1 + 0.1 L_Depth, both adjoints")
+    forms["temporal_online"] = form_line("temporal_online", w, time_form(TemporalOnline(w, frames_np, device),
+                                                                         steps=min(K, 100)),
+                                         "refine + splat + temporal weight + fusion with the previous output "
+                                         "(Supplement A.2) + guided mask, fixed novel viewpoint")
     forms.update(time_batched(device, steps=min(K, 20)))
     wd = configs.diff_640x360()
     forms["fwd_bwd_640x360"] = form_line("fwd_bwd_640x360", wd,
@@ -381,6 +385,32 @@ def time_form(pipe, steps):
     torch.cuda.synchronize()
     return {"ms_per_step": round(a.elapsed_time(b) / steps, 4), "steps": steps,
             "storage": "depth f16, (d, w) map half2, FP32 arithmetic" if pipe.half else "f32"}
+
+
+class TemporalOnline:
+    """The online video loop with the temporal term, for a fixed novel viewpoint:
+    refine (binary masks) -> weight map -> splat (winners) -> temporal weight ->
+    fusion with the previous output as an extra input -> guided mask."""
+
+    def __init__(self, w, frames_np, device):
+        import torch
+        from paper_2505_18932_gb300 import gvs
+        self.torch, self.gvs, self.w = torch, gvs, w
+        self.half = False
+        self.tgt = w.targets[0]
+        self.rgba = [torch.from_numpy(c.view(np.int32)).to(device) for c, _ in frames_np]
+        self.depth = [torch.from_numpy(d).to(device) for _, d in frames_np]
+        self.state = self.depth[0].clone()
+        N, H, W = self.depth[0].shape
+        self.mask = torch.empty((N, H, W), dtype=torch.uint8, device=device)
+        self.map = gvs.workspace(gvs.fuse_workspace_bytes(N, W, H), device)
+        self.tf = gvs.TemporalFusion(w.inputs, self.tgt, w.num_samples, w.z_near, w.z_far, w.mu, device=device)
+
+    def step(self, i, events=None):
+        w, gvs = self.w, self.gvs
+        cur, prev = i % len(self.rgba), (i - 1) % len(self.rgba)
+        gvs.refine_depth(self.rgba[cur], self.rgba[prev], self.depth[cur], self.state, self.mask, tau=w.tau)
+        self.tf.step(self.state, self.rgba[cur], self.mask, ws_map=self.map)
 
 
 def time_batched(device, steps):
