@@ -143,7 +143,8 @@ class Pipeline:
         self.fused = torch.empty((Ht, Wt), dtype=torch.float32, device=device)
         self.cross = torch.empty((Ht, Wt), dtype=torch.int16, device=device)
         self.ws_fuse = gvs.workspace(gvs.fuse_workspace_bytes(N, W, H), device)
-        self.ws_splat = gvs.workspace(gvs.splat_workspace_bytes(N, Wt, Ht), device)
+        # two z-buffers: two views per scatter/resolve pass (measured fastest; four overflow L2)
+        self.ws_splat = gvs.workspace(2 * gvs.splat_workspace_bytes(N, Wt, Ht), device)
         shape = (N, Ht, Wt)
         self.outs = {"winner": torch.empty(shape, dtype=torch.int32, device=device),
                      "warped_rgba": torch.empty(shape, dtype=torch.int32, device=device),

@@ -127,6 +127,11 @@ typedef struct {
     float max_half_width;      /* footprint half-width cap in target pixels (>= 0.5), e.g. 2 */
     float mu_guide;            /* guided mask: |warped depth - fused depth| <= mu_guide */
     int32_t depth_dtype;       /* GVS_F32 or GVS_F16: element type of in_depths */
+    int32_t guide_reject;      /* 1: before the depth test, drop every candidate lying in front of the
+                                  fused surface, h.z < fused_depth - mu_guide (FP32 subtraction), so the
+                                  z-buffer keeps the nearest surface consistent with the fused depth
+                                  (the alternative reading of the fused-depth guidance, Sec. 3.1);
+                                  needs fused_depth; a fused depth of 0 (no crossing) drops nothing */
 } gvs_splat_params;
 
 /* Differentiable colour splat (Sec. 3.1 / Supplement A.3, pixel-sized Gaussians as weights). */
@@ -431,6 +436,8 @@ GVS_API size_t gvs_splat_workspace_bytes(int32_t n_views, int32_t target_width, 
  *   point    : covers (rint(x), rint(y))
  *   key = (float bits of h.z) << 32 | (v * width + u); per target pixel the
  *   smallest key wins: the nearest surface, ties to the lower source index.
+ *   guide_reject: a candidate for target pixel p with h.z < fused_depth[p] - mu_guide
+ *   takes no part in the depth test at p.
  * in_depths is [n_views][height][width] of params->depth_dtype (widened to FP32).
  * Outputs, each [n_views][target.height][target.width] (NULL to skip, except winner):
  *   winner       int32  source pixel index v*width+u, or -1

@@ -78,7 +78,8 @@ def _load():
             lib.orc_weight.restype = dbl
             lib.orc_fuse_depth.argtypes = [cp, vp, i32, cp, i32, dbl, dbl, dbl, dbl, i32, i32, vp, i64,
                                            vp, vp, vp, vp, i32]
-            lib.orc_forward_splat.argtypes = [cp, vp, vp, i32, cp, i32, flt, flt, vp, vp, vp, vp, vp, vp, vp, vp]
+            lib.orc_forward_splat.argtypes = [cp, vp, vp, i32, cp, i32, flt, flt, i32, vp, vp, vp, vp, vp, vp, vp,
+                                              vp]
             lib.orc_splat_bruteforce.argtypes = [cp, vp, i32, cp, i32, flt, vp]
             lib.orc_fuse_depth_grad.argtypes = [cp, vp, i32, cp, i32, dbl, dbl, dbl, dbl, i32, vp, vp]
             lib.orc_refine_depth_soft.argtypes = [i32, i32, i32, vp, vp, vp, vp, dbl, dbl, vp, vp]
@@ -236,8 +237,9 @@ def fuse_depth_grad(in_cams, depths, target, num_samples, z_near, z_far, mu, gra
 
 
 def forward_splat(in_cams, depths, rgba_u32, target, footprint=True, max_half_width=2.0, mu_guide=0.04,
-                  fused=None, count_fp64=False):
-    """Per-view z-buffered forward render into the target.
+                  fused=None, count_fp64=False, guide_reject=False):
+    """Per-view z-buffered forward render into the target.  guide_reject: candidates with
+    z < float32(fused) - mu_guide (FP32) take no part in the depth test (needs `fused`).
 
     Returns dict(winner int32 [N, Ht, Wt] (-1 none), warped_rgba uint32, warped_depth float32,
     alpha uint8, guided uint8, guided_ambiguous uint8, fp64_mismatch int)."""
@@ -256,7 +258,7 @@ def forward_splat(in_cams, depths, rgba_u32, target, footprint=True, max_half_wi
     mism = ctypes.c_int64(0)
     rc = lib.orc_forward_splat(_cams(in_cams), _ptr(depths), _ptr(rgba_u32), N, ctypes.byref(_cam(target)),
                                int(bool(footprint)), ctypes.c_float(max_half_width), ctypes.c_float(mu_guide),
-                               _ptr(fz), _ptr(win), _ptr(wr), _ptr(wd), _ptr(al), _ptr(gu), _ptr(ga),
+                               int(bool(guide_reject)), _ptr(fz), _ptr(win), _ptr(wr), _ptr(wd), _ptr(al), _ptr(gu), _ptr(ga),
                                ctypes.addressof(mism) if count_fp64 else None)
     if rc != 0:
         raise ValueError("orc_forward_splat rejected its arguments")

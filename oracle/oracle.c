@@ -375,10 +375,11 @@ static uint64_t make_key(float z, uint32_t src) {
 }
 
 int orc_forward_splat(const orc_camera *in_cams, const float *depths, const uint32_t *rgba, int n_views,
-                      const orc_camera *target, int footprint, float max_hw, float mu_guide,
+                      const orc_camera *target, int footprint, float max_hw, float mu_guide, int guide_reject,
                       const double *fused, int32_t *winner, uint32_t *warped_rgba, float *warped_depth,
                       uint8_t *alpha, uint8_t *guided, uint8_t *guided_amb, int64_t *fp64_mismatch) {
     if (!in_cams || !depths || !rgba || n_views <= 0 || !target || !winner) return -1;
+    if (guide_reject && !fused) return -1;
     int Wt = target->width, Ht = target->height;
     size_t np = (size_t)Wt * Ht;
     uint64_t *key = malloc(sizeof(uint64_t) * np);
@@ -401,6 +402,13 @@ int orc_forward_splat(const orc_camera *in_cams, const float *depths, const uint
                 uint64_t kk = make_key(g.z, (uint32_t)(v * W + u));
                 for (int jj = g.j0; jj <= g.j1; ++jj)
                     for (int ii = g.i0; ii <= g.i1; ++ii) {
+                        if (guide_reject) {
+                            /* the alternative reading of the fused-depth guidance (Sec. 3.1): a candidate
+                             * in front of the fused surface by more than mu takes no part in the depth
+                             * test; an integer decision, taken in FP32 like the kernel's */
+                            float lim = (float)fused[(size_t)jj * Wt + ii] - mu_guide;
+                            if (g.z < lim) continue;
+                        }
                         uint64_t *slot = &key[(size_t)jj * Wt + ii];
                         if (kk < *slot) *slot = kk;
                     }

@@ -41,7 +41,9 @@ class BatchPlan:
         self.cross = [[torch.empty((t.height, t.width), dtype=torch.int16, device=dev) for t in self.targets]
                       for _ in range(self.F)]
         big = max(t.width * t.height for t in self.targets)
-        self.ws_splat = gvs.workspace(gvs.splat_workspace_bytes(N, big, 1), dev)
+        # room for two z-buffers of the largest target (two views per splat pass; smaller
+        # targets fit more), which stays L2-resident next to the streamed outputs
+        self.ws_splat = gvs.workspace(2 * gvs.splat_workspace_bytes(N, big, 1), dev)
         self.splat = [[{k: torch.empty((N, t.height, t.width), dtype=dt, device=dev)
                         for k, dt in (("winner", torch.int32), ("warped_rgba", torch.int32),
                                       ("warped_depth", torch.float32), ("alpha", torch.uint8),
@@ -124,5 +126,8 @@ class BatchPlan:
     def launches_per_run(self) -> int:
         n_refine = 1 + (1 if (self.N * self.shape[1] * self.shape[2]) % 4 else 0)
         per_frame = n_refine + 3                      # refine, weight map + two bound kernels
-        per_splat = 1 + 2 * self.N                    # key clear, scatter + resolve per view (one slot)
-        return self.F * per_frame + 1 + self.F * len(self.targets) * per_splat
+        per_splat = 0
+        for t in self.targets:                        # key clear, scatter + resolve per group of views
+            slots = max(1, min(self.N, self.ws_splat.numel() // (t.width * t.height * 8)))
+            per_splat += 1 + 2 * ((self.N + slots - 1) // slots)
+        return self.F * per_frame + 1 + self.F * per_splat

@@ -466,6 +466,11 @@ gvs_status gvs_forward_splat(const gvs_camera *in_cams, const void *in_depths, c
     if (guided && !(isfinite(p.mu_guide) && p.mu_guide >= 0.0f))
         return fail(GVS_ERR_INVALID_ARG, "splat: mu_guide must be >= 0");
     if (guided && !fused_depth) return fail(GVS_ERR_INVALID_ARG, "splat: guided mask needs fused_depth");
+    if (p.guide_reject != 0 && p.guide_reject != 1)
+        return fail(GVS_ERR_INVALID_ARG, "splat: guide_reject must be 0 or 1");
+    if (p.guide_reject && !fused_depth) return fail(GVS_ERR_INVALID_ARG, "splat: guide_reject needs fused_depth");
+    if (p.guide_reject && !(isfinite(p.mu_guide) && p.mu_guide >= 0.0f))
+        return fail(GVS_ERR_INVALID_ARG, "splat: mu_guide must be >= 0");
     if (n_views == 0) return GVS_OK;
     if (!in_depths || !in_rgba || !winner) return fail(GVS_ERR_INVALID_ARG, "splat: NULL array");
     const void *arrs[] = {in_depths, in_rgba, fused_depth, winner, warped_rgba, warped_depth, alpha, guided};
@@ -485,6 +490,7 @@ gvs_status gvs_forward_splat(const gvs_camera *in_cams, const void *in_depths, c
     a.Wt = target->width;
     a.Ht = target->height;
     a.footprint = p.footprint;
+    a.guide_reject = p.guide_reject;
     a.max_hw = p.max_half_width;
     a.mu_guide = p.mu_guide;
     a.fused = fused_depth;

@@ -179,23 +179,29 @@ __global__ void __launch_bounds__(256) bounds_overlap_kernel(char *__restrict__ 
     reinterpret_cast<float2 *>(map + L.off_O[l])[((size_t)k * th + ty) * tw + tx] = o;
 }
 
-template <int KMAX, typename MT, typename T>
+template <int KMAX, typename MT, typename T, bool TMP>
 __global__ void __launch_bounds__(32 * FZ_WARPS, GVS_FUSE_MIN_BLOCKS) fuse_kernel(const __grid_constant__ FuseArgs a) {
     const int nbundles = ((a.Wt + T::bx - 1) / T::bx) * ((a.Ht + T::by - 1) / T::by);
     const int bundle = blockIdx.x * FZ_WARPS + (threadIdx.x >> 5);
     if (bundle >= nbundles) return;  // the whole warp leaves together
-    march_bundle<KMAX, MT, T>(a, bundle, threadIdx.x & 31);
+    march_bundle<KMAX, MT, T, TMP>(a, bundle, threadIdx.x & 31);
 }
 
-template <int KMAX, typename MT, typename T>
+template <int KMAX, typename MT, typename T, bool TMP>
 void launch_fuse_t(const FuseArgs &a, cudaStream_t st) {
     const int64_t nb = (int64_t)((a.Wt + T::bx - 1) / T::bx) * ((a.Ht + T::by - 1) / T::by);
-    fuse_kernel<KMAX, MT, T><<<(unsigned)((nb + FZ_WARPS - 1) / FZ_WARPS), 32 * FZ_WARPS, 0, st>>>(a);
+    fuse_kernel<KMAX, MT, T, TMP><<<(unsigned)((nb + FZ_WARPS - 1) / FZ_WARPS), 32 * FZ_WARPS, 0, st>>>(a);
 }
 
 template <int KMAX, typename MT, typename T>
 struct FuseLaunch {
-    static void run(const FuseArgs &a, cudaStream_t st) { launch_fuse_t<KMAX, MT, T>(a, st); }
+    static void run(const FuseArgs &a, cudaStream_t st) { launch_fuse_t<KMAX, MT, T, false>(a, st); }
+};
+
+// With the temporal input (Supplement A.2): the default tile only.
+template <int KMAX, typename MT, typename T>
+struct FuseLaunchTemporal {
+    static void run(const FuseArgs &a, cudaStream_t st) { launch_fuse_t<KMAX, MT, T, true>(a, st); }
 };
 template <int R, typename DT, typename MT>
 cudaError_t launch_wm(const void *depth, char *map, const MapLayout &L, float mu, float wconst, float inv_w2,
@@ -255,7 +261,10 @@ int bundle_count(int Wt, int Ht, int K, int variant) {
 }
 
 cudaError_t launch_fuse(const FuseArgs &a, cudaStream_t st) {
-    by_kmax<FuseLaunch>(a.K, a.map_dtype, a.variant, a, st);
+    if (a.tmp_depth || a.wview)
+        by_kmax_tile0<FuseLaunchTemporal>(a.K, a.map_dtype, a, st);
+    else
+        by_kmax<FuseLaunch>(a.K, a.map_dtype, a.variant, a, st);
     return cudaGetLastError();
 }
 

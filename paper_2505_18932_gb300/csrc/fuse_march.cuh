@@ -184,7 +184,9 @@ __device__ __forceinline__ void evaluate_sample(const FuseArgs &a, const Ray (&r
 // crossing end for any ray of the bundle; otherwise every ray still marching
 // evaluates sample s (all KMAX views unrolled, one 8-byte gather each) and
 // checks its own crossing.  The result equals the full uniform march.
-template <int KMAX, typename MT, typename T>
+// TMP: the temporal input (previous output depth and weight) and the views'
+// weight at the crossing are compiled in only where they are used.
+template <int KMAX, typename MT, typename T, bool TMP = false>
 __device__ __forceinline__ void march_bundle(const FuseArgs &a, int bundle, int lane) {
     constexpr int BX = T::bx, BY = T::by, SKIP_LONG = T::llong, SKIP_SHORT = T::lshort;
     constexpr int NSEG = 32 / KMAX;
@@ -226,7 +228,7 @@ __device__ __forceinline__ void march_bundle(const FuseArgs &a, int bundle, int 
     }
     // temporal input at this ray's pixel, and its depth range over the bundle's rays
     float td = 0.0f, tw = 0.0f;
-    if (a.tmp_depth && inside) {
+    if (TMP && a.tmp_depth && inside) {
         const size_t o = (size_t)j * a.Wt + i;
         const float d = a.tmp_depth[o], w = a.tmp_weight[o];
         if (valid_depth(d) && w > 0.0f) {
@@ -235,10 +237,12 @@ __device__ __forceinline__ void march_bundle(const FuseArgs &a, int bundle, int 
         }
     }
     float tlo = tw > 0.0f ? td : kInf, thi = tw > 0.0f ? td : -kInf;
+    if (TMP) {
 #pragma unroll
-    for (int m = 16; m >= 1; m >>= 1) {
-        tlo = fminf(tlo, __shfl_xor_sync(0xffffffffu, tlo, m));
-        thi = fmaxf(thi, __shfl_xor_sync(0xffffffffu, thi, m));
+        for (int m = 16; m >= 1; m >>= 1) {
+            tlo = fminf(tlo, __shfl_xor_sync(0xffffffffu, tlo, m));
+            thi = fmaxf(thi, __shfl_xor_sync(0xffffffffu, thi, m));
+        }
     }
     float S_prev = 0.0f, W_prev = 0.0f, z_prev = 0.0f, Wv_prev = 0.0f;
     float wview = 0.0f;
@@ -260,7 +264,7 @@ __device__ __forceinline__ void march_bundle(const FuseArgs &a, int bundle, int 
                 const float z0 = __fmaf_rn((float)sa, a.dz, a.zn), z1 = __fmaf_rn((float)sb, a.dz, a.zn);
                 f = !tview || slab_view_free(a, tk, corner, tb0, tb1, tb2, z0, z1);
                 // the temporal input sits at the ray's own pixel: its projected depth is the sample depth
-                f = f && (z1 < tlo || z0 > thi + a.behind);
+                if (TMP) f = f && (z1 < tlo || z0 > thi + a.behind);
             }
             const unsigned ball = __ballot_sync(0xffffffffu, f);
             int nfree = 0;
@@ -286,7 +290,7 @@ __device__ __forceinline__ void march_bundle(const FuseArgs &a, int bundle, int 
             float S, Wsum;
             evaluate_sample<KMAX, MT>(a, ray, zs, S, Wsum);
             const float Wv = Wsum;
-            if (tw > 0.0f) {
+            if (TMP && tw > 0.0f) {
                 const float sdf = (td - zs) * a.inv_mu;
                 if (sdf >= -1.0f) {
                     S = fmaf(tw, fminf(sdf, 1.0f), S);
@@ -297,7 +301,7 @@ __device__ __forceinline__ void march_bundle(const FuseArgs &a, int bundle, int 
             if (have_prev && W_prev > 0.0f && Wsum > 0.0f && S_prev > 0.0f && S <= 0.0f) {
                 const float t = S_prev / (S_prev - S);
                 out = z_prev + (zs - z_prev) * t;
-                wview = Wv_prev + t * (Wv - Wv_prev);
+                if (TMP) wview = Wv_prev + t * (Wv - Wv_prev);
                 idx = s - 1;
                 done = true;
             }
@@ -314,7 +318,7 @@ __device__ __forceinline__ void march_bundle(const FuseArgs &a, int bundle, int 
         const size_t o = (size_t)j * a.Wt + i;
         a.fused[o] = out;
         if (a.crossing) a.crossing[o] = (int16_t)idx;
-        if (a.wview) a.wview[o] = wview;
+        if (TMP && a.wview) a.wview[o] = wview;
     }
 }
 
@@ -345,6 +349,22 @@ void by_kmax(int K, int map_dtype, int variant, Args... args) {
         else if (K <= 8) by_variant<8, float2, F>(variant, args...);
         else if (K <= 16) by_variant<16, float2, F>(variant, args...);
         else by_variant<32, float2, F>(variant, args...);
+    }
+}
+
+// The same for kernels built with the default tile only.
+template <template <int, typename, typename> class F, typename... Args>
+void by_kmax_tile0(int K, int map_dtype, Args... args) {
+    if (map_dtype == GVS_F16) {
+        if (K <= 4) F<4, __half2, Tile0>::run(args...);
+        else if (K <= 8) F<8, __half2, Tile0>::run(args...);
+        else if (K <= 16) F<16, __half2, Tile0>::run(args...);
+        else F<32, __half2, Tile0>::run(args...);
+    } else {
+        if (K <= 4) F<4, float2, Tile0>::run(args...);
+        else if (K <= 8) F<8, float2, Tile0>::run(args...);
+        else if (K <= 16) F<16, float2, Tile0>::run(args...);
+        else F<32, float2, Tile0>::run(args...);
     }
 }
 

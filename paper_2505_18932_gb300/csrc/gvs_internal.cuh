@@ -113,6 +113,7 @@ struct SplatArgs {
     const uint32_t *rgba;      // [K][H][W]
     int W, H, Wt, Ht;
     int footprint;
+    int guide_reject;          // drop candidates with z < fused - mu_guide before the depth test
     float max_hw, mu_guide;
     const float *fused;        // [Ht][Wt] or null
     int32_t *winner;

@@ -85,24 +85,112 @@ __device__ __forceinline__ Geo contract(const SplatView &sv, int u, int v, float
     return g;
 }
 
-// DT: float or __half depth storage, widened to FP32 before the contract.
-template <typename DT>
-__global__ void __launch_bounds__(256) splat_scatter(const SplatArgs a, int k0, int kn) {
-    const int64_t HW = (int64_t)a.W * a.H;
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= (int64_t)kn * HW) return;
-    const int kk = (int)(p / HW);
+// The covered target pixels of the contract above without its correctly
+// rounded divisions.  The three quotients are taken with the fast approximate
+// division (at most 2 ulp from the exact quotient for divisors in
+// [2^-126, 2^126]); each bound is then an integer decision on a value within
+// eps of the contract's own value, with
+//   eps = 2e-6 * (|x| + hw)   (>= 3x the worst-case difference: 2.5 ulp of the
+//                              quotient, the rho product and the two roundings
+//                              of x -/+ hw),
+// so a value further than eps from every decision boundary (an integer for
+// ceil/floor, a half-integer for round-to-nearest) gives the contract's bound.
+// Returns 1 (covered pixels in i0..j1), 0 (no pixel), or -1 when some value is
+// within eps of a boundary or out of the fast division's range: the caller
+// then evaluates the exact contract.  z is h2, computed exactly as there.
+struct Bounds {
+    int i0, i1, j0, j1;
+    float z;
+};
+
+__device__ __forceinline__ float dist_to_integer(float t) { return fabsf(t - rintf(t)); }
+
+__device__ __forceinline__ int contract_bounds_fast(const SplatView &sv, int u, int v, float d, int Wt, int Ht,
+                                                    int footprint, float max_hw, Bounds &o) {
+    if (!valid_depth(d)) return 0;
+    const float *A = sv.xf.M;
+    const float *c = sv.xf.b;
+    const float fu = (float)u, fv = (float)v;
+    const float m0 = __fmaf_rn(A[0], fu, __fmaf_rn(A[1], fv, A[2]));
+    const float m1 = __fmaf_rn(A[3], fu, __fmaf_rn(A[4], fv, A[5]));
+    const float m2 = __fmaf_rn(A[6], fu, __fmaf_rn(A[7], fv, A[8]));
+    const float h0 = __fmaf_rn(d, m0, c[0]);
+    const float h1 = __fmaf_rn(d, m1, c[1]);
+    const float h2 = __fmaf_rn(d, m2, c[2]);
+    if (!(h2 > 1e-6f)) return 0;
+    if (!(h2 < 1e30f)) return -1;
+    const float x = __fdividef(h0, h2);
+    const float y = __fdividef(h1, h2);
+    // far outside any target (|x| < 2^22 keeps eps below one pixel), or NaN: exact path
+    if (!(fabsf(x) < 4.0e6f) || !(fabsf(y) < 4.0e6f)) return -1;
+    float lox, hix, loy, hiy;
+    if (footprint) {
+        const float rho = __fmul_rn(sv.f_ratio, __fdividef(d, h2));
+        const float hw = fminf(fmaxf(__fmul_rn(0.5f, rho), 0.5f), max_hw);
+        const float a0 = __fsub_rn(x, hw), a1 = __fadd_rn(x, hw);
+        const float b0 = __fsub_rn(y, hw), b1 = __fadd_rn(y, hw);
+        const float ex = 2e-6f * (fabsf(x) + hw) + 1e-30f;
+        const float ey = 2e-6f * (fabsf(y) + hw) + 1e-30f;
+        if (!(fminf(dist_to_integer(a0), dist_to_integer(a1)) > ex) ||
+            !(fminf(dist_to_integer(b0), dist_to_integer(b1)) > ey))
+            return -1;
+        lox = ceilf(a0);
+        hix = floorf(a1);
+        loy = ceilf(b0);
+        hiy = floorf(b1);
+    } else {
+        const float ex = 2e-6f * fabsf(x) + 1e-30f, ey = 2e-6f * fabsf(y) + 1e-30f;
+        if (!(dist_to_integer(__fsub_rn(x, 0.5f)) > ex) || !(dist_to_integer(__fsub_rn(y, 0.5f)) > ey))
+            return -1;
+        lox = hix = rintf(x);
+        loy = hiy = rintf(y);
+    }
+    if (lox < 0.0f) lox = 0.0f;
+    if (loy < 0.0f) loy = 0.0f;
+    if (hix > (float)(Wt - 1)) hix = (float)(Wt - 1);
+    if (hiy > (float)(Ht - 1)) hiy = (float)(Ht - 1);
+    if (!(lox <= hix) || !(loy <= hiy)) return 0;
+    o.i0 = (int)lox; o.i1 = (int)hix; o.j0 = (int)loy; o.j1 = (int)hiy;
+    o.z = h2;
+    return 1;
+}
+
+// Block of 32 x 8 source pixels, grid (ceil(W / 32), ceil(H / 8), views of
+// the group): view, row and column come from the block coordinates, so no
+// integer division.  DT: float or __half depth storage, widened to FP32.
+// REJECT: candidates in front of the fused surface (z < fused - mu_guide)
+// take no part in the depth test.
+constexpr int SC_BX = 32, SC_BY = 8;
+
+template <typename DT, bool REJECT = false>
+__global__ void __launch_bounds__(SC_BX * SC_BY) splat_scatter(const SplatArgs a, int k0) {
+    const int u = blockIdx.x * SC_BX + threadIdx.x;
+    const int v = blockIdx.y * SC_BY + threadIdx.y;
+    if (u >= a.W || v >= a.H) return;
+    const int kk = blockIdx.z;
     const int k = k0 + kk;
-    const int src = (int)(p - (int64_t)kk * HW);
-    const int v = src / a.W;
-    const int u = src - v * a.W;
-    const float d = load_depth(reinterpret_cast<const DT *>(a.depth) + (size_t)k * HW + src);
-    const Geo g = contract(a.v[k], u, v, d, a.Wt, a.Ht, a.footprint, a.max_hw);
-    if (!g.ok) return;
-    const unsigned long long key = ((unsigned long long)__float_as_uint(g.z) << 32) | (unsigned)src;
+    const int src = v * a.W + u;
+    const float d = load_depth(reinterpret_cast<const DT *>(a.depth) + (size_t)k * a.W * a.H + src);
+    Bounds b;
+    int ok = contract_bounds_fast(a.v[k], u, v, d, a.Wt, a.Ht, a.footprint, a.max_hw, b);
+    if (ok < 0) {
+        const Geo g = contract(a.v[k], u, v, d, a.Wt, a.Ht, a.footprint, a.max_hw);
+        ok = g.ok;
+        b.i0 = g.i0; b.i1 = g.i1; b.j0 = g.j0; b.j1 = g.j1; b.z = g.z;
+    }
+    if (!ok) return;
+    const unsigned long long key = ((unsigned long long)__float_as_uint(b.z) << 32) | (unsigned)src;
     unsigned long long *slot = a.keys + (size_t)kk * a.Wt * a.Ht;
-    for (int jj = g.j0; jj <= g.j1; ++jj)
-        for (int ii = g.i0; ii <= g.i1; ++ii) atomicMin(&slot[(size_t)jj * a.Wt + ii], key);
+    for (int jj = b.j0; jj <= b.j1; ++jj)
+        for (int ii = b.i0; ii <= b.i1; ++ii) {
+            const size_t t = (size_t)jj * a.Wt + ii;
+            if (REJECT && b.z < __fsub_rn(__ldg(&a.fused[t]), a.mu_guide)) continue;
+            atomicMin(&slot[t], key);
+        }
+}
+
+inline dim3 scatter_grid(int W, int H, int kn) {
+    return dim3((unsigned)((W + SC_BX - 1) / SC_BX), (unsigned)((H + SC_BY - 1) / SC_BY), (unsigned)kn);
 }
 
 __device__ __forceinline__ void decode(unsigned long long key, bool &has, int32_t &w, float &z) {
@@ -111,14 +199,13 @@ __device__ __forceinline__ void decode(unsigned long long key, bool &has, int32_
     z = has ? __uint_as_float((uint32_t)(key >> 32)) : 0.0f;
 }
 
-// One thread per target pixel and view (any size).
-__global__ void __launch_bounds__(256) splat_resolve(const SplatArgs a, int k0, int kn) {
+// One thread per target pixel and view (any size); grid (ceil(Wt Ht / 256), views of the group).
+__global__ void __launch_bounds__(256) splat_resolve(const SplatArgs a, int k0) {
     const int64_t HWt = (int64_t)a.Wt * a.Ht;
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= (int64_t)kn * HWt) return;
-    const int kk = (int)(p / HWt);
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= HWt) return;
+    const int kk = blockIdx.y;
     const int k = k0 + kk;
-    const int64_t t = p - (int64_t)kk * HWt;
     unsigned long long *slot = a.keys + (size_t)kk * HWt;
     const unsigned long long key = slot[t];
     slot[t] = ~0ull;  // ready for the next group of views
@@ -137,14 +224,14 @@ __global__ void __launch_bounds__(256) splat_resolve(const SplatArgs a, int k0, 
 // Four consecutive target pixels per thread, every access a 16-byte (or, for
 // the byte maps, 4-byte) vector; needs Wt * Ht divisible by 4.  The four
 // colour gathers are independent, so each thread keeps four in flight.
-__global__ void __launch_bounds__(256) splat_resolve4(const SplatArgs a, int k0, int kn) {
+// Grid (ceil(Wt Ht / 1024), views of the group).
+__global__ void __launch_bounds__(256) splat_resolve4(const SplatArgs a, int k0) {
     const int64_t HWt = (int64_t)a.Wt * a.Ht;
-    const int64_t q4 = HWt / 4;
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= (int64_t)kn * q4) return;
-    const int kk = (int)(q / q4);
+    const int q4 = (int)(HWt / 4);
+    const int t4 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t4 >= q4) return;
+    const int kk = blockIdx.y;
     const int k = k0 + kk;
-    const int64_t t4 = q - (int64_t)kk * q4;
     ulonglong2 *slot = reinterpret_cast<ulonglong2 *>(a.keys + (size_t)kk * HWt) + 2 * t4;
     const ulonglong2 k01 = slot[0], k23 = slot[1];
     const ulonglong2 ones = make_ulonglong2(~0ull, ~0ull);
@@ -299,7 +386,7 @@ void soft_groups(const SplatArgs &a, int K, cudaStream_t st) {
     for (int k0 = 0; k0 < K; k0 += slots) {
         const int kn = (K - k0) < slots ? (K - k0) : slots;
         const int64_t ns = (int64_t)kn * HW, nt = (int64_t)kn * HWt;
-        splat_scatter<DT><<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(a, k0, kn);
+        splat_scatter<DT><<<scatter_grid(a.W, a.H, kn), dim3(SC_BX, SC_BY), 0, st>>>(a, k0);
         soft_accum<DT, CT><<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(a, k0, kn);
         soft_resolve<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(a, k0, kn);
     }
@@ -310,7 +397,6 @@ void soft_groups(const SplatArgs &a, int K, cudaStream_t st) {
 cudaError_t launch_splat(const SplatArgs &a, int K, cudaStream_t st) {
     if (K == 0) return cudaSuccess;
     const int64_t HWt = (int64_t)a.Wt * a.Ht;
-    const int64_t HW = (int64_t)a.W * a.H;
     const int slots = a.slots < K ? a.slots : K;
     {
         const int64_t n = HWt * slots;
@@ -322,18 +408,18 @@ cudaError_t launch_splat(const SplatArgs &a, int K, cudaStream_t st) {
     }
     for (int k0 = 0; k0 < K; k0 += slots) {
         const int kn = (K - k0) < slots ? (K - k0) : slots;
-        const int64_t ns = (int64_t)kn * HW;
-        if (a.depth_dtype == GVS_F16)
-            splat_scatter<__half><<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(a, k0, kn);
-        else
-            splat_scatter<float><<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(a, k0, kn);
-        if (HWt % 4 == 0) {
-            const int64_t nt = (int64_t)kn * (HWt / 4);
-            splat_resolve4<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(a, k0, kn);
+        const dim3 g = scatter_grid(a.W, a.H, kn), b(SC_BX, SC_BY);
+        if (a.depth_dtype == GVS_F16) {
+            if (a.guide_reject) splat_scatter<__half, true><<<g, b, 0, st>>>(a, k0);
+            else splat_scatter<__half><<<g, b, 0, st>>>(a, k0);
         } else {
-            const int64_t nt = (int64_t)kn * HWt;
-            splat_resolve<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(a, k0, kn);
+            if (a.guide_reject) splat_scatter<float, true><<<g, b, 0, st>>>(a, k0);
+            else splat_scatter<float><<<g, b, 0, st>>>(a, k0);
         }
+        if (HWt % 4 == 0)
+            splat_resolve4<<<dim3((unsigned)((HWt / 4 + 255) / 256), (unsigned)kn), 256, 0, st>>>(a, k0);
+        else
+            splat_resolve<<<dim3((unsigned)((HWt + 255) / 256), (unsigned)kn), 256, 0, st>>>(a, k0);
     }
     return cudaGetLastError();
 }

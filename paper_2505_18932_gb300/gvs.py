@@ -59,7 +59,7 @@ class GvsFuseItem(ctypes.Structure):
 
 class GvsSplatParams(ctypes.Structure):
     _fields_ = [("footprint", ctypes.c_int32), ("max_half_width", ctypes.c_float), ("mu_guide", ctypes.c_float),
-                ("depth_dtype", ctypes.c_int32)]
+                ("depth_dtype", ctypes.c_int32), ("guide_reject", ctypes.c_int32)]
 
 
 class GvsSoftSplatParams(ctypes.Structure):
@@ -366,10 +366,11 @@ def fuse_depth_from_map(in_cams, dw_map, shape, target, num_samples, z_near, z_f
 
 def forward_splat(in_cams, in_depths, in_rgba, target, fused=None, footprint=True, max_half_width=2.0,
                   mu_guide=0.04, outputs=None, ws=None, want=("warped_rgba", "warped_depth", "alpha", "guided"),
-                  stream=None):
+                  guide_reject=False, stream=None):
     """Sec. 3.1 / Supplement A.3.  in_depths float32 [N, H, W]; in_rgba int32 [N, H, W] packed RGBA8.
     Returns dict of [N, Ht, Wt] tensors: winner int32, warped_rgba int32, warped_depth float32,
-    alpha uint8, guided uint8 (guided only when `fused` is given)."""
+    alpha uint8, guided uint8 (guided only when `fused` is given).  guide_reject: candidates in
+    front of fused - mu_guide take no part in the depth test (needs `fused`)."""
     lib = load()
     N = len(in_cams)
     dev = in_depths.device
@@ -384,7 +385,7 @@ def forward_splat(in_cams, in_depths, in_rgba, target, fused=None, footprint=Tru
     if ws is None:
         ws = workspace(splat_workspace_bytes(N, target.width, target.height), dev)
     p = GvsSplatParams(int(bool(footprint)), float(max_half_width), float(mu_guide),
-                       depth_dtype_of(in_depths) if N else GVS_F32)
+                       depth_dtype_of(in_depths) if N else GVS_F32, int(bool(guide_reject)))
     st = lib.gvs_forward_splat(camera_array(in_cams), _ptr(in_depths), _ptr(in_rgba), N,
                                ctypes.byref(camera_struct(target)), ctypes.byref(p), _ptr(fused),
                                _ptr(out["winner"]), _ptr(out.get("warped_rgba")), _ptr(out.get("warped_depth")),

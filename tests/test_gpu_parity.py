@@ -141,7 +141,8 @@ def test_fuse_deterministic(gvs):
 
 # ----------------------------------------------------------------- splat --
 
-def _splat_case(gvs, oracle_mod, w, frame=0, footprint=True, max_hw=2.0, slots=None, fused=None):
+def _splat_case(gvs, oracle_mod, w, frame=0, footprint=True, max_hw=2.0, slots=None, fused=None,
+                guide_reject=False):
     rgb, d = w.render_inputs(frame)
     tgt = w.targets_at(frame)[0]
     if fused is None:
@@ -152,10 +153,12 @@ def _splat_case(gvs, oracle_mod, w, frame=0, footprint=True, max_hw=2.0, slots=N
     if slots:
         ws = gvs.workspace(slots * gvs.splat_workspace_bytes(N, tgt.width, tgt.height))
     out = gvs.forward_splat(w.inputs, to_dev(d), to_dev(u32(rgb)), tgt, fused=to_dev(fused.astype(np.float32)),
-                            footprint=footprint, max_half_width=max_hw, mu_guide=w.mu, ws=ws)
+                            footprint=footprint, max_half_width=max_hw, mu_guide=w.mu, ws=ws,
+                            guide_reject=guide_reject)
     torch.cuda.synchronize()
     ref = oracle_mod.forward_splat(w.inputs, d, u32(rgb), tgt, footprint=footprint, max_half_width=max_hw,
-                                   mu_guide=w.mu, fused=fused.astype(np.float32).astype(np.float64))
+                                   mu_guide=w.mu, fused=fused.astype(np.float32).astype(np.float64),
+                                   guide_reject=guide_reject)
     assert np.array_equal(out["winner"].cpu().numpy(), ref["winner"])
     assert np.array_equal(out["warped_rgba"].cpu().numpy().view(np.uint32), ref["warped_rgba"])
     assert np.array_equal(out["warped_depth"].cpu().numpy().view(np.uint32), ref["warped_depth"].view(np.uint32))
@@ -205,6 +208,50 @@ def test_splat_end_to_end_with_fused(gvs, oracle_mod):
     amb = ref["guided_ambiguous"].astype(bool) | rf["ambiguous"].astype(bool)[None]
     g = out["guided"].cpu().numpy()
     assert np.array_equal(g[~amb], ref["guided"][~amb])
+
+
+@pytest.mark.parametrize("footprint", [True, False])
+@pytest.mark.parametrize("disparity", [5.5, 0.5, 12.25])
+def test_splat_on_rounding_boundaries(gvs, oracle_mod, footprint, disparity):
+    """Fronto-parallel planes whose disparity puts every projected x on (or one
+    rounding away from) a half-integer, the decision boundary of both the
+    footprint bounds and the nearest pixel: the kernel's fast division must
+    hand every such pixel to the exact contract.  Depths vary per row so that
+    the quotients land on both sides of the boundary."""
+    from synth import camera_at
+    W, H = 96, 64
+    tgt = camera_at(W, H, (0.0, 0.0, 0.0))
+    base = 2.0
+    src = camera_at(W, H, (disparity * base / tgt.fx, 0.0, 0.0))
+    rows = base * (1.0 + np.ldexp(np.arange(H) - H // 2, -22))   # a few ulps around the base depth
+    dep = np.repeat(rows[:, None], W, axis=1).astype(np.float32)[None]
+    rgb = np.arange(W * H, dtype=np.uint32).reshape(1, H, W)
+    out = gvs.forward_splat([src], to_dev(dep), to_dev(rgb.view(np.int32)), tgt, footprint=footprint,
+                            want=("warped_rgba", "warped_depth", "alpha"))
+    torch.cuda.synchronize()
+    ref = oracle_mod.forward_splat([src], dep, rgb, tgt, footprint=footprint)
+    assert np.array_equal(out["winner"].cpu().numpy(), ref["winner"])
+    assert np.array_equal(out["warped_depth"].cpu().numpy().view(np.uint32), ref["warped_depth"].view(np.uint32))
+
+
+@pytest.mark.parametrize("footprint", [True, False])
+def test_splat_guide_reject_tiny(gvs, oracle_mod, footprint):
+    """Candidates in front of the (analytic) fused depth minus mu dropped before the depth test."""
+    from synth import configs
+    _splat_case(gvs, oracle_mod, configs.tiny(70, 45, 3, 24), footprint=footprint, guide_reject=True)
+
+
+def test_splat_guide_reject_plain_320x240(gvs, oracle_mod):
+    w = _workload("plain_320x240")
+    _, gt = w.render_target_gt(w.targets[0], 0)
+    # a fused depth with holes (0) and a band pushed back by 3 mu, so that some front surfaces are dropped
+    f = gt.astype(np.float32).copy()
+    f[::7, :] = 0.0
+    f[:, 100:140] += 3 * w.mu
+    ref = _splat_case(gvs, oracle_mod, w, fused=f, guide_reject=True)
+    rgb, d = w.render_inputs(0)
+    plain = oracle_mod.forward_splat(w.inputs, d, u32(rgb), w.targets[0])
+    assert not np.array_equal(ref["winner"], plain["winner"])
 
 
 def test_splat_deterministic(gvs):

@@ -102,3 +102,43 @@ def test_guided_mask_definition(oracle_mod, synth_mod):
     r = oracle_mod.forward_splat(w.inputs[:1], d[:1], _u32(rgb)[:1], w.targets[0], mu_guide=0.04,
                                  fused=fused + 0.05)
     assert r["guided"].max() == 0
+
+
+def _occluder_case():
+    """Source camera shifted along x; a background plane at depth 2 and a square
+    occluder at depth 1 in the source view, so the occluder covers background
+    pixels in the target (parallax of 10 px against 5 px)."""
+    from synth import camera_at
+    W, H = 48, 32
+    tgt = camera_at(W, H, (0.0, 0.0, 0.0))
+    src = camera_at(W, H, (10.0 / tgt.fx, 0.0, 0.0))
+    dep = np.full((1, H, W), 2.0, np.float32)
+    dep[0, 8:20, 14:30] = 1.0
+    rgb = np.arange(W * H, dtype=np.uint32).reshape(1, H, W)
+    return src, tgt, dep, rgb
+
+
+def test_guide_reject_drops_surfaces_in_front(oracle_mod, synth_mod):
+    """With the fused depth on the background plane everywhere, rejecting candidates in
+    front of fused - mu equals splatting a source whose occluder pixels are invalid; a
+    fused depth of 0 (no crossing) rejects nothing; one far behind everything rejects all."""
+    src, tgt, dep, rgb = _occluder_case()
+    H, W = dep.shape[1:]
+    plane = np.full((H, W), 2.0)
+    r = oracle_mod.forward_splat([src], dep, rgb, tgt, fused=plane, mu_guide=0.04, guide_reject=True)
+    cut = dep.copy()
+    cut[dep < 1.5] = 0.0
+    ref = oracle_mod.forward_splat([src], cut, rgb, tgt)
+    assert np.array_equal(r["winner"], ref["winner"])
+    plain = oracle_mod.forward_splat([src], dep, rgb, tgt)
+    assert not np.array_equal(plain["winner"], ref["winner"])   # the occluder did win somewhere
+    r0 = oracle_mod.forward_splat([src], dep, rgb, tgt, fused=np.zeros((H, W)), mu_guide=0.04, guide_reject=True)
+    assert np.array_equal(r0["winner"], plain["winner"])
+    far = oracle_mod.forward_splat([src], dep, rgb, tgt, fused=np.full((H, W), 50.0), mu_guide=0.04,
+                                   guide_reject=True)
+    assert far["winner"].max() == -1
+    # mu: a fused depth 0.5 in front of the plane still keeps the plane (z >= fused - mu) only if mu >= 0.5
+    near = np.full((H, W), 2.5)
+    kept = oracle_mod.forward_splat([src], cut, rgb, tgt, fused=near, mu_guide=0.5, guide_reject=True)
+    dropped = oracle_mod.forward_splat([src], cut, rgb, tgt, fused=near, mu_guide=0.49, guide_reject=True)
+    assert np.array_equal(kept["winner"], ref["winner"]) and dropped["winner"].max() == -1
