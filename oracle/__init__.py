@@ -86,6 +86,7 @@ def _load():
             lib.orc_temporal_weight.argtypes = [vp, vp, i32, i32, i32, i32, i32, vp, vp, dbl, dbl, vp, vp]
             lib.orc_fuse_depth_temporal.argtypes = [cp, vp, i32, cp, i32, dbl, dbl, dbl, dbl, i32, vp, vp, vp, vp,
                                                     vp, vp]
+            lib.orc_gauss_splat.argtypes = [cp, vp, vp, i32, cp, flt, i32, vp, i64, vp, vp, vp]
             lib.orc_soft_splat.argtypes = [cp, vp, vp, i32, cp, flt, flt, vp, vp, vp, vp, vp]
             lib.orc_soft_splat_grad.argtypes = [cp, vp, vp, i32, cp, flt, flt, vp, vp, vp, vp]
             _lib = lib
@@ -314,3 +315,30 @@ def splat_bruteforce(in_cams, depths, target, footprint=True, max_half_width=2.0
     lib.orc_splat_bruteforce(_cams(in_cams), _ptr(depths), N, ctypes.byref(_cam(target)), int(bool(footprint)),
                              ctypes.c_float(max_half_width), _ptr(win))
     return win
+
+
+def gauss_splat(in_cams, depths, rgba_u32, target, scale_px=0.5, max_radius=8, pixels=None):
+    """Pixel-sized Gaussians, alpha-composited per view (Sec. 3.1, Supplement A.3).
+    pixels: flat target indices (j * Wt + i) or None for the whole target.
+
+    Returns dict(color float64 [N, P, 4] (premultiplied rgb, opacity), depth float64 [N, P],
+    ambiguous uint8 [N, P]) with P = Ht * Wt (reshaped to [N, Ht, Wt(, 4)]) when pixels is None."""
+    lib = _load()
+    depths = np.ascontiguousarray(depths, np.float32)
+    rgba_u32 = np.ascontiguousarray(rgba_u32, np.uint32)
+    N = len(in_cams)
+    px = None if pixels is None else np.ascontiguousarray(pixels, np.int32)
+    P = target.width * target.height if px is None else len(px)
+    col = np.empty((N, P, 4), np.float64)
+    dep = np.empty((N, P), np.float64)
+    amb = np.zeros((N, P), np.uint8)
+    rc = lib.orc_gauss_splat(_cams(in_cams), _ptr(depths), _ptr(rgba_u32), N, ctypes.byref(_cam(target)),
+                             ctypes.c_float(scale_px), int(max_radius), _ptr(px), P, _ptr(col), _ptr(dep),
+                             _ptr(amb))
+    if rc != 0:
+        raise ValueError("orc_gauss_splat rejected its arguments")
+    if px is None:
+        col = col.reshape(N, target.height, target.width, 4)
+        dep = dep.reshape(N, target.height, target.width)
+        amb = amb.reshape(N, target.height, target.width)
+    return {"color": col, "depth": dep, "ambiguous": amb}

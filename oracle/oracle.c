@@ -22,6 +22,9 @@
  *   splat      Sec. 3.1 and Supplement A.3 (each input view forward-rendered
  *              separately with pixel-sized, fully opaque primitives, depth
  *              test for occlusion), as a z-buffer with a pixel footprint.
+ *   gauss      the same render with pixel-sized isotropic 3D Gaussians,
+ *              alpha-composited front to back by the rasterisation rules of
+ *              3D Gaussian splatting (see orc_gauss_splat).
  *
  * Readings where the paper is silent or inconsistent:
  *   - sign: sdf = (d_in - z_proj) / mu, positive in front of the surface,
@@ -946,5 +949,209 @@ int orc_fuse_depth_temporal(const orc_camera *in_cams, const float *depths, int 
     fuse_worker(&jb);
     free(M);
     free(b);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 3.1 / Supplement A.3: pixel-sized 3D Gaussians, alpha-composited    */
+/* front to back, each input view rendered separately (the rasterisation    */
+/* rules of 3D Gaussian splatting, Kerbl et al. 2023, restated).            */
+/*                                                                          */
+/* Per source pixel (u, v) with valid depth d: an isotropic Gaussian of     */
+/* world standard deviation s = scale_px * d / fx_source (its projection    */
+/* into the source image spans one pixel), opacity 1, colour = the pixel.   */
+/* Its mean projects to (x, y) with depth z = h.z by the splat contract.    */
+/* EWA projection into the target (isotropic, so the rotation drops out):   */
+/*   Sigma = (scale_px rho)^2 [[1 + a^2, q a b], [q a b, q^2 (1 + b^2)]]     */
+/*           + 0.3 I,                                                       */
+/*   rho = (fx_t / fx_s) (d / z), a = (x - cx)/fx, b = (y - cy)/fy,          */
+/*   q = fy / fx (target intrinsics), 0.3 px^2 the anti-aliasing dilation.   */
+/* Radius r = min(ceil(3 sqrt(lambda_max)), max_radius), lambda_max =       */
+/* mid + sqrt(max(0.1, mid^2 - det)); covered target pixels                 */
+/* i in [ceil(x - r), floor(x + r)], j alike.  Per target pixel the covering */
+/* Gaussians are taken in ascending key (bits(z) << 32 | source index):     */
+/*   alpha = min(0.99, exp(-0.5 (dx, dy) Sigma^-1 (dx, dy)^T)), (dx, dy) =   */
+/*   (x - i, y - j); alpha < 1/255: skipped; T' = T (1 - alpha) < 1e-4:     */
+/*   stop before this Gaussian; otherwise C += c alpha T, Z += z alpha T,   */
+/*   A += alpha T, T = T'.                                                  */
+/* Outputs: colour C (premultiplied, black background), opacity 1 - T,      */
+/* depth Z / A (0 where A = 0).                                             */
+/* The radius, the covered pixels and the key are integer decisions taken   */
+/* in FP32 op for op as the kernel takes them; alpha, colour and depth are  */
+/* FP64.  A pixel is flagged ambiguous where some alpha lies within 1e-4    */
+/* relative of 1/255, or some T' within 1e-4 relative of 1e-4 (an FP32      */
+/* evaluation may decide those thresholds the other way).                   */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int ok;
+    float x, y, z, r;
+    double cxx, cxy, cyy; /* inverse of Sigma (FP64) */
+    double rgb[3];
+    uint64_t key;
+    int i0, i1, j0, j1;
+} gauss_rec;
+
+static gauss_rec gauss_contract(const float A[9], const float c[3], float f_ratio, double f_ratio_d,
+                                float scale_px, const float in32[5], const double in64[5], int max_radius,
+                                int u, int v, float d, uint32_t rgba, int Wt, int Ht) {
+    gauss_rec g;
+    memset(&g, 0, sizeof(g));
+    if (!depth_valid(d)) return g;
+    float m0 = fmaf(A[0], (float)u, fmaf(A[1], (float)v, A[2]));
+    float m1 = fmaf(A[3], (float)u, fmaf(A[4], (float)v, A[5]));
+    float m2 = fmaf(A[6], (float)u, fmaf(A[7], (float)v, A[8]));
+    float h0 = fmaf(d, m0, c[0]);
+    float h1 = fmaf(d, m1, c[1]);
+    float h2 = fmaf(d, m2, c[2]);
+    if (!(h2 > 1e-6f)) return g;
+    float x = h0 / h2, y = h1 / h2;
+    /* FP32 radius, op for op as the kernel (in32 = fx, fy, cx, cy, fy/fx of the target) */
+    float rho = f_ratio * (d / h2);
+    float t = scale_px * rho;
+    float s2 = t * t;
+    float a = (x - in32[2]) / in32[0], b = (y - in32[3]) / in32[1];
+    float q = in32[4];
+    float aa = a * a, bb = b * b, ab = a * b, qq = q * q;
+    float sxx = s2 * (1.0f + aa) + 0.3f;
+    float sxy = s2 * (q * ab);
+    float syy = s2 * (qq * (1.0f + bb)) + 0.3f;
+    float p1 = sxx * syy, p2 = sxy * sxy;
+    float det = p1 - p2;
+    if (!(det > 0.0f)) return g;
+    float mid = 0.5f * (sxx + syy);
+    float disc = mid * mid - det;
+    disc = disc > 0.1f ? disc : 0.1f;
+    float lam = mid + sqrtf(disc);
+    float rr = ceilf(3.0f * sqrtf(lam));
+    if (!(rr <= (float)max_radius)) rr = (float)max_radius;
+    float lo_x = ceilf(x - rr), hi_x = floorf(x + rr);
+    float lo_y = ceilf(y - rr), hi_y = floorf(y + rr);
+    if (lo_x < 0.0f) lo_x = 0.0f;
+    if (lo_y < 0.0f) lo_y = 0.0f;
+    if (hi_x > (float)(Wt - 1)) hi_x = (float)(Wt - 1);
+    if (hi_y > (float)(Ht - 1)) hi_y = (float)(Ht - 1);
+    if (!(lo_x <= hi_x) || !(lo_y <= hi_y)) return g;
+    /* FP64 covariance and its inverse (in64 = fx, fy, cx, cy, fy/fx) */
+    double rho_d = f_ratio_d * ((double)d / (double)h2);
+    double s2d = ((double)scale_px * rho_d) * ((double)scale_px * rho_d);
+    double ad = ((double)x - in64[2]) / in64[0], bd = ((double)y - in64[3]) / in64[1], qd = in64[4];
+    double Sxx = s2d * (1.0 + ad * ad) + 0.3;
+    double Sxy = s2d * qd * ad * bd;
+    double Syy = s2d * qd * qd * (1.0 + bd * bd) + 0.3;
+    double detd = Sxx * Syy - Sxy * Sxy;
+    g.cxx = Syy / detd;
+    g.cxy = -Sxy / detd;
+    g.cyy = Sxx / detd;
+    g.ok = 1;
+    g.x = x; g.y = y; g.z = h2; g.r = rr;
+    g.i0 = (int)lo_x; g.i1 = (int)hi_x; g.j0 = (int)lo_y; g.j1 = (int)hi_y;
+    for (int ch = 0; ch < 3; ++ch) g.rgb[ch] = (double)((rgba >> (8 * ch)) & 0xffu) / 255.0;
+    return g;
+}
+
+typedef struct {
+    uint64_t key;
+    int32_t rec;
+} gauss_ref;
+
+static int cmp_gauss_ref(const void *pa, const void *pb) {
+    uint64_t a = ((const gauss_ref *)pa)->key, b = ((const gauss_ref *)pb)->key;
+    return a < b ? -1 : (a > b ? 1 : 0);
+}
+
+/* pixels: target pixel indices (j * Wt + i) to evaluate, or NULL for all (n_pixels ignored).
+ * Outputs [n_views][P]: color [.][.][4] (r, g, b premultiplied, opacity), depth, amb. */
+int orc_gauss_splat(const orc_camera *in_cams, const float *depths, const uint32_t *rgba, int n_views,
+                    const orc_camera *target, float scale_px, int max_radius, const int32_t *pixels,
+                    int64_t n_pixels, double *color, double *depth_out, uint8_t *amb) {
+    if (!in_cams || !depths || !rgba || n_views <= 0 || !target || !color || !depth_out) return -1;
+    if (!(scale_px > 0.0f) || max_radius < 1) return -1;
+    const int Wt = target->width, Ht = target->height;
+    const int64_t np = (int64_t)Wt * Ht;
+    const int64_t P = pixels ? n_pixels : np;
+    /* slot of each target pixel among the evaluated ones (-1: not evaluated) */
+    int64_t *slot = malloc(sizeof(int64_t) * (size_t)np);
+    for (int64_t p = 0; p < np; ++p) slot[p] = pixels ? -1 : p;
+    if (pixels)
+        for (int64_t s = 0; s < P; ++s) slot[pixels[s]] = s;
+    const float in32[5] = {(float)target->fx, (float)target->fy, (float)target->cx, (float)target->cy,
+                           (float)(target->fy / target->fx)};
+    const double in64[5] = {target->fx, target->fy, target->cx, target->cy, target->fy / target->fx};
+    size_t in_off = 0;
+    for (int k = 0; k < n_views; ++k) {
+        const orc_camera *vc = &in_cams[k];
+        const int W = vc->width, H = vc->height;
+        float Am[9], cm[3];
+        compose(target, vc, Am, cm);
+        const float f_ratio = (float)(target->fx / vc->fx);
+        const double f_ratio_d = target->fx / vc->fx;
+        gauss_rec *rec = malloc(sizeof(gauss_rec) * (size_t)W * H);
+        int64_t *count = calloc((size_t)P + 1, sizeof(int64_t));
+        for (int v = 0; v < H; ++v)
+            for (int u = 0; u < W; ++u) {
+                size_t s = (size_t)v * W + u;
+                rec[s] = gauss_contract(Am, cm, f_ratio, f_ratio_d, scale_px, in32, in64, max_radius, u, v,
+                                        depths[in_off + s], rgba[in_off + s], Wt, Ht);
+                rec[s].key = make_key(rec[s].z, (uint32_t)s);
+                if (!rec[s].ok) continue;
+                for (int j = rec[s].j0; j <= rec[s].j1; ++j)
+                    for (int i = rec[s].i0; i <= rec[s].i1; ++i) {
+                        int64_t sl = slot[(int64_t)j * Wt + i];
+                        if (sl >= 0) ++count[sl + 1];
+                    }
+            }
+        for (int64_t s = 0; s < P; ++s) count[s + 1] += count[s];
+        gauss_ref *list = malloc(sizeof(gauss_ref) * (size_t)(count[P] > 0 ? count[P] : 1));
+        int64_t *fill = malloc(sizeof(int64_t) * (size_t)(P > 0 ? P : 1));
+        for (int64_t s = 0; s < P; ++s) fill[s] = count[s];
+        for (size_t s = 0; s < (size_t)W * H; ++s) {
+            if (!rec[s].ok) continue;
+            for (int j = rec[s].j0; j <= rec[s].j1; ++j)
+                for (int i = rec[s].i0; i <= rec[s].i1; ++i) {
+                    int64_t sl = slot[(int64_t)j * Wt + i];
+                    if (sl >= 0) {
+                        list[fill[sl]].key = rec[s].key;
+                        list[fill[sl]].rec = (int32_t)s;
+                        ++fill[sl];
+                    }
+                }
+        }
+        for (int64_t s = 0; s < P; ++s) {
+            const int64_t p = pixels ? pixels[s] : s;
+            const double pi = (double)(p % Wt), pj = (double)(p / Wt);
+            gauss_ref *L = list + count[s];
+            const int64_t n = count[s + 1] - count[s];
+            qsort(L, (size_t)n, sizeof(gauss_ref), cmp_gauss_ref);
+            double T = 1.0, C[3] = {0.0, 0.0, 0.0}, Z = 0.0, Acc = 0.0;
+            int am = 0;
+            for (int64_t e = 0; e < n; ++e) {
+                const gauss_rec *g = &rec[L[e].rec];
+                double dx = (double)g->x - pi, dy = (double)g->y - pj;
+                double power = -0.5 * (g->cxx * dx * dx + g->cyy * dy * dy) - g->cxy * dx * dy;
+                if (power > 0.0) continue;
+                double al = exp(power);
+                al = al < 0.99 ? al : 0.99;
+                if (fabs(al - 1.0 / 255.0) <= 1e-4 / 255.0) am = 1;
+                if (al < 1.0 / 255.0) continue;
+                double Tn = T * (1.0 - al);
+                if (fabs(Tn - 1e-4) <= 1e-8) am = 1;
+                if (Tn < 1e-4) break;
+                for (int ch = 0; ch < 3; ++ch) C[ch] += g->rgb[ch] * al * T;
+                Z += (double)g->z * al * T;
+                Acc += al * T;
+                T = Tn;
+            }
+            double *o = color + ((size_t)k * P + s) * 4;
+            o[0] = C[0]; o[1] = C[1]; o[2] = C[2]; o[3] = 1.0 - T;
+            depth_out[(size_t)k * P + s] = Acc > 0.0 ? Z / Acc : 0.0;
+            if (amb) amb[(size_t)k * P + s] = (uint8_t)am;
+        }
+        free(rec);
+        free(count);
+        free(list);
+        free(fill);
+        in_off += (size_t)W * H;
+    }
+    free(slot);
     return 0;
 }
