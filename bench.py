@@ -279,6 +279,10 @@ def run_gvs(args, rank, local_rank, world):
                                                                          steps=min(K, 100)),
                                          "refine + splat + temporal weight + fusion with the previous output "
                                          "(Supplement A.2) + guided mask, fixed novel viewpoint")
+    forms["gauss_render"] = form_line("gauss_render", w, time_form(GaussRender(w, frames_np, device),
+                                                                   steps=min(K, 20)),
+                                      "8 views rendered separately with pixel-sized Gaussians, alpha-composited "
+                                      "front to back (Supplement A.3, 3DGS rules); render only")
     forms.update(time_batched(device, steps=min(K, 20)))
     wd = configs.diff_640x360()
     forms["fwd_bwd_640x360"] = form_line("fwd_bwd_640x360", wd,
@@ -412,6 +416,29 @@ class TemporalOnline:
         cur, prev = i % len(self.rgba), (i - 1) % len(self.rgba)
         gvs.refine_depth(self.rgba[cur], self.rgba[prev], self.depth[cur], self.state, self.mask, tau=w.tau)
         self.tf.step(self.state, self.rgba[cur], self.mask, ws_map=self.map)
+
+
+class GaussRender:
+    """The paper's own forward render: every input view rendered into the target with
+    pixel-sized Gaussians, alpha-composited (8 views, per frame of the ring)."""
+
+    def __init__(self, w, frames_np, device):
+        import torch
+        from paper_2505_18932_gb300 import gvs
+        self.gvs, self.w, self.half = gvs, w, False
+        self.tgt = w.targets[0]
+        self.rgba = [torch.from_numpy(c.view(np.int32)).to(device) for c, _ in frames_np]
+        self.depth = [torch.from_numpy(d).to(device) for _, d in frames_np]
+        N, H, W = self.depth[0].shape
+        shape = (N, self.tgt.height, self.tgt.width)
+        self.color = torch.empty(shape + (4,), dtype=torch.float32, device=device)
+        self.out_depth = torch.empty(shape, dtype=torch.float32, device=device)
+        self.ws = gvs.workspace(gvs.gauss_splat_workspace_bytes(W, H, self.tgt.width, self.tgt.height), device)
+
+    def step(self, i, events=None):
+        cur = i % len(self.rgba)
+        self.gvs.gauss_splat(self.w.inputs, self.depth[cur], self.rgba[cur], self.tgt, color=self.color,
+                             depth=self.out_depth, ws=self.ws)
 
 
 def time_batched(device, steps):

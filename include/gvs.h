@@ -142,6 +142,15 @@ typedef struct {
     int32_t color_dtype;       /* GVS_F32 (float RGBA) or GVS_BF16 (bfloat16 RGBA) */
 } gvs_soft_splat_params;
 
+/* Pixel-sized Gaussian forward render (Sec. 3.1, Supplement A.3). */
+#define GVS_MAX_GAUSS_RADIUS 32
+typedef struct {
+    float scale_px;            /* world standard deviation of each Gaussian = scale_px * depth / fx of its
+                                  source view, i.e. scale_px source pixels (0.5: one pixel wide at +-1 sigma) */
+    int32_t max_radius;        /* cap on the screen-space radius in target pixels, 1..GVS_MAX_GAUSS_RADIUS */
+    int32_t depth_dtype;       /* GVS_F32 or GVS_F16 */
+} gvs_gauss_params;
+
 /* Library identification and diagnostics. */
 GVS_API const char *gvs_version(void);
 GVS_API const char *gvs_status_string(gvs_status s);
@@ -478,6 +487,39 @@ GVS_API gvs_status gvs_forward_splat_noalloc(const gvs_camera *in_cams, const vo
                                              const gvs_splat_params *params, const float *fused_depth,
                                              int32_t *winner, uint32_t *warped_rgba, float *warped_depth,
                                              uint8_t *alpha, uint8_t *guided, void *stream);
+
+/*
+ * gvs_gauss_splat -- Sec. 3.1 and Supplement A.3 as the paper renders them: every
+ * input pixel becomes an isotropic, fully opaque 3D Gaussian (colour = the pixel,
+ * position from its depth, scale one source pixel) and each input view is rendered
+ * separately into the target with the rasterisation rules of 3D Gaussian splatting
+ * (Kerbl et al. 2023).  For source pixel (u, v) of view k with valid depth d:
+ *   x, y, h.z, rho      the splat contract of gvs_forward_splat (footprint mode)
+ *   a = (x - cx) / fx,  b = (y - cy) / fy,  q = fy / fx   (target intrinsics as FP32)
+ *   Sigma = (scale_px rho)^2 [[1 + a^2, q a b], [q a b, q^2 (1 + b^2)]] + 0.3 I
+ *           (the EWA projection of the isotropic Gaussian plus the 0.3 px^2 dilation)
+ *   r = min(ceil(3 sqrt(mid + sqrt(max(0.1, mid^2 - det(Sigma))))), max_radius),
+ *       mid = (Sigma_xx + Sigma_yy) / 2
+ *   covered target pixels i in [ceil(x - r), floor(x + r)], j alike
+ * All of the above in FP32, each operation rounded as written (no contraction).
+ * Per target pixel (i, j) the covering Gaussians in ascending key
+ * (float bits of h.z) << 32 | (v * width + u)   (nearest first, ties to the lower index):
+ *   alpha = min(0.99, exp(-0.5 (dx, dy) Sigma^-1 (dx, dy)^T)), (dx, dy) = (x - i, y - j);
+ *   alpha < 1/255: skipped;  T' = T (1 - alpha) < 1e-4: the walk stops before it;
+ *   otherwise C += colour * alpha * T, Z += h.z * alpha * T, A += alpha * T, T = T'.
+ * Outputs, [n_views][target.height][target.width]:
+ *   color  float4 (C.r, C.g, C.b, 1 - T): colour premultiplied (black background), opacity
+ *   depth  float  Z / A (0 where nothing lands)
+ * Colours are the RGBA8 channels / 255 (alpha channel unused).  workspace: at least
+ * gvs_gauss_splat_workspace_bytes(width, height, target width, target height, max_radius)
+ * bytes, 256-byte aligned; it holds per-pixel records and per-16x16-tile key lists.
+ */
+GVS_API size_t gvs_gauss_splat_workspace_bytes(int32_t width, int32_t height, int32_t target_width,
+                                               int32_t target_height, int32_t max_radius);
+GVS_API gvs_status gvs_gauss_splat(const gvs_camera *in_cams, const void *in_depths, const uint32_t *in_rgba,
+                                   int32_t n_views, const gvs_camera *target, const gvs_gauss_params *params,
+                                   float *color, float *depth, void *workspace, size_t workspace_bytes,
+                                   void *stream);
 
 #ifdef __cplusplus
 }

@@ -12,6 +12,7 @@
 #include <new>
 #include <vector>
 
+#include "gauss_internal.cuh"
 #include "gvs_internal.cuh"
 
 namespace {
@@ -768,5 +769,72 @@ gvs_status gvs_fuse_batch_launch(const gvs_fuse_batch *b, void *stream) {
 }
 
 void gvs_fuse_batch_destroy(gvs_fuse_batch *b) { delete b; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Pixel-sized Gaussian forward render (Sec. 3.1, Supplement A.3).
+// ---------------------------------------------------------------------------
+extern "C" {
+
+size_t gvs_gauss_splat_workspace_bytes(int32_t width, int32_t height, int32_t target_width, int32_t target_height,
+                                       int32_t max_radius) {
+    if (width < 1 || height < 1 || target_width < 1 || target_height < 1 || max_radius < 1 ||
+        max_radius > GVS_MAX_GAUSS_RADIUS)
+        return 0;
+    return gvs::gauss_layout(width, height, target_width, target_height, max_radius).total;
+}
+
+gvs_status gvs_gauss_splat(const gvs_camera *in_cams, const void *in_depths, const uint32_t *in_rgba,
+                           int32_t n_views, const gvs_camera *target, const gvs_gauss_params *params, float *color,
+                           float *depth, void *workspace, size_t workspace_bytes, void *stream) {
+    int32_t W = 0, H = 0;
+    if (!params) return fail(GVS_ERR_INVALID_ARG, "gauss splat: params is NULL");
+    if (!views_ok(in_cams, n_views, &W, &H))
+        return fail(GVS_ERR_INVALID_ARG, "gauss splat: input cameras invalid, of different sizes, or n_views out of range");
+    if (!camera_ok(target)) return fail(GVS_ERR_INVALID_ARG, "gauss splat: target camera invalid");
+    const gvs_gauss_params &p = *params;
+    if (!(isfinite(p.scale_px) && p.scale_px > 0.0f && p.scale_px <= 16.0f))
+        return fail(GVS_ERR_INVALID_ARG, "gauss splat: scale_px must be in (0, 16]");
+    if (p.max_radius < 1 || p.max_radius > GVS_MAX_GAUSS_RADIUS)
+        return fail(GVS_ERR_INVALID_ARG, "gauss splat: max_radius must be in [1, %d]", GVS_MAX_GAUSS_RADIUS);
+    if (p.depth_dtype != GVS_F32 && p.depth_dtype != GVS_F16)
+        return fail(GVS_ERR_UNSUPPORTED, "gauss splat: depth_dtype must be GVS_F32 or GVS_F16");
+    if (n_views == 0) return GVS_OK;
+    if (!in_depths || !in_rgba || !color || !depth) return fail(GVS_ERR_INVALID_ARG, "gauss splat: NULL array");
+    const void *arrs[] = {in_depths, in_rgba, color, depth};
+    for (const void *q : arrs)
+        if (!aligned(q, 16)) return fail(GVS_ERR_INVALID_ARG, "gauss splat: arrays must be 16-byte aligned");
+    const size_t need = gvs_gauss_splat_workspace_bytes(W, H, target->width, target->height, p.max_radius);
+    if (!workspace || workspace_bytes < need || !aligned(workspace, 256))
+        return fail(GVS_ERR_WORKSPACE, "gauss splat: workspace needs at least %zu bytes, 256-byte aligned", need);
+    gvs::GaussArgs a;
+    memset(&a, 0, sizeof(a));
+    a.depth = in_depths;
+    a.depth_dtype = p.depth_dtype;
+    a.rgba = in_rgba;
+    a.W = W;
+    a.H = H;
+    a.Wt = target->width;
+    a.Ht = target->height;
+    a.scale_px = p.scale_px;
+    a.max_radius = p.max_radius;
+    a.in32[0] = (float)target->fx;
+    a.in32[1] = (float)target->fy;
+    a.in32[2] = (float)target->cx;
+    a.in32[3] = (float)target->cy;
+    a.in32[4] = (float)(target->fy / target->fx);
+    a.color = reinterpret_cast<float4 *>(color);
+    a.depth_out = depth;
+    a.ws = reinterpret_cast<char *>(workspace);
+    a.L = gvs::gauss_layout(W, H, target->width, target->height, p.max_radius);
+    for (int k = 0; k < n_views; ++k) {
+        a.xf[k] = compose(*target, in_cams[k]);
+        a.f_ratio[k] = (float)(target->fx / in_cams[k].fx);
+    }
+    cudaError_t e = gvs::launch_gauss_splat(a, n_views, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "gauss splat: launch");
+    return GVS_OK;
+}
 
 }  // extern "C"

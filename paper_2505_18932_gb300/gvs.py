@@ -62,6 +62,10 @@ class GvsSplatParams(ctypes.Structure):
                 ("depth_dtype", ctypes.c_int32), ("guide_reject", ctypes.c_int32)]
 
 
+class GvsGaussParams(ctypes.Structure):
+    _fields_ = [("scale_px", ctypes.c_float), ("max_radius", ctypes.c_int32), ("depth_dtype", ctypes.c_int32)]
+
+
 class GvsSoftSplatParams(ctypes.Structure):
     _fields_ = [("max_half_width", ctypes.c_float), ("mu_band", ctypes.c_float), ("depth_dtype", ctypes.c_int32),
                 ("color_dtype", ctypes.c_int32)]
@@ -124,6 +128,10 @@ API = {
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                          ctypes.c_void_p]),
+    "gvs_gauss_splat_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32] * 5),
+    "gvs_gauss_splat": (ctypes.c_int, [ctypes.POINTER(GvsCamera), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                       ctypes.POINTER(GvsCamera), ctypes.POINTER(GvsGaussParams), ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "gvs_forward_splat_noalloc": (ctypes.c_int, [ctypes.POINTER(GvsCamera), ctypes.c_void_p, ctypes.c_void_p,
                                                  ctypes.c_int32, ctypes.POINTER(GvsCamera),
                                                  ctypes.POINTER(GvsSplatParams), ctypes.c_void_p, ctypes.c_void_p,
@@ -401,6 +409,36 @@ def _color_dtype_of(t) -> int:
     if t.dtype == torch.bfloat16:
         return GVS_BF16
     raise ValueError(f"gvs: soft-splat colour must be float32 or bfloat16, got {t.dtype}")
+
+
+def gauss_splat_workspace_bytes(width, height, target_width, target_height, max_radius=8) -> int:
+    return int(load().gvs_gauss_splat_workspace_bytes(width, height, target_width, target_height, max_radius))
+
+
+def gauss_splat(in_cams, in_depths, in_rgba, target, scale_px=0.5, max_radius=8, color=None, depth=None, ws=None,
+                stream=None):
+    """Pixel-sized Gaussians alpha-composited per view (Sec. 3.1, Supplement A.3).
+    in_depths float32/float16 [N, H, W]; in_rgba int32 [N, H, W] packed RGBA8.
+    Returns (color float32 [N, Ht, Wt, 4] premultiplied rgb + opacity, depth float32 [N, Ht, Wt])."""
+    lib = load()
+    N = len(in_cams)
+    dev = in_depths.device
+    shape = (N, target.height, target.width)
+    if color is None:
+        color = torch.empty(shape + (4,), dtype=torch.float32, device=dev)
+    if depth is None:
+        depth = torch.empty(shape, dtype=torch.float32, device=dev)
+    if N == 0:
+        return color, depth
+    H, W = in_depths.shape[1], in_depths.shape[2]
+    if ws is None:
+        ws = workspace(gauss_splat_workspace_bytes(W, H, target.width, target.height, max_radius), dev)
+    p = GvsGaussParams(float(scale_px), int(max_radius), depth_dtype_of(in_depths))
+    st = lib.gvs_gauss_splat(camera_array(in_cams), _ptr(in_depths), _ptr(in_rgba), N,
+                             ctypes.byref(camera_struct(target)), ctypes.byref(p), _ptr(color), _ptr(depth), _ptr(ws),
+                             ws.numel(), _stream(stream))
+    _check("gvs_gauss_splat", st)
+    return color, depth
 
 
 def soft_splat(in_cams, in_depths, in_color, target, max_half_width=2.0, mu_band=0.04, outputs=None, ws=None,

@@ -116,6 +116,48 @@ def test_splat_rejects_bad_arguments(lib):
     assert call(wsb=ws - 8) == 3
 
 
+def test_splat_guide_reject_arguments(lib):
+    from paper_2505_18932_gb300 import gvs
+    cams = (gvs.GvsCamera * 1)(_cam(gvs))
+    tgt = _cam(gvs)
+    ws = lib.gvs_splat_workspace_bytes(1, 64, 48)
+
+    def call(rej, fused=FAKE, mug=0.04):
+        p = gvs.GvsSplatParams(1, 2.0, mug, 0, rej)
+        return lib.gvs_forward_splat(cams, FAKE, FAKE, 1, ctypes.byref(tgt), ctypes.byref(p), fused, FAKE,
+                                     None, None, None, None, FAKE, ws, None)
+
+    assert call(2) == 1
+    assert call(1, fused=None) == 1     # rejection needs the fused depth
+    assert call(1, mug=float("nan")) == 1
+
+
+def test_gauss_splat_rejects_bad_arguments(lib):
+    from paper_2505_18932_gb300 import gvs
+    cams = (gvs.GvsCamera * 1)(_cam(gvs))
+    tgt = _cam(gvs)
+    ws = lib.gvs_gauss_splat_workspace_bytes(64, 48, 64, 48, 8)
+    # records, 4 x 3 tile counters and offsets, at most 9 tile entries per source pixel
+    assert ws >= 64 * 48 * 32 + 64 * 48 * 9 * 8
+    assert lib.gvs_gauss_splat_workspace_bytes(64, 48, 64, 48, 0) == 0
+    assert lib.gvs_gauss_splat_workspace_bytes(64, 48, 64, 48, 33) == 0
+
+    def call(scale=0.5, rmax=8, dt=0, color=FAKE, depth=FAKE, wsb=ws, params=True):
+        p = gvs.GvsGaussParams(scale, rmax, dt)
+        return lib.gvs_gauss_splat(cams, FAKE, FAKE, 1, ctypes.byref(tgt), ctypes.byref(p) if params else None,
+                                   color, depth, FAKE, wsb, None)
+
+    assert call(params=False) == 1
+    assert call(scale=0.0) == 1
+    assert call(scale=float("inf")) == 1
+    assert call(rmax=0) == 1
+    assert call(rmax=33) == 1
+    assert call(dt=2) == 2
+    assert call(color=None) == 1
+    assert call(depth=FAKE + 4) == 1
+    assert call(wsb=ws - 256) == 3
+
+
 def test_refine_rejects_bad_arguments(lib):
     from paper_2505_18932_gb300 import gvs
 

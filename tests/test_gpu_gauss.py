@@ -1,0 +1,140 @@
+"""GPU parity of the pixel-sized Gaussian render (Sec. 3.1, Supplement A.3)
+against the FP64 oracle: colour and opacity within 2e-5 absolute, depth within
+2e-5 relative, on every pixel the oracle does not flag (an alpha within 1e-4
+relative of 1/255 or a transmittance within 1e-4 relative of the 1e-4 stop).
+The radius, the covered pixels and the order are integer decisions taken by
+both sides in FP32, so every other pixel composites the same Gaussians in the
+same order."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from gpu_util import MAX_AMBIGUOUS, to_dev, u32
+
+pytestmark = pytest.mark.gpu
+
+COLOR_ATOL = 2e-5
+DEPTH_RTOL = 2e-5
+
+
+@pytest.fixture(scope="module")
+def gvs():
+    assert torch.cuda.is_available()
+    from paper_2505_18932_gb300 import gvs as g
+    g.load()
+    return g
+
+
+def _compare(col, dep, ref, pixels=None):
+    c = col.cpu().numpy().astype(np.float64)
+    d = dep.cpu().numpy().astype(np.float64)
+    N = c.shape[0]
+    if pixels is not None:
+        c = c.reshape(N, -1, 4)[:, pixels]
+        d = d.reshape(N, -1)[:, pixels]
+    amb = ref["ambiguous"].astype(bool)
+    ok = ~amb
+    err = np.abs(c - ref["color"]).max(axis=-1)
+    bad = ok & (err > COLOR_ATOL)
+    assert not bad.any(), f"colour differs at {bad.sum()} px, worst {err[bad].max():.3e}"
+    rd = ref["depth"]
+    derr = np.abs(d - rd)
+    bad = ok & (derr > DEPTH_RTOL * np.abs(rd))
+    assert not bad.any(), f"depth differs at {bad.sum()} px, worst {derr[bad].max():.3e}"
+    assert amb.mean() < MAX_AMBIGUOUS
+    return amb.mean()
+
+
+def _case(gvs, oracle_mod, w, frame=0, target=None, scale_px=0.5, max_radius=8, pixels=None, half=False):
+    rgb, d = w.render_inputs(frame)
+    tgt = target or w.targets_at(frame)[0]
+    if half:
+        d = d.astype(np.float16).astype(np.float32)
+    dd = to_dev(d).half() if half else to_dev(d)
+    col, dep = gvs.gauss_splat(w.inputs, dd, to_dev(u32(rgb)), tgt, scale_px=scale_px, max_radius=max_radius)
+    torch.cuda.synchronize()
+    ref = oracle_mod.gauss_splat(w.inputs, d, u32(rgb), tgt, scale_px=scale_px, max_radius=max_radius,
+                                 pixels=pixels)
+    _compare(col, dep, ref, pixels)
+    return col, dep, ref
+
+
+def test_gauss_single_gaussian_closed_form(gvs):
+    """One Gaussian at the principal point of an identical source and target camera:
+    alpha = min(0.99, exp(-(dx^2 + dy^2) / 1.1)), zero below 1/255."""
+    from synth import Camera
+    cam = Camera(32, 24, 100.0, 100.0, 10.0, 8.0, np.eye(3), np.zeros(3))
+    dep = np.zeros((1, 24, 32), np.float32)
+    dep[0, 8, 10] = 2.0
+    rgb = np.full((1, 24, 32), 0x00c08040, np.uint32)
+    col, d = gvs.gauss_splat([cam], to_dev(dep), to_dev(rgb), cam)
+    torch.cuda.synchronize()
+    a = col[0, ..., 3].cpu().numpy()
+    for (i, j), e in {(10, 8): 0.99, (11, 8): math.exp(-1 / 1.1), (11, 9): math.exp(-2 / 1.1),
+                      (12, 8): math.exp(-4 / 1.1), (13, 8): 0.0}.items():
+        assert a[j, i] == pytest.approx(e, abs=1e-6), (i, j)
+    assert d[0, 8, 11].item() == pytest.approx(2.0, rel=1e-6)
+
+
+def test_gauss_tiny_ragged(gvs, oracle_mod):
+    from synth import configs
+    _case(gvs, oracle_mod, configs.tiny(70, 45, 3, 24))
+
+
+def test_gauss_plain_320x240(gvs, oracle_mod):
+    from synth import configs
+    _, _, ref = _case(gvs, oracle_mod, configs.plain_320x240())
+    assert (ref["color"][..., 3] > 0.5).mean() > 0.7
+
+
+@pytest.mark.parametrize("scale_px,max_radius", [(0.5, 1), (1.5, 8), (3.0, 32)])
+def test_gauss_scales_and_radius_caps(gvs, oracle_mod, scale_px, max_radius):
+    from synth import configs
+    _case(gvs, oracle_mod, configs.tiny(64, 48, 2, 16), scale_px=scale_px, max_radius=max_radius)
+
+
+def test_gauss_magnified_target(gvs, oracle_mod):
+    """Three times the focal length: footprints of several pixels, radii up to the cap."""
+    from synth import configs
+    w = configs.tiny(64, 48, 2, 16)
+    t = w.targets[0]
+    t.fx, t.fy = t.fx * 3.0, t.fy * 3.0
+    _case(gvs, oracle_mod, w)
+
+
+def test_gauss_minified_target_long_tile_lists(gvs, oracle_mod):
+    """A quarter of the focal length: 16 Gaussians per target pixel, tile lists of several
+    thousand keys, longer than the shared-memory sort takes (the in-place global sort runs)."""
+    from synth import configs
+    w = configs.tiny(160, 120, 2, 16)
+    t = w.targets[0]
+    t.fx, t.fy = t.fx * 0.25, t.fy * 0.25
+    _case(gvs, oracle_mod, w)
+
+
+def test_gauss_f16_depth(gvs, oracle_mod):
+    from synth import configs
+    _case(gvs, oracle_mod, configs.tiny(70, 45, 3, 24), half=True)
+
+
+def test_gauss_full_size_sampled(gvs, oracle_mod):
+    """8 x 1920x1080 inputs into one 1920x1080 target, 3000 sampled target pixels."""
+    from synth import configs
+    w = configs.headline_8x1080p()
+    t = w.targets[0]
+    rng = np.random.default_rng(7)
+    px = rng.choice(t.width * t.height, 3000, replace=False).astype(np.int32)
+    _case(gvs, oracle_mod, w, frame=1, pixels=px)
+
+
+def test_gauss_deterministic(gvs):
+    from synth import configs
+    w = configs.plain_320x240()
+    rgb, d = w.render_inputs(0)
+    dd, cc = to_dev(d), to_dev(u32(rgb))
+    a = gvs.gauss_splat(w.inputs, dd, cc, w.targets[0])
+    b = gvs.gauss_splat(w.inputs, dd, cc, w.targets[0])
+    torch.cuda.synchronize()
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
