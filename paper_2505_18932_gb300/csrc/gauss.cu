@@ -5,9 +5,10 @@
 //            (x, y) and depth z; EWA covariance
 //              Sigma = (scale rho)^2 [[1 + a^2, q a b], [q a b, q^2 (1 + b^2)]] + 0.3 I
 //            (rho = f (d / z), a = (x - cx) / fx, b = (y - cy) / fy, q = fy / fx);
-//            radius r = min(ceil(3 sqrt(lambda_max)), max_radius); the
-//            record (x, y, z, r | conic, colour); one counter increment per
-//            16 x 16 target tile its box [x - r, x + r] x [y - r, y + r] meets.
+//            radius r = min(ceil(3 sqrt(lambda_max)), max_radius), narrowed
+//            to where alpha can reach 1/255 (see GaussRec); the record
+//            (x, y, z, half-widths | conic, colour); one counter increment per
+//            16 x 16 target tile its box meets (warp-aggregated atomics).
 //   scan   : exclusive scan of the tile counters -> list offsets.
 //   fill   : each Gaussian writes its key (bits(z) << 32 | source index) into
 //            the list of every tile it meets.
@@ -32,20 +33,44 @@ __device__ __forceinline__ bool valid_depth(float d) { return isfinite(d) && d >
 __device__ __forceinline__ float load_depth(const float *p) { return __ldg(p); }
 __device__ __forceinline__ float load_depth(const __half *p) { return __half2float(__ldg(p)); }
 
+// a.w holds the half-widths (hx, hy) of the Gaussian's box as a half2 (bits 0:
+// no Gaussian): the contract radius r, tightened to the extent of the ellipse
+// where alpha can reach 1/255, sqrt(2 ln 255 Sigma_xx) (and yy), widened by
+// 0.1 % + 1e-3 px and rounded up.  A pixel between that box and the contract's
+// [x - r, x + r] box has alpha below 1/255 by more than 1 % and is skipped by
+// both, so the narrower box changes no result; it only shortens the lists.
 struct GaussRec {
-    float4 a;  // x, y, z, r (r = 0: no Gaussian)
-    float4 b;  // conic xx, xy, yy, colour bits
+    float4 a;  // x, y, z, half2 (hx, hy)
+    float4 b;  // -conic_xx / 2, -conic_xy, -conic_yy / 2, colour bits
 };
+
+__device__ __forceinline__ float2 half_widths(float w) {
+    const unsigned bits = __float_as_uint(w);
+    return __half22float2(*reinterpret_cast<const __half2 *>(&bits));
+}
+
+// Warp-aggregated atomicAdd of 1 on ctr[t]: lanes adding to the same counter
+// share one atomic; each gets a distinct old value.
+__device__ __forceinline__ unsigned agg_increment(unsigned *ctr, int t) {
+    const unsigned peers = __match_any_sync(__activemask(), t);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(&ctr[t], (unsigned)__popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    return base + __popc(peers & ((1u << lane) - 1u));
+}
 
 __device__ __forceinline__ GaussRec *recs(const GaussArgs &g) {
     return reinterpret_cast<GaussRec *>(g.ws + g.L.off_rec);
 }
 
-// Covered target pixels of a record: [ceil(x - r), floor(x + r)] clipped (and y alike).
+// Target pixels of a record's box: [ceil(x - hx), floor(x + hx)] clipped (and y alike).
 __device__ __forceinline__ bool box_of(const GaussArgs &g, float4 a, int &i0, int &i1, int &j0, int &j1) {
-    if (!(a.w > 0.0f)) return false;
-    float lx = ceilf(__fsub_rn(a.x, a.w)), hx = floorf(__fadd_rn(a.x, a.w));
-    float ly = ceilf(__fsub_rn(a.y, a.w)), hy = floorf(__fadd_rn(a.y, a.w));
+    if (__float_as_uint(a.w) == 0u) return false;
+    const float2 h = half_widths(a.w);
+    float lx = ceilf(__fsub_rn(a.x, h.x)), hx = floorf(__fadd_rn(a.x, h.x));
+    float ly = ceilf(__fsub_rn(a.y, h.y)), hy = floorf(__fadd_rn(a.y, h.y));
     if (lx < 0.0f) lx = 0.0f;
     if (ly < 0.0f) ly = 0.0f;
     if (hx > (float)(g.Wt - 1)) hx = (float)(g.Wt - 1);
@@ -96,19 +121,24 @@ __global__ void __launch_bounds__(256) gauss_prep(const GaussArgs g, int k) {
                 const float lam = __fadd_rn(mid, __fsqrt_rn(disc));
                 float rr = ceilf(__fmul_rn(3.0f, __fsqrt_rn(lam)));
                 if (!(rr <= (float)g.max_radius)) rr = (float)g.max_radius;
-                r.a = make_float4(x, y, h2, rr);
+                const float ex = fmaf(sqrtf(11.0825271f * sxx), 1.001f, 1e-3f);  // 2 ln 255 = 11.0825271
+                const float ey = fmaf(sqrtf(11.0825271f * syy), 1.001f, 1e-3f);
+                const __half2 hw = __halves2half2(__float2half_ru(fminf(ex, rr)), __float2half_ru(fminf(ey, rr)));
+                r.a = make_float4(x, y, h2, __uint_as_float(*reinterpret_cast<const unsigned *>(&hw)));
                 const float inv = 1.0f / det;
-                r.b = make_float4(syy * inv, -sxy * inv, sxx * inv, __uint_as_float(__ldg(&g.rgba[(size_t)k * HW + src])));
+                r.b = make_float4(-0.5f * syy * inv, sxy * inv, -0.5f * sxx * inv,
+                                  __uint_as_float(__ldg(&g.rgba[(size_t)k * HW + src])));
             }
         }
     }
     int i0, i1, j0, j1;
-    if (!box_of(g, r.a, i0, i1, j0, j1)) r.a.w = 0.0f;
+    const bool any = box_of(g, r.a, i0, i1, j0, j1);
+    if (!any) r.a.w = 0.0f;
     recs(g)[src] = r;
-    if (r.a.w > 0.0f) {
+    if (any) {
         unsigned *count = reinterpret_cast<unsigned *>(g.ws + g.L.off_count);
         for (int ty = j0 / GS_TILE; ty <= j1 / GS_TILE; ++ty)
-            for (int tx = i0 / GS_TILE; tx <= i1 / GS_TILE; ++tx) atomicAdd(&count[ty * g.L.tiles_x + tx], 1u);
+            for (int tx = i0 / GS_TILE; tx <= i1 / GS_TILE; ++tx) agg_increment(count, ty * g.L.tiles_x + tx);
     }
 }
 
@@ -168,7 +198,7 @@ __global__ void __launch_bounds__(256) gauss_fill(const GaussArgs g) {
     for (int ty = j0 / GS_TILE; ty <= j1 / GS_TILE; ++ty)
         for (int tx = i0 / GS_TILE; tx <= i1 / GS_TILE; ++tx) {
             const int t = ty * g.L.tiles_x + tx;
-            keys[off[t] + atomicAdd(&cursor[t], 1u)] = key;
+            keys[off[t] + agg_increment(cursor, t)] = key;
         }
 }
 
@@ -204,9 +234,14 @@ __device__ void block_sort(unsigned long long *key, int n) {
     }
 }
 
+// Threads of a block: 8 warps, each an 8 x 4 rectangle of the 16 x 16 tile
+// (2 across, 4 down).  Per batch of 256 sorted Gaussians every warp first
+// compacts, in order, the ones whose box meets its rectangle, then each lane
+// walks that shorter list for its pixel.
 __global__ void __launch_bounds__(GS_THREADS) gauss_render(const GaussArgs g, int k) {
     __shared__ unsigned long long skeys[GS_SORT_CAP];
-    __shared__ float4 sa[GS_THREADS], sb[GS_THREADS];
+    __shared__ float4 sa[GS_THREADS], sb[GS_THREADS], sc[GS_THREADS];
+    __shared__ unsigned char wlist[GS_THREADS / 32][GS_THREADS];
     const int t = blockIdx.y * g.L.tiles_x + blockIdx.x;
     const unsigned long long *off = reinterpret_cast<const unsigned long long *>(g.ws + g.L.off_offset);
     unsigned long long *gkeys = reinterpret_cast<unsigned long long *>(g.ws + g.L.off_keys) + off[t];
@@ -218,9 +253,12 @@ __global__ void __launch_bounds__(GS_THREADS) gauss_render(const GaussArgs g, in
     }
     __syncthreads();
     block_sort(keys, n);
-    const int i = blockIdx.x * GS_TILE + (threadIdx.x % GS_TILE);
-    const int j = blockIdx.y * GS_TILE + (threadIdx.x / GS_TILE);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rx = blockIdx.x * GS_TILE + (warp & 1) * 8, ry = blockIdx.y * GS_TILE + (warp >> 1) * 4;
+    const int i = rx + (lane & 7);
+    const int j = ry + (lane >> 3);
     const bool inside = i < g.Wt && j < g.Ht;
+    const float rx0 = (float)rx, rx1 = (float)(rx + 7), ry0 = (float)ry, ry1 = (float)(ry + 3);
     const float fi = (float)i, fj = (float)j;
     bool done = !inside;
     float T = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f, zs = 0.0f, ws = 0.0f;
@@ -230,21 +268,46 @@ __global__ void __launch_bounds__(GS_THREADS) gauss_render(const GaussArgs g, in
         const int e = b0 + threadIdx.x;
         if (e < n) {
             const unsigned src = (unsigned)(keys[e] & 0xffffffffull);
-            sa[threadIdx.x] = rec[src].a;
-            sb[threadIdx.x] = rec[src].b;
+            const GaussRec r = rec[src];
+            sa[threadIdx.x] = r.a;
+            sb[threadIdx.x] = r.b;
+            const unsigned col = __float_as_uint(r.b.w);
+            sc[threadIdx.x] = make_float4((float)(col & 0xffu) * (1.0f / 255.0f),
+                                          (float)((col >> 8) & 0xffu) * (1.0f / 255.0f),
+                                          (float)((col >> 16) & 0xffu) * (1.0f / 255.0f), 0.0f);
         }
         __syncthreads();
         const int m = min(GS_THREADS, n - b0);
-        for (int q = 0; q < m && !done; ++q) {
+        // the Gaussians of this batch whose box meets the warp's rectangle (same rounded
+        // bounds as the per-pixel test, so none that covers one of its pixels is dropped)
+        int cnt = 0;
+        for (int base = 0; base < m; base += 32) {
+            const int q = base + lane;
+            bool hit = false;
+            if (q < m) {
+                const float4 a = sa[q];
+                const float2 h = half_widths(a.w);
+                hit = !(rx1 < __fsub_rn(a.x, h.x) || rx0 > __fadd_rn(a.x, h.x) || ry1 < __fsub_rn(a.y, h.y) ||
+                        ry0 > __fadd_rn(a.y, h.y));
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, hit);
+            if (hit) wlist[warp][cnt + __popc(bal & ((1u << lane) - 1u))] = (unsigned char)q;
+            cnt += __popc(bal);
+        }
+        __syncwarp();
+        for (int e = 0; e < cnt && !done; ++e) {
+            const int q = wlist[warp][e];
             const float4 a = sa[q];
-            if (fi < __fsub_rn(a.x, a.w) || fi > __fadd_rn(a.x, a.w) || fj < __fsub_rn(a.y, a.w) ||
-                fj > __fadd_rn(a.y, a.w))
+            const float2 h = half_widths(a.w);
+            if (fi < __fsub_rn(a.x, h.x) || fi > __fadd_rn(a.x, h.x) || fj < __fsub_rn(a.y, h.y) ||
+                fj > __fadd_rn(a.y, h.y))
                 continue;
             const float4 c = sb[q];
             const float dx = a.x - fi, dy = a.y - fj;
-            const float power = -0.5f * (c.x * dx * dx + c.z * dy * dy) - c.y * dx * dy;
-            if (power > 0.0f) continue;
-            const float al = fminf(0.99f, expf(power));
+            const float power = fmaf(dx, fmaf(c.x, dx, c.y * dy), c.z * dy * dy);
+            // exp(-5.6) < 1/255 whatever the rounding of the exponential: skip without it
+            if (power > 0.0f || power < -5.6f) continue;
+            const float al = fminf(0.99f, __expf(power));
             if (al < 1.0f / 255.0f) continue;
             const float Tn = T * (1.0f - al);
             if (Tn < 1e-4f) {
@@ -252,10 +315,10 @@ __global__ void __launch_bounds__(GS_THREADS) gauss_render(const GaussArgs g, in
                 break;
             }
             const float wgt = al * T;
-            const unsigned col = __float_as_uint(c.w);
-            cr = fmaf((float)(col & 0xffu) * (1.0f / 255.0f), wgt, cr);
-            cg = fmaf((float)((col >> 8) & 0xffu) * (1.0f / 255.0f), wgt, cg);
-            cb = fmaf((float)((col >> 16) & 0xffu) * (1.0f / 255.0f), wgt, cb);
+            const float4 cc = sc[q];
+            cr = fmaf(cc.x, wgt, cr);
+            cg = fmaf(cc.y, wgt, cg);
+            cb = fmaf(cc.z, wgt, cb);
             zs = fmaf(a.z, wgt, zs);
             ws += wgt;
             T = Tn;

@@ -7,7 +7,7 @@
 namespace gvs {
 
 constexpr int GS_TILE = 16;        // target tiles of 16 x 16 pixels, one block each
-constexpr int GS_SORT_CAP = 4096;  // tile lists up to this length are sorted in shared memory
+constexpr int GS_SORT_CAP = 2048;  // tile lists up to this length are sorted in shared memory
 
 // Byte layout of the Gaussian-render workspace (256-byte aligned sections):
 // per source pixel two float4 records, per target tile a counter and a 64-bit
