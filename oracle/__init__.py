@@ -86,6 +86,8 @@ def _load():
             lib.orc_temporal_weight.argtypes = [vp, vp, i32, i32, i32, i32, i32, vp, vp, dbl, dbl, vp, vp]
             lib.orc_fuse_depth_temporal.argtypes = [cp, vp, i32, cp, i32, dbl, dbl, dbl, dbl, i32, vp, vp, vp, vp,
                                                     vp, vp]
+            lib.orc_blend_features.argtypes = [cp, i32, cp, vp, vp, vp, vp, vp]
+            lib.orc_blend.argtypes = [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
             lib.orc_gauss_splat.argtypes = [cp, vp, vp, i32, cp, flt, i32, vp, i64, vp, vp, vp]
             lib.orc_soft_splat.argtypes = [cp, vp, vp, i32, cp, flt, flt, vp, vp, vp, vp, vp]
             lib.orc_soft_splat_grad.argtypes = [cp, vp, vp, i32, cp, flt, flt, vp, vp, vp, vp]
@@ -342,3 +344,39 @@ def gauss_splat(in_cams, depths, rgba_u32, target, scale_px=0.5, max_radius=8, p
         dep = dep.reshape(N, target.height, target.width)
         amb = amb.reshape(N, target.height, target.width)
     return {"color": col, "depth": dep, "ambiguous": amb}
+
+
+def blend_features(in_cams, target, warped_rgba, warped_depth, alpha, fused):
+    """The (9K + 1) x Ht x Wt input of the blending network (Sec. 3.3 and the supplement's
+    input list), FP64.  warped_rgba uint32 [K, Ht, Wt], warped_depth float32, alpha uint8,
+    fused float32 [Ht, Wt]."""
+    lib = _load()
+    K = len(in_cams)
+    wr = np.ascontiguousarray(warped_rgba, np.uint32)
+    wd = np.ascontiguousarray(warped_depth, np.float32)
+    al = np.ascontiguousarray(alpha, np.uint8)
+    fz = np.ascontiguousarray(fused, np.float32)
+    out = np.empty((9 * K + 1, target.height, target.width), np.float64)
+    rc = lib.orc_blend_features(_cams(in_cams), K, ctypes.byref(_cam(target)), _ptr(wr), _ptr(wd), _ptr(al),
+                                _ptr(fz), _ptr(out))
+    if rc != 0:
+        raise ValueError("orc_blend_features rejected its arguments")
+    return out
+
+
+def blend(warped_rgba, alpha, warped_depth, fused, w, w_bg, i_bg):
+    """Eqs. 4-5 and L_Depth.  w float [K, H, W], w_bg [H, W], i_bg [3, H, W].
+    Returns (image float64 [3, H, W], L_Depth)."""
+    lib = _load()
+    wr = np.ascontiguousarray(warped_rgba, np.uint32)
+    K, H, W = wr.shape
+    out = np.empty((3, H, W), np.float64)
+    L = ctypes.c_double(0.0)
+    rc = lib.orc_blend(K, W, H, _ptr(wr), _ptr(np.ascontiguousarray(alpha, np.uint8)),
+                       _ptr(np.ascontiguousarray(warped_depth, np.float32)),
+                       _ptr(np.ascontiguousarray(fused, np.float32)), _ptr(np.ascontiguousarray(w, np.float64)),
+                       _ptr(np.ascontiguousarray(w_bg, np.float64)), _ptr(np.ascontiguousarray(i_bg, np.float64)),
+                       _ptr(out), ctypes.addressof(L))
+    if rc != 0:
+        raise ValueError("orc_blend rejected its arguments")
+    return out, L.value

@@ -1155,3 +1155,149 @@ int orc_gauss_splat(const orc_camera *in_cams, const float *depths, const uint32
     free(slot);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 3.3 and the supplement's network-input list: the (9K + 1) x H x W   */
+/* input of the blending network, and the blend of Eqs. 4-5 with L_Depth.   */
+/*                                                                          */
+/* Channels, in the listed order: forward-rendered colours (3K, k-major,    */
+/* RGB / 255), their depths D_k (K), alphas (K), the TSDF depth D (1), then */
+/* per view k: n . d_k (K), r_t . d_k (K), |c_k - c_t| (K), z_k . z_t (K).  */
+/* With P the target-camera point of pixel p at depth D(p), n the normal of */
+/* D at p, d_k the unit ray from view k's centre to P, r_t = P / |P|, z the */
+/* cameras' optical axes; all vectors in the target camera frame.          */
+/* n = (P(i+1,j) - P(i-1,j)) x (P(i,j+1) - P(i,j-1)), turned to face the     */
+/* camera and normalised; 0 where p or one of its four neighbours has no    */
+/* depth (or lies outside the image).  The differences are formed as        */
+/*   dx: (delta (i - cx) + sigma) / fx, delta (j - cy) / fy, delta          */
+/* with delta = D+ - D-, sigma = D+ + D- (the same vector, written without  */
+/* subtracting two large coordinates).  n . d_k and r_t . d_k are 0 where   */
+/* D(p) is 0.                                                               */
+/* ------------------------------------------------------------------------ */
+static void target_point(const orc_camera *t, double i, double j, double D, double P[3]) {
+    P[0] = D * (i - t->cx) / t->fx;
+    P[1] = D * (j - t->cy) / t->fy;
+    P[2] = D;
+}
+
+static void centre_in_target(const orc_camera *t, const orc_camera *c, double o[3]) {
+    double w[3];
+    for (int r = 0; r < 3; ++r) w[r] = -(c->R[0 + r] * c->t[0] + c->R[3 + r] * c->t[1] + c->R[6 + r] * c->t[2]);
+    for (int r = 0; r < 3; ++r) o[r] = t->R[3 * r + 0] * w[0] + t->R[3 * r + 1] * w[1] + t->R[3 * r + 2] * w[2] + t->t[r];
+}
+
+int orc_blend_features(const orc_camera *in_cams, int n_views, const orc_camera *target,
+                       const uint32_t *warped_rgba, const float *warped_depth, const uint8_t *alpha,
+                       const float *fused, double *features) {
+    if (!in_cams || n_views <= 0 || !target || !warped_rgba || !warped_depth || !alpha || !fused || !features)
+        return -1;
+    const int K = n_views, W = target->width, H = target->height;
+    const size_t np = (size_t)W * H;
+    double (*ck)[3] = malloc(sizeof(double[3]) * K);
+    double *dist = malloc(sizeof(double) * K), *axis = malloc(sizeof(double) * K);
+    double ct_world[3];
+    for (int r = 0; r < 3; ++r)
+        ct_world[r] = -(target->R[0 + r] * target->t[0] + target->R[3 + r] * target->t[1] + target->R[6 + r] * target->t[2]);
+    for (int k = 0; k < K; ++k) {
+        centre_in_target(target, &in_cams[k], ck[k]);
+        double cw[3], s = 0.0, a = 0.0;
+        for (int r = 0; r < 3; ++r)
+            cw[r] = -(in_cams[k].R[0 + r] * in_cams[k].t[0] + in_cams[k].R[3 + r] * in_cams[k].t[1] +
+                      in_cams[k].R[6 + r] * in_cams[k].t[2]);
+        for (int r = 0; r < 3; ++r) {
+            s += (cw[r] - ct_world[r]) * (cw[r] - ct_world[r]);
+            a += in_cams[k].R[6 + r] * target->R[6 + r];
+        }
+        dist[k] = sqrt(s);
+        axis[k] = a;
+    }
+#define FEAT(c, p) features[(size_t)(c) * np + (p)]
+    for (int j = 0; j < H; ++j)
+        for (int i = 0; i < W; ++i) {
+            const size_t p = (size_t)j * W + i;
+            for (int k = 0; k < K; ++k) {
+                const size_t o = (size_t)k * np + p;
+                const uint32_t c = warped_rgba[o];
+                for (int ch = 0; ch < 3; ++ch) FEAT(3 * k + ch, p) = (double)((c >> (8 * ch)) & 0xffu) / 255.0;
+                FEAT(3 * K + k, p) = (double)warped_depth[o];
+                FEAT(4 * K + k, p) = (double)alpha[o];
+                FEAT(5 * K + 1 + 2 * K + k, p) = dist[k];
+                FEAT(5 * K + 1 + 3 * K + k, p) = axis[k];
+            }
+            const double D = (double)fused[p];
+            FEAT(5 * K, p) = D;
+            const int have = depth_valid(fused[p]);
+            double n[3] = {0.0, 0.0, 0.0};
+            if (have && i > 0 && i < W - 1 && j > 0 && j < H - 1 && depth_valid(fused[p - 1]) &&
+                depth_valid(fused[p + 1]) && depth_valid(fused[p - W]) && depth_valid(fused[p + W])) {
+                const double dh = (double)fused[p + 1] - (double)fused[p - 1];
+                const double sh = (double)fused[p + 1] + (double)fused[p - 1];
+                const double dv = (double)fused[p + W] - (double)fused[p - W];
+                const double sv = (double)fused[p + W] + (double)fused[p - W];
+                const double a[3] = {(dh * (i - target->cx) + sh) / target->fx, dh * (j - target->cy) / target->fy, dh};
+                const double b[3] = {dv * (i - target->cx) / target->fx, (dv * (j - target->cy) + sv) / target->fy, dv};
+                n[0] = a[1] * b[2] - a[2] * b[1];
+                n[1] = a[2] * b[0] - a[0] * b[2];
+                n[2] = a[0] * b[1] - a[1] * b[0];
+                double P[3];
+                target_point(target, i, j, D, P);
+                if (n[0] * P[0] + n[1] * P[1] + n[2] * P[2] > 0.0) { n[0] = -n[0]; n[1] = -n[1]; n[2] = -n[2]; }
+                const double len = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+                if (len > 0.0) { n[0] /= len; n[1] /= len; n[2] /= len; }
+            }
+            for (int k = 0; k < K; ++k) {
+                double nd = 0.0, rd = 0.0;
+                if (have) {
+                    double P[3], d[3];
+                    target_point(target, i, j, D, P);
+                    for (int r = 0; r < 3; ++r) d[r] = P[r] - ck[k][r];
+                    const double ld = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                    const double lp = sqrt(P[0] * P[0] + P[1] * P[1] + P[2] * P[2]);
+                    for (int r = 0; r < 3; ++r) {
+                        nd += n[r] * d[r] / ld;
+                        rd += P[r] / lp * d[r] / ld;
+                    }
+                }
+                FEAT(5 * K + 1 + k, p) = nd;
+                FEAT(5 * K + 1 + K + k, p) = rd;
+            }
+        }
+#undef FEAT
+    free(ck);
+    free(dist);
+    free(axis);
+    return 0;
+}
+
+/* Eq. 4 (denominator read as the sum over views), Eq. 5 and L_Depth:       */
+/*   I_FG = sum_k I_k a_k w_k / sum_k a_k w_k   (0 where the sum is 0)       */
+/*   I    = (1 - w_BG) I_FG + w_BG I_BG                                      */
+/*   L_Depth = 1/(H W K) sum_p | D(p) - sum_k D_k a_k w_k / sum_k a_k w_k |  */
+/* w [K][H][W], w_bg [H][W], i_bg [3][H][W]; out [3][H][W].                  */
+int orc_blend(int n_views, int W, int H, const uint32_t *warped_rgba, const uint8_t *alpha,
+              const float *warped_depth, const float *fused, const double *w, const double *w_bg,
+              const double *i_bg, double *out, double *l_depth) {
+    if (n_views <= 0 || W <= 0 || H <= 0 || !warped_rgba || !alpha || !warped_depth || !fused || !w || !w_bg ||
+        !i_bg || !out)
+        return -1;
+    const size_t np = (size_t)W * H;
+    double L = 0.0;
+    for (size_t p = 0; p < np; ++p) {
+        double den = 0.0, num[3] = {0.0, 0.0, 0.0}, dnum = 0.0;
+        for (int k = 0; k < n_views; ++k) {
+            const size_t o = (size_t)k * np + p;
+            const double aw = (double)alpha[o] * w[o];
+            const uint32_t c = warped_rgba[o];
+            for (int ch = 0; ch < 3; ++ch) num[ch] += (double)((c >> (8 * ch)) & 0xffu) / 255.0 * aw;
+            dnum += (double)warped_depth[o] * aw;
+            den += aw;
+        }
+        for (int ch = 0; ch < 3; ++ch) {
+            const double fg = den > 0.0 ? num[ch] / den : 0.0;
+            out[(size_t)ch * np + p] = (1.0 - w_bg[p]) * fg + w_bg[p] * i_bg[(size_t)ch * np + p];
+        }
+        L += fabs((double)fused[p] - (den > 0.0 ? dnum / den : 0.0));
+    }
+    if (l_depth) *l_depth = L / ((double)np * n_views);
+    return 0;
+}
