@@ -283,6 +283,10 @@ def run_gvs(args, rank, local_rank, world):
                                                                    steps=min(K, 20)),
                                       "8 views rendered separately with pixel-sized Gaussians, alpha-composited "
                                       "front to back (Supplement A.3, 3DGS rules); render only")
+    forms["network_frame_k4"] = form_line("network_frame_k4", w, time_form(NetworkFrame(w, frames_np, device),
+                                                                           steps=min(K, 20)),
+                                          "K = 4 closest views: refine, fusion, splat, network input (bf16), "
+                                          "4-level U-Net with random weights (cuDNN, bf16), Eq. 4-5 blend")
     forms.update(time_batched(device, steps=min(K, 20)))
     wd = configs.diff_640x360()
     forms["fwd_bwd_640x360"] = form_line("fwd_bwd_640x360", wd,
@@ -439,6 +443,38 @@ class GaussRender:
         cur = i % len(self.rgba)
         self.gvs.gauss_splat(self.w.inputs, self.depth[cur], self.rgba[cur], self.tgt, color=self.color,
                              depth=self.out_depth, ws=self.ws)
+
+
+class NetworkFrame:
+    """The paper's whole per-frame path with K = 4 closest views: refine, fusion and splat of
+    those views, the network input (bf16), the blending U-Net with seeded random weights
+    (cuDNN convolutions, bf16) and the Eq. 4-5 blend with L_Depth."""
+
+    def __init__(self, w, frames_np, device, K=4):
+        import torch
+        from paper_2505_18932_gb300 import gvs
+        from paper_2505_18932_gb300.blendnet import BlendUNet
+        self.torch, self.gvs, self.w, self.half = torch, gvs, w, False
+        self.tgt = w.targets[0]
+        self.sel = gvs.select_views(w.inputs, self.tgt, K)
+        self.cams = [w.inputs[i] for i in self.sel]
+        self.pipe = Pipeline(type(w)(**{**w.__dict__, "inputs": self.cams}), [(c[self.sel], d[self.sel])
+                                                                               for c, d in frames_np], device)
+        self.net = BlendUNet(K).to(device).to(torch.bfloat16).eval()
+        Ht, Wt = self.tgt.height, self.tgt.width
+        self.feats = torch.empty((9 * K + 1, Ht, Wt), dtype=torch.bfloat16, device=device)
+        self.image = torch.empty((3, Ht, Wt), dtype=torch.float32, device=device)
+        self.L = torch.empty((), dtype=torch.float64, device=device)
+
+    def step(self, i, events=None):
+        p, gvs, torch = self.pipe, self.gvs, self.torch
+        p.step(i)
+        gvs.blend_features(self.cams, self.tgt, p.outs["warped_rgba"], p.outs["warped_depth"], p.outs["alpha"],
+                           p.fused, out=self.feats)
+        with torch.no_grad():
+            wk, wbg, ibg = self.net(self.feats[None])
+        gvs.blend(p.outs["warped_rgba"], p.outs["alpha"], p.outs["warped_depth"], p.fused, wk, wbg, ibg,
+                  image=self.image, l_depth=self.L)
 
 
 def time_batched(device, steps):

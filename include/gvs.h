@@ -521,6 +521,45 @@ GVS_API gvs_status gvs_gauss_splat(const gvs_camera *in_cams, const void *in_dep
                                    float *color, float *depth, void *workspace, size_t workspace_bytes,
                                    void *stream);
 
+/*
+ * gvs_blend_features -- the input of the blending network (Sec. 3.3; the
+ * supplement's list of network inputs), (9K + 1) channel planes
+ * [9K + 1][target.height][target.width] of out_dtype (GVS_F32, GVS_F16 or GVS_BF16), in order:
+ *   3K  forward-rendered colours, view-major, channel byte / 255 (R, G, B of warped_rgba)
+ *   K   their depths (warped_depth)            K   their alphas (0 or 1)
+ *   1   the TSDF depth D (fused_depth)
+ *   K   n . d_k    K   r_t . d_k    K   |c_k - c_t|    K   z_k . z_t
+ * with P the target-camera point of pixel (i, j) at depth D, n the normal of D at
+ * (i, j) from central differences of the back-projected points (formed as
+ * ((delta (i - cx) + sigma) / fx, delta (j - cy) / fy, delta), delta = D(i+1) - D(i-1),
+ * sigma = D(i+1) + D(i-1), and alike vertically), turned to face the camera and
+ * normalised, 0 where (i, j) or a 4-neighbour has no depth or lies on the border;
+ * d_k the unit vector from view k's centre to P; r_t = P / |P|; c the camera centres;
+ * z the optical axes; all in the target frame.  n . d_k and r_t . d_k are 0 where D
+ * is 0.  Inputs as gvs_forward_splat writes them, [n_views][target.height][target.width].
+ */
+GVS_API gvs_status gvs_blend_features(const gvs_camera *in_cams, int32_t n_views, const gvs_camera *target,
+                                      const uint32_t *warped_rgba, const float *warped_depth,
+                                      const uint8_t *alpha, const float *fused_depth, int32_t out_dtype,
+                                      void *features, void *stream);
+
+/*
+ * gvs_blend -- Eq. 4 and Eq. 5 with L_Depth (Sec. 3.3):
+ *   I_FG = sum_k I_k a_k w_k / sum_k a_k w_k   (0 where the sum is 0; the printed
+ *          denominator is read as the sum over views)
+ *   image = (1 - w_BG) I_FG + w_BG I_BG                         [3][Ht][Wt] float
+ *   l_depth = 1/(Ht Wt K) sum_p | D(p) - sum_k D_k a_k w_k / sum_k a_k w_k |   (one double)
+ * w [n_views][Ht][Wt], w_bg [Ht][Wt], i_bg [3][Ht][Wt] of weight_dtype (GVS_F32 or
+ * GVS_BF16): the network's output planes.  l_depth may be NULL.  The reduction is
+ * in a fixed order (bit-reproducible).  workspace: gvs_blend_workspace_bytes(...).
+ */
+GVS_API size_t gvs_blend_workspace_bytes(int32_t target_width, int32_t target_height);
+GVS_API gvs_status gvs_blend(int32_t n_views, int32_t target_width, int32_t target_height,
+                             const uint32_t *warped_rgba, const uint8_t *alpha, const float *warped_depth,
+                             const float *fused_depth, int32_t weight_dtype, const void *w, const void *w_bg,
+                             const void *i_bg, float *image, double *l_depth, void *workspace,
+                             size_t workspace_bytes, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -12,6 +12,7 @@
 #include <new>
 #include <vector>
 
+#include "blend_internal.cuh"
 #include "gauss_internal.cuh"
 #include "gvs_internal.cuh"
 
@@ -834,6 +835,120 @@ gvs_status gvs_gauss_splat(const gvs_camera *in_cams, const void *in_depths, con
     }
     cudaError_t e = gvs::launch_gauss_splat(a, n_views, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "gauss splat: launch");
+    return GVS_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Blending-network input and blend (Sec. 3.3).
+// ---------------------------------------------------------------------------
+namespace {
+
+bool blend_common(int32_t n_views, int32_t Wt, int32_t Ht, const uint32_t *warped_rgba, const float *warped_depth,
+                  const uint8_t *alpha, const float *fused_depth, const char *what, gvs_status *st) {
+    if (n_views < 1 || n_views > GVS_MAX_VIEWS || Wt < 1 || Ht < 1 || Wt > GVS_MAX_DIM || Ht > GVS_MAX_DIM) {
+        *st = fail(GVS_ERR_INVALID_ARG, "%s: n_views or target size out of range", what);
+        return false;
+    }
+    if (!warped_rgba || !warped_depth || !alpha || !fused_depth) {
+        *st = fail(GVS_ERR_INVALID_ARG, "%s: NULL array", what);
+        return false;
+    }
+    const void *arrs[] = {warped_rgba, warped_depth, alpha, fused_depth};
+    for (const void *q : arrs)
+        if (!aligned(q, 16)) {
+            *st = fail(GVS_ERR_INVALID_ARG, "%s: arrays must be 16-byte aligned", what);
+            return false;
+        }
+    return true;
+}
+
+gvs::BlendArgs blend_args(int32_t n_views, int32_t Wt, int32_t Ht, const uint32_t *warped_rgba,
+                          const float *warped_depth, const uint8_t *alpha, const float *fused_depth) {
+    gvs::BlendArgs a;
+    memset(&a, 0, sizeof(a));
+    a.K = n_views;
+    a.Wt = Wt;
+    a.Ht = Ht;
+    a.rgba = warped_rgba;
+    a.wdepth = warped_depth;
+    a.alpha = alpha;
+    a.fused = fused_depth;
+    return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+gvs_status gvs_blend_features(const gvs_camera *in_cams, int32_t n_views, const gvs_camera *target,
+                              const uint32_t *warped_rgba, const float *warped_depth, const uint8_t *alpha,
+                              const float *fused_depth, int32_t out_dtype, void *features, void *stream) {
+    if (!camera_ok(target)) return fail(GVS_ERR_INVALID_ARG, "blend features: target camera invalid");
+    if (!in_cams) return fail(GVS_ERR_INVALID_ARG, "blend features: in_cams is NULL");
+    gvs_status st = GVS_OK;
+    if (!blend_common(n_views, target->width, target->height, warped_rgba, warped_depth, alpha, fused_depth,
+                      "blend features", &st))
+        return st;
+    for (int k = 0; k < n_views; ++k)
+        if (!camera_ok(&in_cams[k])) return fail(GVS_ERR_INVALID_ARG, "blend features: camera %d invalid", k);
+    if (out_dtype != GVS_F32 && out_dtype != GVS_F16 && out_dtype != GVS_BF16)
+        return fail(GVS_ERR_UNSUPPORTED, "blend features: out_dtype must be GVS_F32, GVS_F16 or GVS_BF16");
+    if (!features || !aligned(features, 16)) return fail(GVS_ERR_INVALID_ARG, "blend features: features NULL or unaligned");
+    gvs::BlendArgs a = blend_args(n_views, target->width, target->height, warped_rgba, warped_depth, alpha, fused_depth);
+    a.fx = (float)target->fx;
+    a.fy = (float)target->fy;
+    a.cx = (float)target->cx;
+    a.cy = (float)target->cy;
+    // centres and axes in FP64, rounded once
+    double ct[3];
+    for (int r = 0; r < 3; ++r)
+        ct[r] = -(target->R[0 + r] * target->t[0] + target->R[3 + r] * target->t[1] + target->R[6 + r] * target->t[2]);
+    for (int k = 0; k < n_views; ++k) {
+        const gvs_camera &c = in_cams[k];
+        double cw[3], s = 0.0, ax = 0.0;
+        for (int r = 0; r < 3; ++r) cw[r] = -(c.R[0 + r] * c.t[0] + c.R[3 + r] * c.t[1] + c.R[6 + r] * c.t[2]);
+        for (int r = 0; r < 3; ++r) {
+            a.ck[k][r] = (float)(target->R[3 * r + 0] * cw[0] + target->R[3 * r + 1] * cw[1] +
+                                 target->R[3 * r + 2] * cw[2] + target->t[r]);
+            s += (cw[r] - ct[r]) * (cw[r] - ct[r]);
+            ax += c.R[6 + r] * target->R[6 + r];
+        }
+        a.dist[k] = (float)sqrt(s);
+        a.axis[k] = (float)ax;
+    }
+    cudaError_t e = gvs::launch_blend_features(a, out_dtype, features, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "blend features: launch");
+    return GVS_OK;
+}
+
+size_t gvs_blend_workspace_bytes(int32_t target_width, int32_t target_height) {
+    if (target_width < 1 || target_height < 1) return 0;
+    return align_up((size_t)gvs::blend_blocks(target_width, target_height) * sizeof(double), 256);
+}
+
+gvs_status gvs_blend(int32_t n_views, int32_t target_width, int32_t target_height, const uint32_t *warped_rgba,
+                     const uint8_t *alpha, const float *warped_depth, const float *fused_depth, int32_t weight_dtype,
+                     const void *w, const void *w_bg, const void *i_bg, float *image, double *l_depth,
+                     void *workspace, size_t workspace_bytes, void *stream) {
+    gvs_status st = GVS_OK;
+    if (!blend_common(n_views, target_width, target_height, warped_rgba, warped_depth, alpha, fused_depth, "blend",
+                      &st))
+        return st;
+    if (weight_dtype != GVS_F32 && weight_dtype != GVS_BF16)
+        return fail(GVS_ERR_UNSUPPORTED, "blend: weight_dtype must be GVS_F32 or GVS_BF16");
+    if (!w || !w_bg || !i_bg || !image) return fail(GVS_ERR_INVALID_ARG, "blend: NULL array");
+    const void *arrs[] = {image, l_depth};
+    for (const void *q : arrs)
+        if (q && !aligned(q, 8)) return fail(GVS_ERR_INVALID_ARG, "blend: outputs must be 8-byte aligned");
+    const size_t need = gvs_blend_workspace_bytes(target_width, target_height);
+    if (!workspace || workspace_bytes < need || !aligned(workspace, 256))
+        return fail(GVS_ERR_WORKSPACE, "blend: workspace needs at least %zu bytes, 256-byte aligned", need);
+    gvs::BlendArgs a = blend_args(n_views, target_width, target_height, warped_rgba, warped_depth, alpha, fused_depth);
+    cudaError_t e = gvs::launch_blend(a, weight_dtype, w, w_bg, i_bg, image, l_depth,
+                                      reinterpret_cast<double *>(workspace), (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "blend: launch");
     return GVS_OK;
 }
 

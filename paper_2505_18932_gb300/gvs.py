@@ -132,6 +132,11 @@ API = {
     "gvs_gauss_splat": (ctypes.c_int, [ctypes.POINTER(GvsCamera), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                        ctypes.POINTER(GvsCamera), ctypes.POINTER(GvsGaussParams), ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "gvs_blend_features": (ctypes.c_int, [ctypes.POINTER(GvsCamera), ctypes.c_int32, ctypes.POINTER(GvsCamera)] +
+                           [ctypes.c_void_p] * 4 + [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
+    "gvs_blend_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32] * 2),
+    "gvs_blend": (ctypes.c_int, [ctypes.c_int32] * 3 + [ctypes.c_void_p] * 4 + [ctypes.c_int32] +
+                  [ctypes.c_void_p] * 6 + [ctypes.c_size_t, ctypes.c_void_p]),
     "gvs_forward_splat_noalloc": (ctypes.c_int, [ctypes.POINTER(GvsCamera), ctypes.c_void_p, ctypes.c_void_p,
                                                  ctypes.c_int32, ctypes.POINTER(GvsCamera),
                                                  ctypes.POINTER(GvsSplatParams), ctypes.c_void_p, ctypes.c_void_p,
@@ -439,6 +444,47 @@ def gauss_splat(in_cams, in_depths, in_rgba, target, scale_px=0.5, max_radius=8,
                              ws.numel(), _stream(stream))
     _check("gvs_gauss_splat", st)
     return color, depth
+
+
+_FEATURE_DTYPES = {torch.float32: GVS_F32, torch.float16: GVS_F16, torch.bfloat16: GVS_BF16}
+
+
+def blend_features(in_cams, target, warped_rgba, warped_depth, alpha, fused, dtype=torch.float32, out=None,
+                   stream=None):
+    """The blending network's (9K + 1) x Ht x Wt input (Sec. 3.3 and the supplement's list),
+    from the splat outputs (warped_rgba int32, warped_depth float32, alpha uint8, each
+    [K, Ht, Wt]) and the TSDF depth fused float32 [Ht, Wt]."""
+    lib = load()
+    K = len(in_cams)
+    if out is None:
+        out = torch.empty((9 * K + 1, target.height, target.width), dtype=dtype, device=fused.device)
+    st = lib.gvs_blend_features(camera_array(in_cams), K, ctypes.byref(camera_struct(target)), _ptr(warped_rgba),
+                                _ptr(warped_depth), _ptr(alpha), _ptr(fused), _FEATURE_DTYPES[out.dtype], _ptr(out),
+                                _stream(stream))
+    _check("gvs_blend_features", st)
+    return out
+
+
+def blend(warped_rgba, alpha, warped_depth, fused, w, w_bg, i_bg, image=None, l_depth=None, ws=None, stream=None):
+    """Eqs. 4-5 and L_Depth.  w [K, Ht, Wt], w_bg [Ht, Wt], i_bg [3, Ht, Wt], float32 or bfloat16
+    (contiguous planes, e.g. slices of the network output).  Returns (image float32 [3, Ht, Wt],
+    L_Depth float64 scalar tensor on the device)."""
+    lib = load()
+    K, Ht, Wt = warped_rgba.shape
+    dev = fused.device
+    if image is None:
+        image = torch.empty((3, Ht, Wt), dtype=torch.float32, device=dev)
+    if l_depth is None:
+        l_depth = torch.empty((), dtype=torch.float64, device=dev)
+    if ws is None:
+        ws = workspace(int(lib.gvs_blend_workspace_bytes(Wt, Ht)), dev)
+    wdt = {torch.float32: GVS_F32, torch.bfloat16: GVS_BF16}[w.dtype]
+    for t in (w, w_bg, i_bg):
+        assert t.dtype == w.dtype and t.is_contiguous()
+    st = lib.gvs_blend(K, Wt, Ht, _ptr(warped_rgba), _ptr(alpha), _ptr(warped_depth), _ptr(fused), wdt, _ptr(w),
+                       _ptr(w_bg), _ptr(i_bg), _ptr(image), _ptr(l_depth), _ptr(ws), ws.numel(), _stream(stream))
+    _check("gvs_blend", st)
+    return image, l_depth
 
 
 def soft_splat(in_cams, in_depths, in_color, target, max_half_width=2.0, mu_band=0.04, outputs=None, ws=None,
