@@ -88,6 +88,9 @@ def _load():
                                                     vp, vp]
             lib.orc_blend_features.argtypes = [cp, i32, cp, vp, vp, vp, vp, vp]
             lib.orc_blend.argtypes = [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+            lib.orc_weight_f32.restype = flt
+            lib.orc_weight_f32.argtypes = [vp, i32, i32, i32, i32, flt, flt, i32, flt]
+            lib.orc_fuse_depth_sphere.argtypes = [cp, vp, i32, cp, dbl, dbl, dbl, dbl, i32, i32, dbl, vp, vp]
             lib.orc_gauss_splat.argtypes = [cp, vp, vp, i32, cp, flt, i32, vp, i64, vp, vp, vp]
             lib.orc_soft_splat.argtypes = [cp, vp, vp, i32, cp, flt, flt, vp, vp, vp, vp, vp]
             lib.orc_soft_splat_grad.argtypes = [cp, vp, vp, i32, cp, flt, flt, vp, vp, vp, vp]
@@ -380,3 +383,29 @@ def blend(warped_rgba, alpha, warped_depth, fused, w, w_bg, i_bg):
     if rc != 0:
         raise ValueError("orc_blend rejected its arguments")
     return out, L.value
+
+
+def weight_f32(depth, u, v, mu, weight_const=0.001, window=7):
+    """Supplement A.1's confidence weight as the sphere-tracing path evaluates it (FP32)."""
+    lib = _load()
+    d = np.ascontiguousarray(depth, np.float32)
+    H, W = d.shape
+    return float(lib.orc_weight_f32(_ptr(d), H, W, int(u), int(v), ctypes.c_float(mu), ctypes.c_float(weight_const),
+                                    int(window), ctypes.c_float(1.0 / (window * window))))
+
+
+def fuse_depth_sphere(in_cams, depths, target, z_near, z_far, mu, weight_const=0.001, window=7, max_steps=1024,
+                      min_frac=0.0625):
+    """Supplement A.1's raymarch (0.8 s steps, three bisections), FP32 as the kernel takes it.
+
+    Returns dict(depth float32 [Ht, Wt] (0: no crossing), evals int32 [Ht, Wt])."""
+    lib = _load()
+    depths = np.ascontiguousarray(depths, np.float32)
+    out = np.empty((target.height, target.width), np.float32)
+    ev = np.empty((target.height, target.width), np.int32)
+    rc = lib.orc_fuse_depth_sphere(_cams(in_cams), _ptr(depths), len(in_cams), ctypes.byref(_cam(target)),
+                                   float(z_near), float(z_far), float(mu), float(weight_const), int(window),
+                                   int(max_steps), float(min_frac), _ptr(out), _ptr(ev))
+    if rc != 0:
+        raise ValueError("orc_fuse_depth_sphere rejected its arguments")
+    return {"depth": out, "evals": ev}

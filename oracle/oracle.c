@@ -1301,3 +1301,149 @@ int orc_blend(int n_views, int W, int H, const uint32_t *warped_rgba, const uint
     if (l_depth) *l_depth = L / ((double)np * n_views);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Supplement A.1, the paper's own raymarch: advance along the ray by 0.8 s */
+/* until s changes sign, then three bisection steps.                        */
+/*                                                                          */
+/* Every quantity on the path decides where the next sample lands, so the   */
+/* whole march is taken in FP32, each operation rounded as written, the     */
+/* kernel's precision (no FP64 step: an FP64 trajectory would drift from    */
+/* any FP32 one and visit other pixels).  Readings:                         */
+/*   s_n = S / W (the weighted mean of clamp(sdf, -1, 1), sdf = (d - z)/mu);  */
+/*   the step is 0.8 mu max(s_n, min_frac) where W > 0 (min_frac > 0 keeps   */
+/*   the march moving: with s_n = (d - z)/mu the plain 0.8 s step would     */
+/*   approach the surface geometrically and never cross it) and 0.8 mu     */
+/*   (a full truncation) where no view sees the point (W = 0);             */
+/*   a crossing is a sample with W > 0 and S <= 0 after one with W > 0 and   */
+/*   S > 0; bisection keeps the lower half where W > 0 and S > 0 at the      */
+/*   midpoint, else the upper; the depth is the final bracket's midpoint.   */
+/*   The march starts at z_near, stops past z_far or after max_steps         */
+/*   samples (no crossing: depth 0).                                        */
+/* The weights are the confidence weights of Supplement A.1 in FP32:        */
+/*   nu = fma(t, t, nu) over the window in raster order, t = min(|dc - dn|,  */
+/*   mu) (mu for an invalid neighbour), omega = min(wconst / sqrt(nu / w^2), */
+/*   1) (1 where nu = 0, 0 for an invalid centre).                          */
+/* ------------------------------------------------------------------------ */
+float orc_weight_f32(const float *depth, int H, int W, int u, int v, float mu, float wconst, int window,
+                     float inv_w2) {
+    float dc = depth[(size_t)v * W + u];
+    if (!depth_valid(dc)) return 0.0f;
+    int r = window / 2;
+    float nu = 0.0f;
+    for (int dy = -r; dy <= r; ++dy)
+        for (int dx = -r; dx <= r; ++dx) {
+            int q = v + dy, p = u + dx;
+            q = q < 0 ? 0 : (q >= H ? H - 1 : q);
+            p = p < 0 ? 0 : (p >= W ? W - 1 : p);
+            float dn = depth[(size_t)q * W + p];
+            float t = depth_valid(dn) ? fminf(fabsf(dc - dn), mu) : mu;
+            nu = fmaf(t, t, nu);
+        }
+    if (!(nu > 0.0f)) return 1.0f;
+    float w = wconst / sqrtf(nu * inv_w2);
+    return w < 1.0f ? w : 1.0f;
+}
+
+typedef struct {
+    const orc_camera *in_cams; const float *depths; int K;
+    const orc_camera *target;
+    float zn, zf, inv_mu, c08mu, min_frac, mu, wconst, inv_w2; int window, max_steps;
+    float (*M)[9]; float (*b)[3];
+    float *wmap; /* [K][H][W] FP32 weights */
+} sphere_job;
+
+static void sphere_eval(const sphere_job *jb, const float (*a)[3], float z, float *S_out, float *W_out) {
+    float S = 0.0f, Wt = 0.0f;
+    for (int k = 0; k < jb->K; ++k) {
+        const orc_camera *vc = &jb->in_cams[k];
+        float h2 = fmaf(z, a[k][2], jb->b[k][2]);
+        if (!(h2 > 1e-6f)) continue;
+        float h0 = fmaf(z, a[k][0], jb->b[k][0]);
+        float h1 = fmaf(z, a[k][1], jb->b[k][1]);
+        double u = nearest_of_quotient(h0, h2), v = nearest_of_quotient(h1, h2);
+        if (u < 0 || v < 0 || u > vc->width - 1 || v > vc->height - 1) continue;
+        size_t o = (size_t)k * vc->width * vc->height + (size_t)v * vc->width + (size_t)u;
+        float d = jb->depths[o];
+        if (!depth_valid(d)) continue;   /* stored as (0, 0): sdf < -1 */
+        float sdf = (d - h2) * jb->inv_mu;
+        if (!(sdf >= -1.0f)) continue;
+        float w = jb->wmap[o];
+        S = fmaf(w, sdf < 1.0f ? sdf : 1.0f, S);
+        Wt = Wt + w;
+    }
+    *S_out = S;
+    *W_out = Wt;
+}
+
+int orc_fuse_depth_sphere(const orc_camera *in_cams, const float *depths, int n_views, const orc_camera *target,
+                          double z_near, double z_far, double mu, double weight_const, int window, int max_steps,
+                          double min_frac, float *out_depth, int32_t *out_evals) {
+    if (!in_cams || !depths || n_views <= 0 || !target || !(z_near < z_far) || !(mu > 0) || window < 1 ||
+        !(window & 1) || max_steps < 1 || !(min_frac > 0) || !out_depth)
+        return -1;
+    sphere_job jb;
+    jb.in_cams = in_cams; jb.depths = depths; jb.K = n_views; jb.target = target;
+    jb.zn = (float)z_near; jb.zf = (float)z_far; jb.inv_mu = (float)(1.0 / mu); jb.c08mu = (float)(0.8 * mu);
+    jb.min_frac = (float)min_frac; jb.mu = (float)mu; jb.wconst = (float)weight_const;
+    jb.inv_w2 = (float)(1.0 / ((double)window * (double)window));
+    jb.window = window; jb.max_steps = max_steps;
+    jb.M = malloc(sizeof(float[9]) * n_views);
+    jb.b = malloc(sizeof(float[3]) * n_views);
+    for (int k = 0; k < n_views; ++k) compose(&in_cams[k], target, jb.M[k], jb.b[k]);
+    size_t off = 0;
+    for (int k = 0; k < n_views; ++k) off += (size_t)in_cams[k].width * in_cams[k].height;
+    jb.wmap = malloc(sizeof(float) * (off > 0 ? off : 1));
+    off = 0;
+    for (int k = 0; k < n_views; ++k) {
+        const int W = in_cams[k].width, H = in_cams[k].height;
+        for (int v = 0; v < H; ++v)
+            for (int u = 0; u < W; ++u)
+                jb.wmap[off + (size_t)v * W + u] =
+                    orc_weight_f32(depths + off, H, W, u, v, jb.mu, jb.wconst, window, jb.inv_w2);
+        off += (size_t)W * H;
+    }
+    float (*a)[3] = malloc(sizeof(float[3]) * n_views);
+    for (int j = 0; j < target->height; ++j)
+        for (int i = 0; i < target->width; ++i) {
+            for (int k = 0; k < n_views; ++k) {
+                const float *M = jb.M[k];
+                a[k][0] = fmaf(M[0], (float)i, fmaf(M[1], (float)j, M[2]));
+                a[k][1] = fmaf(M[3], (float)i, fmaf(M[4], (float)j, M[5]));
+                a[k][2] = fmaf(M[6], (float)i, fmaf(M[7], (float)j, M[8]));
+            }
+            float z = jb.zn, z_prev = 0.0f, S_prev = 0.0f, W_prev = 0.0f, out = 0.0f;
+            int have_prev = 0, evals = 0;
+            for (int it = 0; it < max_steps && z <= jb.zf; ++it) {
+                float S, Wt;
+                sphere_eval(&jb, (const float (*)[3])a, z, &S, &Wt);
+                ++evals;
+                if (have_prev && W_prev > 0.0f && Wt > 0.0f && S_prev > 0.0f && S <= 0.0f) {
+                    float lo = z_prev, hi = z;
+                    for (int bstep = 0; bstep < 3; ++bstep) {
+                        float m = 0.5f * (lo + hi), Sm, Wm;
+                        sphere_eval(&jb, (const float (*)[3])a, m, &Sm, &Wm);
+                        ++evals;
+                        if (Wm > 0.0f && Sm > 0.0f) lo = m;
+                        else hi = m;
+                    }
+                    out = 0.5f * (lo + hi);
+                    break;
+                }
+                float stepn = 1.0f;
+                if (Wt > 0.0f) {
+                    float sn = S / Wt;
+                    stepn = sn > jb.min_frac ? sn : jb.min_frac;
+                }
+                S_prev = S; W_prev = Wt; z_prev = z; have_prev = 1;
+                z = z + jb.c08mu * stepn;
+            }
+            out_depth[(size_t)j * target->width + i] = out;
+            if (out_evals) out_evals[(size_t)j * target->width + i] = evals;
+        }
+    free(a);
+    free(jb.M);
+    free(jb.b);
+    free(jb.wmap);
+    return 0;
+}
