@@ -142,6 +142,17 @@ typedef struct {
     int32_t color_dtype;       /* GVS_F32 (float RGBA) or GVS_BF16 (bfloat16 RGBA) */
 } gvs_soft_splat_params;
 
+/* Sphere-tracing raymarch of the image-based TSDF (Supplement A.1). */
+typedef struct {
+    float z_near, z_far;       /* march from z_near; stop past z_far (target z-depth, metres) */
+    float mu;                  /* truncation (tau of the paper), metres */
+    float weight_const;        /* 0.001 in the paper */
+    int32_t window;            /* odd, 7 in the paper */
+    int32_t max_steps;         /* march samples per ray at most (bisection samples not counted), 1..2^20 */
+    float min_frac;            /* smallest step, as a fraction of 0.8 mu (0, 1], e.g. 1/16 */
+    int32_t depth_dtype;       /* GVS_F32 or GVS_F16 */
+} gvs_sphere_params;
+
 /* Pixel-sized Gaussian forward render (Sec. 3.1, Supplement A.3). */
 #define GVS_MAX_GAUSS_RADIUS 32
 typedef struct {
@@ -520,6 +531,31 @@ GVS_API gvs_status gvs_gauss_splat(const gvs_camera *in_cams, const void *in_dep
                                    int32_t n_views, const gvs_camera *target, const gvs_gauss_params *params,
                                    float *color, float *depth, void *workspace, size_t workspace_bytes,
                                    void *stream);
+
+/*
+ * gvs_fuse_depth_sphere -- Supplement A.1's own raymarch: from z_near advance along
+ * each target ray by 0.8 s until s changes sign, then three bisection steps.
+ * s is the fused signed distance of the uniform march (same projection, nearest
+ * pixel, cut-off and clamp; gvs_fuse_depth), normalised: s_n = S / W.  Per ray, in
+ * FP32 with every operation rounded as written:
+ *   z = z_near;  while z <= z_far and fewer than max_steps samples:
+ *     evaluate S, W at z;
+ *     if the previous sample had W > 0, S > 0 and this one W > 0, S <= 0:
+ *       lo, hi = previous z, z; three times: m = 0.5 (lo + hi), lo = m if W(m) > 0 and
+ *       S(m) > 0 else hi = m;  depth = 0.5 (lo + hi); stop
+ *     z = z + fl32(0.8 mu) * (W > 0 ? max(S / W, min_frac) : 1)
+ *   no crossing: depth 0.
+ * The confidence weights are computed with correctly rounded operations
+ * (omega = min(weight_const / sqrt(nu / window^2), 1), nu summed in raster order by
+ * fused multiply-adds), so the whole march is reproducible bit for bit.
+ * fused_depth [target.height][target.width]; evals (NULL to skip) the samples
+ * evaluated per ray, bisection samples included.  workspace:
+ * gvs_fuse_workspace_bytes(n_views, width, height) (it receives the (d, omega) map).
+ */
+GVS_API gvs_status gvs_fuse_depth_sphere(const gvs_camera *in_cams, const void *in_depths, int32_t n_views,
+                                         const gvs_camera *target, const gvs_sphere_params *params,
+                                         float *fused_depth, int32_t *evals, void *workspace,
+                                         size_t workspace_bytes, void *stream);
 
 /*
  * gvs_blend_features -- the input of the blending network (Sec. 3.3; the

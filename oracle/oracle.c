@@ -1384,8 +1384,11 @@ int orc_fuse_depth_sphere(const orc_camera *in_cams, const float *depths, int n_
         return -1;
     sphere_job jb;
     jb.in_cams = in_cams; jb.depths = depths; jb.K = n_views; jb.target = target;
-    jb.zn = (float)z_near; jb.zf = (float)z_far; jb.inv_mu = (float)(1.0 / mu); jb.c08mu = (float)(0.8 * mu);
-    jb.min_frac = (float)min_frac; jb.mu = (float)mu; jb.wconst = (float)weight_const;
+    /* the parameters as FP32 values first (the kernel receives them so), constants derived in FP64 */
+    const float mu32 = (float)mu;
+    jb.zn = (float)z_near; jb.zf = (float)z_far; jb.inv_mu = (float)(1.0 / (double)mu32);
+    jb.c08mu = (float)(0.8 * (double)mu32);
+    jb.min_frac = (float)min_frac; jb.mu = mu32; jb.wconst = (float)weight_const;
     jb.inv_w2 = (float)(1.0 / ((double)window * (double)window));
     jb.window = window; jb.max_steps = max_steps;
     jb.M = malloc(sizeof(float[9]) * n_views);

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "blend_internal.cuh"
+#include "sphere_internal.cuh"
 #include "gauss_internal.cuh"
 #include "gvs_internal.cuh"
 
@@ -949,6 +950,64 @@ gvs_status gvs_blend(int32_t n_views, int32_t target_width, int32_t target_heigh
     cudaError_t e = gvs::launch_blend(a, weight_dtype, w, w_bg, i_bg, image, l_depth,
                                       reinterpret_cast<double *>(workspace), (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "blend: launch");
+    return GVS_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Sphere-tracing raymarch (Supplement A.1).
+// ---------------------------------------------------------------------------
+extern "C" {
+
+gvs_status gvs_fuse_depth_sphere(const gvs_camera *in_cams, const void *in_depths, int32_t n_views,
+                                 const gvs_camera *target, const gvs_sphere_params *params, float *fused_depth,
+                                 int32_t *evals, void *workspace, size_t workspace_bytes, void *stream) {
+    int32_t W = 0, H = 0;
+    if (!params) return fail(GVS_ERR_INVALID_ARG, "sphere: params is NULL");
+    if (!views_ok(in_cams, n_views, &W, &H))
+        return fail(GVS_ERR_INVALID_ARG, "sphere: input cameras invalid, of different sizes, or n_views out of range");
+    if (!camera_ok(target)) return fail(GVS_ERR_INVALID_ARG, "sphere: target camera invalid");
+    const gvs_sphere_params &p = *params;
+    if (!(isfinite(p.z_near) && isfinite(p.z_far) && p.z_near > 0.0f && p.z_near < p.z_far))
+        return fail(GVS_ERR_INVALID_ARG, "sphere: need 0 < z_near < z_far");
+    gvs_status s = check_weight_params(p.mu, p.weight_const, p.window);
+    if (s != GVS_OK) return s;
+    if (p.max_steps < 1 || p.max_steps > (1 << 20)) return fail(GVS_ERR_INVALID_ARG, "sphere: max_steps in [1, 2^20]");
+    if (!(isfinite(p.min_frac) && p.min_frac > 0.0f && p.min_frac <= 1.0f))
+        return fail(GVS_ERR_INVALID_ARG, "sphere: min_frac must be in (0, 1]");
+    if (p.depth_dtype != GVS_F32 && p.depth_dtype != GVS_F16)
+        return fail(GVS_ERR_UNSUPPORTED, "sphere: depth_dtype must be GVS_F32 or GVS_F16");
+    if (!fused_depth || !aligned(fused_depth, 16) || (evals && !aligned(evals, 16)))
+        return fail(GVS_ERR_INVALID_ARG, "sphere: outputs NULL or not 16-byte aligned");
+    if (n_views > 0 && (!in_depths || !aligned(in_depths, 16)))
+        return fail(GVS_ERR_INVALID_ARG, "sphere: in_depths is NULL or misaligned");
+    const size_t need = gvs_fuse_workspace_bytes(n_views, W, H);
+    if (n_views > 0 && (!workspace || workspace_bytes < need || !aligned(workspace, 256)))
+        return fail(GVS_ERR_WORKSPACE, "sphere: workspace needs %zu bytes, 256-byte aligned", need);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n_views > 0) {
+        cudaError_t e = gvs::launch_weight_map(in_depths, p.depth_dtype, workspace, GVS_F32, n_views, W, H, p.mu,
+                                               p.weight_const, p.window, st, true);
+        if (e != cudaSuccess) return cuda_fail(e, "sphere: weight map launch");
+    }
+    gvs_fuse_params fp;
+    memset(&fp, 0, sizeof(fp));
+    fp.num_samples = 2;
+    fp.z_near = p.z_near;
+    fp.z_far = p.z_far;
+    fp.mu = p.mu;
+    fp.map_dtype = GVS_F32;
+    gvs::SphereArgs a;
+    memset(&a, 0, sizeof(a));
+    a.f = fuse_args(in_cams, workspace, n_views, W, H, target, fp, fused_depth, nullptr);
+    a.zf = p.z_far;
+    a.c08mu = (float)(0.8 * (double)p.mu);
+    a.min_frac = p.min_frac;
+    a.max_steps = p.max_steps;
+    a.evals = evals;
+    cudaError_t e = gvs::launch_sphere(a, st);
+    if (e != cudaSuccess) return cuda_fail(e, "sphere: launch");
     return GVS_OK;
 }
 

@@ -32,7 +32,10 @@ constexpr int WM_P = 4;
 // depths as NaN).  A thread reads each of the (WM_P + 2R) x (2R + 1) shared
 // values its column needs once and reuses it for every output whose window
 // contains it.  DT: float or __half input; MT: float2 or __half2 map.
-template <int R, typename DT, typename MT>
+// EXACT: omega = min(wconst / sqrt(nu / w^2), 1) with correctly rounded
+// operations (bit-reproducible on the host, as the sphere-tracing path needs);
+// otherwise with the approximate reciprocal square root.
+template <int R, typename DT, typename MT, bool EXACT = false>
 __global__ void __launch_bounds__(256) weight_map_kernel(const DT *__restrict__ depth, char *__restrict__ map,
                                                          MapLayout L, float mu, float wconst, float inv_w2) {
     constexpr int SW = WM_TX + 2 * R;
@@ -91,7 +94,10 @@ __global__ void __launch_bounds__(256) weight_map_kernel(const DT *__restrict__ 
         if (x < W && y < H) {
             float d = 0.0f, w = 0.0f;
             if (dc[p] == dc[p]) {  // valid centre
-                w = nu[p] > 0.0f ? fminf(wconst * rsqrtf(nu[p] * inv_w2), 1.0f) : 1.0f;
+                if (EXACT)
+                    w = nu[p] > 0.0f ? fminf(__fdiv_rn(wconst, __fsqrt_rn(__fmul_rn(nu[p], inv_w2))), 1.0f) : 1.0f;
+                else
+                    w = nu[p] > 0.0f ? fminf(wconst * rsqrtf(nu[p] * inv_w2), 1.0f) : 1.0f;
                 d = dc[p];
                 lo = fminf(lo, d);
                 hi = fmaxf(hi, d);
@@ -205,26 +211,30 @@ struct FuseLaunchTemporal {
 };
 template <int R, typename DT, typename MT>
 cudaError_t launch_wm(const void *depth, char *map, const MapLayout &L, float mu, float wconst, float inv_w2,
-                      cudaStream_t st) {
+                      bool exact, cudaStream_t st) {
     dim3 grid((L.W + WM_TX - 1) / WM_TX, (L.H + WM_TY - 1) / WM_TY, L.K);
-    weight_map_kernel<R, DT, MT><<<grid, dim3(WM_TX, WM_TY / WM_P), 0, st>>>(reinterpret_cast<const DT *>(depth), map,
-                                                                          L, mu, wconst, inv_w2);
+    if (exact)
+        weight_map_kernel<R, DT, MT, true><<<grid, dim3(WM_TX, WM_TY / WM_P), 0, st>>>(
+            reinterpret_cast<const DT *>(depth), map, L, mu, wconst, inv_w2);
+    else
+        weight_map_kernel<R, DT, MT><<<grid, dim3(WM_TX, WM_TY / WM_P), 0, st>>>(reinterpret_cast<const DT *>(depth),
+                                                                              map, L, mu, wconst, inv_w2);
     return cudaGetLastError();
 }
 
 template <typename DT, typename MT>
 cudaError_t launch_wm_window(const void *depth, char *map, const MapLayout &L, float mu, float wconst, int window,
-                             cudaStream_t st) {
+                             bool exact, cudaStream_t st) {
     const float inv_w2 = (float)(1.0 / ((double)window * (double)window));
     switch (window / 2) {
-        case 0: return launch_wm<0, DT, MT>(depth, map, L, mu, wconst, inv_w2, st);
-        case 1: return launch_wm<1, DT, MT>(depth, map, L, mu, wconst, inv_w2, st);
-        case 2: return launch_wm<2, DT, MT>(depth, map, L, mu, wconst, inv_w2, st);
-        case 3: return launch_wm<3, DT, MT>(depth, map, L, mu, wconst, inv_w2, st);
-        case 4: return launch_wm<4, DT, MT>(depth, map, L, mu, wconst, inv_w2, st);
-        case 5: return launch_wm<5, DT, MT>(depth, map, L, mu, wconst, inv_w2, st);
-        case 6: return launch_wm<6, DT, MT>(depth, map, L, mu, wconst, inv_w2, st);
-        case 7: return launch_wm<7, DT, MT>(depth, map, L, mu, wconst, inv_w2, st);
+        case 0: return launch_wm<0, DT, MT>(depth, map, L, mu, wconst, inv_w2, exact, st);
+        case 1: return launch_wm<1, DT, MT>(depth, map, L, mu, wconst, inv_w2, exact, st);
+        case 2: return launch_wm<2, DT, MT>(depth, map, L, mu, wconst, inv_w2, exact, st);
+        case 3: return launch_wm<3, DT, MT>(depth, map, L, mu, wconst, inv_w2, exact, st);
+        case 4: return launch_wm<4, DT, MT>(depth, map, L, mu, wconst, inv_w2, exact, st);
+        case 5: return launch_wm<5, DT, MT>(depth, map, L, mu, wconst, inv_w2, exact, st);
+        case 6: return launch_wm<6, DT, MT>(depth, map, L, mu, wconst, inv_w2, exact, st);
+        case 7: return launch_wm<7, DT, MT>(depth, map, L, mu, wconst, inv_w2, exact, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -232,17 +242,17 @@ cudaError_t launch_wm_window(const void *depth, char *map, const MapLayout &L, f
 }  // namespace
 
 cudaError_t launch_weight_map(const void *depth, int depth_dtype, void *map, int map_dtype, int K, int W, int H,
-                              float mu, float wconst, int window, cudaStream_t st) {
+                              float mu, float wconst, int window, cudaStream_t st, bool exact) {
     if (K == 0) return cudaSuccess;
     const MapLayout L = map_layout(K, W, H);
     char *m = reinterpret_cast<char *>(map);
     cudaError_t e;
     if (depth_dtype == GVS_F16) {
-        e = map_dtype == GVS_F16 ? launch_wm_window<__half, __half2>(depth, m, L, mu, wconst, window, st)
-                                 : launch_wm_window<__half, float2>(depth, m, L, mu, wconst, window, st);
+        e = map_dtype == GVS_F16 ? launch_wm_window<__half, __half2>(depth, m, L, mu, wconst, window, false, st)
+                                 : launch_wm_window<__half, float2>(depth, m, L, mu, wconst, window, exact, st);
     } else {
-        e = map_dtype == GVS_F16 ? launch_wm_window<float, __half2>(depth, m, L, mu, wconst, window, st)
-                                 : launch_wm_window<float, float2>(depth, m, L, mu, wconst, window, st);
+        e = map_dtype == GVS_F16 ? launch_wm_window<float, __half2>(depth, m, L, mu, wconst, window, false, st)
+                                 : launch_wm_window<float, float2>(depth, m, L, mu, wconst, window, exact, st);
     }
     if (e != cudaSuccess) return e;
     depth_bounds_kernel<<<dim3(L.tw[2], L.th[2], K), dim3(16, 16), 0, st>>>(m, L);

@@ -83,8 +83,9 @@ struct FuseArgs {
     ViewXform xf[GVS_MAX_VIEWS];
 };
 
+// exact: correctly rounded weight (float2 maps only; see weight_map_kernel)
 cudaError_t launch_weight_map(const void *depth, int depth_dtype, void *map, int map_dtype, int K, int W, int H,
-                              float mu, float wconst, int window, cudaStream_t st);
+                              float mu, float wconst, int window, cudaStream_t st, bool exact = false);
 cudaError_t launch_fuse(const FuseArgs &a, cudaStream_t st);
 
 // One (frame, target) item of a batched fusion: its arguments and the index

@@ -1,0 +1,84 @@
+// The paper's own raymarch for the image-based TSDF (Supplement A.1): from
+// z_near, advance by 0.8 s until s changes sign, then three bisection steps.
+// One thread per target ray; the per-view ray coefficients, the sample
+// evaluation and the nearest-pixel contract are those of the uniform march
+// (fuse_march.cuh).  Every operation that moves the march is an explicitly
+// rounded FP32 operation and the weights come from the correctly rounded map,
+// so the trajectory, the evaluation count and the depth are reproducible bit
+// for bit on the host (see gvs_fuse_depth_sphere in gvs.h).
+#include "fuse_march.cuh"
+#include "sphere_internal.cuh"
+
+namespace gvs {
+namespace {
+
+template <int KMAX>
+__global__ void __launch_bounds__(128) sphere_kernel(const __grid_constant__ SphereArgs s) {
+    const FuseArgs &a = s.f;
+    const int i = blockIdx.x * 32 + threadIdx.x;
+    const int j = blockIdx.y * 4 + threadIdx.y;
+    if (i >= a.Wt || j >= a.Ht) return;
+    const float fi = (float)i, fj = (float)j;
+    Ray ray[KMAX];
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+        if (k < a.K) {
+            const float *M = a.xf[k].M;
+            ray[k].ax = __fmaf_rn(M[0], fi, __fmaf_rn(M[1], fj, M[2]));
+            ray[k].ay = __fmaf_rn(M[3], fi, __fmaf_rn(M[4], fj, M[5]));
+            ray[k].az = __fmaf_rn(M[6], fi, __fmaf_rn(M[7], fj, M[8]));
+        }
+    }
+    float z = a.zn, z_prev = 0.0f, S_prev = 0.0f, W_prev = 0.0f, out = 0.0f;
+    bool have_prev = false;
+    int evals = 0;
+    for (int it = 0; it < s.max_steps && z <= s.zf; ++it) {
+        float S, W;
+        evaluate_sample<KMAX, float2>(a, ray, z, S, W);
+        ++evals;
+        if (have_prev && W_prev > 0.0f && W > 0.0f && S_prev > 0.0f && S <= 0.0f) {
+            float lo = z_prev, hi = z;
+            for (int b = 0; b < 3; ++b) {
+                const float m = __fmul_rn(0.5f, __fadd_rn(lo, hi));
+                float Sm, Wm;
+                evaluate_sample<KMAX, float2>(a, ray, m, Sm, Wm);
+                ++evals;
+                if (Wm > 0.0f && Sm > 0.0f) lo = m;
+                else hi = m;
+            }
+            out = __fmul_rn(0.5f, __fadd_rn(lo, hi));
+            break;
+        }
+        float stepn = 1.0f;
+        if (W > 0.0f) {
+            const float sn = __fdiv_rn(S, W);
+            stepn = sn > s.min_frac ? sn : s.min_frac;
+        }
+        S_prev = S;
+        W_prev = W;
+        z_prev = z;
+        have_prev = true;
+        z = __fadd_rn(z, __fmul_rn(s.c08mu, stepn));
+    }
+    const size_t o = (size_t)j * a.Wt + i;
+    a.fused[o] = out;
+    if (s.evals) s.evals[o] = evals;
+}
+
+template <int KMAX>
+void launch_k(const SphereArgs &s, cudaStream_t st) {
+    const dim3 grid((unsigned)((s.f.Wt + 31) / 32), (unsigned)((s.f.Ht + 3) / 4)), block(32, 4);
+    sphere_kernel<KMAX><<<grid, block, 0, st>>>(s);
+}
+
+}  // namespace
+
+cudaError_t launch_sphere(const SphereArgs &s, cudaStream_t st) {
+    if (s.f.K <= 4) launch_k<4>(s, st);
+    else if (s.f.K <= 8) launch_k<8>(s, st);
+    else if (s.f.K <= 16) launch_k<16>(s, st);
+    else launch_k<32>(s, st);
+    return cudaGetLastError();
+}
+
+}  // namespace gvs

@@ -66,6 +66,12 @@ class GvsGaussParams(ctypes.Structure):
     _fields_ = [("scale_px", ctypes.c_float), ("max_radius", ctypes.c_int32), ("depth_dtype", ctypes.c_int32)]
 
 
+class GvsSphereParams(ctypes.Structure):
+    _fields_ = [("z_near", ctypes.c_float), ("z_far", ctypes.c_float), ("mu", ctypes.c_float),
+                ("weight_const", ctypes.c_float), ("window", ctypes.c_int32), ("max_steps", ctypes.c_int32),
+                ("min_frac", ctypes.c_float), ("depth_dtype", ctypes.c_int32)]
+
+
 class GvsSoftSplatParams(ctypes.Structure):
     _fields_ = [("max_half_width", ctypes.c_float), ("mu_band", ctypes.c_float), ("depth_dtype", ctypes.c_int32),
                 ("color_dtype", ctypes.c_int32)]
@@ -137,6 +143,9 @@ API = {
     "gvs_blend_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32] * 2),
     "gvs_blend": (ctypes.c_int, [ctypes.c_int32] * 3 + [ctypes.c_void_p] * 4 + [ctypes.c_int32] +
                   [ctypes.c_void_p] * 6 + [ctypes.c_size_t, ctypes.c_void_p]),
+    "gvs_fuse_depth_sphere": (ctypes.c_int, [ctypes.POINTER(GvsCamera), ctypes.c_void_p, ctypes.c_int32,
+                                             ctypes.POINTER(GvsCamera), ctypes.POINTER(GvsSphereParams)] +
+                              [ctypes.c_void_p] * 3 + [ctypes.c_size_t, ctypes.c_void_p]),
     "gvs_forward_splat_noalloc": (ctypes.c_int, [ctypes.POINTER(GvsCamera), ctypes.c_void_p, ctypes.c_void_p,
                                                  ctypes.c_int32, ctypes.POINTER(GvsCamera),
                                                  ctypes.POINTER(GvsSplatParams), ctypes.c_void_p, ctypes.c_void_p,
@@ -356,6 +365,29 @@ def weight_map(in_depths, mu, weight_const=0.001, window=7, ws=None, map_half=Fa
                             _stream(stream))
     _check("gvs_weight_map", st)
     return ws
+
+
+def fuse_depth_sphere(in_cams, in_depths, target, z_near, z_far, mu, weight_const=0.001, window=7, max_steps=1024,
+                      min_frac=0.0625, fused=None, evals=None, ws=None, stream=None):
+    """Supplement A.1's sphere-tracing raymarch (0.8 s steps, three bisections).
+    Returns (fused float32 [Ht, Wt] (0: no crossing), evals int32 [Ht, Wt])."""
+    lib = load()
+    N = len(in_cams)
+    dev = in_depths.device
+    shape = (target.height, target.width)
+    if fused is None:
+        fused = torch.empty(shape, dtype=torch.float32, device=dev)
+    if evals is None:
+        evals = torch.empty(shape, dtype=torch.int32, device=dev)
+    H, W = (in_depths.shape[1], in_depths.shape[2]) if N else (0, 0)
+    if ws is None:
+        ws = workspace(fuse_workspace_bytes(N, W, H), dev)
+    p = GvsSphereParams(float(z_near), float(z_far), float(mu), float(weight_const), int(window), int(max_steps),
+                        float(min_frac), depth_dtype_of(in_depths) if N else GVS_F32)
+    st = lib.gvs_fuse_depth_sphere(camera_array(in_cams), _ptr(in_depths), N, ctypes.byref(camera_struct(target)),
+                                   ctypes.byref(p), _ptr(fused), _ptr(evals), _ptr(ws), ws.numel(), _stream(stream))
+    _check("gvs_fuse_depth_sphere", st)
+    return fused, evals
 
 
 def fuse_depth_from_map(in_cams, dw_map, shape, target, num_samples, z_near, z_far, mu, normalize=False,
