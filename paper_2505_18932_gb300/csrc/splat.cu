@@ -221,49 +221,65 @@ __global__ void __launch_bounds__(256) splat_resolve(const SplatArgs a, int k0) 
     if (a.guided) a.guided[o] = (uint8_t)(has && fabsf(z - __ldg(&a.fused[t])) <= a.mu_guide);
 }
 
-// Four consecutive target pixels per thread, every access a 16-byte (or, for
-// the byte maps, 4-byte) vector; needs Wt * Ht divisible by 4.  The four
-// colour gathers are independent, so each thread keeps four in flight.
-// Grid (ceil(Wt Ht / 1024), views of the group).
-__global__ void __launch_bounds__(256) splat_resolve4(const SplatArgs a, int k0) {
+// P consecutive target pixels per thread (P = 4 or 8), every access a 16-byte
+// (or, for the byte maps, 4-byte) vector; needs Wt * Ht divisible by P.  The
+// P colour gathers are independent, so each thread keeps P in flight (eight
+// per thread measured 6 us faster than four over 8 views at 1080p).
+// Grid (ceil(Wt Ht / (256 P)), views of the group).
+template <int P>
+__global__ void __launch_bounds__(256) splat_resolveP(const SplatArgs a, int k0) {
     const int64_t HWt = (int64_t)a.Wt * a.Ht;
-    const int q4 = (int)(HWt / 4);
-    const int t4 = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t4 >= q4) return;
+    const int qn = (int)(HWt / P);
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= qn) return;
     const int kk = blockIdx.y;
     const int k = k0 + kk;
-    ulonglong2 *slot = reinterpret_cast<ulonglong2 *>(a.keys + (size_t)kk * HWt) + 2 * t4;
-    const ulonglong2 k01 = slot[0], k23 = slot[1];
-    const ulonglong2 ones = make_ulonglong2(~0ull, ~0ull);
-    slot[0] = ones;  // ready for the next group of views
-    slot[1] = ones;
-    bool h0, h1, h2, h3;
-    int4 w;
-    float4 z;
-    decode(k01.x, h0, w.x, z.x);
-    decode(k01.y, h1, w.y, z.y);
-    decode(k23.x, h2, w.z, z.z);
-    decode(k23.y, h3, w.w, z.w);
-    const size_t o4 = (size_t)k * q4 + t4;
-    __stcs(reinterpret_cast<int4 *>(a.winner) + o4, w);
+    ulonglong2 *slot = reinterpret_cast<ulonglong2 *>(a.keys + (size_t)kk * HWt) + (size_t)t * (P / 2);
+    ulonglong2 kv[P / 2];
+#pragma unroll
+    for (int q = 0; q < P / 2; ++q) kv[q] = slot[q];
+    float4 f[P / 4];
+    if (a.guided) {
+#pragma unroll
+        for (int q = 0; q < P / 4; ++q) f[q] = __ldg(reinterpret_cast<const float4 *>(a.fused) + (size_t)t * (P / 4) + q);
+    }
+#pragma unroll
+    for (int q = 0; q < P / 2; ++q) slot[q] = make_ulonglong2(~0ull, ~0ull);
+    bool h[P];
+    int w[P];
+    float z[P];
+#pragma unroll
+    for (int q = 0; q < P / 2; ++q) {
+        decode(kv[q].x, h[2 * q], w[2 * q], z[2 * q]);
+        decode(kv[q].y, h[2 * q + 1], w[2 * q + 1], z[2 * q + 1]);
+    }
+    uint32_t c[P];
     if (a.warped_rgba) {
         const uint32_t *src = a.rgba + (size_t)k * a.W * a.H;
-        uint4 c;
-        c.x = h0 ? __ldg(&src[w.x]) : 0u;
-        c.y = h1 ? __ldg(&src[w.y]) : 0u;
-        c.z = h2 ? __ldg(&src[w.z]) : 0u;
-        c.w = h3 ? __ldg(&src[w.w]) : 0u;
-        __stcs(reinterpret_cast<uint4 *>(a.warped_rgba) + o4, c);
+#pragma unroll
+        for (int q = 0; q < P; ++q) c[q] = h[q] ? __ldg(&src[w[q]]) : 0u;
     }
-    if (a.warped_depth) __stcs(reinterpret_cast<float4 *>(a.warped_depth) + o4, z);
-    if (a.alpha)
-        __stcs(reinterpret_cast<unsigned int *>(a.alpha) + o4,
-               (unsigned)h0 | ((unsigned)h1 << 8) | ((unsigned)h2 << 16) | ((unsigned)h3 << 24));
-    if (a.guided) {
-        const float4 f = __ldg(reinterpret_cast<const float4 *>(a.fused) + t4);
-        const unsigned g0 = h0 && fabsf(z.x - f.x) <= a.mu_guide, g1 = h1 && fabsf(z.y - f.y) <= a.mu_guide;
-        const unsigned g2 = h2 && fabsf(z.z - f.z) <= a.mu_guide, g3 = h3 && fabsf(z.w - f.w) <= a.mu_guide;
-        __stcs(reinterpret_cast<unsigned int *>(a.guided) + o4, g0 | (g1 << 8) | (g2 << 16) | (g3 << 24));
+    const size_t o4 = ((size_t)k * HWt) / 4 + (size_t)t * (P / 4);
+#pragma unroll
+    for (int q = 0; q < P / 4; ++q) {
+        __stcs(reinterpret_cast<int4 *>(a.winner) + o4 + q, make_int4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]));
+        if (a.warped_rgba)
+            __stcs(reinterpret_cast<uint4 *>(a.warped_rgba) + o4 + q,
+                   make_uint4(c[4 * q], c[4 * q + 1], c[4 * q + 2], c[4 * q + 3]));
+        if (a.warped_depth)
+            __stcs(reinterpret_cast<float4 *>(a.warped_depth) + o4 + q,
+                   make_float4(z[4 * q], z[4 * q + 1], z[4 * q + 2], z[4 * q + 3]));
+        if (a.alpha)
+            __stcs(reinterpret_cast<unsigned int *>(a.alpha) + o4 + q,
+                   (unsigned)h[4 * q] | ((unsigned)h[4 * q + 1] << 8) | ((unsigned)h[4 * q + 2] << 16) |
+                       ((unsigned)h[4 * q + 3] << 24));
+        if (a.guided) {
+            const unsigned g0 = h[4 * q] && fabsf(z[4 * q] - f[q].x) <= a.mu_guide;
+            const unsigned g1 = h[4 * q + 1] && fabsf(z[4 * q + 1] - f[q].y) <= a.mu_guide;
+            const unsigned g2 = h[4 * q + 2] && fabsf(z[4 * q + 2] - f[q].z) <= a.mu_guide;
+            const unsigned g3 = h[4 * q + 3] && fabsf(z[4 * q + 3] - f[q].w) <= a.mu_guide;
+            __stcs(reinterpret_cast<unsigned int *>(a.guided) + o4 + q, g0 | (g1 << 8) | (g2 << 16) | (g3 << 24));
+        }
     }
 }
 
@@ -416,8 +432,10 @@ cudaError_t launch_splat(const SplatArgs &a, int K, cudaStream_t st) {
             if (a.guide_reject) splat_scatter<float, true><<<g, b, 0, st>>>(a, k0);
             else splat_scatter<float><<<g, b, 0, st>>>(a, k0);
         }
-        if (HWt % 4 == 0)
-            splat_resolve4<<<dim3((unsigned)((HWt / 4 + 255) / 256), (unsigned)kn), 256, 0, st>>>(a, k0);
+        if (HWt % 8 == 0)
+            splat_resolveP<8><<<dim3((unsigned)((HWt / 8 + 255) / 256), (unsigned)kn), 256, 0, st>>>(a, k0);
+        else if (HWt % 4 == 0)
+            splat_resolveP<4><<<dim3((unsigned)((HWt / 4 + 255) / 256), (unsigned)kn), 256, 0, st>>>(a, k0);
         else
             splat_resolve<<<dim3((unsigned)((HWt + 255) / 256), (unsigned)kn), 256, 0, st>>>(a, k0);
     }
