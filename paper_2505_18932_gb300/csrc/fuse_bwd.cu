@@ -21,8 +21,12 @@ namespace {
 //           + sum_{c whose window holds x, with multiplicity}
 //                 P(c) (-2) (d_c - d_x) [|d_c - d_x| < mu]
 // where P(c) = A(c) domega/dnu(c) (0 when the weight is saturated or c is
-// invalid).  Nothing of size D x H x W is stored; the bracketing samples are
-// recomputed by the forward's own code, so they are bit-identical to it.
+// invalid).  With omega = w_c (nu / w^2)^(-1/2) unsaturated, domega/dnu =
+// -0.5 omega / nu = -0.5 omega^3 / (w^2 w_c^2), so a float2 map gives P(c)
+// from its stored omega without re-summing the window; for a half2 map (omega
+// rounded to half) nu is re-summed from the depths.  Nothing of size D x H x W
+// is stored; the bracketing samples are recomputed by the forward's own code,
+// so they are bit-identical to it.
 // ---------------------------------------------------------------------------
 
 template <int KMAX, typename MT>
@@ -92,11 +96,14 @@ __device__ __forceinline__ int window_multiplicity(int c, int x, int n, int R) {
     return abs(c - x) <= R ? 1 : 0;
 }
 
-constexpr int GB_TX = 32;
-constexpr int GB_TY = 8;
+constexpr int GB_TX = 32;    // block of 32 x 32 input pixels: 32 x 8 threads,
+constexpr int GB_TY = 32;    // each thread GB_ROWS rows 8 apart
+constexpr int GB_ROWS = 4;
 
+// wmap: the forward's float2 (d, omega) planes, or null (re-sum nu).
 template <int R, typename DT>
-__global__ void __launch_bounds__(GB_TX *GB_TY) fuse_bwd_gather(const DT *__restrict__ depth,
+__global__ void __launch_bounds__(GB_TX *(GB_TY / GB_ROWS)) fuse_bwd_gather(const DT *__restrict__ depth,
+                                                                const float2 *__restrict__ wmap,
                                                                 const float2 *__restrict__ acc,
                                                                 float *__restrict__ grad, int W, int H, float mu,
                                                                 float wconst, float inv_w2) {
@@ -109,7 +116,8 @@ __global__ void __launch_bounds__(GB_TX *GB_TY) fuse_bwd_gather(const DT *__rest
     const float2 *ak = acc + (size_t)k * W * H;
     const int bx = blockIdx.x * GB_TX, by = blockIdx.y * GB_TY;
     const int tid = threadIdx.y * GB_TX + threadIdx.x;
-    for (int e = tid; e < DW * DH; e += GB_TX * GB_TY) {
+    constexpr int NT = GB_TX * (GB_TY / GB_ROWS);
+    for (int e = tid; e < DW * DH; e += NT) {
         const int sy = e / DW, sx = e - sy * DW;
         const int gx = min(max(bx - 2 * R + sx, 0), W - 1), gy = min(max(by - 2 * R + sy, 0), H - 1);
         const float d = load_depth(&dep[(size_t)gy * W + gx]);
@@ -117,14 +125,19 @@ __global__ void __launch_bounds__(GB_TX *GB_TY) fuse_bwd_gather(const DT *__rest
     }
     __syncthreads();
     // P(c) = A(c) domega/dnu(c) on the outputs and an R halo
-    for (int e = tid; e < PW * PH; e += GB_TX * GB_TY) {
+    for (int e = tid; e < PW * PH; e += NT) {
         const int py = e / PW, px = e - py * PW;
         const int cx = bx - R + px, cy = by - R + py;
         float P = 0.0f;
         if (cx >= 0 && cx < W && cy >= 0 && cy < H) {
             const float A = ak[(size_t)cy * W + cx].x;
             const float dc = dt[py + R][px + R];
-            if (A != 0.0f && dc == dc) {
+            if (wmap) {
+                if (A != 0.0f && dc == dc) {
+                    const float om = __ldg(&wmap[(size_t)k * W * H + (size_t)cy * W + cx]).y;
+                    if (om < 1.0f) P = A * (-0.5f * om * om * om * (inv_w2 / (wconst * wconst)));
+                }
+            } else if (A != 0.0f && dc == dc) {
                 float nu = 0.0f;
                 for (int dy = 0; dy <= 2 * R; ++dy)
                     for (int dx = 0; dx <= 2 * R; ++dx) {
@@ -138,60 +151,79 @@ __global__ void __launch_bounds__(GB_TX *GB_TY) fuse_bwd_gather(const DT *__rest
         pt[py][px] = P;
     }
     __syncthreads();
-    const int x = bx + threadIdx.x, y = by + threadIdx.y;
-    if (x >= W || y >= H) return;
-    const float dx0 = dt[threadIdx.y + 2 * R][threadIdx.x + 2 * R];
-    float g = ak[(size_t)y * W + x].y;  // B(x)
-    if (dx0 == dx0) {
-        const float Px = pt[threadIdx.y + R][threadIdx.x + R];
-        if (Px != 0.0f) {
-            float sum = 0.0f;
-            for (int ey = -R; ey <= R; ++ey)
-                for (int ex = -R; ex <= R; ++ex) {
-                    const float dn = dt[threadIdx.y + 2 * R + ey][threadIdx.x + 2 * R + ex];
-                    const float diff = dx0 - dn;
-                    if (fabsf(diff) < mu) sum += 2.0f * diff;  // false for a NaN (invalid) neighbour
+    // a block whose windows of windows stay inside the image sees every window entry once
+    const bool interior = bx >= 2 * R && by >= 2 * R && bx + GB_TX + 2 * R <= W && by + GB_TY + 2 * R <= H;
+    const int x = bx + threadIdx.x;
+#pragma unroll 1
+    for (int rr = 0; rr < GB_ROWS; ++rr) {
+        const int ly = threadIdx.y + rr * (GB_TY / GB_ROWS);  // row within the block
+        const int y = by + ly;
+        if (x >= W || y >= H) continue;
+        const float dx0 = dt[ly + 2 * R][threadIdx.x + 2 * R];
+        float g = ak[(size_t)y * W + x].y;  // B(x)
+        if (dx0 == dx0) {
+            const float Px = pt[ly + R][threadIdx.x + R];
+            if (interior) {
+                // entry n of x's window and window centre c = n coincide: one pass,
+                // 2 (d_x - d_n) (P(x) + P(n)) where |d_x - d_n| < mu (false for an invalid n)
+#pragma unroll
+                for (int oy = -R; oy <= R; ++oy)
+#pragma unroll
+                    for (int ox = -R; ox <= R; ++ox) {
+                        const float diff = dx0 - dt[ly + 2 * R + oy][threadIdx.x + 2 * R + ox];
+                        if (fabsf(diff) < mu) g = fmaf(2.0f * diff, Px + pt[ly + R + oy][threadIdx.x + R + ox], g);
+                    }
+            } else {
+                if (Px != 0.0f) {
+                    float sum = 0.0f;
+                    for (int ey = -R; ey <= R; ++ey)
+                        for (int ex = -R; ex <= R; ++ex) {
+                            const float dn = dt[ly + 2 * R + ey][threadIdx.x + 2 * R + ex];
+                            const float diff = dx0 - dn;
+                            if (fabsf(diff) < mu) sum += 2.0f * diff;  // false for a NaN (invalid) neighbour
+                        }
+                    g += Px * sum;
                 }
-            g += Px * sum;
-        }
-        for (int cyo = -R; cyo <= R; ++cyo) {
-            const int my = window_multiplicity(y + cyo, y, H, R);
-            if (my == 0) continue;
-            for (int cxo = -R; cxo <= R; ++cxo) {
-                const int mx = window_multiplicity(x + cxo, x, W, R);
-                if (mx == 0) continue;
-                const float Pc = pt[threadIdx.y + R + cyo][threadIdx.x + R + cxo];
-                if (Pc == 0.0f) continue;
-                const float diff = dt[threadIdx.y + 2 * R + cyo][threadIdx.x + 2 * R + cxo] - dx0;
-                if (fabsf(diff) < mu) g += (float)(mx * my) * Pc * (-2.0f) * diff;
+                for (int cyo = -R; cyo <= R; ++cyo) {
+                    const int my = window_multiplicity(y + cyo, y, H, R);
+                    if (my == 0) continue;
+                    for (int cxo = -R; cxo <= R; ++cxo) {
+                        const int mx = window_multiplicity(x + cxo, x, W, R);
+                        if (mx == 0) continue;
+                        const float Pc = pt[ly + R + cyo][threadIdx.x + R + cxo];
+                        if (Pc == 0.0f) continue;
+                        const float diff = dt[ly + 2 * R + cyo][threadIdx.x + 2 * R + cxo] - dx0;
+                        if (fabsf(diff) < mu) g += (float)(mx * my) * Pc * (-2.0f) * diff;
+                    }
+                }
             }
         }
+        grad[(size_t)k * W * H + (size_t)y * W + x] = g;
     }
-    grad[(size_t)k * W * H + (size_t)y * W + x] = g;
 }
 
 template <int R, typename DT>
-cudaError_t launch_bwd_gather_r(const void *depth, const float2 *acc, float *grad, int K, int W, int H, float mu,
-                                float wconst, float inv_w2, cudaStream_t st) {
+cudaError_t launch_bwd_gather_r(const void *depth, const float2 *wmap, const float2 *acc, float *grad, int K, int W,
+                                int H, float mu, float wconst, float inv_w2, cudaStream_t st) {
     dim3 grid((W + GB_TX - 1) / GB_TX, (H + GB_TY - 1) / GB_TY, K);
-    fuse_bwd_gather<R, DT><<<grid, dim3(GB_TX, GB_TY), 0, st>>>(reinterpret_cast<const DT *>(depth), acc, grad, W, H,
-                                                                mu, wconst, inv_w2);
+    fuse_bwd_gather<R, DT><<<grid, dim3(GB_TX, GB_TY / GB_ROWS), 0, st>>>(reinterpret_cast<const DT *>(depth), wmap, acc, grad,
+                                                                W, H, mu, wconst, inv_w2);
     return cudaGetLastError();
 }
 
 template <typename DT>
-cudaError_t launch_bwd_gather(const void *depth, const float2 *acc, float *grad, int K, int W, int H, float mu,
-                              float wconst, int window, cudaStream_t st) {
+cudaError_t launch_bwd_gather(const void *depth, const float2 *wmap, const float2 *acc, float *grad, int K, int W,
+                              int H, float mu, float wconst, int window, cudaStream_t st) {
     const float inv_w2 = (float)(1.0 / ((double)window * (double)window));
     switch (window / 2) {
-        case 0: return launch_bwd_gather_r<0, DT>(depth, acc, grad, K, W, H, mu, wconst, inv_w2, st);
-        case 1: return launch_bwd_gather_r<1, DT>(depth, acc, grad, K, W, H, mu, wconst, inv_w2, st);
-        case 2: return launch_bwd_gather_r<2, DT>(depth, acc, grad, K, W, H, mu, wconst, inv_w2, st);
-        case 3: return launch_bwd_gather_r<3, DT>(depth, acc, grad, K, W, H, mu, wconst, inv_w2, st);
-        case 4: return launch_bwd_gather_r<4, DT>(depth, acc, grad, K, W, H, mu, wconst, inv_w2, st);
-        case 5: return launch_bwd_gather_r<5, DT>(depth, acc, grad, K, W, H, mu, wconst, inv_w2, st);
-        case 6: return launch_bwd_gather_r<6, DT>(depth, acc, grad, K, W, H, mu, wconst, inv_w2, st);
-        case 7: return launch_bwd_gather_r<7, DT>(depth, acc, grad, K, W, H, mu, wconst, inv_w2, st);
+        case 0: return launch_bwd_gather_r<0, DT>(depth, wmap, acc, grad, K, W, H, mu, wconst, inv_w2, st);
+        case 1: return launch_bwd_gather_r<1, DT>(depth, wmap, acc, grad, K, W, H, mu, wconst, inv_w2, st);
+        case 2: return launch_bwd_gather_r<2, DT>(depth, wmap, acc, grad, K, W, H, mu, wconst, inv_w2, st);
+        case 3: return launch_bwd_gather_r<3, DT>(depth, wmap, acc, grad, K, W, H, mu, wconst, inv_w2, st);
+        case 4: return launch_bwd_gather_r<4, DT>(depth, wmap, acc, grad, K, W, H, mu, wconst, inv_w2, st);
+        case 5: return launch_bwd_gather_r<5, DT>(depth, wmap, acc, grad, K, W, H, mu, wconst, inv_w2, st);
+        case 6: return launch_bwd_gather_r<6, DT>(depth, wmap, acc, grad, K, W, H, mu, wconst, inv_w2, st);
+        case 7: return launch_bwd_gather_r<7, DT>(depth, wmap, acc, grad, K, W, H, mu, wconst, inv_w2, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -218,9 +250,10 @@ cudaError_t launch_fuse_backward(const FuseArgs &a, const void *depth, int depth
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    const float2 *wmap = a.map_dtype == GVS_F16 ? nullptr : reinterpret_cast<const float2 *>(a.dw);
     return depth_dtype == GVS_F16
-               ? launch_bwd_gather<__half>(depth, acc, grad_depths, a.K, a.W, a.H, mu, wconst, window, st)
-               : launch_bwd_gather<float>(depth, acc, grad_depths, a.K, a.W, a.H, mu, wconst, window, st);
+               ? launch_bwd_gather<__half>(depth, wmap, acc, grad_depths, a.K, a.W, a.H, mu, wconst, window, st)
+               : launch_bwd_gather<float>(depth, wmap, acc, grad_depths, a.K, a.W, a.H, mu, wconst, window, st);
 }
 
 }  // namespace gvs

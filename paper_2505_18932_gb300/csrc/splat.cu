@@ -299,15 +299,16 @@ __device__ __forceinline__ float4 load_color(const uint2 *p) {  // four bfloat16
                        __uint_as_float(r.y & 0xffff0000u));
 }
 
+// Grid as splat_scatter: blocks of 32 x 8 source pixels, z = view of the group.
 template <typename DT, typename CT>
-__global__ void __launch_bounds__(256) soft_accum(const SplatArgs a, int k0, int kn) {
+__global__ void __launch_bounds__(SC_BX * SC_BY) soft_accum(const SplatArgs a, int k0) {
     const int64_t HW = (int64_t)a.W * a.H;
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= (int64_t)kn * HW) return;
-    const int kk = (int)(p / HW);
+    const int u = blockIdx.x * SC_BX + threadIdx.x;
+    const int v = blockIdx.y * SC_BY + threadIdx.y;
+    if (u >= a.W || v >= a.H) return;
+    const int kk = blockIdx.z;
     const int k = k0 + kk;
-    const int src = (int)(p - (int64_t)kk * HW);
-    const int v = src / a.W, u = src - v * a.W;
+    const int src = v * a.W + u;
     const float d = load_depth(reinterpret_cast<const DT *>(a.depth) + (size_t)k * HW + src);
     const Geo g = contract(a.v[k], u, v, d, a.Wt, a.Ht, 1, a.max_hw);
     if (!g.ok) return;
@@ -326,13 +327,13 @@ __global__ void __launch_bounds__(256) soft_accum(const SplatArgs a, int k0, int
         }
 }
 
-__global__ void __launch_bounds__(256) soft_resolve(const SplatArgs a, int k0, int kn) {
+// One thread per target pixel (any size); grid (ceil(Wt Ht / 256), views of the group).
+__global__ void __launch_bounds__(256) soft_resolve(const SplatArgs a, int k0) {
     const int64_t HWt = (int64_t)a.Wt * a.Ht;
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= (int64_t)kn * HWt) return;
-    const int kk = (int)(p / HWt);
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= HWt) return;
+    const int kk = blockIdx.y;
     const int k = k0 + kk;
-    const int64_t t = p - (int64_t)kk * HWt;
     unsigned long long *slot = a.keys + (size_t)kk * HWt;
     float4 *acc = a.acc + (size_t)kk * HWt;
     const unsigned long long key = slot[t];
@@ -352,14 +353,54 @@ __global__ void __launch_bounds__(256) soft_resolve(const SplatArgs a, int k0, i
     a.out_color[o] = make_float4(s.x * r, s.y * r, s.z * r, 0.0f);
 }
 
+// Four consecutive target pixels per thread, every access a 16-byte (bytes:
+// 4-byte) vector; needs Wt * Ht divisible by 4.  Grid (ceil(Wt Ht / 1024), views).
+__global__ void __launch_bounds__(256) soft_resolve4(const SplatArgs a, int k0) {
+    const int64_t HWt = (int64_t)a.Wt * a.Ht;
+    const int t4 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t4 >= (int)(HWt / 4)) return;
+    const int kk = blockIdx.y;
+    const int k = k0 + kk;
+    ulonglong2 *slot = reinterpret_cast<ulonglong2 *>(a.keys + (size_t)kk * HWt) + 2 * (size_t)t4;
+    float4 *acc = a.acc + (size_t)kk * HWt + 4 * (size_t)t4;
+    const ulonglong2 k01 = slot[0], k23 = slot[1];
+    float4 s[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) s[q] = acc[q];
+    slot[0] = make_ulonglong2(~0ull, ~0ull);  // ready for the next group of views
+    slot[1] = make_ulonglong2(~0ull, ~0ull);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    bool h[4];
+    int32_t w[4];
+    float z[4];
+    decode(k01.x, h[0], w[0], z[0]);
+    decode(k01.y, h[1], w[1], z[1]);
+    decode(k23.x, h[2], w[2], z[2]);
+    decode(k23.y, h[3], w[3], z[3]);
+    const size_t o4 = ((size_t)k * HWt) / 4 + t4;
+    __stcs(reinterpret_cast<int4 *>(a.winner) + o4, make_int4(w[0], w[1], w[2], w[3]));
+    if (a.warped_depth) __stcs(reinterpret_cast<float4 *>(a.warped_depth) + o4, make_float4(z[0], z[1], z[2], z[3]));
+    if (a.alpha)
+        __stcs(reinterpret_cast<unsigned int *>(a.alpha) + o4,
+               (unsigned)h[0] | ((unsigned)h[1] << 8) | ((unsigned)h[2] << 16) | ((unsigned)h[3] << 24));
+    __stcs(reinterpret_cast<float4 *>(a.wsum) + o4, make_float4(s[0].w, s[1].w, s[2].w, s[3].w));
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float r = (h[q] && s[q].w > 0.0f) ? 1.0f / s[q].w : 0.0f;
+        __stcs(a.out_color + 4 * o4 + q, make_float4(s[q].x * r, s[q].y * r, s[q].z * r, 0.0f));
+    }
+}
+
+// Grid as splat_scatter over all views: blocks of 32 x 8 source pixels, z = view.
 template <typename DT, typename CT>
-__global__ void __launch_bounds__(256) soft_bwd(const SplatArgs a, int K) {
+__global__ void __launch_bounds__(SC_BX * SC_BY) soft_bwd(const SplatArgs a) {
     const int64_t HW = (int64_t)a.W * a.H, HWt = (int64_t)a.Wt * a.Ht;
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= (int64_t)K * HW) return;
-    const int k = (int)(p / HW);
-    const int src = (int)(p - (int64_t)k * HW);
-    const int v = src / a.W, u = src - v * a.W;
+    const int u = blockIdx.x * SC_BX + threadIdx.x;
+    const int v = blockIdx.y * SC_BY + threadIdx.y;
+    if (u >= a.W || v >= a.H) return;
+    const int k = blockIdx.z;
+    const int src = v * a.W + u;
     const float d = load_depth(reinterpret_cast<const DT *>(a.depth) + (size_t)k * HW + src);
     const Geo g = contract(a.v[k], u, v, d, a.Wt, a.Ht, 1, a.max_hw);
     float gd = 0.0f;
@@ -397,14 +438,16 @@ __global__ void __launch_bounds__(256) soft_bwd(const SplatArgs a, int K) {
 
 template <typename DT, typename CT>
 void soft_groups(const SplatArgs &a, int K, cudaStream_t st) {
-    const int64_t HWt = (int64_t)a.Wt * a.Ht, HW = (int64_t)a.W * a.H;
+    const int64_t HWt = (int64_t)a.Wt * a.Ht;
     const int slots = a.slots < K ? a.slots : K;
     for (int k0 = 0; k0 < K; k0 += slots) {
         const int kn = (K - k0) < slots ? (K - k0) : slots;
-        const int64_t ns = (int64_t)kn * HW, nt = (int64_t)kn * HWt;
         splat_scatter<DT><<<scatter_grid(a.W, a.H, kn), dim3(SC_BX, SC_BY), 0, st>>>(a, k0);
-        soft_accum<DT, CT><<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(a, k0, kn);
-        soft_resolve<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(a, k0, kn);
+        soft_accum<DT, CT><<<scatter_grid(a.W, a.H, kn), dim3(SC_BX, SC_BY), 0, st>>>(a, k0);
+        if (HWt % 4 == 0)
+            soft_resolve4<<<dim3((unsigned)((HWt / 4 + 255) / 256), (unsigned)kn), 256, 0, st>>>(a, k0);
+        else
+            soft_resolve<<<dim3((unsigned)((HWt + 255) / 256), (unsigned)kn), 256, 0, st>>>(a, k0);
     }
 }
 
@@ -468,14 +511,13 @@ cudaError_t launch_soft_splat(const SplatArgs &a, int K, cudaStream_t st) {
 
 cudaError_t launch_soft_splat_backward(const SplatArgs &a, int K, cudaStream_t st) {
     if (K == 0) return cudaSuccess;
-    const int64_t n = (int64_t)K * a.W * a.H;
-    const unsigned grid = (unsigned)((n + 255) / 256);
+    const dim3 grid = scatter_grid(a.W, a.H, K), block(SC_BX, SC_BY);
     if (a.depth_dtype == GVS_F16) {
-        if (a.color_dtype == GVS_BF16) soft_bwd<__half, uint2><<<grid, 256, 0, st>>>(a, K);
-        else soft_bwd<__half, float4><<<grid, 256, 0, st>>>(a, K);
+        if (a.color_dtype == GVS_BF16) soft_bwd<__half, uint2><<<grid, block, 0, st>>>(a);
+        else soft_bwd<__half, float4><<<grid, block, 0, st>>>(a);
     } else {
-        if (a.color_dtype == GVS_BF16) soft_bwd<float, uint2><<<grid, 256, 0, st>>>(a, K);
-        else soft_bwd<float, float4><<<grid, 256, 0, st>>>(a, K);
+        if (a.color_dtype == GVS_BF16) soft_bwd<float, uint2><<<grid, block, 0, st>>>(a);
+        else soft_bwd<float, float4><<<grid, block, 0, st>>>(a);
     }
     return cudaGetLastError();
 }
