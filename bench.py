@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only-form", default=None, choices=sorted(FORM_CLASSES),
+                    help="time one form of the 8x1080p frame alone (for profiling) and print its ms per step")
     return ap.parse_args()
 
 
@@ -815,9 +817,38 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+FORM_CLASSES = ("fwd_bwd", "gauss_render", "network_frame_k4", "sphere_trace_fusion", "temporal_online")
+
+
+def run_only_form(args):
+    """One form of the 8x1080p frame, alone: max(3, warmup) untimed steps, then `steps`
+    steps between CUDA events.  Used to profile a form's kernels."""
+    import torch
+    from synth import configs
+    w = configs.headline_8x1080p()
+    frames_np = render_frames(w, rank_frames(0))
+    cls = {"fwd_bwd": FwdBwd, "gauss_render": GaussRender, "network_frame_k4": NetworkFrame,
+           "sphere_trace_fusion": SphereTrace, "temporal_online": TemporalOnline}[args.only_form]
+    form = cls(w, frames_np[:2] if cls is FwdBwd else frames_np, torch.device("cuda", 0))
+    for i in range(max(3, args.warmup)):
+        form.step(i)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for i in range(args.steps):
+        form.step(i + 1)
+    b.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"form": args.only_form, "ms_per_step": round(a.elapsed_time(b) / max(args.steps, 1), 4),
+                      "steps": args.steps, "workload": w.name}), flush=True)
+
+
 def main():
     args = parse()
     rank, local_rank, world = dist_env()
+    if args.only_form:
+        run_only_form(args)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
