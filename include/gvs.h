@@ -596,6 +596,16 @@ GVS_API gvs_status gvs_blend(int32_t n_views, int32_t target_width, int32_t targ
                              const void *i_bg, float *image, double *l_depth, void *workspace,
                              size_t workspace_bytes, void *stream);
 
+/*
+ * gvs_debug_bounds_error -- a service of the library (the paper has no counterpart).
+ * In a build compiled with GVS_BOUNDS_CHECK every kernel checks its computed
+ * gather / scatter indices (fusion map and bound tiles, splat keys and colour
+ * gathers, Gaussian records and tile lists), skips an out-of-range access and records
+ * the first one; this returns ((site << 48) | index) of that access, 0 if none, and
+ * clears the record.  A normal build checks nothing and always returns 0.
+ */
+GVS_API uint64_t gvs_debug_bounds_error(void);
+
 #ifdef __cplusplus
 }
 #endif

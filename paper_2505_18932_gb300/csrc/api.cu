@@ -12,7 +12,10 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "blend_internal.cuh"
+#include "bounds_check.cuh"
 #include "sphere_internal.cuh"
 #include "gauss_internal.cuh"
 #include "gvs_internal.cuh"
@@ -20,6 +23,12 @@
 namespace {
 
 thread_local char g_err[512] = "";
+
+// NVTX range around each entry point (a no-op unless a profiler is attached).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
 
 gvs_status fail(gvs_status s, const char *fmt, ...) {
     va_list ap;
@@ -130,6 +139,7 @@ const char *gvs_last_error(void) { return g_err; }
 gvs_status gvs_refine_depth(const uint32_t *rgba_t, const uint32_t *rgba_prev, const void *depth_t,
                             void *depth_state, uint8_t *mask, int32_t n_views, int32_t width, int32_t height,
                             const gvs_refine_params *params, void *stream) {
+    const Range nvtx_range("gvs_refine_depth");
     if (!params) return fail(GVS_ERR_INVALID_ARG, "refine: params is NULL");
     if (n_views < 0 || n_views > GVS_MAX_VIEWS) return fail(GVS_ERR_INVALID_ARG, "refine: n_views out of range");
     if (width < 1 || height < 1 || width > GVS_MAX_DIM || height > GVS_MAX_DIM)
@@ -159,6 +169,7 @@ gvs_status gvs_refine_depth_soft(const uint32_t *rgba_t, const uint32_t *rgba_pr
                                  void *depth_state, float *mask, int32_t n_views, int32_t width, int32_t height,
                                  const gvs_refine_soft_params *params, void *workspace, size_t workspace_bytes,
                                  void *stream) {
+    const Range nvtx_range("gvs_refine_depth_soft");
     if (!params) return fail(GVS_ERR_INVALID_ARG, "soft refine: params is NULL");
     if (n_views < 0 || n_views > GVS_MAX_VIEWS) return fail(GVS_ERR_INVALID_ARG, "soft refine: n_views out of range");
     if (width < 1 || height < 1 || width > GVS_MAX_DIM || height > GVS_MAX_DIM)
@@ -187,6 +198,7 @@ gvs_status gvs_refine_depth_soft(const uint32_t *rgba_t, const uint32_t *rgba_pr
 
 gvs_status gvs_select_views(const gvs_camera *cams, int32_t n, const gvs_camera *target, int32_t k,
                             int32_t *out_idx) {
+    const Range nvtx_range("gvs_select_views");
     if (!cams || !target || !out_idx || n < 1 || k < 1 || k > n)
         return fail(GVS_ERR_INVALID_ARG, "select views: need cameras, a target, out_idx and 1 <= k <= n");
     for (int i = 0; i < n; ++i)
@@ -294,6 +306,7 @@ extern "C" {
 gvs_status gvs_weight_map(const void *in_depths, int32_t depth_dtype, int32_t n_views, int32_t width,
                           int32_t height, float mu, float weight_const, int32_t window, int32_t map_dtype, void *map,
                           size_t map_bytes, void *stream) {
+    const Range nvtx_range("gvs_weight_map");
     if (n_views < 0 || n_views > GVS_MAX_VIEWS) return fail(GVS_ERR_INVALID_ARG, "weight map: n_views out of range");
     if (width < 1 || height < 1 || width > GVS_MAX_DIM || height > GVS_MAX_DIM)
         return fail(GVS_ERR_INVALID_ARG, "weight map: image size out of range");
@@ -317,6 +330,7 @@ gvs_status gvs_weight_map(const void *in_depths, int32_t depth_dtype, int32_t n_
 gvs_status gvs_fuse_depth_from_map(const gvs_camera *in_cams, const void *map, size_t map_bytes, int32_t n_views,
                                    const gvs_camera *target, const gvs_fuse_params *params, float *fused_depth,
                                    int16_t *crossing, void *stream) {
+    const Range nvtx_range("gvs_fuse_depth_from_map");
     int32_t W = 0, H = 0;
     gvs_status s = check_fuse_common(in_cams, n_views, target, params, fused_depth, crossing, &W, &H);
     if (s != GVS_OK) return s;
@@ -333,6 +347,7 @@ gvs_status gvs_fuse_depth_temporal(const gvs_camera *in_cams, const void *map, s
                                    const gvs_camera *target, const gvs_fuse_params *params, const float *prev_depth,
                                    const float *w_tmp, float *fused_depth, int16_t *crossing, float *view_weight,
                                    void *stream) {
+    const Range nvtx_range("gvs_fuse_depth_temporal");
     int32_t W = 0, H = 0;
     gvs_status s = check_fuse_common(in_cams, n_views, target, params, fused_depth, crossing, &W, &H);
     if (s != GVS_OK) return s;
@@ -355,6 +370,7 @@ gvs_status gvs_temporal_weight(const void *masks, int32_t mask_dtype, const int3
                                int32_t width, int32_t height, int32_t target_width, int32_t target_height,
                                const float *w_tmp_prev, const float *w_view_prev, float beta_t, float eta,
                                float *w_tmp, float *target_mask, void *stream) {
+    const Range nvtx_range("gvs_temporal_weight");
     if (n_views < 0 || n_views > GVS_MAX_VIEWS || width < 1 || height < 1 || target_width < 1 || target_height < 1 ||
         width > GVS_MAX_DIM || height > GVS_MAX_DIM || target_width > GVS_MAX_DIM || target_height > GVS_MAX_DIM)
         return fail(GVS_ERR_INVALID_ARG, "temporal weight: sizes out of range");
@@ -374,6 +390,7 @@ gvs_status gvs_temporal_weight(const void *masks, int32_t mask_dtype, const int3
 gvs_status gvs_guided_mask(const float *warped_depth, const uint8_t *alpha, const float *fused_depth,
                            int32_t n_views, int32_t target_width, int32_t target_height, float mu_guide,
                            uint8_t *guided, void *stream) {
+    const Range nvtx_range("gvs_guided_mask");
     if (n_views < 0 || n_views > GVS_MAX_VIEWS || target_width < 1 || target_height < 1)
         return fail(GVS_ERR_INVALID_ARG, "guided mask: sizes out of range");
     if (!(isfinite(mu_guide) && mu_guide >= 0.0f)) return fail(GVS_ERR_INVALID_ARG, "guided mask: mu_guide must be >= 0");
@@ -389,6 +406,7 @@ gvs_status gvs_guided_mask(const float *warped_depth, const uint8_t *alpha, cons
 gvs_status gvs_fuse_depth(const gvs_camera *in_cams, const void *in_depths, int32_t n_views,
                           const gvs_camera *target, const gvs_fuse_params *params, float *fused_depth,
                           int16_t *crossing, void *workspace, size_t workspace_bytes, void *stream) {
+    const Range nvtx_range("gvs_fuse_depth");
     int32_t W = 0, H = 0;
     gvs_status s = check_fuse_common(in_cams, n_views, target, params, fused_depth, crossing, &W, &H);
     if (s != GVS_OK) return s;
@@ -418,6 +436,7 @@ gvs_status gvs_fuse_depth_backward(const gvs_camera *in_cams, const void *in_dep
                                    const gvs_camera *target, const gvs_fuse_params *params, const void *map,
                                    size_t map_bytes, const int16_t *crossing, const float *grad_fused,
                                    float *grad_depths, void *workspace, size_t workspace_bytes, void *stream) {
+    const Range nvtx_range("gvs_fuse_depth_backward");
     int32_t W = 0, H = 0;
     // the checks of the forward, with the fused-depth output replaced by its gradient
     gvs_status s = check_fuse_common(in_cams, n_views, target, params, grad_fused, crossing, &W, &H);
@@ -455,6 +474,7 @@ gvs_status gvs_forward_splat(const gvs_camera *in_cams, const void *in_depths, c
                              const float *fused_depth, int32_t *winner, uint32_t *warped_rgba, float *warped_depth,
                              uint8_t *alpha, uint8_t *guided, void *workspace, size_t workspace_bytes,
                              void *stream) {
+    const Range nvtx_range("gvs_forward_splat");
     int32_t W = 0, H = 0;
     if (!params) return fail(GVS_ERR_INVALID_ARG, "splat: params is NULL");
     if (!views_ok(in_cams, n_views, &W, &H))
@@ -582,6 +602,7 @@ gvs_status gvs_soft_splat(const gvs_camera *in_cams, const void *in_depths, cons
                           const gvs_camera *target, const gvs_soft_splat_params *params, int32_t *winner,
                           float *warped_color, float *warped_depth, float *weight_sum, uint8_t *alpha,
                           void *workspace, size_t workspace_bytes, void *stream) {
+    const Range nvtx_range("gvs_soft_splat");
     gvs::SplatArgs a;
     gvs_status s = soft_common(in_cams, in_depths, in_color, n_views, target, params, &a);
     if (s != GVS_OK) return s;
@@ -614,6 +635,7 @@ gvs_status gvs_soft_splat_backward(const gvs_camera *in_cams, const void *in_dep
                                    const int32_t *winner, const float *warped_color, const float *warped_depth,
                                    const float *weight_sum, const float *grad_color, const float *grad_depth,
                                    float *grad_in_depth, float *grad_in_color, void *stream) {
+    const Range nvtx_range("gvs_soft_splat_backward");
     gvs::SplatArgs a;
     gvs_status s = soft_common(in_cams, in_depths, in_color, n_views, target, params, &a);
     if (s != GVS_OK) return s;
@@ -723,6 +745,7 @@ size_t gvs_fuse_batch_bytes(int32_t n_items) {
 gvs_status gvs_fuse_batch_create(const gvs_camera *in_cams, int32_t n_views, const gvs_fuse_item *items,
                                  int32_t n_items, const gvs_fuse_params *params, void *table, size_t table_bytes,
                                  gvs_fuse_batch **out) {
+    const Range nvtx_range("gvs_fuse_batch_create");
     if (!out) return fail(GVS_ERR_INVALID_ARG, "fuse batch: out is NULL");
     *out = nullptr;
     if (n_items < 1 || n_items > GVS_MAX_BATCH_ITEMS || !items)
@@ -763,6 +786,7 @@ gvs_status gvs_fuse_batch_create(const gvs_camera *in_cams, int32_t n_views, con
 }
 
 gvs_status gvs_fuse_batch_launch(const gvs_fuse_batch *b, void *stream) {
+    const Range nvtx_range("gvs_fuse_batch_launch");
     if (!b) return fail(GVS_ERR_INVALID_ARG, "fuse batch: NULL batch");
     cudaError_t e = gvs::launch_fuse_batch(b->d_items, b->n_items, b->total, b->d_counter, b->K, b->map_dtype,
                                            b->variant, (cudaStream_t)stream);
@@ -790,6 +814,7 @@ size_t gvs_gauss_splat_workspace_bytes(int32_t width, int32_t height, int32_t ta
 gvs_status gvs_gauss_splat(const gvs_camera *in_cams, const void *in_depths, const uint32_t *in_rgba,
                            int32_t n_views, const gvs_camera *target, const gvs_gauss_params *params, float *color,
                            float *depth, void *workspace, size_t workspace_bytes, void *stream) {
+    const Range nvtx_range("gvs_gauss_splat");
     int32_t W = 0, H = 0;
     if (!params) return fail(GVS_ERR_INVALID_ARG, "gauss splat: params is NULL");
     if (!views_ok(in_cams, n_views, &W, &H))
@@ -886,6 +911,7 @@ extern "C" {
 gvs_status gvs_blend_features(const gvs_camera *in_cams, int32_t n_views, const gvs_camera *target,
                               const uint32_t *warped_rgba, const float *warped_depth, const uint8_t *alpha,
                               const float *fused_depth, int32_t out_dtype, void *features, void *stream) {
+    const Range nvtx_range("gvs_blend_features");
     if (!camera_ok(target)) return fail(GVS_ERR_INVALID_ARG, "blend features: target camera invalid");
     if (!in_cams) return fail(GVS_ERR_INVALID_ARG, "blend features: in_cams is NULL");
     gvs_status st = GVS_OK;
@@ -933,6 +959,7 @@ gvs_status gvs_blend(int32_t n_views, int32_t target_width, int32_t target_heigh
                      const uint8_t *alpha, const float *warped_depth, const float *fused_depth, int32_t weight_dtype,
                      const void *w, const void *w_bg, const void *i_bg, float *image, double *l_depth,
                      void *workspace, size_t workspace_bytes, void *stream) {
+    const Range nvtx_range("gvs_blend");
     gvs_status st = GVS_OK;
     if (!blend_common(n_views, target_width, target_height, warped_rgba, warped_depth, alpha, fused_depth, "blend",
                       &st))
@@ -963,6 +990,7 @@ extern "C" {
 gvs_status gvs_fuse_depth_sphere(const gvs_camera *in_cams, const void *in_depths, int32_t n_views,
                                  const gvs_camera *target, const gvs_sphere_params *params, float *fused_depth,
                                  int32_t *evals, void *workspace, size_t workspace_bytes, void *stream) {
+    const Range nvtx_range("gvs_fuse_depth_sphere");
     int32_t W = 0, H = 0;
     if (!params) return fail(GVS_ERR_INVALID_ARG, "sphere: params is NULL");
     if (!views_ok(in_cams, n_views, &W, &H))
@@ -1009,6 +1037,22 @@ gvs_status gvs_fuse_depth_sphere(const gvs_camera *in_cams, const void *in_depth
     cudaError_t e = gvs::launch_sphere(a, st);
     if (e != cudaSuccess) return cuda_fail(e, "sphere: launch");
     return GVS_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Debug builds: the first out-of-range gather / scatter index.
+// ---------------------------------------------------------------------------
+extern "C" {
+
+uint64_t gvs_debug_bounds_error(void) {
+    const unsigned long long r[] = {gvs::bounds_take_fuse(),   gvs::bounds_take_fuse_batch(),
+                                    gvs::bounds_take_fuse_bwd(), gvs::bounds_take_sphere(),
+                                    gvs::bounds_take_splat(),  gvs::bounds_take_gauss()};
+    for (unsigned long long v : r)
+        if (v) return v;
+    return 0;
 }
 
 }  // extern "C"

@@ -278,4 +278,6 @@ cudaError_t launch_fuse(const FuseArgs &a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+GVS_BOUNDS_TAKE_FN(bounds_take_fuse)
+
 }  // namespace gvs

@@ -56,4 +56,6 @@ cudaError_t launch_fuse_batch(const BatchItem *items, int n_items, int total, un
     by_kmax<BatchLaunch>(K, map_dtype, variant, items, n_items, total, counter, st);
     return cudaGetLastError();
 }
+GVS_BOUNDS_TAKE_FN(bounds_take_fuse_batch)
+
 }  // namespace gvs

@@ -256,4 +256,6 @@ cudaError_t launch_fuse_backward(const FuseArgs &a, const void *depth, int depth
                : launch_bwd_gather<float>(depth, wmap, acc, grad_depths, a.K, a.W, a.H, mu, wconst, window, st);
 }
 
+GVS_BOUNDS_TAKE_FN(bounds_take_fuse_bwd)
+
 }  // namespace gvs

@@ -6,6 +6,7 @@
 #include <cuda_fp16.h>
 #include <math.h>
 
+#include "bounds_check.cuh"
 #include "gvs_internal.cuh"
 
 namespace gvs {
@@ -143,6 +144,7 @@ __device__ __forceinline__ bool slab_view_free(const FuseArgs &a, int k, const R
         p = a.ob[2] + ((size_t)k * a.th[2] + (by0 >> 7)) * a.tw[2] + (bx0 >> 7);
     else
         p = a.tg + k;
+    if (!GVS_IN_BOUNDS(p - a.ob[0], (const float2 *)(a.tg + a.K) - a.ob[0], GVS_SITE_FUSE_BOUNDS)) return false;
     const float2 b = __ldg(p);
     return zhi < b.x || zlo > b.y + a.behind;
 }
@@ -165,7 +167,8 @@ __device__ __forceinline__ void evaluate_sample(const FuseArgs &a, const Ray (&r
                 const float hy = __fmaf_rn(zs, ray[k].ay, a.xf[k].b[1]);
                 int u, v;
                 nearest_pixel(hx, hy, hz, u, v);
-                if ((unsigned)u < (unsigned)a.W && (unsigned)v < (unsigned)a.H) {
+                if ((unsigned)u < (unsigned)a.W && (unsigned)v < (unsigned)a.H &&
+                    GVS_IN_BOUNDS((size_t)k * plane + (size_t)v * a.W + u, (size_t)a.K * plane, GVS_SITE_FUSE_MAP)) {
                     const float2 p = load_map(&map[(size_t)k * plane + (size_t)v * a.W + u]);
                     const float sdf = (p.x - hz) * a.inv_mu;
                     if (sdf >= -1.0f) {

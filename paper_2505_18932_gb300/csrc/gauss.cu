@@ -22,6 +22,7 @@
 #include <cuda_fp16.h>
 #include <math.h>
 
+#include "bounds_check.cuh"
 #include "gauss_internal.cuh"
 
 namespace gvs {
@@ -198,7 +199,8 @@ __global__ void __launch_bounds__(256) gauss_fill(const GaussArgs g) {
     for (int ty = j0 / GS_TILE; ty <= j1 / GS_TILE; ++ty)
         for (int tx = i0 / GS_TILE; tx <= i1 / GS_TILE; ++tx) {
             const int t = ty * g.L.tiles_x + tx;
-            keys[off[t] + agg_increment(cursor, t)] = key;
+            const unsigned long long pos = off[t] + agg_increment(cursor, t);
+            if (GVS_IN_BOUNDS(pos, g.L.n_keys, GVS_SITE_GAUSS_KEY)) keys[pos] = key;
         }
 }
 
@@ -267,7 +269,8 @@ __global__ void __launch_bounds__(GS_THREADS) gauss_render(const GaussArgs g, in
         if (__syncthreads_count(!done) == 0) break;  // also orders the reuse of sa / sb
         const int e = b0 + threadIdx.x;
         if (e < n) {
-            const unsigned src = (unsigned)(keys[e] & 0xffffffffull);
+            unsigned src = (unsigned)(keys[e] & 0xffffffffull);
+            if (!GVS_IN_BOUNDS(src, (size_t)g.W * g.H, GVS_SITE_GAUSS_REC)) src = 0;
             const GaussRec r = rec[src];
             sa[threadIdx.x] = r.a;
             sb[threadIdx.x] = r.b;
@@ -349,5 +352,7 @@ cudaError_t launch_gauss_splat(const GaussArgs &a, int K, cudaStream_t st) {
     }
     return cudaGetLastError();
 }
+
+GVS_BOUNDS_TAKE_FN(bounds_take_gauss)
 
 }  // namespace gvs

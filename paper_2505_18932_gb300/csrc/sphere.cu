@@ -81,4 +81,6 @@ cudaError_t launch_sphere(const SphereArgs &s, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+GVS_BOUNDS_TAKE_FN(bounds_take_sphere)
+
 }  // namespace gvs

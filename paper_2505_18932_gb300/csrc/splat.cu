@@ -16,6 +16,7 @@
 #include <cuda_fp16.h>
 #include <math.h>
 
+#include "bounds_check.cuh"
 #include "gvs_internal.cuh"
 
 namespace gvs {
@@ -184,6 +185,7 @@ __global__ void __launch_bounds__(SC_BX * SC_BY) splat_scatter(const SplatArgs a
     for (int jj = b.j0; jj <= b.j1; ++jj)
         for (int ii = b.i0; ii <= b.i1; ++ii) {
             const size_t t = (size_t)jj * a.Wt + ii;
+            if (!GVS_IN_BOUNDS(t, (size_t)a.Wt * a.Ht, GVS_SITE_SPLAT_KEY)) continue;
             if (REJECT && b.z < __fsub_rn(__ldg(&a.fused[t]), a.mu_guide)) continue;
             atomicMin(&slot[t], key);
         }
@@ -257,7 +259,8 @@ __global__ void __launch_bounds__(256) splat_resolveP(const SplatArgs a, int k0)
     if (a.warped_rgba) {
         const uint32_t *src = a.rgba + (size_t)k * a.W * a.H;
 #pragma unroll
-        for (int q = 0; q < P; ++q) c[q] = h[q] ? __ldg(&src[w[q]]) : 0u;
+        for (int q = 0; q < P; ++q)
+            c[q] = (h[q] && GVS_IN_BOUNDS(w[q], (size_t)a.W * a.H, GVS_SITE_SPLAT_SRC)) ? __ldg(&src[w[q]]) : 0u;
     }
     const size_t o4 = ((size_t)k * HWt) / 4 + (size_t)t * (P / 4);
 #pragma unroll
@@ -581,5 +584,7 @@ cudaError_t launch_guided_mask(const float *warped_depth, const uint8_t *alpha, 
                                                                     guided);
     return cudaGetLastError();
 }
+
+GVS_BOUNDS_TAKE_FN(bounds_take_splat)
 
 }  // namespace gvs

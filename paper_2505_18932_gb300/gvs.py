@@ -146,6 +146,7 @@ API = {
     "gvs_fuse_depth_sphere": (ctypes.c_int, [ctypes.POINTER(GvsCamera), ctypes.c_void_p, ctypes.c_int32,
                                              ctypes.POINTER(GvsCamera), ctypes.POINTER(GvsSphereParams)] +
                               [ctypes.c_void_p] * 3 + [ctypes.c_size_t, ctypes.c_void_p]),
+    "gvs_debug_bounds_error": (ctypes.c_uint64, []),
     "gvs_forward_splat_noalloc": (ctypes.c_int, [ctypes.POINTER(GvsCamera), ctypes.c_void_p, ctypes.c_void_p,
                                                  ctypes.c_int32, ctypes.POINTER(GvsCamera),
                                                  ctypes.POINTER(GvsSplatParams), ctypes.c_void_p, ctypes.c_void_p,
@@ -699,3 +700,16 @@ class TemporalFusion:
         sp["guided"] = guided_mask(sp["warped_depth"], sp["alpha"], fused, c["mu"])
         self.prev, self.w_tmp_prev, self.w_view_prev = fused, w_tmp, wview
         return fused, crossing, sp, w_tmp
+
+    _STATE = ("prev", "w_tmp_prev", "w_view_prev")
+
+    def state_dict(self):
+        """Checkpoint of the online state (host copies).  With the caller's refined input
+        depths it is everything a later frame depends on: restoring both resumes the
+        stream bit for bit."""
+        return {k: getattr(self, k).cpu() for k in self._STATE}
+
+    def load_state_dict(self, sd):
+        dev = self.prev.device
+        for k in self._STATE:
+            setattr(self, k, sd[k].to(device=dev, dtype=torch.float32).clone())

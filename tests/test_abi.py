@@ -210,3 +210,8 @@ def test_select_views_host_only(lib):
     assert gvs.select_views(twins, camera_at(64, 48, (0, 0, 0)), 3) == [2, 0, 1]   # tie -> lower index
     with pytest.raises(gvs.GvsError):
         gvs.select_views(twins, camera_at(64, 48, (0, 0, 0)), 4)
+
+
+def test_normal_build_checks_no_bounds(lib):
+    """Without GVS_BOUNDS_CHECK the debug accessor is a constant 0 (no CUDA call)."""
+    assert lib.gvs_debug_bounds_error() == 0
