@@ -378,13 +378,15 @@ class FwdBwd:
         c = self.color[cur].detach().requires_grad_(True)
         fused, _ = gvs.FuseDepth.apply(d, w.inputs, self.tgt, self.cfg)
         color, wdepth, alpha = gvs.SoftSplat.apply(d, c, w.inputs, self.tgt, {"mu_band": w.mu})
-        a = alpha.to(torch.float32).unsqueeze(-1)
+        a = alpha.to(torch.float32)
         asum = a.sum(0)
         valid = asum > 0
-        blend = (color[..., :3] * a).sum(0) / asum.clamp_min(1.0)
-        l1 = ((blend - self.gt[cur]).abs() * valid).sum() / (3.0 * valid.sum().clamp_min(1))
-        dblend = (wdepth * alpha).sum(0) / asum[..., 0].clamp_min(1.0)
-        dvalid = valid[..., 0] & (fused > 0)
+        inv = 1.0 / asum.clamp_min(1.0)
+        # RGBA planes with A = 0 blend to A = 0: blend all four, drop A after the sum
+        blend = (color * a.unsqueeze(-1)).sum(0)[..., :3] * inv.unsqueeze(-1)
+        l1 = ((blend - self.gt[cur]).abs().sum(-1) * valid).sum() / (3.0 * valid.sum().clamp_min(1))
+        dblend = (wdepth * a).sum(0) * inv
+        dvalid = valid & (fused > 0)
         ldepth = ((fused - dblend).abs() * dvalid).sum() / (len(w.inputs) * dvalid.numel())
         loss = 0.8 * l1 + 0.1 * ldepth
         loss.backward()
