@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gvs", choices=["gvs", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=60)
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-form", default=None, choices=sorted(FORM_CLASSES),
@@ -309,6 +309,7 @@ def run_gvs(args, rank, local_rank, world):
     step_bytes = sum(ab.values())
     fuse_bytes = ab["fuse"]
     st_ms = {k: statistics.median(v) for k, v in stage.items()}
+    counters = recorded_counters()
     stage_time = {"refine": st_ms["refine"], "weight_map": st_ms["fuse"] - fuse_kernel_ms, "fuse": fuse_kernel_ms,
                   "splat": st_ms["splat"]}
     by_stage = {k: {"alg_bytes": ab[k], "ms": round(t, 4), "gbs": round(ab[k] / (t * 1e-3) / 1e9, 1),
@@ -330,7 +331,9 @@ def run_gvs(args, rank, local_rank, world):
                         "move memory"},
         "roofline": {"kernel": "fuse_kernel", "bound": "alu", "achieved": round(achieved, 3),
                      "peak": round(alu_peak, 2), "unit": "T FP32 lane-ops/s",
-                     "frac": round(achieved / alu_peak, 4), "traffic": recorded_traffic(),
+                     "frac": round(achieved / alu_peak, 4),
+                     "traffic": counters["dram_bytes_per_launch"] if counters else None,
+                     "ncu_issue_active": counters.get("issue_active_frac") if counters else None,
                      "units_per_launch": units, "ops_per_unit": OPS_PER_SAMPLE_VIEW,
                      "kernel_ms": round(fuse_kernel_ms, 4), "hole_fraction": round(holes, 4),
                      "peak_source": f"{device_sms()} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (measured max SM clock)",
@@ -338,7 +341,8 @@ def run_gvs(args, rank, local_rank, world):
                      "hbm_frac": round(fuse_bytes / (fuse_kernel_ms * 1e-3) / 1e9 / hbm_peak, 4),
                      "note": ("units: sample-views of the uniform D-sample march up to each ray's crossing "
                               "(all D where none), 20 FP32 instructions each; the kernel proves most of them "
-                              "crossing-free without evaluating them, so frac can exceed 1")},
+                              "crossing-free without evaluating them, so frac can exceed 1; the binding resource "
+                              "is instruction issue: ncu_issue_active is the fraction of issue slots used")},
         "e2e": e2e,
         "forms": forms,
         "gpu_launches": pipe.launches_per_step() * K,
@@ -614,9 +618,9 @@ def form_line(name, w, f, note):
             "workload": w.name, "note": note}
 
 
-def recorded_traffic(kernel_file="fuse_kernel_traffic.txt"):
-    """DRAM bytes per launch of the roofline kernel from the committed ncu record,
-    or None when the kernel's sources changed since the counters were taken."""
+def recorded_counters(kernel_file="fuse_kernel_traffic.txt"):
+    """The committed ncu record of the roofline kernel (DRAM bytes per launch, issue-active
+    fraction, warp instructions), or None when the kernel's sources changed since."""
     import hashlib
     path = os.path.join(ROOT, "profiles", kernel_file)
     if not os.path.exists(path):
@@ -627,7 +631,7 @@ def recorded_traffic(kernel_file="fuse_kernel_traffic.txt"):
     for src in rec["source_files"]:
         with open(os.path.join(ROOT, src), "rb") as f:
             h.update(f.read())
-    return rec["dram_bytes_per_launch"] if h.hexdigest() == rec["source_sha256"] else None
+    return rec if h.hexdigest() == rec["source_sha256"] else None
 
 
 def device_sms():
