@@ -2,11 +2,11 @@
 weights: the paper's trained weights are not available, so this exists to time
 the whole per-frame path end to end, not to produce images worth looking at.
 
-Its convolutions are PyTorch / cuDNN library calls in bfloat16 (channels-last
-layout is supported: convert the module and the input with
-memory_format=torch.channels_last; the outputs are contiguous planes either way).  The input
-assembly before it (`gvs.blend_features`) and the blend after it (`gvs.blend`,
-Eqs. 4-5) are this library's kernels.
+Its convolutions are PyTorch / cuDNN library calls in bfloat16; the
+channels-last layout works too (convert the module and the input with
+memory_format=torch.channels_last; the outputs are contiguous planes either
+way).  The input assembly before it (`gvs.blend_features`) and the blend
+after it (`gvs.blend`, Eqs. 4-5) are this library's kernels.
 
 Output heads (readings; the paper gives no activations): w_k = sigmoid (Eq. 4
 normalises by the sum over views anyway), w_BG = sigmoid, I_BG = sigmoid.
