@@ -52,3 +52,4 @@ unsigned long long bounds_take_gauss();
 #define GVS_SITE_SPLAT_SRC 4ull     // winner's colour gather of the resolve
 #define GVS_SITE_GAUSS_REC 5ull     // Gaussian record gather of the render
 #define GVS_SITE_GAUSS_KEY 6ull     // tile-list write of the fill
+#define GVS_SITE_SOFT_ACC 7ull      // key / accumulator of the differentiable splat

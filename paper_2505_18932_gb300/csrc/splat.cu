@@ -322,6 +322,7 @@ __global__ void __launch_bounds__(SC_BX * SC_BY) soft_accum(const SplatArgs a, i
     for (int jj = g.j0; jj <= g.j1; ++jj)
         for (int ii = g.i0; ii <= g.i1; ++ii) {
             const size_t t = (size_t)jj * a.Wt + ii;
+            if (!GVS_IN_BOUNDS(t, (size_t)a.Wt * a.Ht, GVS_SITE_SOFT_ACC)) continue;
             const float zw = __uint_as_float((uint32_t)(keys[t] >> 32));
             if (!(g.z <= __fadd_rn(zw, a.mu_band))) continue;
             const float ex = g.x - (float)ii, ey = g.y - (float)jj;

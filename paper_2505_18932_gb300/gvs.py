@@ -228,6 +228,40 @@ def _want(t, dtype, shape, name):
         raise ValueError(f"gvs: {name} must be {dtype} of shape {tuple(shape)}, got {t.dtype} {tuple(t.shape)}")
 
 
+def _check_views(in_cams, in_depths, per_pixel=()):
+    """The C ABI takes every image size from the cameras, so the tensors must match them:
+    in_depths [N, H, W], and each (tensor, bytes per pixel, name) of `per_pixel` N H W times
+    that many bytes (a packed int32 or a uint8 [..., 4] RGBA image both hold 4)."""
+    N = len(in_cams)
+    if N == 0:
+        return
+    H, W = int(in_cams[0].height), int(in_cams[0].width)
+    if tuple(in_depths.shape) != (N, H, W):
+        raise ValueError(f"gvs: in_depths must have shape {(N, H, W)} (from the cameras), got {tuple(in_depths.shape)}")
+    for t, nb, name in per_pixel:
+        if t is not None and t.numel() * t.element_size() != N * H * W * nb:
+            raise ValueError(f"gvs: {name} must hold {nb} bytes per input pixel ({N * H * W * nb} bytes), "
+                             f"got {t.dtype} {tuple(t.shape)}")
+
+
+def _check_outputs(out, spec):
+    """Caller-supplied output tensors must have the dtype and shape the kernels write."""
+    for n, (sh, dt) in spec.items():
+        if out.get(n) is not None:
+            _want(out[n], dt, sh, n)
+
+
+def _check_refine(rgba_t, rgba_prev, depth_t, depth_state, mask, mask_dtype):
+    N, H, W = depth_t.shape
+    if tuple(depth_state.shape) != (N, H, W):
+        raise ValueError(f"gvs: depth_state must have shape {(N, H, W)}, got {tuple(depth_state.shape)}")
+    for t, name in ((rgba_t, "rgba_t"), (rgba_prev, "rgba_prev")):
+        if t.numel() * t.element_size() != N * H * W * 4:
+            raise ValueError(f"gvs: {name} must hold 4 bytes per pixel of {(N, H, W)}, got {t.dtype} {tuple(t.shape)}")
+    if mask is not None:
+        _want(mask, mask_dtype, (N, H, W), "mask")
+
+
 def refine_depth(rgba_t, rgba_prev, depth_t, depth_state, mask=None, tau: float = 0.03, stream=None):
     """Sec. 3.2 Eq. 1-2 (binary mask).  rgba_* int32/uint32 [N, H, W] packed RGBA8 (or uint8 [N, H, W, 4]);
     depth_t, depth_state float32 [N, H, W] (depth_state updated in place); mask uint8 [N, H, W] or None."""
@@ -235,6 +269,7 @@ def refine_depth(rgba_t, rgba_prev, depth_t, depth_state, mask=None, tau: float 
     N, H, W = depth_t.shape
     if depth_state.dtype != depth_t.dtype:
         raise ValueError("gvs: depth_t and depth_state must share a dtype")
+    _check_refine(rgba_t, rgba_prev, depth_t, depth_state, mask, torch.uint8)
     p = GvsRefineParams(float(tau), depth_dtype_of(depth_t))
     st = lib.gvs_refine_depth(_ptr(rgba_t), _ptr(rgba_prev), _ptr(depth_t), _ptr(depth_state), _ptr(mask),
                               N, W, H, ctypes.byref(p), _stream(stream))
@@ -248,6 +283,7 @@ def refine_depth_soft(rgba_t, rgba_prev, depth_t, depth_state, mask=None, beta=0
     depth_state (float32/float16 [N, H, W]) is updated in place; mask: float32 [N, H, W] or None."""
     lib = load()
     N, H, W = depth_t.shape
+    _check_refine(rgba_t, rgba_prev, depth_t, depth_state, mask, torch.float32)
     if ws is None:
         ws = workspace(int(lib.gvs_refine_soft_workspace_bytes(N, W, H)), depth_t.device)
     p = GvsRefineSoftParams(float(beta), float(lambda_t), depth_dtype_of(depth_t))
@@ -268,6 +304,10 @@ def select_views(in_cams, target, k):
 
 def fuse_workspace_bytes(n_views, width, height) -> int:
     return int(load().gvs_fuse_workspace_bytes(n_views, width, height))
+
+
+def soft_splat_workspace_bytes(n_views, target_width, target_height) -> int:
+    return int(load().gvs_soft_splat_workspace_bytes(n_views, target_width, target_height))
 
 
 def splat_workspace_bytes(n_views, target_width, target_height) -> int:
@@ -291,6 +331,10 @@ def fuse_depth(in_cams, in_depths, target, num_samples, z_near, z_far, mu, weigh
         fused = torch.empty((target.height, target.width), dtype=torch.float32, device=dev)
     if crossing is None and want_crossing:
         crossing = torch.empty((target.height, target.width), dtype=torch.int16, device=dev)
+    _check_views(in_cams, in_depths)
+    _want(fused, torch.float32, (target.height, target.width), "fused")
+    if crossing is not None:
+        _want(crossing, torch.int16, (target.height, target.width), "crossing")
     H, W = (in_depths.shape[1], in_depths.shape[2]) if N else (0, 0)
     need = fuse_workspace_bytes(N, W, H)
     if ws is None:
@@ -309,12 +353,16 @@ def fuse_depth_backward(in_cams, in_depths, target, num_samples, z_near, z_far, 
     """Adjoint of fuse_depth: gradient w.r.t. in_depths (float32 [N, H, W]).  `ws` is the forward's map."""
     lib = load()
     N = len(in_cams)
+    _check_views(in_cams, in_depths)
+    _want(crossing, torch.int16, (target.height, target.width), "crossing")
     H, W = (in_depths.shape[1], in_depths.shape[2]) if N else (0, 0)
     if grad_depths is None:
         grad_depths = torch.empty(in_depths.shape, dtype=torch.float32, device=in_depths.device)
     if bwd_ws is None:
         bwd_ws = workspace(int(lib.gvs_fuse_backward_workspace_bytes(N, W, H)), in_depths.device)
     grad_fused = grad_fused.contiguous().to(torch.float32)
+    _want(grad_fused, torch.float32, (target.height, target.width), "grad_fused")
+    _want(grad_depths, torch.float32, tuple(in_depths.shape), "grad_depths")
     p = GvsFuseParams(int(num_samples), float(z_near), float(z_far), float(mu), float(weight_const), int(window), 0,
                       depth_dtype_of(in_depths) if N else GVS_F32, GVS_F16 if map_half else GVS_F32)
     st = lib.gvs_fuse_depth_backward(camera_array(in_cams), _ptr(in_depths), N, ctypes.byref(camera_struct(target)),
@@ -380,6 +428,9 @@ def fuse_depth_sphere(in_cams, in_depths, target, z_near, z_far, mu, weight_cons
         fused = torch.empty(shape, dtype=torch.float32, device=dev)
     if evals is None:
         evals = torch.empty(shape, dtype=torch.int32, device=dev)
+    _check_views(in_cams, in_depths)
+    _want(fused, torch.float32, shape, "fused")
+    _want(evals, torch.int32, shape, "evals")
     H, W = (in_depths.shape[1], in_depths.shape[2]) if N else (0, 0)
     if ws is None:
         ws = workspace(fuse_workspace_bytes(N, W, H), dev)
@@ -401,6 +452,11 @@ def fuse_depth_from_map(in_cams, dw_map, shape, target, num_samples, z_near, z_f
         fused = torch.empty((target.height, target.width), dtype=torch.float32, device=dev)
     if crossing is None and want_crossing:
         crossing = torch.empty((target.height, target.width), dtype=torch.int16, device=dev)
+    _want(fused, torch.float32, (target.height, target.width), "fused")
+    if crossing is not None:
+        _want(crossing, torch.int16, (target.height, target.width), "crossing")
+    if N and tuple(shape) != (N, int(in_cams[0].height), int(in_cams[0].width)):
+        raise ValueError(f"gvs: shape {tuple(shape)} does not match the {N} cameras")
     p = GvsFuseParams(int(num_samples), float(z_near), float(z_far), float(mu), 0.001, 7, int(bool(normalize)),
                       GVS_F32, GVS_F16 if map_half else GVS_F32, int(variant))
     st = lib.gvs_fuse_depth_from_map(camera_array(in_cams), _ptr(dw_map), dw_map.numel() * dw_map.element_size(), N,
@@ -425,6 +481,10 @@ def forward_splat(in_cams, in_depths, in_rgba, target, fused=None, footprint=Tru
     dtypes = {"winner": torch.int32, "warped_rgba": torch.int32, "warped_depth": torch.float32,
               "alpha": torch.uint8, "guided": torch.uint8}
     names = ["winner"] + [n for n in want if n != "guided" or fused is not None]
+    _check_views(in_cams, in_depths, [(in_rgba, 4, "in_rgba")])
+    _check_outputs(out, {n: (shape, dt) for n, dt in dtypes.items()})
+    if fused is not None:
+        _want(fused, torch.float32, shape[1:], "fused")
     for n in names:
         if n not in out:
             out[n] = torch.empty(shape, dtype=dtypes[n], device=dev)
@@ -466,8 +526,11 @@ def gauss_splat(in_cams, in_depths, in_rgba, target, scale_px=0.5, max_radius=8,
         color = torch.empty(shape + (4,), dtype=torch.float32, device=dev)
     if depth is None:
         depth = torch.empty(shape, dtype=torch.float32, device=dev)
+    _want(color, torch.float32, shape + (4,), "color")
+    _want(depth, torch.float32, shape, "depth")
     if N == 0:
         return color, depth
+    _check_views(in_cams, in_depths, [(in_rgba, 4, "in_rgba")])
     H, W = in_depths.shape[1], in_depths.shape[2]
     if ws is None:
         ws = workspace(gauss_splat_workspace_bytes(W, H, target.width, target.height, max_radius), dev)
@@ -491,6 +554,14 @@ def blend_features(in_cams, target, warped_rgba, warped_depth, alpha, fused, dty
     K = len(in_cams)
     if out is None:
         out = torch.empty((9 * K + 1, target.height, target.width), dtype=dtype, device=fused.device)
+    sh = (K, target.height, target.width)
+    _want(warped_rgba, warped_rgba.dtype, sh, "warped_rgba")
+    if warped_rgba.element_size() != 4:
+        raise ValueError("gvs: warped_rgba must be packed 32-bit RGBA")
+    _want(warped_depth, torch.float32, sh, "warped_depth")
+    _want(alpha, torch.uint8, sh, "alpha")
+    _want(fused, torch.float32, sh[1:], "fused")
+    _want(out, out.dtype, (9 * K + 1,) + sh[1:], "out")
     st = lib.gvs_blend_features(camera_array(in_cams), K, ctypes.byref(camera_struct(target)), _ptr(warped_rgba),
                                 _ptr(warped_depth), _ptr(alpha), _ptr(fused), _FEATURE_DTYPES[out.dtype], _ptr(out),
                                 _stream(stream))
@@ -512,8 +583,15 @@ def blend(warped_rgba, alpha, warped_depth, fused, w, w_bg, i_bg, image=None, l_
     if ws is None:
         ws = workspace(int(lib.gvs_blend_workspace_bytes(Wt, Ht)), dev)
     wdt = {torch.float32: GVS_F32, torch.bfloat16: GVS_BF16}[w.dtype]
-    for t in (w, w_bg, i_bg):
-        assert t.dtype == w.dtype and t.is_contiguous()
+    if warped_rgba.element_size() != 4:
+        raise ValueError("gvs: warped_rgba must be packed 32-bit RGBA")
+    _want(alpha, torch.uint8, (K, Ht, Wt), "alpha")
+    _want(warped_depth, torch.float32, (K, Ht, Wt), "warped_depth")
+    _want(fused, torch.float32, (Ht, Wt), "fused")
+    _want(w, w.dtype, (K, Ht, Wt), "w")
+    _want(w_bg, w.dtype, (Ht, Wt), "w_bg")
+    _want(i_bg, w.dtype, (3, Ht, Wt), "i_bg")
+    _want(image, torch.float32, (3, Ht, Wt), "image")
     st = lib.gvs_blend(K, Wt, Ht, _ptr(warped_rgba), _ptr(alpha), _ptr(warped_depth), _ptr(fused), wdt, _ptr(w),
                        _ptr(w_bg), _ptr(i_bg), _ptr(image), _ptr(l_depth), _ptr(ws), ws.numel(), _stream(stream))
     _check("gvs_blend", st)
@@ -531,6 +609,10 @@ def soft_splat(in_cams, in_depths, in_color, target, max_half_width=2.0, mu_band
     out = dict(outputs or {})
     spec = {"winner": (shape, torch.int32), "color": (shape + (4,), torch.float32), "depth": (shape, torch.float32),
             "wsum": (shape, torch.float32), "alpha": (shape, torch.uint8)}
+    _check_views(in_cams, in_depths)
+    if N and tuple(in_color.shape) != tuple(in_depths.shape) + (4,):
+        raise ValueError(f"gvs: in_color must have shape {tuple(in_depths.shape) + (4,)}, got {tuple(in_color.shape)}")
+    _check_outputs(out, spec)
     for n, (sh, dt) in spec.items():
         if n not in out:
             out[n] = torch.empty(sh, dtype=dt, device=dev)
@@ -551,11 +633,19 @@ def soft_splat_backward(in_cams, in_depths, in_color, target, fwd, grad_color, g
     """Adjoint of soft_splat: (grad w.r.t. in_depths float32 [N, H, W], w.r.t. in_color float32 [N, H, W, 4])."""
     lib = load()
     N = len(in_cams)
+    _check_views(in_cams, in_depths)
+    shape = (N, target.height, target.width)
+    if N and tuple(in_color.shape) != tuple(in_depths.shape) + (4,):
+        raise ValueError(f"gvs: in_color must have shape {tuple(in_depths.shape) + (4,)}, got {tuple(in_color.shape)}")
+    _check_outputs(fwd, {"winner": (shape, torch.int32), "color": (shape + (4,), torch.float32),
+                         "depth": (shape, torch.float32), "wsum": (shape, torch.float32)})
     gd = torch.empty(in_depths.shape, dtype=torch.float32, device=in_depths.device)
     gc = torch.empty(tuple(in_color.shape[:3]) + (4,), dtype=torch.float32, device=in_depths.device)
     grad_color = grad_color.contiguous().to(torch.float32)
+    _want(grad_color, torch.float32, shape + (4,), "grad_color")
     if grad_depth is not None:
         grad_depth = grad_depth.contiguous().to(torch.float32)
+        _want(grad_depth, torch.float32, shape, "grad_depth")
     p = GvsSoftSplatParams(float(max_half_width), float(mu_band), depth_dtype_of(in_depths) if N else GVS_F32,
                            _color_dtype_of(in_color) if N else GVS_F32)
     st = lib.gvs_soft_splat_backward(camera_array(in_cams), _ptr(in_depths), _ptr(in_color), N,
@@ -601,6 +691,9 @@ class FuseBatch:
         self._targets = [camera_struct(t) for _, t, _, _ in items]
         arr = (GvsFuseItem * len(items))()
         for n, (m, t, f, c) in enumerate(items):
+            _want(f, torch.float32, (t.height, t.width), f"items[{n}] fused")
+            if c is not None:
+                _want(c, torch.int16, (t.height, t.width), f"items[{n}] crossing")
             arr[n] = GvsFuseItem(_ptr(m), m.numel() * m.element_size(), ctypes.pointer(self._targets[n]), _ptr(f),
                                  _ptr(c))
         p = GvsFuseParams(int(num_samples), float(z_near), float(z_far), float(mu), 0.001, 7, int(bool(normalize)),
@@ -636,6 +729,11 @@ def temporal_weight(masks, winner, w_tmp_prev, w_view_prev, beta_t=1.0, eta=15.0
     Ht, Wt = winner.shape[1:]
     if w_tmp is None:
         w_tmp = torch.empty((Ht, Wt), dtype=torch.float32, device=masks.device)
+    _want(winner, torch.int32, (N, Ht, Wt), "winner")
+    for t, name in ((w_tmp_prev, "w_tmp_prev"), (w_view_prev, "w_view_prev"), (w_tmp, "w_tmp")):
+        _want(t, torch.float32, (Ht, Wt), name)
+    if target_mask is not None:
+        _want(target_mask, torch.float32, (Ht, Wt), "target_mask")
     md = GVS_U8 if masks.dtype == torch.uint8 else GVS_F32
     st = lib.gvs_temporal_weight(_ptr(masks), md, _ptr(winner), N, W, H, Wt, Ht, _ptr(w_tmp_prev), _ptr(w_view_prev),
                                  float(beta_t), float(eta), _ptr(w_tmp), _ptr(target_mask), _stream(stream))
@@ -656,6 +754,10 @@ def fuse_depth_temporal(in_cams, dw_map, target, num_samples, z_near, z_far, mu,
         crossing = torch.empty(shape, dtype=torch.int16, device=dev)
     if view_weight is None:
         view_weight = torch.empty(shape, dtype=torch.float32, device=dev)
+    for t, dt, name in ((prev_depth, torch.float32, "prev_depth"), (w_tmp, torch.float32, "w_tmp"),
+                        (fused, torch.float32, "fused"), (crossing, torch.int16, "crossing"),
+                        (view_weight, torch.float32, "view_weight")):
+        _want(t, dt, shape, name)
     p = GvsFuseParams(int(num_samples), float(z_near), float(z_far), float(mu), 0.001, 7, 0, GVS_F32, GVS_F32, 0)
     st = lib.gvs_fuse_depth_temporal(camera_array(in_cams), _ptr(dw_map), dw_map.numel(), N,
                                      ctypes.byref(camera_struct(target)), ctypes.byref(p), _ptr(prev_depth),
@@ -669,6 +771,9 @@ def guided_mask(warped_depth, alpha, fused, mu_guide, guided=None, stream=None):
     N, Ht, Wt = warped_depth.shape
     if guided is None:
         guided = torch.empty((N, Ht, Wt), dtype=torch.uint8, device=warped_depth.device)
+    _want(alpha, torch.uint8, (N, Ht, Wt), "alpha")
+    _want(fused, torch.float32, (Ht, Wt), "fused")
+    _want(guided, torch.uint8, (N, Ht, Wt), "guided")
     st = lib.gvs_guided_mask(_ptr(warped_depth), _ptr(alpha), _ptr(fused), N, Wt, Ht, float(mu_guide), _ptr(guided),
                              _stream(stream))
     _check("gvs_guided_mask", st)
