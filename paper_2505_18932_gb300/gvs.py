@@ -256,7 +256,7 @@ def _check_refine(rgba_t, rgba_prev, depth_t, depth_state, mask, mask_dtype):
     if tuple(depth_state.shape) != (N, H, W):
         raise ValueError(f"gvs: depth_state must have shape {(N, H, W)}, got {tuple(depth_state.shape)}")
     for t, name in ((rgba_t, "rgba_t"), (rgba_prev, "rgba_prev")):
-        if t.numel() * t.element_size() != N * H * W * 4:
+        if t is not None and t.numel() * t.element_size() != N * H * W * 4:
             raise ValueError(f"gvs: {name} must hold 4 bytes per pixel of {(N, H, W)}, got {t.dtype} {tuple(t.shape)}")
     if mask is not None:
         _want(mask, mask_dtype, (N, H, W), "mask")

@@ -97,3 +97,27 @@ def test_blend_planes_checked(gvs):
         gvs.blend(rgba, a, wd, _z(Ht, Wt + 1), _z(K, Ht, Wt), _z(Ht, Wt), _z(3, Ht, Wt))
     with pytest.raises(ValueError, match="alpha"):
         gvs.guided_mask(wd, _z(K, Ht, Wt + 1, dtype=torch.uint8), _z(Ht, Wt), 0.05)
+
+
+def test_valid_shapes_pass_the_checks(gvs, scene):
+    """Correctly shaped CPU tensors get past every shape check and stop only at the
+    device check (optional arguments left out, as the header allows)."""
+    cams, tgt = scene
+    d = _z(3, 24, 40)
+    rgba = _z(3, 24, 40, dtype=torch.int32)
+    rgba8 = _z(3, 24, 40, 4, dtype=torch.uint8)
+    calls = [
+        lambda: gvs.refine_depth(rgba, None, d, d.clone()),
+        lambda: gvs.refine_depth(rgba8, rgba, d, d.clone(), mask=_z(3, 24, 40, dtype=torch.uint8)),
+        lambda: gvs.forward_splat(cams, d, rgba8, tgt, fused=_z(20, 32)),
+        lambda: gvs.soft_splat(cams, d, _z(3, 24, 40, 4, dtype=torch.bfloat16), tgt),
+        lambda: gvs.fuse_depth(cams, d.half(), tgt, 64, 0.5, 5.0, 0.05),
+        lambda: gvs.fuse_depth_sphere(cams, d, tgt, 0.5, 5.0, 0.05),
+        lambda: gvs.gauss_splat(cams, d, rgba, tgt),
+        lambda: gvs.blend(_z(3, 20, 32, dtype=torch.int32), _z(3, 20, 32, dtype=torch.uint8), _z(3, 20, 32),
+                          _z(20, 32), _z(3, 20, 32), _z(20, 32), _z(3, 20, 32)),
+        lambda: gvs.guided_mask(_z(3, 20, 32), _z(3, 20, 32, dtype=torch.uint8), _z(20, 32), 0.05),
+    ]
+    for c in calls:
+        with pytest.raises(ValueError, match="CUDA device"):
+            c()
