@@ -290,6 +290,7 @@ def run_gvs(args, rank, local_rank, world):
                                           "K = 4 closest views: refine, fusion, splat, network input (bf16), "
                                           "4-level U-Net with random weights (cuDNN, bf16), Eq. 4-5 blend")
     forms["sphere_trace_fusion"] = sphere_form(w, frames_np, device, steps=min(K, 20))
+    forms["mixed_precision_16x1080p_stereo"] = mixed_form(device, steps=min(K, 10))
     forms.update(time_batched(device, steps=min(K, 20)))
     wd = configs.diff_640x360()
     forms["fwd_bwd_640x360"] = form_line("fwd_bwd_640x360", wd,
@@ -561,6 +562,88 @@ class FineUniform:
         self.gvs.refine_depth(p.rgba[cur], p.rgba[prev], p.depth[cur], p.state, p.mask, tau=w.tau)
         self.gvs.fuse_depth(w.inputs, p.state, p.tgt, self.D, w.z_near, w.z_far, w.mu, fused=p.fused,
                             crossing=p.cross, ws=p.ws_fuse)
+
+
+class MixedScale:
+    """Mixed precision at scale: 16 inputs at 1920x1080 (4x4 rig), depth stored as FP16 and
+    the (d, w) map as half2, colour for the differentiable splat as bfloat16, D = 192,
+    a stereo pair of targets.  Per step: refine, one weight map, fusion into both targets,
+    the hard splat and the differentiable colour splat of all 16 views into both."""
+
+    def __init__(self, w, frames_np, device, half=True):
+        import torch
+        from paper_2505_18932_gb300 import gvs
+        self.torch, self.gvs, self.w, self.half = torch, gvs, w, half
+        ddt = torch.float16 if half else torch.float32
+        cdt = torch.bfloat16 if half else torch.float32
+        self.rgba = [torch.from_numpy(c.view(np.int32)).to(device) for c, _ in frames_np]
+        self.depth = [torch.from_numpy(d).to(device).to(ddt) for _, d in frames_np]
+        # packed RGBA8 -> [N, H, W, 4] in [0, 1]
+        self.color = [torch.from_numpy(np.ascontiguousarray(c).view(np.uint8).reshape(c.shape + (4,))).to(device)
+                      .to(torch.float32).div_(255.0).to(cdt) for c, _ in frames_np]
+        self.state = self.depth[0].clone()
+        N, H, W = self.depth[0].shape
+        self.N, self.H, self.W = N, H, W
+        self.mask = torch.empty((N, H, W), dtype=torch.uint8, device=device)
+        self.ws = gvs.workspace(gvs.fuse_workspace_bytes(N, W, H), device)
+        self.tg = w.targets
+        Ht, Wt = self.tg[0].height, self.tg[0].width
+        self.fused = [torch.empty((Ht, Wt), dtype=torch.float32, device=device) for _ in self.tg]
+        self.cross = [torch.empty((Ht, Wt), dtype=torch.int16, device=device) for _ in self.tg]
+        self.ws_splat = gvs.workspace(2 * gvs.splat_workspace_bytes(N, Wt, Ht), device)
+        self.ws_soft = gvs.workspace(gvs.soft_splat_workspace_bytes(N, Wt, Ht), device)
+        self.outs = [None] * len(self.tg)
+        self.soft = [None] * len(self.tg)
+
+    def step(self, i, events=None):
+        w, gvs = self.w, self.gvs
+        cur, prev = i % len(self.rgba), (i - 1) % len(self.rgba)
+        gvs.refine_depth(self.rgba[cur], self.rgba[prev], self.depth[cur], self.state, self.mask, tau=w.tau)
+        gvs.weight_map(self.state, w.mu, ws=self.ws, map_half=self.half)
+        for t, tgt in enumerate(self.tg):
+            gvs.fuse_depth_from_map(w.inputs, self.ws, (self.N, self.H, self.W), tgt, w.num_samples, w.z_near,
+                                    w.z_far, w.mu, fused=self.fused[t], crossing=self.cross[t], map_half=self.half)
+            self.outs[t] = gvs.forward_splat(w.inputs, self.state, self.rgba[cur], tgt, fused=self.fused[t],
+                                             mu_guide=w.mu, outputs=self.outs[t], ws=self.ws_splat)
+            self.soft[t] = gvs.soft_splat(w.inputs, self.state, self.color[cur], tgt, mu_band=w.mu,
+                                          outputs=self.soft[t], ws=self.ws_soft)
+
+
+def mixed_form(device, steps):
+    """Time the mixed-precision form and compare its outputs with the same frame in FP32."""
+    import torch
+    from synth import configs
+    w = configs.mixed_16x1080p()
+    fr = render_frames(w, [0, 1])
+    lo, hi = MixedScale(w, fr, device, half=True), MixedScale(w, fr, device, half=False)
+    f = time_form(lo, steps)
+    for m in (lo, hi):
+        m.state.copy_(m.depth[0])
+        m.step(1)
+    torch.cuda.synchronize()
+    acc = {}
+    for t in range(len(w.targets)):
+        a, b = lo.fused[t], hi.fused[t]
+        both = (a > 0) & (b > 0)
+        rel = ((a - b).abs() / b.clamp(min=1e-6))[both]
+        hit = (lo.soft[t]["alpha"] > 0) & (hi.soft[t]["alpha"] > 0)
+        cd = (lo.soft[t]["color"] - hi.soft[t]["color"])[..., :3].abs().amax(dim=-1)[hit].float()
+        cd = cd[torch.randperm(cd.numel(), device=cd.device, generator=torch.Generator(device=cd.device)
+                               .manual_seed(0))[:1 << 24]]  # quantile() takes at most 2^24 elements
+        acc[f"target{t}"] = {
+            "fused_rel_diff_median": float(rel.median()), "fused_rel_diff_p99": float(rel.quantile(0.99)),
+            "crossing_index_agree": round(float((lo.cross[t] == hi.cross[t]).float().mean()), 6),
+            "splat_winner_agree": round(float((lo.outs[t]["winner"] == hi.outs[t]["winner"]).float().mean()), 6),
+            # the FP16 depth moves ~1 % of the winners, and a moved winner moves the front band
+            "soft_colour_abs_diff_median": float(cd.median()), "soft_colour_abs_diff_p99": float(cd.quantile(0.99)),
+            "soft_colour_within_1_255": round(float((cd <= 1.0 / 255).float().mean()), 6)}
+    tpx = sum(t.width * t.height for t in w.targets)
+    return {**f, "value": round(tpx / (f["ms_per_step"] * 1e-3) / 1e6, 3), "unit": "target Mpix/s",
+            "workload": w.name, "storage": "depth f16, map half2, colour bf16; FP32 arithmetic",
+            "vs_fp32_same_frame": acc,
+            "note": "16 x 1920x1080 inputs, stereo pair of targets, D = 192: refine, map, fusion, hard splat and "
+                    "differentiable colour splat of all views into both targets; the errors against the FP64 "
+                    "oracle are asserted in the precision tests"}
 
 
 def time_batched(device, steps):
