@@ -64,7 +64,10 @@ __device__ __forceinline__ void nearest_pixel(float hx, float hy, float hz, int 
     v = __float2int_rz(ny);
 }
 
-constexpr int FZ_WARPS = 4;
+#ifndef GVS_FUSE_WARPS
+#define GVS_FUSE_WARPS 4        // warps (bundles) per fusion block
+#endif
+constexpr int FZ_WARPS = GVS_FUSE_WARPS;
 #ifndef GVS_FUSE_MIN_BLOCKS
 #define GVS_FUSE_MIN_BLOCKS 8   // resident blocks per SM requested from the register allocator (64 registers)
 #endif
@@ -151,6 +154,9 @@ __device__ __forceinline__ bool slab_view_free(const FuseArgs &a, int k, const R
 
 // S and W of one sample over the input views (Supplement A.1), before the
 // temporal term and the optional normalisation, exactly as the march computes them.
+// A view whose sample lies behind its camera or off its image, or in front of
+// the surface by more than mu, enters with weight 0 (a predicated gather, no
+// branch): adding 0 * x leaves S and W as they were.
 template <int KMAX, typename MT>
 __device__ __forceinline__ void evaluate_sample(const FuseArgs &a, const Ray (&ray)[KMAX], float zs, float &S,
                                                 float &Wsum) {
@@ -162,21 +168,19 @@ __device__ __forceinline__ void evaluate_sample(const FuseArgs &a, const Ray (&r
     for (int k = 0; k < KMAX; ++k) {
         if (k < a.K) {
             const float hz = __fmaf_rn(zs, ray[k].az, a.xf[k].b[2]);
-            if (hz > 1e-6f) {
-                const float hx = __fmaf_rn(zs, ray[k].ax, a.xf[k].b[0]);
-                const float hy = __fmaf_rn(zs, ray[k].ay, a.xf[k].b[1]);
-                int u, v;
-                nearest_pixel(hx, hy, hz, u, v);
-                if ((unsigned)u < (unsigned)a.W && (unsigned)v < (unsigned)a.H &&
-                    GVS_IN_BOUNDS((size_t)k * plane + (size_t)v * a.W + u, (size_t)a.K * plane, GVS_SITE_FUSE_MAP)) {
-                    const float2 p = load_map(&map[(size_t)k * plane + (size_t)v * a.W + u]);
-                    const float sdf = (p.x - hz) * a.inv_mu;
-                    if (sdf >= -1.0f) {
-                        S = fmaf(p.y, fminf(sdf, 1.0f), S);
-                        Wsum += p.y;
-                    }
-                }
-            }
+            const float hx = __fmaf_rn(zs, ray[k].ax, a.xf[k].b[0]);
+            const float hy = __fmaf_rn(zs, ray[k].ay, a.xf[k].b[1]);
+            int u, v;
+            nearest_pixel(hx, hy, hz, u, v);
+            const bool in = hz > 1e-6f && (unsigned)u < (unsigned)a.W && (unsigned)v < (unsigned)a.H &&
+                            GVS_IN_BOUNDS((size_t)k * plane + (size_t)v * a.W + u, (size_t)a.K * plane,
+                                          GVS_SITE_FUSE_MAP);
+            float2 p = make_float2(0.0f, 0.0f);
+            if (in) p = load_map(&map[(size_t)k * plane + (size_t)v * a.W + u]);
+            const float sdf = (p.x - hz) * a.inv_mu;
+            const float w = (in && sdf >= -1.0f) ? p.y : 0.0f;
+            S = fmaf(w, fminf(sdf, 1.0f), S);
+            Wsum += w;
         }
     }
 }
@@ -289,9 +293,10 @@ __device__ __forceinline__ void march_bundle(const FuseArgs &a, int bundle, int 
             cool = SKIP_COOL;
         }
         const float zs = __fmaf_rn((float)s, a.dz, a.zn);
+        // every lane evaluates (the warp issues the sample anyway); lanes still marching record it
+        float S, Wsum;
+        evaluate_sample<KMAX, MT>(a, ray, zs, S, Wsum);
         if (!done) {
-            float S, Wsum;
-            evaluate_sample<KMAX, MT>(a, ray, zs, S, Wsum);
             const float Wv = Wsum;
             if (TMP && tw > 0.0f) {
                 const float sdf = (td - zs) * a.inv_mu;
