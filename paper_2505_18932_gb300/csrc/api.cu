@@ -296,6 +296,8 @@ gvs::FuseArgs fuse_args(const gvs_camera *in_cams, const void *map, int32_t n_vi
     a.fused = fused;
     a.crossing = crossing;
     for (int k = 0; k < n_views; ++k) a.xf[k] = compose(in_cams[k], *target);
+    const size_t elem = p.map_dtype == GVS_F16 ? 4 : 8;  // half2 or float2 (d, omega)
+    for (int k = 0; k < n_views; ++k) a.vb[k] = reinterpret_cast<const char *>(a.dw) + (size_t)k * W * H * elem;
     return a;
 }
 

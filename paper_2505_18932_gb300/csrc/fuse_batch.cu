@@ -22,7 +22,7 @@ __global__ void __launch_bounds__(32 * FZ_WARPS, GVS_FUSE_MIN_BLOCKS)
             const int mid = (lo + hi + 1) >> 1;
             if (items[mid].bundle_begin <= b) lo = mid; else hi = mid - 1;
         }
-        march_bundle<KMAX, MT, T>(items[lo].args, b - items[lo].bundle_begin, lane);
+        march_bundle<KMAX, MT, T, false, false>(items[lo].args, b - items[lo].bundle_begin, lane);
     }
 }
 

@@ -50,18 +50,33 @@ __device__ __forceinline__ float exact_nearest_fixup(float num, float den, float
     return n;
 }
 
+// Nearest integer by the 1.5 * 2^23 shift: for |q| < 2^22 the sum q + 1.5 * 2^23
+// lies in [2^23, 2^24), where the FP32 values are the integers, so the rounded
+// sum is the shift plus rint(q) (ties to even: the shift is even) and its low
+// bits hold rint(q) + 2^22.  Full-rate additions in place of a round and a
+// conversion.
+__device__ __forceinline__ float shift_round(float q, int &n) {
+    const float t = __fadd_rn(q, 12582912.0f);
+    n = __float_as_int(t) - 0x4B400000;
+    return __fsub_rn(t, 12582912.0f);
+}
+
+// Every |q| >= 2^22 has a margin above 0.5 and takes the exact path; an
+// infinite q (NaN margin) leaves a shifted index far outside any image, as the
+// conversion would.
 __device__ __forceinline__ void nearest_pixel(float hx, float hy, float hz, int &u, int &v) {
     const float r = __fdividef(1.0f, hz);
     const float qx = hx * r, qy = hy * r;
-    float nx = rintf(qx), ny = rintf(qy);
+    int iu, iv;
+    const float nx = shift_round(qx, iu), ny = shift_round(qy, iv);
     const float mx = fmaf(fabsf(qx), 4e-7f, fabsf(qx - nx));
     const float my = fmaf(fabsf(qy), 4e-7f, fabsf(qy - ny));
     if (fmaxf(mx, my) > 0.5f) {
-        nx = exact_nearest_fixup(hx, hz, nx);
-        ny = exact_nearest_fixup(hy, hz, ny);
+        iu = __float2int_rz(exact_nearest_fixup(hx, hz, rintf(qx)));
+        iv = __float2int_rz(exact_nearest_fixup(hy, hz, rintf(qy)));
     }
-    u = __float2int_rz(nx);
-    v = __float2int_rz(ny);
+    u = iu;
+    v = iv;
 }
 
 #ifndef GVS_FUSE_WARPS
@@ -79,11 +94,20 @@ constexpr int SKIP_COOL = 4;    // samples evaluated after both slab tests fail,
 //   bx x by : target pixels one warp marches together (bx * by = 32)
 //   llong   : samples per segment in the first slab test
 //   lshort  : samples per segment in the second test when the first fails
-template <int BX_, int BY_, int LLONG_, int LSHORT_>
+//   full    : the call has exactly KMAX views, so the per-view guard k < K
+//             compiles away and the unrolled views form one block of code
+template <int BX_, int BY_, int LLONG_, int LSHORT_, bool FULL_ = false>
 struct Tile {
     static constexpr int bx = BX_, by = BY_, llong = LLONG_, lshort = LSHORT_;
+    static constexpr bool full = FULL_;
     static_assert(bx * by == 32, "a bundle is one warp");
     static_assert(llong >= 1 && lshort >= 1, "skip lengths must advance the march");
+};
+template <typename T>
+struct FullTile;
+template <int BX_, int BY_, int LLONG_, int LSHORT_, bool FULL_>
+struct FullTile<Tile<BX_, BY_, LLONG_, LSHORT_, FULL_>> {
+    using type = Tile<BX_, BY_, LLONG_, LSHORT_, true>;
 };
 using Tile0 = Tile<8, 4, 8, 2>;
 using Tile1 = Tile<8, 4, 16, 4>;
@@ -157,16 +181,18 @@ __device__ __forceinline__ bool slab_view_free(const FuseArgs &a, int k, const R
 // A view whose sample lies behind its camera or off its image, or in front of
 // the surface by more than mu, enters with weight 0 (a predicated gather, no
 // branch): adding 0 * x leaves S and W as they were.
-template <int KMAX, typename MT>
+// FULL: the call has exactly KMAX views (no per-view guard).  PLANES: address
+// view k's map through a.vb[k] (a constant-bank read for a __grid_constant__
+// FuseArgs); otherwise from a.dw (where the arguments sit in global memory).
+template <int KMAX, typename MT, bool FULL = false, bool PLANES = true>
 __device__ __forceinline__ void evaluate_sample(const FuseArgs &a, const Ray (&ray)[KMAX], float zs, float &S,
                                                 float &Wsum) {
-    const MT *map = reinterpret_cast<const MT *>(a.dw);
     const size_t plane = (size_t)a.W * a.H;
     S = 0.0f;
     Wsum = 0.0f;
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) {
-        if (k < a.K) {
+        if (FULL || k < a.K) {
             const float hz = __fmaf_rn(zs, ray[k].az, a.xf[k].b[2]);
             const float hx = __fmaf_rn(zs, ray[k].ax, a.xf[k].b[0]);
             const float hy = __fmaf_rn(zs, ray[k].ay, a.xf[k].b[1]);
@@ -176,7 +202,11 @@ __device__ __forceinline__ void evaluate_sample(const FuseArgs &a, const Ray (&r
                             GVS_IN_BOUNDS((size_t)k * plane + (size_t)v * a.W + u, (size_t)a.K * plane,
                                           GVS_SITE_FUSE_MAP);
             float2 p = make_float2(0.0f, 0.0f);
-            if (in) p = load_map(&map[(size_t)k * plane + (size_t)v * a.W + u]);
+            if (in) {
+                const MT *plane_k = PLANES ? reinterpret_cast<const MT *>(a.vb[k])
+                                           : reinterpret_cast<const MT *>(a.dw) + (size_t)k * plane;
+                p = load_map(plane_k + (v * a.W + u));  // v W + u < 2^28
+            }
             const float sdf = (p.x - hz) * a.inv_mu;
             const float w = (in && sdf >= -1.0f) ? p.y : 0.0f;
             S = fmaf(w, fminf(sdf, 1.0f), S);
@@ -192,8 +222,9 @@ __device__ __forceinline__ void evaluate_sample(const FuseArgs &a, const Ray (&r
 // evaluates sample s (all KMAX views unrolled, one 8-byte gather each) and
 // checks its own crossing.  The result equals the full uniform march.
 // TMP: the temporal input (previous output depth and weight) and the views'
-// weight at the crossing are compiled in only where they are used.
-template <int KMAX, typename MT, typename T, bool TMP = false>
+// weight at the crossing are compiled in only where they are used.  PLANES as
+// in evaluate_sample.
+template <int KMAX, typename MT, typename T, bool TMP = false, bool PLANES = true>
 __device__ __forceinline__ void march_bundle(const FuseArgs &a, int bundle, int lane) {
     constexpr int BX = T::bx, BY = T::by, SKIP_LONG = T::llong, SKIP_SHORT = T::lshort;
     constexpr int NSEG = 32 / KMAX;
@@ -207,7 +238,7 @@ __device__ __forceinline__ void march_bundle(const FuseArgs &a, int bundle, int 
     Ray ray[KMAX];
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) {
-        if (k < a.K) {
+        if (T::full || k < a.K) {
             const float *M = a.xf[k].M;
             ray[k].ax = __fmaf_rn(M[0], fi, __fmaf_rn(M[1], fj, M[2]));
             ray[k].ay = __fmaf_rn(M[3], fi, __fmaf_rn(M[4], fj, M[5]));
@@ -295,7 +326,7 @@ __device__ __forceinline__ void march_bundle(const FuseArgs &a, int bundle, int 
         const float zs = __fmaf_rn((float)s, a.dz, a.zn);
         // every lane evaluates (the warp issues the sample anyway); lanes still marching record it
         float S, Wsum;
-        evaluate_sample<KMAX, MT>(a, ray, zs, S, Wsum);
+        evaluate_sample<KMAX, MT, T::full, PLANES>(a, ray, zs, S, Wsum);
         if (!done) {
             const float Wv = Wsum;
             if (TMP && tw > 0.0f) {
@@ -330,33 +361,40 @@ __device__ __forceinline__ void march_bundle(const FuseArgs &a, int bundle, int 
     }
 }
 
-// Calls F<Tile_i>::run(...) for the variant; views counts other than 8 and 16
-// use the default tile only (fewer instantiations to build).
+// Calls F<Tile_i>::run(...) for the variant, with the full form of the tile
+// when the call has exactly KMAX views; views counts other than 8 and 16 use
+// the default tile only (fewer instantiations to build).
+template <int KMAX, typename MT, template <int, typename, typename> class F, typename T, typename... Args>
+void full_or_not(int K, Args... args) {
+    if (K == KMAX) F<KMAX, MT, typename FullTile<T>::type>::run(args...);
+    else F<KMAX, MT, T>::run(args...);
+}
+
 template <int KMAX, typename MT, template <int, typename, typename> class F, typename... Args>
-void by_variant(int variant, Args... args) {
+void by_variant(int K, int variant, Args... args) {
     if (KMAX == 8 || KMAX == 16) {
         switch (variant) {
-            case 1: F<KMAX, MT, Tile1>::run(args...); return;
-            case 2: F<KMAX, MT, Tile2>::run(args...); return;
-            case 3: F<KMAX, MT, Tile3>::run(args...); return;
+            case 1: full_or_not<KMAX, MT, F, Tile1>(K, args...); return;
+            case 2: full_or_not<KMAX, MT, F, Tile2>(K, args...); return;
+            case 3: full_or_not<KMAX, MT, F, Tile3>(K, args...); return;
             default: break;
         }
     }
-    F<KMAX, MT, Tile0>::run(args...);
+    full_or_not<KMAX, MT, F, Tile0>(K, args...);
 }
 
 template <template <int, typename, typename> class F, typename... Args>
 void by_kmax(int K, int map_dtype, int variant, Args... args) {
     if (map_dtype == GVS_F16) {
-        if (K <= 4) by_variant<4, __half2, F>(variant, args...);
-        else if (K <= 8) by_variant<8, __half2, F>(variant, args...);
-        else if (K <= 16) by_variant<16, __half2, F>(variant, args...);
-        else by_variant<32, __half2, F>(variant, args...);
+        if (K <= 4) by_variant<4, __half2, F>(K, variant, args...);
+        else if (K <= 8) by_variant<8, __half2, F>(K, variant, args...);
+        else if (K <= 16) by_variant<16, __half2, F>(K, variant, args...);
+        else by_variant<32, __half2, F>(K, variant, args...);
     } else {
-        if (K <= 4) by_variant<4, float2, F>(variant, args...);
-        else if (K <= 8) by_variant<8, float2, F>(variant, args...);
-        else if (K <= 16) by_variant<16, float2, F>(variant, args...);
-        else by_variant<32, float2, F>(variant, args...);
+        if (K <= 4) by_variant<4, float2, F>(K, variant, args...);
+        else if (K <= 8) by_variant<8, float2, F>(K, variant, args...);
+        else if (K <= 16) by_variant<16, float2, F>(K, variant, args...);
+        else by_variant<32, float2, F>(K, variant, args...);
     }
 }
 
@@ -364,15 +402,15 @@ void by_kmax(int K, int map_dtype, int variant, Args... args) {
 template <template <int, typename, typename> class F, typename... Args>
 void by_kmax_tile0(int K, int map_dtype, Args... args) {
     if (map_dtype == GVS_F16) {
-        if (K <= 4) F<4, __half2, Tile0>::run(args...);
-        else if (K <= 8) F<8, __half2, Tile0>::run(args...);
-        else if (K <= 16) F<16, __half2, Tile0>::run(args...);
-        else F<32, __half2, Tile0>::run(args...);
+        if (K <= 4) full_or_not<4, __half2, F, Tile0>(K, args...);
+        else if (K <= 8) full_or_not<8, __half2, F, Tile0>(K, args...);
+        else if (K <= 16) full_or_not<16, __half2, F, Tile0>(K, args...);
+        else full_or_not<32, __half2, F, Tile0>(K, args...);
     } else {
-        if (K <= 4) F<4, float2, Tile0>::run(args...);
-        else if (K <= 8) F<8, float2, Tile0>::run(args...);
-        else if (K <= 16) F<16, float2, Tile0>::run(args...);
-        else F<32, float2, Tile0>::run(args...);
+        if (K <= 4) full_or_not<4, float2, F, Tile0>(K, args...);
+        else if (K <= 8) full_or_not<8, float2, F, Tile0>(K, args...);
+        else if (K <= 16) full_or_not<16, float2, F, Tile0>(K, args...);
+        else full_or_not<32, float2, F, Tile0>(K, args...);
     }
 }
 

@@ -81,6 +81,7 @@ struct FuseArgs {
     float *fused;
     int16_t *crossing;
     ViewXform xf[GVS_MAX_VIEWS];
+    const char *vb[GVS_MAX_VIEWS];  // view k's map plane: dw + k W H map elements
 };
 
 // exact: correctly rounded weight (float2 maps only; see weight_map_kernel)
