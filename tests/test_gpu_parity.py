@@ -95,6 +95,26 @@ def test_fuse_view_counts(gvs, oracle_mod, K):
     _fuse_case(gvs, oracle_mod, configs.tiny(24, 18, K, 96))
 
 
+def test_blind_view_changes_nothing(gvs):
+    """A ninth view facing away from every sample of the target (h_z < 0 throughout) adds no
+    term, so the fused depth and crossing index equal the 8-view result bit for bit: the
+    9-view call runs the per-view-guarded code compiled for 16 views with two slab-test
+    segments, the 8-view call the unguarded code compiled for exactly 8 with four."""
+    from synth import camera_at, configs
+    w = configs.tiny(70, 45, 8, 96)
+    _, d = w.render_inputs(0)
+    tgt = w.targets[0]
+    centre = -tgt.R.T @ tgt.t
+    c0 = w.inputs[0]
+    blind = camera_at(c0.width, c0.height, centre, R=np.diag([1.0, -1.0, -1.0]) @ tgt.R)
+    d9 = np.concatenate([d, d[:1]], axis=0)
+    f8, c8 = gvs.fuse_depth(w.inputs, to_dev(d), tgt, w.num_samples, w.z_near, w.z_far, w.mu)
+    f9, c9 = gvs.fuse_depth(list(w.inputs) + [blind], to_dev(d9), tgt, w.num_samples, w.z_near, w.z_far, w.mu)
+    torch.cuda.synchronize()
+    assert (c8 >= 0).float().mean() > 0.5
+    assert torch.equal(f8.view(torch.int32), f9.view(torch.int32)) and torch.equal(c8, c9)
+
+
 def test_fuse_full_size_sampled(gvs, oracle_mod):
     """8 x 1920x1080 inputs, D=128, in the launch configuration the benchmark times;
     2048 seeded target pixels checked against the oracle one by one."""
