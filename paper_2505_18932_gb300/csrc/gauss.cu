@@ -298,33 +298,31 @@ __global__ void __launch_bounds__(GS_THREADS) gauss_render(const GaussArgs g, in
             cnt += __popc(bal);
         }
         __syncwarp();
-        for (int e = 0; e < cnt && !done; ++e) {
+        for (int e = 0; e < cnt; ++e) {
+            if (__all_sync(0xffffffffu, done)) break;
             const int q = wlist[warp][e];
             const float4 a = sa[q];
             const float2 h = half_widths(a.w);
-            if (fi < __fsub_rn(a.x, h.x) || fi > __fadd_rn(a.x, h.x) || fj < __fsub_rn(a.y, h.y) ||
-                fj > __fadd_rn(a.y, h.y))
-                continue;
+            const bool inbox = !(fi < __fsub_rn(a.x, h.x) || fi > __fadd_rn(a.x, h.x) || fj < __fsub_rn(a.y, h.y) ||
+                                 fj > __fadd_rn(a.y, h.y));
             const float4 c = sb[q];
             const float dx = a.x - fi, dy = a.y - fj;
             const float power = fmaf(dx, fmaf(c.x, dx, c.y * dy), c.z * dy * dy);
             // exp(-5.6) < 1/255 whatever the rounding of the exponential: skip without it
-            if (power > 0.0f || power < -5.6f) continue;
             const float al = fminf(0.99f, __expf(power));
-            if (al < 1.0f / 255.0f) continue;
+            const bool use = !done && inbox && !(power > 0.0f || power < -5.6f) && !(al < 1.0f / 255.0f);
             const float Tn = T * (1.0f - al);
-            if (Tn < 1e-4f) {
-                done = true;
-                break;
-            }
-            const float wgt = al * T;
+            const bool stop = use && Tn < 1e-4f;
+            done = done || stop;
+            const bool acc = use && !stop;
+            const float wgt = acc ? al * T : 0.0f;  // adding 0 leaves every sum as it was
             const float4 cc = sc[q];
             cr = fmaf(cc.x, wgt, cr);
             cg = fmaf(cc.y, wgt, cg);
             cb = fmaf(cc.z, wgt, cb);
             zs = fmaf(a.z, wgt, zs);
             ws += wgt;
-            T = Tn;
+            T = acc ? Tn : T;
         }
     }
     if (inside) {
