@@ -383,14 +383,16 @@ class FwdBwd:
         c = self.color[cur].detach().requires_grad_(True)
         fused, _ = gvs.FuseDepth.apply(d, w.inputs, self.tgt, self.cfg)
         color, wdepth, alpha = gvs.SoftSplat.apply(d, c, w.inputs, self.tgt, {"mu_band": w.mu})
-        a = alpha.to(torch.float32)
-        asum = a.sum(0)
+        asum = alpha.sum(0, dtype=torch.float32)
         valid = asum > 0
         inv = 1.0 / asum.clamp_min(1.0)
-        # RGBA planes with A = 0 blend to A = 0: blend all four, drop A after the sum
-        blend = (color * a.unsqueeze(-1)).sum(0)[..., :3] * inv.unsqueeze(-1)
+        # alpha is 0 or 1 and the splat's colour and depth are 0 wherever it is 0, so the
+        # alpha-weighted sums over the views are plain sums (the same values, and the
+        # gradient reaching an uncovered pixel is ignored by the splat's adjoint).
+        # RGBA planes with A = 0 blend to A = 0: blend all four, drop A after the sum.
+        blend = color.sum(0)[..., :3] * inv.unsqueeze(-1)
         l1 = ((blend - self.gt[cur]).abs().sum(-1) * valid).sum() / (3.0 * valid.sum().clamp_min(1))
-        dblend = (wdepth * a).sum(0) * inv
+        dblend = wdepth.sum(0) * inv
         dvalid = valid & (fused > 0)
         ldepth = ((fused - dblend).abs() * dvalid).sum() / (len(w.inputs) * dvalid.numel())
         loss = 0.8 * l1 + 0.1 * ldepth

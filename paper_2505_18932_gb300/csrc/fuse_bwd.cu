@@ -29,7 +29,8 @@ namespace {
 // so they are bit-identical to it.
 // ---------------------------------------------------------------------------
 
-template <int KMAX, typename MT>
+// FULL: the call has exactly KMAX views (no per-view guard).
+template <int KMAX, typename MT, bool FULL>
 __global__ void __launch_bounds__(128) fuse_bwd_scatter(const FuseArgs a, const int16_t *__restrict__ crossing,
                                                         const float *__restrict__ grad_fused, float2 *__restrict__ acc) {
     const int i = blockIdx.x * 16 + threadIdx.x;
@@ -43,7 +44,7 @@ __global__ void __launch_bounds__(128) fuse_bwd_scatter(const FuseArgs a, const 
     Ray ray[KMAX];
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) {
-        if (k < a.K) {
+        if (FULL || k < a.K) {
             const float *M = a.xf[k].M;
             ray[k].ax = __fmaf_rn(M[0], fi, __fmaf_rn(M[1], fj, M[2]));
             ray[k].ay = __fmaf_rn(M[3], fi, __fmaf_rn(M[4], fj, M[5]));
@@ -52,8 +53,8 @@ __global__ void __launch_bounds__(128) fuse_bwd_scatter(const FuseArgs a, const 
     }
     const float z0 = __fmaf_rn((float)s, a.dz, a.zn), z1 = __fmaf_rn((float)(s + 1), a.dz, a.zn);
     float S0, S1, W0, W1;
-    evaluate_sample<KMAX, MT>(a, ray, z0, S0, W0);
-    evaluate_sample<KMAX, MT>(a, ray, z1, S1, W1);
+    evaluate_sample<KMAX, MT, FULL>(a, ray, z0, S0, W0);
+    evaluate_sample<KMAX, MT, FULL>(a, ray, z1, S1, W1);
     const float den = (S0 - S1) * (S0 - S1);
     const float gS[2] = {G * (z1 - z0) * (-S1) / den, G * (z1 - z0) * S0 / den};
     const MT *map = reinterpret_cast<const MT *>(a.dw);
@@ -63,7 +64,7 @@ __global__ void __launch_bounds__(128) fuse_bwd_scatter(const FuseArgs a, const 
         const float zs = t ? z1 : z0;
 #pragma unroll
         for (int k = 0; k < KMAX; ++k) {
-            if (k < a.K) {
+            if (FULL || k < a.K) {
                 const float hz = __fmaf_rn(zs, ray[k].az, a.xf[k].b[2]);
                 if (hz > 1e-6f) {
                     const float hx = __fmaf_rn(zs, ray[k].ax, a.xf[k].b[0]);
@@ -84,6 +85,14 @@ __global__ void __launch_bounds__(128) fuse_bwd_scatter(const FuseArgs a, const 
             }
         }
     }
+}
+
+template <int KMAX, typename MT>
+void bwd_scatter_k(const FuseArgs &a, const int16_t *crossing, const float *grad_fused, float2 *acc,
+                   cudaStream_t st) {
+    const dim3 grid((a.Wt + 15) / 16, (a.Ht + 7) / 8), block(16, 8);
+    if (a.K == KMAX) fuse_bwd_scatter<KMAX, MT, true><<<grid, block, 0, st>>>(a, crossing, grad_fused, acc);
+    else fuse_bwd_scatter<KMAX, MT, false><<<grid, block, 0, st>>>(a, crossing, grad_fused, acc);
 }
 
 // Entries e in [-R, R] of a clamp-to-edge window centred at c that land on x
@@ -236,17 +245,16 @@ cudaError_t launch_fuse_backward(const FuseArgs &a, const void *depth, int depth
     if (a.K == 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(acc, 0, (size_t)a.K * a.W * a.H * sizeof(float2), st);
     if (e != cudaSuccess) return e;
-    const dim3 grid((a.Wt + 15) / 16, (a.Ht + 7) / 8), block(16, 8);
     if (a.map_dtype == GVS_F16) {
-        if (a.K <= 4) fuse_bwd_scatter<4, __half2><<<grid, block, 0, st>>>(a, crossing, grad_fused, acc);
-        else if (a.K <= 8) fuse_bwd_scatter<8, __half2><<<grid, block, 0, st>>>(a, crossing, grad_fused, acc);
-        else if (a.K <= 16) fuse_bwd_scatter<16, __half2><<<grid, block, 0, st>>>(a, crossing, grad_fused, acc);
-        else fuse_bwd_scatter<32, __half2><<<grid, block, 0, st>>>(a, crossing, grad_fused, acc);
+        if (a.K <= 4) bwd_scatter_k<4, __half2>(a, crossing, grad_fused, acc, st);
+        else if (a.K <= 8) bwd_scatter_k<8, __half2>(a, crossing, grad_fused, acc, st);
+        else if (a.K <= 16) bwd_scatter_k<16, __half2>(a, crossing, grad_fused, acc, st);
+        else bwd_scatter_k<32, __half2>(a, crossing, grad_fused, acc, st);
     } else {
-        if (a.K <= 4) fuse_bwd_scatter<4, float2><<<grid, block, 0, st>>>(a, crossing, grad_fused, acc);
-        else if (a.K <= 8) fuse_bwd_scatter<8, float2><<<grid, block, 0, st>>>(a, crossing, grad_fused, acc);
-        else if (a.K <= 16) fuse_bwd_scatter<16, float2><<<grid, block, 0, st>>>(a, crossing, grad_fused, acc);
-        else fuse_bwd_scatter<32, float2><<<grid, block, 0, st>>>(a, crossing, grad_fused, acc);
+        if (a.K <= 4) bwd_scatter_k<4, float2>(a, crossing, grad_fused, acc, st);
+        else if (a.K <= 8) bwd_scatter_k<8, float2>(a, crossing, grad_fused, acc, st);
+        else if (a.K <= 16) bwd_scatter_k<16, float2>(a, crossing, grad_fused, acc, st);
+        else bwd_scatter_k<32, float2>(a, crossing, grad_fused, acc, st);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
