@@ -111,3 +111,33 @@ def test_soft_autograd_blend_loss(gvs):
     loss.backward()
     assert torch.isfinite(dd.grad).all() and torch.isfinite(cc.grad).all()
     assert dd.grad.abs().sum() > 0 and cc.grad.abs().sum() > 0
+
+
+@pytest.mark.parametrize("slots", [2, 3])
+def test_soft_several_views_per_pass(gvs, oracle_mod, slots):
+    """A workspace with room for several views processes them per pass (5 views: passes of
+    2 + 2 + 1 or 3 + 2); every output still matches the oracle.  Where no source covers a
+    target pixel (alpha 0) the colour and depth are exactly 0."""
+    from synth import configs
+    w = configs.tiny(70, 45, 5, 16)
+    rgb, d = w.render_inputs(0)
+    tgt = w.targets[0]
+    HWt = tgt.width * tgt.height
+    nbytes = (slots * HWt * 8 + 255) // 256 * 256 + slots * HWt * 16
+    ws = gvs.workspace(nbytes, torch.device("cuda"))
+    col = np.ascontiguousarray(rgb, np.float32) / 255.0
+    out = gvs.soft_splat(w.inputs, torch.from_numpy(d).cuda(), torch.from_numpy(col).cuda(), tgt, mu_band=w.mu,
+                         ws=ws)
+    torch.cuda.synchronize()
+    ref = oracle_mod.soft_splat(w.inputs, d, col, tgt, mu_band=w.mu)
+    assert np.array_equal(out["winner"].cpu().numpy(), ref["winner"])
+    alpha = out["alpha"].cpu().numpy()
+    assert np.array_equal(alpha, ref["alpha"])
+    depth = out["depth"].cpu().numpy()
+    assert np.array_equal(depth.view(np.uint32), ref["depth"].view(np.uint32))
+    color = out["color"].cpu().numpy()
+    assert np.abs(color - ref["color"]).max() <= 1e-3
+    np.testing.assert_allclose(out["wsum"].cpu().numpy(), ref["wsum"], rtol=1e-5, atol=1e-7)
+    empty = alpha == 0
+    assert empty.any() and not empty.all()
+    assert np.all(color[empty].view(np.uint32) == 0) and np.all(depth[empty].view(np.uint32) == 0)
