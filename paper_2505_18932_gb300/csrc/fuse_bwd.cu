@@ -106,7 +106,7 @@ __device__ __forceinline__ int window_multiplicity(int c, int x, int n, int R) {
 }
 
 constexpr int GB_TX = 32;    // block of 32 x 32 input pixels: 32 x 8 threads,
-constexpr int GB_TY = 32;    // each thread GB_ROWS rows 8 apart
+constexpr int GB_TY = 32;    // each thread GB_ROWS consecutive rows
 constexpr int GB_ROWS = 4;
 
 // wmap: the forward's float2 (d, omega) planes, or null (re-sum nu).
@@ -163,47 +163,67 @@ __global__ void __launch_bounds__(GB_TX *(GB_TY / GB_ROWS)) fuse_bwd_gather(cons
     // a block whose windows of windows stay inside the image sees every window entry once
     const bool interior = bx >= 2 * R && by >= 2 * R && bx + GB_TX + 2 * R <= W && by + GB_TY + 2 * R <= H;
     const int x = bx + threadIdx.x;
+    const int ly0 = threadIdx.y * GB_ROWS;  // this thread's GB_ROWS consecutive rows
+    if (interior) {
+        // entry n of x's window and window centre c = n coincide: one pass,
+        // 2 (d_x - d_n) (P(x) + P(n)) where |d_x - d_n| < mu (false for an invalid n, and
+        // for an invalid x, whose NaN depth fails every test).  The thread's outputs share
+        // their window rows: each shared value is read once and serves every output whose
+        // window holds it, each output taking its entries in the same order as alone.
+        float dx0[GB_ROWS], Px[GB_ROWS], g[GB_ROWS];
+#pragma unroll
+        for (int p = 0; p < GB_ROWS; ++p) {
+            dx0[p] = dt[ly0 + p + 2 * R][threadIdx.x + 2 * R];
+            Px[p] = pt[ly0 + p + R][threadIdx.x + R];
+            g[p] = ak[(size_t)(by + ly0 + p) * W + x].y;  // B(x)
+        }
+#pragma unroll
+        for (int r = 0; r < GB_ROWS + 2 * R; ++r) {
+#pragma unroll
+            for (int ox = -R; ox <= R; ++ox) {
+                const float dn = dt[ly0 + R + r][threadIdx.x + 2 * R + ox];
+                const float pn = pt[ly0 + r][threadIdx.x + R + ox];
+#pragma unroll
+                for (int p = 0; p < GB_ROWS; ++p) {
+                    if (r - p < 0 || r - p > 2 * R) continue;  // row offset oy = r - p - R outside the window
+                    const float diff = dx0[p] - dn;
+                    if (fabsf(diff) < mu) g[p] = fmaf(2.0f * diff, Px[p] + pn, g[p]);
+                }
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < GB_ROWS; ++p) grad[(size_t)k * W * H + (size_t)(by + ly0 + p) * W + x] = g[p];
+        return;
+    }
 #pragma unroll 1
     for (int rr = 0; rr < GB_ROWS; ++rr) {
-        const int ly = threadIdx.y + rr * (GB_TY / GB_ROWS);  // row within the block
+        const int ly = ly0 + rr;  // row within the block
         const int y = by + ly;
         if (x >= W || y >= H) continue;
         const float dx0 = dt[ly + 2 * R][threadIdx.x + 2 * R];
         float g = ak[(size_t)y * W + x].y;  // B(x)
         if (dx0 == dx0) {
             const float Px = pt[ly + R][threadIdx.x + R];
-            if (interior) {
-                // entry n of x's window and window centre c = n coincide: one pass,
-                // 2 (d_x - d_n) (P(x) + P(n)) where |d_x - d_n| < mu (false for an invalid n)
-#pragma unroll
-                for (int oy = -R; oy <= R; ++oy)
-#pragma unroll
-                    for (int ox = -R; ox <= R; ++ox) {
-                        const float diff = dx0 - dt[ly + 2 * R + oy][threadIdx.x + 2 * R + ox];
-                        if (fabsf(diff) < mu) g = fmaf(2.0f * diff, Px + pt[ly + R + oy][threadIdx.x + R + ox], g);
+            if (Px != 0.0f) {
+                float sum = 0.0f;
+                for (int ey = -R; ey <= R; ++ey)
+                    for (int ex = -R; ex <= R; ++ex) {
+                        const float dn = dt[ly + 2 * R + ey][threadIdx.x + 2 * R + ex];
+                        const float diff = dx0 - dn;
+                        if (fabsf(diff) < mu) sum += 2.0f * diff;  // false for a NaN (invalid) neighbour
                     }
-            } else {
-                if (Px != 0.0f) {
-                    float sum = 0.0f;
-                    for (int ey = -R; ey <= R; ++ey)
-                        for (int ex = -R; ex <= R; ++ex) {
-                            const float dn = dt[ly + 2 * R + ey][threadIdx.x + 2 * R + ex];
-                            const float diff = dx0 - dn;
-                            if (fabsf(diff) < mu) sum += 2.0f * diff;  // false for a NaN (invalid) neighbour
-                        }
-                    g += Px * sum;
-                }
-                for (int cyo = -R; cyo <= R; ++cyo) {
-                    const int my = window_multiplicity(y + cyo, y, H, R);
-                    if (my == 0) continue;
-                    for (int cxo = -R; cxo <= R; ++cxo) {
-                        const int mx = window_multiplicity(x + cxo, x, W, R);
-                        if (mx == 0) continue;
-                        const float Pc = pt[ly + R + cyo][threadIdx.x + R + cxo];
-                        if (Pc == 0.0f) continue;
-                        const float diff = dt[ly + 2 * R + cyo][threadIdx.x + 2 * R + cxo] - dx0;
-                        if (fabsf(diff) < mu) g += (float)(mx * my) * Pc * (-2.0f) * diff;
-                    }
+                g += Px * sum;
+            }
+            for (int cyo = -R; cyo <= R; ++cyo) {
+                const int my = window_multiplicity(y + cyo, y, H, R);
+                if (my == 0) continue;
+                for (int cxo = -R; cxo <= R; ++cxo) {
+                    const int mx = window_multiplicity(x + cxo, x, W, R);
+                    if (mx == 0) continue;
+                    const float Pc = pt[ly + R + cyo][threadIdx.x + R + cxo];
+                    if (Pc == 0.0f) continue;
+                    const float diff = dt[ly + 2 * R + cyo][threadIdx.x + 2 * R + cxo] - dx0;
+                    if (fabsf(diff) < mu) g += (float)(mx * my) * Pc * (-2.0f) * diff;
                 }
             }
         }
