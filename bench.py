@@ -153,6 +153,25 @@ class Pipeline:
                      "warped_depth": torch.empty(shape, dtype=torch.float32, device=device),
                      "alpha": torch.empty(shape, dtype=torch.uint8, device=device),
                      "guided": torch.empty(shape, dtype=torch.uint8, device=device)}
+        self.variant, self.tune_ms = self.tune()
+
+    def tune(self):
+        """The fusion's bundle shape for this workload, picked by the library's autotuner
+        on the first frame (every variant gives the same bits; only the time differs)."""
+        from paper_2505_18932_gb300 import autotune
+        w, gvs = self.w, self.gvs
+        mapped = []
+
+        def runner(v):  # called only when the choice is not cached
+            if not mapped:
+                gvs.weight_map(self.depth[0], w.mu, ws=self.ws_fuse, map_half=self.half)
+                mapped.append(True)
+            return lambda: gvs.fuse_depth_from_map(w.inputs, self.ws_fuse, (self.N, self.H, self.W), self.tgt,
+                                                   w.num_samples, w.z_near, w.z_far, w.mu, fused=self.fused,
+                                                   crossing=self.cross, map_half=self.half, variant=v)
+        shape = {"views": (self.N, self.H, self.W), "target": (self.Wt, self.Ht), "D": w.num_samples,
+                 "z": (w.z_near, w.z_far), "mu": w.mu, "map_half": self.half}
+        return autotune.choose(shape, runner)
 
     def step(self, i, events=None):
         """Frame i of the ring: refine -> fuse -> splat.  `events`: 4 CUDA events bracketing the stages."""
@@ -164,7 +183,8 @@ class Pipeline:
         if events:
             events[1].record()
         gvs.fuse_depth(w.inputs, self.state, self.tgt, w.num_samples, w.z_near, w.z_far, w.mu,
-                       fused=self.fused, crossing=self.cross, ws=self.ws_fuse, map_half=self.half)
+                       fused=self.fused, crossing=self.cross, ws=self.ws_fuse, map_half=self.half,
+                       variant=self.variant)
         if events:
             events[2].record()
         gvs.forward_splat(w.inputs, self.state, self.rgba[cur], self.tgt, fused=self.fused, mu_guide=w.mu,
@@ -310,7 +330,7 @@ def run_gvs(args, rank, local_rank, world):
     step_bytes = sum(ab.values())
     fuse_bytes = ab["fuse"]
     st_ms = {k: statistics.median(v) for k, v in stage.items()}
-    counters = recorded_counters()
+    counters = recorded_counters(pipe.variant)
     stage_time = {"refine": st_ms["refine"], "weight_map": st_ms["fuse"] - fuse_kernel_ms, "fuse": fuse_kernel_ms,
                   "splat": st_ms["splat"]}
     by_stage = {k: {"alg_bytes": ab[k], "ms": round(t, 4), "gbs": round(ab[k] / (t * 1e-3) / 1e9, 1),
@@ -322,7 +342,8 @@ def run_gvs(args, rank, local_rank, world):
         "config": {"workload": w.name, "inputs": f"{pipe.N}x{pipe.W}x{pipe.H}", "target": f"{pipe.Wt}x{pipe.Ht}",
                    "num_samples": w.num_samples, "z_range": [w.z_near, w.z_far], "mu": w.mu, "tau": w.tau,
                    "l2": f"inputs > L2: {RING}-frame ring, {round((pipe.N * pipe.H * pipe.W * 16) / 1e6)} MB read per step",
-                   "parallelism": f"replicas{world}"},
+                   "parallelism": f"replicas{world}", "fuse_variant": pipe.variant,
+                   "fuse_autotune_ms": {str(v): round(t, 4) for v, t in pipe.tune_ms.items()}},
         "stage_ms": {k: round(statistics.median(v), 4) for k, v in stage.items()},
         "hbm": {"alg_bytes_per_step": step_bytes, "achieved_gbs": round(step_bytes / (ms_per_step * 1e-3) / 1e9, 1),
                 "peak_gbs": hbm_peak, "frac": round(step_bytes / (ms_per_step * 1e-3) / 1e9 / hbm_peak, 4),
@@ -704,9 +725,10 @@ def form_line(name, w, f, note):
             "workload": w.name, "note": note}
 
 
-def recorded_counters(kernel_file="fuse_kernel_traffic.txt"):
+def recorded_counters(variant, kernel_file="fuse_kernel_traffic.txt"):
     """The committed ncu record of the roofline kernel (DRAM bytes per launch, issue-active
-    fraction, warp instructions), or None when the kernel's sources changed since."""
+    fraction, warp instructions), or None when the kernel's sources changed since or the
+    record is of another bundle shape than the one timed."""
     import hashlib
     path = os.path.join(ROOT, "profiles", kernel_file)
     if not os.path.exists(path):
@@ -717,7 +739,7 @@ def recorded_counters(kernel_file="fuse_kernel_traffic.txt"):
     for src in rec["source_files"]:
         with open(os.path.join(ROOT, src), "rb") as f:
             h.update(f.read())
-    return rec if h.hexdigest() == rec["source_sha256"] else None
+    return rec if h.hexdigest() == rec["source_sha256"] and rec.get("variant", 0) == variant else None
 
 
 def device_sms():
@@ -738,7 +760,8 @@ def time_fuse_kernel(pipe, K):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         gvs.fuse_depth_from_map(w.inputs, pipe.ws_fuse, (pipe.N, pipe.H, pipe.W), pipe.tgt, w.num_samples,
-                                w.z_near, w.z_far, w.mu, fused=pipe.fused, crossing=pipe.cross)
+                                w.z_near, w.z_far, w.mu, fused=pipe.fused, crossing=pipe.cross,
+                                variant=pipe.variant)
         b.record()
         if i >= 3:
             durs.append((a, b))
