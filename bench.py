@@ -125,6 +125,25 @@ def render_frames(w, frames):
 
 # --------------------------------------------------------------- GPU path --
 
+def tune_fusion(w, depth0, ws, tgt, half, fused, cross):
+    """The fusion's bundle shape for a workload, picked by the library's autotuner on its
+    first frame (every variant gives the same bits; only the time differs).  Returns
+    (variant, {variant: ms}); the choice is cached per device and workload."""
+    from paper_2505_18932_gb300 import autotune, gvs
+    N, H, W = depth0.shape
+    mapped = []
+
+    def runner(v):  # called only when the choice is not cached
+        if not mapped:
+            gvs.weight_map(depth0, w.mu, ws=ws, map_half=half)
+            mapped.append(True)
+        return lambda: gvs.fuse_depth_from_map(w.inputs, ws, (N, H, W), tgt, w.num_samples, w.z_near, w.z_far,
+                                               w.mu, fused=fused, crossing=cross, map_half=half, variant=v)
+    shape = {"views": (N, H, W), "target": (tgt.width, tgt.height), "D": w.num_samples,
+             "z": (w.z_near, w.z_far), "mu": w.mu, "map_half": half}
+    return autotune.choose(shape, runner)
+
+
 class Pipeline:
     """Device buffers and the per-frame call sequence through the C ABI."""
 
@@ -156,22 +175,7 @@ class Pipeline:
         self.variant, self.tune_ms = self.tune()
 
     def tune(self):
-        """The fusion's bundle shape for this workload, picked by the library's autotuner
-        on the first frame (every variant gives the same bits; only the time differs)."""
-        from paper_2505_18932_gb300 import autotune
-        w, gvs = self.w, self.gvs
-        mapped = []
-
-        def runner(v):  # called only when the choice is not cached
-            if not mapped:
-                gvs.weight_map(self.depth[0], w.mu, ws=self.ws_fuse, map_half=self.half)
-                mapped.append(True)
-            return lambda: gvs.fuse_depth_from_map(w.inputs, self.ws_fuse, (self.N, self.H, self.W), self.tgt,
-                                                   w.num_samples, w.z_near, w.z_far, w.mu, fused=self.fused,
-                                                   crossing=self.cross, map_half=self.half, variant=v)
-        shape = {"views": (self.N, self.H, self.W), "target": (self.Wt, self.Ht), "D": w.num_samples,
-                 "z": (w.z_near, w.z_far), "mu": w.mu, "map_half": self.half}
-        return autotune.choose(shape, runner)
+        return tune_fusion(self.w, self.depth[0], self.ws_fuse, self.tgt, self.half, self.fused, self.cross)
 
     def step(self, i, events=None):
         """Frame i of the ring: refine -> fuse -> splat.  `events`: 4 CUDA events bracketing the stages."""
@@ -396,6 +400,11 @@ class FwdBwd:
         self.gt = gts
         self.cfg = dict(num_samples=w.num_samples, z_near=w.z_near, z_far=w.z_far, mu=w.mu)
         self.half = False
+        N, H, W = self.depth[0].shape
+        shape_t = (self.tgt.height, self.tgt.width)
+        self.cfg["variant"], _ = tune_fusion(w, self.depth[0], gvs.workspace(gvs.fuse_workspace_bytes(N, W, H), device),
+                                             self.tgt, False, torch.empty(shape_t, device=device),
+                                             torch.empty(shape_t, dtype=torch.int16, device=device))
 
     def step(self, i, events=None):
         torch, gvs, w = self.torch, self.gvs, self.w
@@ -617,6 +626,7 @@ class MixedScale:
         self.ws_soft = gvs.workspace(gvs.soft_splat_workspace_bytes(N, Wt, Ht), device)
         self.outs = [None] * len(self.tg)
         self.soft = [None] * len(self.tg)
+        self.variant, _ = tune_fusion(w, self.state, self.ws, self.tg[0], half, self.fused[0], self.cross[0])
 
     def step(self, i, events=None):
         w, gvs = self.w, self.gvs
@@ -625,7 +635,8 @@ class MixedScale:
         gvs.weight_map(self.state, w.mu, ws=self.ws, map_half=self.half)
         for t, tgt in enumerate(self.tg):
             gvs.fuse_depth_from_map(w.inputs, self.ws, (self.N, self.H, self.W), tgt, w.num_samples, w.z_near,
-                                    w.z_far, w.mu, fused=self.fused[t], crossing=self.cross[t], map_half=self.half)
+                                    w.z_far, w.mu, fused=self.fused[t], crossing=self.cross[t], map_half=self.half,
+                                    variant=self.variant)
             self.outs[t] = gvs.forward_splat(w.inputs, self.state, self.rgba[cur], tgt, fused=self.fused[t],
                                              mu_guide=w.mu, outputs=self.outs[t], ws=self.ws_splat)
             self.soft[t] = gvs.soft_splat(w.inputs, self.state, self.color[cur], tgt, mu_band=w.mu,

@@ -376,7 +376,7 @@ def fuse_depth_backward(in_cams, in_depths, target, num_samples, z_near, z_far, 
 class FuseDepth(torch.autograd.Function):
     """Differentiable image-based TSDF fusion: fused = FuseDepth.apply(in_depths, cams, target, cfg).
 
-    cfg: dict(num_samples, z_near, z_far, mu[, weight_const, window]).  The backward
+    cfg: dict(num_samples, z_near, z_far, mu[, weight_const, window, variant]).  The backward
     is gvs_fuse_depth_backward (through the clamped signed distances and the
     confidence weights; the crossing index itself is piecewise constant)."""
 
@@ -386,7 +386,7 @@ class FuseDepth(torch.autograd.Function):
         N, H, W = in_depths.shape
         ws = workspace(fuse_workspace_bytes(N, W, H), in_depths.device)
         fused, crossing = fuse_depth(in_cams, in_depths, target, cfg["num_samples"], cfg["z_near"], cfg["z_far"],
-                                     cfg["mu"], weight_const=wc, window=win, ws=ws)
+                                     cfg["mu"], weight_const=wc, window=win, ws=ws, variant=cfg.get("variant", 0))
         ctx.save_for_backward(in_depths, ws, crossing)
         ctx.cams, ctx.target, ctx.cfg = in_cams, target, cfg
         ctx.mark_non_differentiable(crossing)
