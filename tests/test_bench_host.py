@@ -1,0 +1,65 @@
+"""Host-side pieces of bench.py that its JSON line rests on: the algorithmic work
+count behind `roofline`, the compulsory-byte accounting behind `hbm`, and the rule
+that the committed ncu counter record is reported only for the kernel it was taken
+from (same sources, same bundle shape).  No GPU."""
+import importlib.util
+import json
+import os
+import shutil
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_algorithmic_fuse_counts_samples_up_to_the_second_bracket(bench):
+    # crossing index s: samples 0..s+1 are needed (min with D); no crossing (-1): all D; times K views
+    s = np.array([[0, -1], [5, 126]], np.int16)
+    assert bench.algorithmic_fuse(s, 128, 8) == (2 + 128 + 7 + 128) * 8
+
+
+def test_compulsory_bytes_per_stage(bench):
+    N, H, W, Ht, Wt = 2, 3, 4, 5, 6
+    px, tpx = N * H * W, Ht * Wt
+    ab = bench.alg_bytes(N, H, W, Ht, Wt)
+    # refine: two RGBA8 frames, depth and state in, state and mask out
+    assert ab["refine"] == px * 16 + px * 5
+    # weight map: depth in, (d, omega) float2 out
+    assert ab["weight_map"] == px * 4 + px * 8
+    # fusion: the map once, fused depth (f32) and crossing (i16) out
+    assert ab["fuse"] == px * 8 + tpx * 6
+    # splat: depth and colour in, per view and target pixel 14 bytes out, fused depth read once
+    assert ab["splat"] == px * 8 + tpx * N * 14 + tpx * 4
+
+
+def test_counter_record_only_for_its_own_kernel(bench, tmp_path, monkeypatch):
+    """A record applies to the sources it names, hashed, and to one bundle shape; a stale
+    record (bench then reports traffic as null) is no test failure."""
+    import hashlib
+    rec = json.load(open(os.path.join(ROOT, "profiles", "fuse_kernel_traffic.txt")))
+    os.makedirs(tmp_path / "profiles")
+    h = hashlib.sha256()
+    for src in rec["source_files"]:
+        dst = tmp_path / src
+        os.makedirs(dst.parent, exist_ok=True)
+        shutil.copy(os.path.join(ROOT, src), dst)
+        h.update(open(dst, "rb").read())
+    rec.update({"source_sha256": h.hexdigest(), "variant": 3})
+    with open(tmp_path / "profiles" / "fuse_kernel_traffic.txt", "w") as f:
+        json.dump(rec, f)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    got = bench.recorded_counters(3)
+    assert got is not None and got["dram_bytes_per_launch"] == rec["dram_bytes_per_launch"]
+    assert bench.recorded_counters(0) is None  # another bundle shape
+    with open(tmp_path / rec["source_files"][0], "ab") as f:
+        f.write(b"\n")
+    assert bench.recorded_counters(3) is None  # the kernel's sources changed
