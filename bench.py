@@ -141,7 +141,7 @@ def tune_fusion(w, depth0, ws, tgt, half, fused, cross):
                                                w.mu, fused=fused, crossing=cross, map_half=half, variant=v)
     shape = {"views": (N, H, W), "target": (tgt.width, tgt.height), "D": w.num_samples,
              "z": (w.z_near, w.z_far), "mu": w.mu, "map_half": half}
-    return autotune.choose(shape, runner)
+    return autotune.choose(shape, runner, candidates=autotune.variants_for(N))
 
 
 class Pipeline:

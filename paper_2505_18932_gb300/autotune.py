@@ -22,6 +22,13 @@ VARIANTS = (0, 1, 2, 3)
 _lock = threading.Lock()
 
 
+def variants_for(n_views: int):
+    """The variants that are distinct kernels for a call with n_views input views: the
+    bundle shapes are compiled for 5..16 views (8- and 16-view kernels); below and above
+    every variant runs the default shape."""
+    return VARIANTS if 5 <= n_views <= 16 else (0,)
+
+
 def device_key() -> str:
     p = torch.cuda.get_device_properties(torch.cuda.current_device())
     return f"{p.name}|{p.multi_processor_count}"
@@ -70,6 +77,8 @@ def time_ms(fn, warmup: int = 2, reps: int = 5) -> float:
 def choose(shape: dict, make_runner, candidates=VARIANTS, use_cache: bool = True):
     """Return (best variant, {variant: ms}).  make_runner(variant) -> zero-argument callable
     that enqueues one run of the workload with that variant."""
+    if len(candidates) == 1:  # nothing to choose between
+        return candidates[0], {}
     key = device_key() + "|" + workload_key(**shape)
     if use_cache:
         hit = _load_cache().get(key)

@@ -84,7 +84,7 @@ class BatchPlan:
         def runner(v):
             batches[v] = self._make_batch(v)
             return batches[v].launch
-        best, timings = autotune.choose(shape, runner)
+        best, timings = autotune.choose(shape, runner, candidates=autotune.variants_for(len(self.cams)))
         for b in batches.values():
             b.close()
         return best, timings

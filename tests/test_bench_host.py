@@ -63,3 +63,16 @@ def test_counter_record_only_for_its_own_kernel(bench, tmp_path, monkeypatch):
     with open(tmp_path / rec["source_files"][0], "ab") as f:
         f.write(b"\n")
     assert bench.recorded_counters(3) is None  # the kernel's sources changed
+
+
+def test_autotuner_chooses_only_between_distinct_kernels():
+    """Bundle shapes are compiled for 5..16 views; elsewhere every variant is the default
+    kernel, so there is nothing to time and the default comes back at once."""
+    from paper_2505_18932_gb300 import autotune
+    assert autotune.variants_for(8) == autotune.VARIANTS and autotune.variants_for(16) == autotune.VARIANTS
+    assert autotune.variants_for(5) == autotune.VARIANTS
+    for k in (1, 4, 17, 32):
+        assert autotune.variants_for(k) == (0,)
+    calls = []
+    best, ms = autotune.choose({"k": 4}, lambda v: calls.append(v), candidates=autotune.variants_for(4))
+    assert best == 0 and ms == {} and calls == []
