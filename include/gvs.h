@@ -340,7 +340,8 @@ GVS_API gvs_status gvs_soft_splat(const gvs_camera *in_cams, const void *in_dept
                                   uint8_t *alpha, void *workspace, size_t workspace_bytes, void *stream);
 
 /*
- * gvs_soft_splat_backward -- adjoint of gvs_soft_splat.  From the upstream
+ * gvs_soft_splat_backward -- adjoint of gvs_soft_splat (Sec. 3.1 and Supplement
+ * A.3, differentiated with respect to the source depths and colours).  From the upstream
  * gradients of the warped colour (grad_color [n_views][Ht][Wt][4], 4th channel
  * ignored) and, optionally, of the warped depth (grad_depth [n_views][Ht][Wt]),
  * writes the gradients of the source depths (grad_in_depth float [n_views][H][W])
@@ -361,7 +362,8 @@ GVS_API gvs_status gvs_soft_splat_backward(const gvs_camera *in_cams, const void
                                            float *grad_in_depth, float *grad_in_color, void *stream);
 
 /*
- * Batched fusion: many (frame, target) items in one persistent launch.  Each
+ * Batched fusion: many (frame, target) items in one persistent launch (a serving
+ * pattern; the paper has no counterpart, each item is Supplement A.1's fusion).  Each
  * item fuses the map of one frame (gvs_weight_map) into one target camera,
  * exactly as gvs_fuse_depth_from_map would; targets may differ in size.  The
  * launch keeps every SM busy with one grid that takes bundles of target pixels
@@ -418,7 +420,7 @@ GVS_API gvs_status gvs_temporal_weight(const void *masks, int32_t mask_dtype, co
                                        float beta_t, float eta, float *w_tmp, float *target_mask, void *stream);
 
 /*
- * gvs_fuse_depth_temporal -- gvs_fuse_depth_from_map with the previous output
+ * gvs_fuse_depth_temporal -- Supplement A.2: gvs_fuse_depth_from_map with the previous output
  * depth prev_depth(p) as one more TSDF input at the ray's own pixel, weighted
  * w_tmp(p) (zero or an invalid depth: absent):
  *   S_s += w_tmp clamp((prev_depth - z_s) / mu, -1, 1), W_s += w_tmp,
@@ -431,7 +433,8 @@ GVS_API gvs_status gvs_fuse_depth_temporal(const gvs_camera *in_cams, const void
                                            const float *prev_depth, const float *w_tmp, float *fused_depth,
                                            int16_t *crossing, float *view_weight, void *stream);
 
-/* gvs_guided_mask -- the guided mask of gvs_forward_splat computed afterwards:
+/* gvs_guided_mask -- the guided mask of gvs_forward_splat (the fused depth guiding
+ * the warped views, Sec. 3.1 and Sec. 3.3) computed afterwards:
  * guided = alpha && |warped_depth - fused_depth| <= mu_guide, all [n_views][Ht][Wt]
  * except fused_depth [Ht][Wt]. */
 GVS_API gvs_status gvs_guided_mask(const float *warped_depth, const uint8_t *alpha, const float *fused_depth,
