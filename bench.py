@@ -329,7 +329,6 @@ def run_gvs(args, rank, local_rank, world):
     hbm_peak, peak_src, peaks = measured_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     alu_peak = device_sms() * 128 * sm_max * 1e6 / 1e12  # T lane-ops/s
-    achieved = units * OPS_PER_SAMPLE_VIEW / (fuse_kernel_ms * 1e-3) / 1e12
     ab = alg_bytes(pipe.N, pipe.H, pipe.W, pipe.Ht, pipe.Wt)
     step_bytes = sum(ab.values())
     fuse_bytes = ab["fuse"]
@@ -355,20 +354,8 @@ def run_gvs(args, rank, local_rank, world):
                 "note": "weight_map = fusion stage minus the fusion kernel (the map and its two bound kernels); "
                         "the map's 49-tap stencil and the fusion march are FP32-issue bound, refine and splat "
                         "move memory"},
-        "roofline": {"kernel": "fuse_kernel", "bound": "alu", "achieved": round(achieved, 3),
-                     "peak": round(alu_peak, 2), "unit": "T FP32 lane-ops/s",
-                     "frac": round(achieved / alu_peak, 4),
-                     "traffic": counters["dram_bytes_per_launch"] if counters else None,
-                     "ncu_issue_active": counters.get("issue_active_frac") if counters else None,
-                     "units_per_launch": units, "ops_per_unit": OPS_PER_SAMPLE_VIEW,
-                     "kernel_ms": round(fuse_kernel_ms, 4), "hole_fraction": round(holes, 4),
-                     "peak_source": f"{device_sms()} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (measured max SM clock)",
-                     "hbm_alg_bytes": fuse_bytes,
-                     "hbm_frac": round(fuse_bytes / (fuse_kernel_ms * 1e-3) / 1e9 / hbm_peak, 4),
-                     "note": ("units: sample-views of the uniform D-sample march up to each ray's crossing "
-                              "(all D where none), 20 FP32 instructions each; the kernel proves most of them "
-                              "crossing-free without evaluating them, so frac can exceed 1; the binding resource "
-                              "is instruction issue: ncu_issue_active is the fraction of issue slots used")},
+        "roofline": fuse_roofline(units, fuse_kernel_ms, counters, alu_peak, sm_max, holes, fuse_bytes, hbm_peak,
+                                  device_sms()),
         "e2e": e2e,
         "forms": forms,
         "gpu_launches": pipe.launches_per_step() * K,
@@ -378,6 +365,36 @@ def run_gvs(args, rank, local_rank, world):
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(w, frames_np, budget_s=15.0)
     print(json.dumps(line), flush=True)
+
+
+def fuse_roofline(units, kernel_ms, counters, alu_peak, sm_max, holes, fuse_bytes, hbm_peak, sms):
+    """Roofline of the dominant kernel, the fusion march: bound by FP32 instruction issue.
+    achieved = executed warp instructions x 32 lanes / the kernel's live CUDA-event time, so
+    frac <= 1 by construction (one warp instruction per cycle per SM sub-partition); the
+    instruction count is the committed ncu record's (null when the kernel's sources changed
+    since).  The algorithmic figure of the uniform march (sample-views up to each ray's
+    crossing x 20 instructions) is reported beside it: the march proves most of those
+    samples crossing-free without evaluating them, so it is a speed-up, not an efficiency."""
+    inst = counters.get("warp_instructions") if counters else None
+    achieved = inst * 32 / (kernel_ms * 1e-3) / 1e12 if inst else None
+    alg = units * OPS_PER_SAMPLE_VIEW / (kernel_ms * 1e-3) / 1e12
+    return {"kernel": "fuse_kernel", "bound": "alu",
+            "achieved": round(achieved, 3) if achieved else None, "peak": round(alu_peak, 2),
+            "unit": "T FP32 lane-instructions/s", "frac": round(achieved / alu_peak, 4) if achieved else None,
+            "traffic": counters["dram_bytes_per_launch"] if counters else None,
+            "kernel_ms": round(kernel_ms, 4), "warp_instructions_per_launch": inst,
+            "ncu_issue_active": counters.get("issue_active_frac") if counters else None,
+            "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (measured max SM clock; "
+                           "one warp instruction per cycle per SM sub-partition)",
+            "algorithmic": {"units_per_launch": units, "ops_per_unit": OPS_PER_SAMPLE_VIEW,
+                            "lane_ops_per_s_T": round(alg, 3),
+                            "speedup_vs_uniform_march": round(units * OPS_PER_SAMPLE_VIEW / (inst * 32), 3)
+                            if inst else None,
+                            "note": "sample-views of the uniform D-sample march up to each ray's crossing (all D "
+                                    "where none) x 20 FP32 instructions; the march skips provably crossing-free "
+                                    "runs, so this can exceed the issue peak"},
+            "hole_fraction": round(holes, 4), "hbm_alg_bytes": fuse_bytes,
+            "hbm_frac": round(fuse_bytes / (kernel_ms * 1e-3) / 1e9 / hbm_peak, 4)}
 
 
 class FwdBwd:
@@ -716,9 +733,9 @@ def time_batched(device, steps):
                                                "item, no graph (refine and maps not counted)"}}
 
 
-def _event_ms(fn, steps):
+def _event_ms(fn, steps, warmup=3):
     import torch
-    for _ in range(3):
+    for _ in range(warmup):
         fn()
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -943,30 +960,52 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-FORM_CLASSES = ("fwd_bwd", "gauss_render", "network_frame_k4", "sphere_trace_fusion", "temporal_online")
+FORM_CLASSES = ("plain", "f16_storage", "fwd_bwd", "fwd_bwd_640x360", "gauss_render", "network_frame_k4",
+                "sphere_trace_fusion", "temporal_online", "batched", "mixed")
 
 
 def run_only_form(args):
-    """One form of the 8x1080p frame, alone: max(3, warmup) untimed steps, then `steps`
-    steps between CUDA events.  Used to profile a form's kernels."""
+    """One form alone: max(3, warmup) untimed steps, then `steps` steps between CUDA events.
+    Builds nothing but that form (no other workload is rendered or put on the device), so a
+    profiler capture of one of its kernels sees only its own launches.  `plain` is the
+    benchmark's own 8 x 1080p frame (refine -> weight map -> fuse -> splat)."""
     import torch
     from synth import configs
-    w = configs.headline_8x1080p()
-    frames_np = render_frames(w, rank_frames(0))
-    cls = {"fwd_bwd": FwdBwd, "gauss_render": GaussRender, "network_frame_k4": NetworkFrame,
-           "sphere_trace_fusion": SphereTrace, "temporal_online": TemporalOnline}[args.only_form]
-    form = cls(w, frames_np[:2] if cls is FwdBwd else frames_np, torch.device("cuda", 0))
-    for i in range(max(3, args.warmup)):
-        form.step(i)
-    torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    for i in range(args.steps):
-        form.step(i + 1)
-    b.record()
-    torch.cuda.synchronize()
-    print(json.dumps({"form": args.only_form, "ms_per_step": round(a.elapsed_time(b) / max(args.steps, 1), 4),
-                      "steps": args.steps, "workload": w.name}), flush=True)
+    device = torch.device("cuda", 0)
+    name = args.only_form
+    if name == "batched":
+        from paper_2505_18932_gb300 import batch
+        w = configs.batched_16_targets()
+        fr = render_frames(w, [0, 1, 2])
+        rgba = [torch.from_numpy(c.view(np.int32)).to(device) for c, _ in fr]
+        dep = [torch.from_numpy(d).to(device) for _, d in fr]
+        plan = batch.BatchPlan(w.inputs, w.targets, rgba[1:], dep[1:], w.num_samples, w.z_near, w.z_far, w.mu,
+                               tau=w.tau, rgba_prev=rgba[0], state0=dep[0], variant=None, graph=True)
+        ms = _event_ms(plan.run, args.steps, warmup=max(3, args.warmup))
+    elif name == "mixed":
+        w = configs.mixed_16x1080p()
+        form = MixedScale(w, render_frames(w, [0, 1]), device, half=True)
+        frame = iter(range(1, 1 << 30))
+        ms = _event_ms(lambda: form.step(next(frame)), args.steps, warmup=max(3, args.warmup))
+    else:
+        w = configs.diff_640x360() if name == "fwd_bwd_640x360" else configs.headline_8x1080p()
+        frames_np = render_frames(w, [0, 1] if name.startswith("fwd_bwd") else rank_frames(0))
+        cls = {"plain": Pipeline, "f16_storage": Pipeline, "fwd_bwd": FwdBwd, "fwd_bwd_640x360": FwdBwd,
+               "gauss_render": GaussRender, "network_frame_k4": NetworkFrame, "sphere_trace_fusion": SphereTrace,
+               "temporal_online": TemporalOnline}[name]
+        form = cls(w, frames_np, device, half=True) if name == "f16_storage" else cls(w, frames_np, device)
+        for i in range(max(3, args.warmup)):
+            form.step(i)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for i in range(args.steps):
+            form.step(i + 1)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / max(args.steps, 1)
+    print(json.dumps({"form": name, "ms_per_step": round(ms, 4), "steps": args.steps, "workload": w.name}),
+          flush=True)
 
 
 def main():

@@ -4,8 +4,14 @@ pixels the oracle does not flag as ambiguous)."""
 import numpy as np
 import torch
 
+import os
+
 DEPTH_RTOL = 1e-4          # fused depth, FP32 kernel vs FP64 oracle
-MAX_AMBIGUOUS = 1e-2       # flagged-pixel fraction above which a case fails
+MAX_AMBIGUOUS = 1e-3       # flagged-pixel fraction above which a case fails
+
+# (test id, flagged pixels, compared pixels) of every fused-depth comparison in
+# this session; the terminal summary of the run reports them
+AMBIGUOUS_LOG = []
 
 
 def u32(rgba):
@@ -38,5 +44,6 @@ def compare_fused(gpu_depth, gpu_index, ref, where=None):
     assert not bad.any(), (f"fused depth differs at {bad.sum()} px, worst rel "
                            f"{(err[bad] / np.maximum(np.abs(rd[bad]), 1e-30)).max():.3e}")
     frac = amb.mean() if amb.size else 0.0
-    assert frac <= MAX_AMBIGUOUS, f"ambiguous fraction {frac:.2e}"
+    AMBIGUOUS_LOG.append((os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0], int(amb.sum()), int(amb.size)))
+    assert frac <= MAX_AMBIGUOUS, f"ambiguous fraction {frac:.2e} ({int(amb.sum())} of {amb.size} px)"
     return frac

@@ -76,3 +76,21 @@ def test_autotuner_chooses_only_between_distinct_kernels():
     calls = []
     best, ms = autotune.choose({"k": 4}, lambda v: calls.append(v), candidates=autotune.variants_for(4))
     assert best == 0 and ms == {} and calls == []
+
+
+def test_roofline_fraction_is_an_issue_fraction(bench):
+    """frac = executed warp instructions x 32 / (kernel time x lane peak): at most 1 whenever the
+    instruction count is one the kernel could have issued in that time; without a record the
+    fraction is null (never the algorithmic figure, which can exceed 1)."""
+    sms, mhz = 152, 2070.0
+    peak = sms * 128 * mhz * 1e6 / 1e12
+    ms = 0.7
+    # the most a kernel can issue in 0.7 ms: one warp instruction per cycle per sub-partition
+    most = int(sms * 4 * mhz * 1e6 * ms * 1e-3)
+    for inst in (most // 2, most):
+        r = bench.fuse_roofline(1.73e9, ms, {"warp_instructions": inst, "dram_bytes_per_launch": 1},
+                                peak, mhz, 0.6, 145e6, 6689.0, sms)
+        assert 0 < r["frac"] <= 1.0 + 1e-9 and r["bound"] == "alu"
+        assert r["algorithmic"]["lane_ops_per_s_T"] > r["achieved"]   # the uniform-march count
+    r = bench.fuse_roofline(1.73e9, ms, None, peak, mhz, 0.6, 145e6, 6689.0, sms)
+    assert r["frac"] is None and r["achieved"] is None and r["traffic"] is None
