@@ -273,10 +273,10 @@ gvs::FuseArgs fuse_args(const gvs_camera *in_cams, const void *map, int32_t n_vi
     const char *m = reinterpret_cast<const char *>(map);
     if (n_views > 0) {
         a.dw = m + L.off_dw;
-        for (int l = 0; l < 3; ++l) a.ob[l] = reinterpret_cast<const float2 *>(m + L.off_O[l]);
-        a.tg = reinterpret_cast<const float2 *>(m + L.off_g);
+        for (int l = 0; l < gvs::kBoundLevels; ++l) a.ob[l] = reinterpret_cast<const gvs::DepthBound *>(m + L.off_O[l]);
+        a.tg = reinterpret_cast<const gvs::DepthBound *>(m + L.off_g);
     }
-    for (int l = 0; l < 3; ++l) {
+    for (int l = 0; l < gvs::kBoundLevels; ++l) {
         a.tw[l] = L.tw[l];
         a.th[l] = L.th[l];
     }

@@ -6,10 +6,11 @@
 //               float2 (d, omega); an invalid pixel is stored as (0, 0), whose
 //               signed distance is below -1 so it never contributes.  7x7
 //               stencil over a shared-memory tile with halo.  The same kernel
-//               writes the min/max valid depth of every 8x8 tile.
-// depth_bounds, bounds_overlap: build the per-view bound pyramid (8, 32 and
-//               128 pixel tiles, each also as overlapping 2x2-tile blocks, and
-//               the whole view) from the 8x8 tiles.
+//               writes the bound of every 16x16 tile: smallest and largest
+//               valid depth and the mask of occupied depth bins.
+// depth_bounds, bounds_overlap: build the per-view bound pyramid (16, 32, 64
+//               and 128 pixel tiles, each also as overlapping 2x2-tile
+//               blocks, and the whole view) from the 16x16 tiles.
 // fuse        : one warp per 8x4 bundle of target pixels, one thread per ray,
 //               marching the D samples in registers (one 8-byte gather per
 //               sample and view) to the first +/- crossing.  Before evaluating
@@ -43,7 +44,8 @@ __global__ void __launch_bounds__(256, 8) weight_map_kernel(const DT *__restrict
     constexpr int SW = WM_TX + 2 * R;
     constexpr int SH = WM_TY + 2 * R;
     __shared__ float2 tile[SH][SW];  // each depth twice: a ready pair for the packed taps
-    __shared__ float2 red[WM_TY / WM_P][WM_TX / 8];
+    __shared__ float2 red[WM_TY / WM_P][WM_TX / 16];
+    __shared__ uint2 mred[WM_TY / WM_P][WM_TX / 16];
     const int W = L.W, H = L.H;
     const int k = blockIdx.z;
     const DT *dep = depth + (size_t)k * W * H;
@@ -52,7 +54,7 @@ __global__ void __launch_bounds__(256, 8) weight_map_kernel(const DT *__restrict
     const int tid = threadIdx.y * WM_TX + threadIdx.x;
     if (blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) {
         // whole-view bounds, reduced into by depth_bounds with integer atomics on the float bits
-        reinterpret_cast<int2 *>(map + L.off_g)[k] = make_int2(0x7f800000, (int)0xff800000u);
+        reinterpret_cast<uint4 *>(map + L.off_g)[k] = make_uint4(0x7f800000u, 0xff800000u, ~0u, ~0u);
     }
     for (int e = tid; e < SW * SH; e += 256) {
         const int sy = e / SW, sx = e - sy * SW;
@@ -125,84 +127,169 @@ __global__ void __launch_bounds__(256, 8) weight_map_kernel(const DT *__restrict
             store_map(&dw[(size_t)y * W + x], d, w);
         }
     }
-    // 8x8 tile bounds: over the 8 lanes of a tile column group, then the 8 / WM_P thread rows of a tile
+    // 16x16 tile bounds: over the 16 lanes of a tile's columns, then its two thread rows
+    static_assert(WM_P == 8 && WM_TX % 16 == 0 && WM_TY % 16 == 0, "a 16x16 tile is 16 lanes x 2 thread rows");
 #pragma unroll
-    for (int m = 1; m < 8; m <<= 1) {
+    for (int m = 1; m < 16; m <<= 1) {
         lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, m));
         hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, m));
     }
-    if ((tx & 7) == 0) red[ty][tx >> 3] = make_float2(lo, hi);
+    if ((tx & 15) == 0) red[ty][tx >> 4] = make_float2(lo, hi);
     __syncthreads();
-    if (tid < (WM_TY / 8) * (WM_TX / 8)) {
-        const int tc = tid % (WM_TX / 8), tr = tid / (WM_TX / 8);
-        const float2 a = red[(8 / WM_P) * tr][tc], b = red[(8 / WM_P) * tr + (8 / WM_P) - 1][tc];
-        const int gx = blockIdx.x * (WM_TX / 8) + tc, gy = blockIdx.y * (WM_TY / 8) + tr;
+    const float tlo = fminf(red[ty & ~1][tx >> 4].x, red[ty | 1][tx >> 4].x);
+    const float thi = fmaxf(red[ty & ~1][tx >> 4].y, red[ty | 1][tx >> 4].y);
+    // the tile's mask: the bin of every valid depth in it, relative to the bin of the smallest
+    unsigned long long mask = 0;
+    const int base = depth_bin(tlo);
+#pragma unroll
+    for (int p = 0; p < WM_P; ++p)
+        if (x < W && yb + p < H && dc[p] == dc[p]) mask |= 1ull << min(depth_bin(dc[p]) - base, kDepthBins - 1);
+    unsigned mlo = (unsigned)mask, mhi = (unsigned)(mask >> 32);
+#pragma unroll
+    for (int m = 1; m < 16; m <<= 1) {
+        mlo |= __shfl_xor_sync(0xffffffffu, mlo, m);
+        mhi |= __shfl_xor_sync(0xffffffffu, mhi, m);
+    }
+    if ((tx & 15) == 0) mred[ty][tx >> 4] = make_uint2(mlo, mhi);
+    __syncthreads();
+    if ((tx & 15) == 0 && (ty & 1) == 0) {
+        const uint2 o = mred[ty | 1][tx >> 4];
+        const int gx = blockIdx.x * (WM_TX / 16) + (tx >> 4), gy = blockIdx.y * (WM_TY / 16) + (ty >> 1);
         if (gx < L.tw[0] && gy < L.th[0])
-            reinterpret_cast<float2 *>(map + L.off_T[0])[((size_t)k * L.th[0] + gy) * L.tw[0] + gx] =
-                make_float2(fminf(a.x, b.x), fmaxf(a.y, b.y));
+            reinterpret_cast<uint4 *>(map + L.off_T[0])[((size_t)k * L.th[0] + gy) * L.tw[0] + gx] =
+                make_uint4(__float_as_uint(tlo), __float_as_uint(thi), mlo | o.x, mhi | o.y);
     }
 }
 
-__device__ __forceinline__ float2 merge(float2 a, float2 b) { return make_float2(fminf(a.x, b.x), fmaxf(a.y, b.y)); }
+__device__ __forceinline__ DepthBound empty_bound() {
+    DepthBound b;
+    b.lo = kInf;
+    b.hi = -kInf;
+    b.mlo = b.mhi = 0u;
+    return b;
+}
 
-// One block per (128x128 pixel tile, view), one thread per 8x8 tile: writes
-// O_3 (needs one tile of halo right and below), T_5, T_7 and the view bounds.
-__global__ void __launch_bounds__(256) depth_bounds_kernel(char *__restrict__ map, MapLayout L) {
-    __shared__ float2 s[17][17];
+__device__ __forceinline__ DepthBound load_bound(const DepthBound *p) {
+    const uint4 v = *reinterpret_cast<const uint4 *>(p);
+    DepthBound b;
+    b.lo = __uint_as_float(v.x);
+    b.hi = __uint_as_float(v.y);
+    b.mlo = v.z;
+    b.mhi = v.w;
+    return b;
+}
+
+__device__ __forceinline__ void store_bound(DepthBound *p, const DepthBound &b) {
+    *reinterpret_cast<uint4 *>(p) = make_uint4(__float_as_uint(b.lo), __float_as_uint(b.hi), b.mlo, b.mhi);
+}
+
+// A child's mask in the bins of a parent whose smallest depth lies sh >= 0 bins
+// lower: bins moved past 63 land on 63.
+__device__ __forceinline__ unsigned long long shift_bins(unsigned long long m, int sh) {
+    if (m == 0ull) return 0ull;
+    if (sh >= 64) return 1ull << 63;
+    if (sh == 0) return m;
+    return (m << sh) | ((m >> (64 - sh)) ? (1ull << 63) : 0ull);
+}
+
+__device__ __forceinline__ void rebin_into(DepthBound &p, const DepthBound &c) {
+    if (!(c.lo <= c.hi)) return;  // no valid depth in c
+    const unsigned long long m =
+        shift_bins(((unsigned long long)c.mhi << 32) | c.mlo, depth_bin(c.lo) - depth_bin(p.lo));
+    p.mlo |= (unsigned)m;
+    p.mhi |= (unsigned)(m >> 32);
+}
+
+__device__ __forceinline__ DepthBound merge4(const DepthBound &a, const DepthBound &b, const DepthBound &c,
+                                             const DepthBound &d) {
+    DepthBound p;
+    p.lo = fminf(fminf(a.lo, b.lo), fminf(c.lo, d.lo));
+    p.hi = fmaxf(fmaxf(a.hi, b.hi), fmaxf(c.hi, d.hi));
+    p.mlo = p.mhi = 0u;
+    if (p.lo <= p.hi) {
+        rebin_into(p, a);
+        rebin_into(p, b);
+        rebin_into(p, c);
+        rebin_into(p, d);
+    }
+    return p;
+}
+
+// One block per (128x128 pixel tile, view), one thread per 16x16 tile of it:
+// writes O_4 (needs one tile of halo right and below), T_5, T_6, T_7 and the
+// view bounds.
+__global__ void __launch_bounds__(64) depth_bounds_kernel(char *__restrict__ map, MapLayout L) {
+    __shared__ DepthBound s4[9][9];
+    __shared__ DepthBound s5[4][4];
+    __shared__ DepthBound s6[2][2];
     const int k = blockIdx.z;
-    const float2 *T3 = reinterpret_cast<const float2 *>(map + L.off_T[0]) + (size_t)k * L.tw[0] * L.th[0];
-    const int tid = threadIdx.y * 16 + threadIdx.x;
-    for (int e = tid; e < 17 * 17; e += 256) {
-        const int ly = e / 17, lx = e - ly * 17;
-        const int tx = blockIdx.x * 16 + lx, ty = blockIdx.y * 16 + ly;
-        s[ly][lx] = (tx < L.tw[0] && ty < L.th[0]) ? T3[(size_t)ty * L.tw[0] + tx] : make_float2(kInf, -kInf);
+    const DepthBound *T4 = reinterpret_cast<const DepthBound *>(map + L.off_T[0]) + (size_t)k * L.tw[0] * L.th[0];
+    const int x = threadIdx.x, y = threadIdx.y;
+    const int tid = y * 8 + x;
+    for (int e = tid; e < 9 * 9; e += 64) {
+        const int ly = e / 9, lx = e - ly * 9;
+        const int tx = blockIdx.x * 8 + lx, ty = blockIdx.y * 8 + ly;
+        s4[ly][lx] = (tx < L.tw[0] && ty < L.th[0]) ? load_bound(&T4[(size_t)ty * L.tw[0] + tx]) : empty_bound();
     }
     __syncthreads();
-    const int x = threadIdx.x, y = threadIdx.y;
-    const int tx = blockIdx.x * 16 + x, ty = blockIdx.y * 16 + y;
-    if (tx < L.tw[0] && ty < L.th[0]) {
-        const float2 o = merge(merge(s[y][x], s[y][x + 1]), merge(s[y + 1][x], s[y + 1][x + 1]));
-        reinterpret_cast<float2 *>(map + L.off_O[0])[((size_t)k * L.th[0] + ty) * L.tw[0] + tx] = o;
+    {
+        const int tx = blockIdx.x * 8 + x, ty = blockIdx.y * 8 + y;
+        if (tx < L.tw[0] && ty < L.th[0])
+            store_bound(reinterpret_cast<DepthBound *>(map + L.off_O[0]) + ((size_t)k * L.th[0] + ty) * L.tw[0] + tx,
+                        merge4(s4[y][x], s4[y][x + 1], s4[y + 1][x], s4[y + 1][x + 1]));
     }
-    if ((x & 3) == 0 && (y & 3) == 0) {
-        float2 c = make_float2(kInf, -kInf);
-#pragma unroll
-        for (int dy = 0; dy < 4; ++dy)
-#pragma unroll
-            for (int dx = 0; dx < 4; ++dx) c = merge(c, s[y + dy][x + dx]);
-        const int x5 = blockIdx.x * 4 + (x >> 2), y5 = blockIdx.y * 4 + (y >> 2);
-        if (x5 < L.tw[1] && y5 < L.th[1])
-            reinterpret_cast<float2 *>(map + L.off_T[1])[((size_t)k * L.th[1] + y5) * L.tw[1] + x5] = c;
+    if (x < 4 && y < 4) {
+        const DepthBound b = merge4(s4[2 * y][2 * x], s4[2 * y][2 * x + 1], s4[2 * y + 1][2 * x],
+                                    s4[2 * y + 1][2 * x + 1]);
+        s5[y][x] = b;
+        const int tx = blockIdx.x * 4 + x, ty = blockIdx.y * 4 + y;
+        if (tx < L.tw[1] && ty < L.th[1])
+            store_bound(reinterpret_cast<DepthBound *>(map + L.off_T[1]) + ((size_t)k * L.th[1] + ty) * L.tw[1] + tx, b);
     }
+    __syncthreads();
+    if (x < 2 && y < 2) {
+        const DepthBound b = merge4(s5[2 * y][2 * x], s5[2 * y][2 * x + 1], s5[2 * y + 1][2 * x],
+                                    s5[2 * y + 1][2 * x + 1]);
+        s6[y][x] = b;
+        const int tx = blockIdx.x * 2 + x, ty = blockIdx.y * 2 + y;
+        if (tx < L.tw[2] && ty < L.th[2])
+            store_bound(reinterpret_cast<DepthBound *>(map + L.off_T[2]) + ((size_t)k * L.th[2] + ty) * L.tw[2] + tx, b);
+    }
+    __syncthreads();
     if (tid == 0) {
-        float2 c = make_float2(kInf, -kInf);
-        for (int i = 0; i < 256; ++i) c = merge(c, s[i >> 4][i & 15]);
-        reinterpret_cast<float2 *>(map + L.off_T[2])[((size_t)k * L.th[2] + blockIdx.y) * L.tw[2] + blockIdx.x] = c;
-        int *g = reinterpret_cast<int *>(map + L.off_g) + 2 * k;
-        if (c.x <= c.y) {  // the tile holds a valid depth
-            atomicMin(&g[0], __float_as_int(c.x));  // positive floats order like their bits
-            atomicMax(&g[1], __float_as_int(c.y));
+        const DepthBound b = merge4(s6[0][0], s6[0][1], s6[1][0], s6[1][1]);
+        store_bound(reinterpret_cast<DepthBound *>(map + L.off_T[3]) +
+                        ((size_t)k * L.th[3] + blockIdx.y) * L.tw[3] + blockIdx.x, b);
+        unsigned *g = reinterpret_cast<unsigned *>(reinterpret_cast<DepthBound *>(map + L.off_g) + k);
+        if (b.lo <= b.hi) {  // the tile holds a valid depth; positive floats order like their bits
+            atomicMin(&g[0], __float_as_uint(b.lo));
+            atomicMax(&g[1], __float_as_uint(b.hi));
         }
     }
 }
 
-// O_l from T_l for levels 5 and 7: one thread per (view, tile).
+// O_l from T_l for levels 5, 6 and 7: one thread per (view, tile).
 __global__ void __launch_bounds__(256) bounds_overlap_kernel(char *__restrict__ map, MapLayout L) {
-    const int64_t n5 = (int64_t)L.tw[1] * L.th[1], n7 = (int64_t)L.tw[2] * L.th[2];
+    int64_t n[kBoundLevels], total = 0;
+    for (int l = 1; l < kBoundLevels; ++l) {
+        n[l] = (int64_t)L.tw[l] * L.th[l];
+        total += n[l];
+    }
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= (int64_t)L.K * (n5 + n7)) return;
-    const int k = (int)(q / (n5 + n7));
-    q -= (int64_t)k * (n5 + n7);
-    const int l = q < n5 ? 1 : 2;
-    if (l == 2) q -= n5;
+    if (q >= (int64_t)L.K * total) return;
+    const int k = (int)(q / total);
+    q -= (int64_t)k * total;
+    int l = 1;
+    while (q >= n[l]) q -= n[l++];
     const int tw = L.tw[l], th = L.th[l];
     const int tx = (int)(q % tw), ty = (int)(q / tw);
-    const float2 *T = reinterpret_cast<const float2 *>(map + L.off_T[l]) + (size_t)k * tw * th;
-    float2 o = T[(size_t)ty * tw + tx];
-    if (tx + 1 < tw) o = merge(o, T[(size_t)ty * tw + tx + 1]);
-    if (ty + 1 < th) o = merge(o, T[(size_t)(ty + 1) * tw + tx]);
-    if (tx + 1 < tw && ty + 1 < th) o = merge(o, T[(size_t)(ty + 1) * tw + tx + 1]);
-    reinterpret_cast<float2 *>(map + L.off_O[l])[((size_t)k * th + ty) * tw + tx] = o;
+    const DepthBound *T = reinterpret_cast<const DepthBound *>(map + L.off_T[l]) + (size_t)k * tw * th;
+    const DepthBound e = empty_bound();
+    const DepthBound a = load_bound(&T[(size_t)ty * tw + tx]);
+    const DepthBound b = tx + 1 < tw ? load_bound(&T[(size_t)ty * tw + tx + 1]) : e;
+    const DepthBound c = ty + 1 < th ? load_bound(&T[(size_t)(ty + 1) * tw + tx]) : e;
+    const DepthBound d = (tx + 1 < tw && ty + 1 < th) ? load_bound(&T[(size_t)(ty + 1) * tw + tx + 1]) : e;
+    store_bound(reinterpret_cast<DepthBound *>(map + L.off_O[l]) + ((size_t)k * th + ty) * tw + tx, merge4(a, b, c, d));
 }
 
 template <int KMAX, typename MT, typename T, bool TMP>
@@ -275,8 +362,10 @@ cudaError_t launch_weight_map(const void *depth, int depth_dtype, void *map, int
                                  : launch_wm_window<float, float2>(depth, m, L, mu, wconst, window, exact, st);
     }
     if (e != cudaSuccess) return e;
-    depth_bounds_kernel<<<dim3(L.tw[2], L.th[2], K), dim3(16, 16), 0, st>>>(m, L);
-    const int64_t n = (int64_t)K * ((int64_t)L.tw[1] * L.th[1] + (int64_t)L.tw[2] * L.th[2]);
+    depth_bounds_kernel<<<dim3(L.tw[3], L.th[3], K), dim3(8, 8), 0, st>>>(m, L);
+    int64_t n = 0;
+    for (int l = 1; l < kBoundLevels; ++l) n += (int64_t)L.tw[l] * L.th[l];
+    n *= K;
     bounds_overlap_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m, L);
     return cudaGetLastError();
 }

@@ -86,7 +86,7 @@ constexpr int FZ_WARPS = GVS_FUSE_WARPS;
 #ifndef GVS_FUSE_MIN_BLOCKS
 #define GVS_FUSE_MIN_BLOCKS 8   // resident blocks per SM requested from the register allocator (64 registers)
 #endif
-constexpr int SKIP_COOL = 4;    // samples evaluated after both slab tests fail, before testing again
+constexpr int SKIP_COOL = 3;    // samples evaluated after both slab tests fail, before testing again
 
 // Bundle shape and slab-test lengths of the march.  Every variant computes the
 // same result; they differ only in speed, and the autotuner picks one per
@@ -123,14 +123,17 @@ struct Ray {
 // inside the hull of the 8 vertex projections and their projected depths lie
 // between the vertices' extremes (both statements exact for an affine depth
 // and a projective map on a convex body in front of the camera; FP32 rounding
-// of the samples is covered by a 1 pixel and 1e-6 relative margin).  The view
-// is free over the slab when every valid depth in the pixel box around that
-// hull is strictly beyond the largest projected depth (sdf > 0: a positive
-// term) or at least 1.0001 mu in front of the smallest (sdf < -1: cut off), or
-// the box is outside the image, or the slab is behind the camera.  One bounds
-// load: the finest tile level whose overlapping 2x2 block covers the box, else
-// the whole view.  When every view is free over the slab, no sample of it can
-// end a crossing (S > 0 wherever W > 0).
+// of the samples is covered by a 1 pixel and 1e-6 relative margin).  A pixel
+// of depth d can make a sample at projected depth z end a crossing only if
+// d <= z (sdf <= 0) and d >= z - mu (not cut off), so the view is free over
+// the slab when no valid depth in the pixel box around that hull lies in
+// [zlo - 1.0001 mu, zhi] (every term positive or cut off), or the box is
+// outside the image, or the slab is behind the camera.  One bound load: the
+// finest tile level whose overlapping 2x2 block covers the box, else the whole
+// view.  The bound's range decides first; failing that, its mask of occupied
+// depth bins (a clear bin holds no depth; see DepthBound), which separates the
+// surfaces of a tile that straddles a depth discontinuity.  When every view is free over the
+// slab, no sample of it can end a crossing (S > 0 wherever W > 0).
 // k is this lane's view; (b0, b1, b2) its offset b_k, held in registers so the
 // lanes of a warp (testing different views) do not serialize on constant loads.
 __device__ __forceinline__ bool slab_view_free(const FuseArgs &a, int k, const Ray (&corner)[4], float b0, float b1,
@@ -162,18 +165,28 @@ __device__ __forceinline__ bool slab_view_free(const FuseArgs &a, int k, const R
     const int by0 = min(max(__float2int_rd(ylo), 0), a.H - 1), by1 = min(max(__float2int_ru(yhi), 0), a.H - 1);
     // a box spanning fewer than 2^l pixels per axis covers at most 2x2 tiles of level l
     const int span = max(bx1 - bx0, by1 - by0);
-    const float2 *p;
-    if (span < 8)
-        p = a.ob[0] + ((size_t)k * a.th[0] + (by0 >> 3)) * a.tw[0] + (bx0 >> 3);
+    const DepthBound *p;
+    if (span < 16)
+        p = a.ob[0] + ((size_t)k * a.th[0] + (by0 >> 4)) * a.tw[0] + (bx0 >> 4);
     else if (span < 32)
         p = a.ob[1] + ((size_t)k * a.th[1] + (by0 >> 5)) * a.tw[1] + (bx0 >> 5);
+    else if (span < 64)
+        p = a.ob[2] + ((size_t)k * a.th[2] + (by0 >> 6)) * a.tw[2] + (bx0 >> 6);
     else if (span < 128)
-        p = a.ob[2] + ((size_t)k * a.th[2] + (by0 >> 7)) * a.tw[2] + (bx0 >> 7);
+        p = a.ob[3] + ((size_t)k * a.th[3] + (by0 >> 7)) * a.tw[3] + (bx0 >> 7);
     else
         p = a.tg + k;
-    if (!GVS_IN_BOUNDS(p - a.ob[0], (const float2 *)(a.tg + a.K) - a.ob[0], GVS_SITE_FUSE_BOUNDS)) return false;
-    const float2 b = __ldg(p);
-    return zhi < b.x || zlo > b.y + a.behind;
+    if (!GVS_IN_BOUNDS(p - a.ob[0], (a.tg + a.K) - a.ob[0], GVS_SITE_FUSE_BOUNDS)) return false;
+    const uint4 b = __ldg(reinterpret_cast<const uint4 *>(p));
+    const float lo = __uint_as_float(b.x), hi = __uint_as_float(b.y);
+    const float qlo = __fsub_rn(zlo, a.behind);
+    if (zhi < lo || qlo > hi) return true;
+    // here lo <= zhi, so 0 <= m1, and m0 <= m1 (the bins are monotone)
+    const int base = depth_bin(lo);
+    const int m0 = min(max(depth_bin(fmaxf(qlo, 0.0f)) - base, 0), kDepthBins - 1);
+    const int m1 = min(depth_bin(zhi) - base, kDepthBins - 1);
+    const unsigned long long occupied = ((unsigned long long)b.w << 32) | b.z;
+    return (occupied & (~0ull << m0) & (~0ull >> (kDepthBins - 1 - m1))) == 0ull;
 }
 
 // S and W of one sample over the input views (Supplement A.1), before the
@@ -312,6 +325,7 @@ __device__ __forceinline__ void march_bundle(const FuseArgs &a, int bundle, int 
             }
             if (nfree > 0) {
                 s = min(s + nfree * L, a.D - 1);  // samples up to s are not crossing ends; s is evaluated next
+                if (s == a.D - 1) break;           // ... unless it is the last: nothing follows it
                 have_prev = false;
                 shorter = false;
                 continue;

@@ -29,43 +29,65 @@ cudaError_t launch_refine_soft(const uint32_t *rgba_t, const uint32_t *rgba_prev
 
 // ---- TSDF fusion -----------------------------------------------------------
 // Byte layout of the fusion workspace ("map"): the packed (depth, weight)
-// float2 per input pixel, then per-view depth bounds (min, max over valid
-// depths; +inf/-inf where there is none).  For each tile level l in {3, 5, 7}
-// (tiles of 2^l x 2^l pixels) T_l holds the bounds of each tile and O_l the
-// bounds of the 2x2 block of tiles anchored at it, so that any pixel box
-// spanning at most two tiles per axis at level l is covered by one O_l
-// entry.  G holds the bounds of the whole view.  Sections are 256-byte
-// aligned.
+// float2 per input pixel, then per-view depth bounds.  For each tile level l
+// in {4, 5, 6, 7} (tiles of 2^l x 2^l pixels) T_l holds the bounds of each
+// tile and O_l the bounds of the 2x2 block of tiles anchored at it, so that
+// any pixel box spanning at most two tiles per axis at level l is covered by
+// one O_l entry.  G holds the bounds of the whole view.  Sections are 256-byte
+// aligned.  A bound (DepthBound) is the smallest and largest valid depth of
+// its pixels (+inf / -inf where there is none) and a 64-bit mask of occupied
+// depth bins.  The bins are those of the FP32 bit pattern: bin(d) = bits(d)
+// >> 18 (exponent and the 5 leading mantissa bits: 32 bins per octave, 1.6 to
+// 3.1 % of the depth wide), monotone in d for d >= 0 and exact.  Bit b of a
+// bound's mask is set when some valid depth d of its pixels has
+// bin(d) - bin(lo) = b, or >= 63 for b = 63.  A coarser bound takes its
+// children's masks shifted by the difference of their bin(lo) (whatever moves
+// past bit 63 lands on bit 63), so a clear bit proves that no depth of the
+// pixels lies in that bin.  G's mask is all ones (it is never consulted).
+struct __align__(16) DepthBound {
+    float lo, hi;
+    unsigned mlo, mhi;  // bins 0..31, 32..63
+};
+constexpr int kBoundLevels = 4;    // levels 4, 5, 6, 7
+constexpr int kBoundShift0 = 4;    // finest tile: 16 x 16 pixels
+constexpr int kDepthBins = 64;
+
 struct MapLayout {
     int K, W, H;
-    int tw[3], th[3];          // tiles per row / column at levels 3, 5, 7
-    size_t off_dw, off_T[3], off_O[3], off_g, total;
+    int tw[kBoundLevels], th[kBoundLevels];  // tiles per row / column at levels 4..7
+    size_t off_dw, off_T[kBoundLevels], off_O[kBoundLevels], off_g, total;
 };
 
 inline MapLayout map_layout(int K, int W, int H) {
     auto up = [](size_t n) { return (n + 255) / 256 * 256; };
     MapLayout m;
     m.K = K; m.W = W; m.H = H;
-    const int shift[3] = {3, 5, 7};
     size_t o = 0;
     m.off_dw = o; o = up(o + (size_t)K * W * H * 8);
-    for (int l = 0; l < 3; ++l) {
-        m.tw[l] = (W + (1 << shift[l]) - 1) >> shift[l];
-        m.th[l] = (H + (1 << shift[l]) - 1) >> shift[l];
-        m.off_T[l] = o; o = up(o + (size_t)K * m.tw[l] * m.th[l] * 8);
-        m.off_O[l] = o; o = up(o + (size_t)K * m.tw[l] * m.th[l] * 8);
+    for (int l = 0; l < kBoundLevels; ++l) {
+        const int sh = kBoundShift0 + l;
+        m.tw[l] = (W + (1 << sh) - 1) >> sh;
+        m.th[l] = (H + (1 << sh) - 1) >> sh;
+        m.off_T[l] = o; o = up(o + (size_t)K * m.tw[l] * m.th[l] * sizeof(DepthBound));
+        m.off_O[l] = o; o = up(o + (size_t)K * m.tw[l] * m.th[l] * sizeof(DepthBound));
     }
-    m.off_g = o; o = up(o + (size_t)K * 8);
+    m.off_g = o; o = up(o + (size_t)K * sizeof(DepthBound));
     m.total = K > 0 ? o : 0;
     return m;
 }
 
+#ifdef __CUDACC__
+// Depth bin of a value d >= 0 (see DepthBound); the same integer arithmetic in
+// the map build and in the slab test.
+__device__ __forceinline__ int depth_bin(float d) { return (int)(__float_as_uint(d) >> 18); }
+#endif
+
 struct FuseArgs {
     const void *dw;            // [K][H][W] packed (depth or 0, weight): float2 or half2 (map_dtype)
     int map_dtype;
-    const float2 *ob[3];       // O_l overlapping 2x2-tile bounds, levels 3, 5, 7: [K][th][tw]
-    const float2 *tg;          // whole-view bounds [K]
-    int tw[3], th[3];
+    const DepthBound *ob[kBoundLevels];  // O_l overlapping 2x2-tile bounds, levels 4..7: [K][th][tw]
+    const DepthBound *tg;                // whole-view bounds [K]
+    int tw[kBoundLevels], th[kBoundLevels];
     int K, W, H;               // input views and their size
     int Wt, Ht;                // target size
     int D;

@@ -11,12 +11,16 @@ import numpy as np
 import pytest
 import torch
 
-from gpu_util import MAX_AMBIGUOUS, to_dev, u32
+from gpu_util import to_dev, u32
 
 pytestmark = pytest.mark.gpu
 
 COLOR_ATOL = 2e-5
 DEPTH_RTOL = 2e-5
+# The render's own flag (an alpha or a transmittance within 1e-4 relative of a threshold of
+# the rasterisation rules), not the fusion's: small magnified cases put a few pixels per
+# thousand there.
+MAX_FLAGGED = 1e-2
 
 
 @pytest.fixture(scope="module")
@@ -43,7 +47,7 @@ def _compare(col, dep, ref, pixels=None):
     derr = np.abs(d - rd)
     bad = ok & (derr > DEPTH_RTOL * np.abs(rd))
     assert not bad.any(), f"depth differs at {bad.sum()} px, worst {derr[bad].max():.3e}"
-    assert amb.mean() < MAX_AMBIGUOUS
+    assert amb.mean() < MAX_FLAGGED
     return amb.mean()
 
 
