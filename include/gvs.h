@@ -488,9 +488,12 @@ GVS_API gvs_status gvs_forward_splat(const gvs_camera *in_cams, const void *in_d
  *   - Arguments, outputs and errors are those of gvs_forward_splat without the
  *     workspace.  Targets of more than 2,097,152 pixels (e.g. larger than
  *     1920 x 1080) are rejected with GVS_ERR_INVALID_ARG before anything runs.
- *   - The first call on a device looks up the array's device address with
- *     cudaGetSymbolAddress (with that device current); make that first call
- *     before any stream capture.
+ *   - The array exists once per CUDA context that loads the library (the
+ *     device's primary context, a context the caller created, the primary
+ *     context created again after cudaDeviceReset).  The first call in a
+ *     context looks up that context's copy with cudaGetSymbolAddress (with the
+ *     context current) and caches it under the driver's unique context id;
+ *     make that first call before any stream capture.
  *   - It calls no cudaMalloc, cudaFree or allocating library routine.
  *   - Every call shares the one array and clears it before use.  Calls whose
  *     work overlaps on the GPU (other streams, other host threads) race on it:

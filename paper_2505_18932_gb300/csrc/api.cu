@@ -677,34 +677,79 @@ namespace {
 constexpr size_t kNoAllocKeys = size_t(1) << 21;  // 16 MiB of 64-bit keys: targets up to 2,097,152 pixels
 static __device__ __align__(256) unsigned long long g_noalloc_keys[kNoAllocKeys];
 
-// Device address of g_noalloc_keys on the current device, looked up once per
-// device.  In host code the symbol is only a host-side handle, never a device
-// address, so it must not be passed to a kernel directly.
-unsigned long long *noalloc_keys_on_current_device(gvs_status *st) {
+// Device address of g_noalloc_keys in the calling thread's current CUDA
+// context.  In host code the symbol is only a host-side handle, never a device
+// address, so it must not be passed to a kernel directly.  A module, and with
+// it the array, is loaded per context: the primary context of a device, a
+// context a host application created itself, or the primary context created
+// again after a cudaDeviceReset each have their own copy at their own address.
+// The lookup is therefore cached per context, keyed by the driver's context id
+// (unique for the life of the process, never reused), not by device ordinal.
+// The two driver calls are fetched through the runtime, so the library does not
+// link the driver library itself.
+typedef int (*ctx_get_current_fn)(void **ctx);
+typedef int (*ctx_get_id_fn)(void *ctx, unsigned long long *id);
+
+bool current_context_id(unsigned long long *id) {
+    static std::once_flag once;
+    static ctx_get_current_fn get_current = nullptr;
+    static ctx_get_id_fn get_id = nullptr;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<ctx_get_current_fn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<ctx_get_id_fn>(f);
+    });
+    if (!get_current || !get_id) return false;
+    void *ctx = nullptr;
+    if (get_current(&ctx) != 0 || !ctx) return false;
+    return get_id(ctx, id) == 0;
+}
+
+unsigned long long *noalloc_keys_on_current_context(gvs_status *st) {
+    constexpr int kSlots = 64;
     static std::mutex mu;
-    static unsigned long long *addr[64] = {nullptr};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) {
-        *st = fail(GVS_ERR_DEVICE, "splat (no-alloc): cudaGetDevice: %s", cudaGetErrorString(e));
-        return nullptr;
-    }
-    if (dev < 0 || dev >= 64) {
-        *st = fail(GVS_ERR_DEVICE, "splat (no-alloc): device index %d out of range", dev);
-        return nullptr;
-    }
+    static unsigned long long ids[kSlots] = {0};
+    static unsigned long long *addr[kSlots] = {nullptr};
+    static int next = 0;
+    unsigned long long id = 0;
     std::lock_guard<std::mutex> lock(mu);
-    if (!addr[dev]) {
+    if (!current_context_id(&id)) {
+        // no context is current yet: the runtime binds the device's primary
+        // context on its first call, so look the array up (which does that) and ask again
         void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_keys);
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_keys);
         if (e != cudaSuccess || !p) {
             *st = fail(GVS_ERR_CUDA, "splat (no-alloc): cudaGetSymbolAddress: %s", cudaGetErrorString(e));
             return nullptr;
         }
-        addr[dev] = reinterpret_cast<unsigned long long *>(p);
+        if (!current_context_id(&id)) {
+            *st = fail(GVS_ERR_DEVICE, "splat (no-alloc): cannot identify the current CUDA context");
+            return nullptr;
+        }
     }
+    for (int i = 0; i < kSlots; ++i)
+        if (addr[i] && ids[i] == id) {
+            *st = GVS_OK;
+            return addr[i];
+        }
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_keys);
+    if (e != cudaSuccess || !p) {
+        *st = fail(GVS_ERR_CUDA, "splat (no-alloc): cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        return nullptr;
+    }
+    // a context destroyed since keeps its entry until it is the oldest of kSlots others
+    ids[next] = id;
+    addr[next] = reinterpret_cast<unsigned long long *>(p);
+    next = (next + 1) % kSlots;
     *st = GVS_OK;
-    return addr[dev];
+    return reinterpret_cast<unsigned long long *>(p);
 }
 
 }  // namespace
@@ -721,7 +766,7 @@ extern "C" gvs_status gvs_forward_splat_noalloc(const gvs_camera *in_cams, const
                     "splat (no-alloc): target has %lld pixels; this entry point holds a z-buffer for at most %zu",
                     (long long)pixels, kNoAllocKeys);
     gvs_status st = GVS_OK;
-    unsigned long long *keys = noalloc_keys_on_current_device(&st);
+    unsigned long long *keys = noalloc_keys_on_current_context(&st);
     if (!keys) return st;
     return gvs_forward_splat(in_cams, in_depths, in_rgba, n_views, target, params, fused_depth, winner,
                              warped_rgba, warped_depth, alpha, guided, keys, kNoAllocKeys * sizeof(unsigned long long),
