@@ -317,6 +317,15 @@ def run_gvs(args, rank, local_rank, world):
     forms["mixed_precision_16x1080p_stereo"] = mixed_form(device, steps=min(K, 10))
     forms.update(time_batched(device, steps=min(K, 20)))
     wd = configs.diff_640x360()
+    w1 = configs.plain_320x240()
+    forms["cfg1_plain_320x240"] = form_line(
+        "cfg1_plain_320x240", w1, time_form(Pipeline(w1, render_frames(w1, range(RING)), device), steps=min(K, 100)),
+        "4 x 320x240 inputs on a 30 degree arc, D = 64 on [0.5, 5]: refine, weight map, fusion, splat of the 4 views")
+    w2 = configs.video_8x720p()
+    forms["cfg2_video_8x720p"] = form_line(
+        "cfg2_video_8x720p", w2, time_form(Pipeline(w2, render_frames(w2, range(RING)), device), steps=min(K, 100)),
+        "one frame of the 8 x 1280x720 video (2x4 rig, sphere moving 1 cm per frame), D = 128: refine, weight map, "
+        "fusion, splat of the 8 views")
     forms["fwd_bwd_640x360"] = form_line("fwd_bwd_640x360", wd,
                                          time_form(FwdBwd(wd, render_frames(wd, [0, 1]), device), steps=min(K, 50)),
                                          "the differentiable workload: 4 x 640x360, D = 96, forward + backward")
@@ -363,7 +372,9 @@ def run_gvs(args, rank, local_rank, world):
         "wall_s": round(wall, 3),
     }
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(w, frames_np, budget_s=15.0)
+        line["cpu_baseline"] = cpu_baseline(w, frames_np, gpu_values={
+            "plain_320x240": forms["cfg1_plain_320x240"]["value"],
+            "diff_640x360_fwd_bwd": forms["fwd_bwd_640x360"]["value"]})
     print(json.dumps(line), flush=True)
 
 
@@ -883,77 +894,171 @@ def run_e2e(pipe, frames_np, steps):
 
 # ------------------------------------------------------------ CPU oracle --
 
-def oracle_step(w, frames_np, i, n_pixels, seed, threads):
-    """One bounded-sample step of the FP64 oracle on frame i of the ring.
-    Returns (seconds, estimated seconds for the full frame)."""
+ORACLE_SAMPLE_PIXELS = 8192  # target pixels per bounded oracle step (4 source rows of 1080 in every view)
+
+
+def _crop_rows(cams, rows):
+    return [c.__class__(**{**c.__dict__, "height": rows}) for c in cams]
+
+
+def oracle_sample_step(w, frames_np, i, n_pixels, seed, threads):
+    """One bounded step of the FP64 oracle on frame i of the ring: every stage on the same
+    fraction f of the frame.  Fusion on n_pixels random target pixels of each target
+    (f = n_pixels / (Wt Ht)); refinement and the splat on a band of round(f H) source rows of
+    every view.  Returns (seconds, f, {stage: seconds}).  Fusion uses `threads` threads; the
+    oracle's refinement and splat are single-threaded."""
     import oracle
     cur, prev = frames_np[i % len(frames_np)], frames_np[(i - 1) % len(frames_np)]
-    rgba_t = cur[0].view(np.uint8).reshape(cur[0].shape + (4,))
-    rgba_p = prev[0].view(np.uint8).reshape(prev[0].shape + (4,))
-    tgt = w.targets[0]
+    H = w.inputs[0].height
+    tgts = w.targets_at(0)
+    Wt, Ht = tgts[0].width, tgts[0].height
+    f = n_pixels / (Wt * Ht)
+    band = max(1, int(round(H * f)))
+    f = band / H  # the same fraction everywhere: the band fixes it
+    n_pixels = max(1, int(round(f * Wt * Ht)))
+    rgba_t = cur[0].view(np.uint8).reshape(cur[0].shape + (4,))[:, :band]
+    rgba_p = prev[0].view(np.uint8).reshape(prev[0].shape + (4,))[:, :band]
     t0 = time.perf_counter()
-    state, _ = oracle.refine_depth(rgba_t, rgba_p, cur[1], prev[1], w.tau)
+    oracle.refine_depth(np.ascontiguousarray(rgba_t), np.ascontiguousarray(rgba_p),
+                        np.ascontiguousarray(cur[1][:, :band]), np.ascontiguousarray(prev[1][:, :band]), w.tau)
     t1 = time.perf_counter()
     rng = np.random.default_rng(seed)
-    pix = np.stack([rng.integers(0, tgt.width, n_pixels), rng.integers(0, tgt.height, n_pixels)], 1).astype(np.int32)
-    r = oracle.fuse_depth(w.inputs, state, tgt, w.num_samples, w.z_near, w.z_far, w.mu, pixels=pix, threads=threads)
+    for tgt in tgts:
+        pix = np.stack([rng.integers(0, tgt.width, n_pixels), rng.integers(0, tgt.height, n_pixels)],
+                       1).astype(np.int32)
+        oracle.fuse_depth(w.inputs, cur[1], tgt, w.num_samples, w.z_near, w.z_far, w.mu, pixels=pix,
+                          threads=threads)
     t2 = time.perf_counter()
-    # the splat runs on a band of source rows (the same fraction of every view)
-    band = max(1, int(round(w.inputs[0].height * n_pixels / (tgt.width * tgt.height))))
-    crop = [c.__class__(**{**c.__dict__, "height": band}) for c in w.inputs]
-    fused_band = np.zeros((tgt.height, tgt.width))
-    oracle.forward_splat(crop, np.ascontiguousarray(state[:, :band]), np.ascontiguousarray(cur[0][:, :band]),
-                         tgt, mu_guide=w.mu, fused=fused_band)
+    crop = _crop_rows(w.inputs, band)
+    for tgt in tgts:
+        oracle.forward_splat(crop, np.ascontiguousarray(cur[1][:, :band]), np.ascontiguousarray(cur[0][:, :band]),
+                             tgt, mu_guide=w.mu, fused=np.zeros((tgt.height, tgt.width)))
     t3 = time.perf_counter()
-    full = (t1 - t0) + (t2 - t1) * (tgt.width * tgt.height / n_pixels) + (t3 - t2) * (w.inputs[0].height / band)
-    return t3 - t0, full
+    return t3 - t0, f, {"refine": t1 - t0, "fuse": t2 - t1, "splat": t3 - t2}
 
 
-def cpu_baseline(w, frames_np, budget_s=15.0):
+def oracle_full_plain(w, threads):
+    """Full frame of a single-target workload: fusion of every target pixel and the splat of
+    every source pixel (no refinement: one frame)."""
+    import oracle
+    rgb, d = w.render_inputs(0)
+    tgt = w.targets[0]
+    t0 = time.perf_counter()
+    r = oracle.fuse_depth(w.inputs, d, tgt, w.num_samples, w.z_near, w.z_far, w.mu, threads=threads)
+    t1 = time.perf_counter()
+    oracle.forward_splat(w.inputs, d, np.ascontiguousarray(rgb).view(np.uint32)[..., 0], tgt, mu_guide=w.mu,
+                         fused=r["depth"])
+    t2 = time.perf_counter()
+    return t2 - t0, {"fuse": t1 - t0, "splat": t2 - t1}
+
+
+def oracle_full_fwd_bwd(w, threads):
+    """Full frame of the differentiable workload: fusion and its adjoint, the differentiable
+    colour splat and its adjoint (upstream gradients of ones)."""
+    import oracle
+    rgb, d = w.render_inputs(0)
+    tgt = w.targets[0]
+    col = rgb.astype(np.float64) / 255.0
+    t0 = time.perf_counter()
+    oracle.fuse_depth(w.inputs, d, tgt, w.num_samples, w.z_near, w.z_far, w.mu, threads=threads)
+    t1 = time.perf_counter()
+    oracle.fuse_depth_grad(w.inputs, d, tgt, w.num_samples, w.z_near, w.z_far, w.mu,
+                           np.ones((tgt.height, tgt.width)))
+    t2 = time.perf_counter()
+    ss = oracle.soft_splat(w.inputs, d, col, tgt, mu_band=w.mu)
+    oracle.soft_splat_grad(w.inputs, d, col, tgt, np.ones(ss["color"].shape), np.ones(ss["depth"].shape),
+                           mu_band=w.mu)
+    t3 = time.perf_counter()
+    return t3 - t0, {"fuse": t1 - t0, "fuse_adjoint": t2 - t1, "soft_splat_fwd_bwd": t3 - t2}
+
+
+def _mpix(px, s):
+    return round(px / s / 1e6, 6)
+
+
+def cpu_baseline(w, frames_np, gpu_values=None, budget_s=8.0):
+    """The FP64 oracle as it stands, timed on this host's cores: the headline on bounded
+    samples (every stage on the same fraction of the frame, measured, not projected), and
+    whole frames of the 4 x 320x240 workload and of the 4 x 640x360 differentiable workload,
+    each at 1 thread and at all cores (only the oracle's fusion is threaded)."""
+    from synth import configs
     threads = os.cpu_count() or 1
-    n_pixels = 8192
-    spent, est = 0.0, []
-    i = 1
-    while spent < budget_s and i < 50:
-        s, full = oracle_step(w, frames_np, i, n_pixels, seed=i, threads=threads)
-        spent += s
-        est.append(full)
-        i += 1
-    full = statistics.median(est)
+    n_pixels = ORACLE_SAMPLE_PIXELS
     tpx = w.targets[0].width * w.targets[0].height
-    return {"value": round(tpx / full / 1e6, 6), "unit": "target Mpix/s", "cores": threads, "kind": "oracle",
-            "sample": (f"{len(est)} frames; per frame: full-frame refine, fuse on {n_pixels} random target px "
-                       f"({threads} threads), splat on a band of source rows of the same fraction (1 thread); "
-                       f"scaled to the full frame")}
+    out = {"kind": "oracle", "unit": "target Mpix/s", "cores": threads, "nproc": threads,
+           "threads_by_stage": {"refine": 1, "fuse": threads, "fuse_adjoint": 1, "splat": 1, "soft_splat": 1}}
+    head = {}
+    for th in (threads, 1):
+        spent, steps, px, stages = 0.0, 0, 0.0, {}
+        i = 1
+        while spent < (budget_s if th == threads else budget_s / 4) and steps < 40:
+            s, f, st = oracle_sample_step(w, frames_np, i, n_pixels, seed=i, threads=th)
+            spent += s
+            px += f * tpx
+            steps += 1
+            i += 1
+            for k, v in st.items():
+                stages[k] = stages.get(k, 0.0) + v
+        head[f"threads_{th}"] = {"value": _mpix(px, spent), "measured_s": round(spent, 3), "steps": steps,
+                                 "fraction_per_step": round(f, 6),
+                                 "stage_s": {k: round(v, 3) for k, v in stages.items()}}
+    out["value"] = head[f"threads_{threads}"]["value"]
+    out["headline"] = head
+    out["sample"] = (f"{w.name}: per step every stage on the same fraction ({head[f'threads_{threads}']['fraction_per_step']:.4f}) "
+                     f"of one frame: refinement and splat on a band of source rows of each view, fusion on as many "
+                     f"random target pixels; value = target pixels processed / measured seconds")
+    full = {}
+    for name, fn, wl in (("plain_320x240", oracle_full_plain, configs.plain_320x240()),
+                         ("diff_640x360_fwd_bwd", oracle_full_fwd_bwd, configs.diff_640x360())):
+        px = wl.targets[0].width * wl.targets[0].height
+        rec = {}
+        for th in (1, threads):
+            s, st = fn(wl, th)
+            rec[f"threads_{th}"] = {"value": _mpix(px, s), "s": round(s, 3),
+                                    "stage_s": {k: round(v, 3) for k, v in st.items()}}
+        if gpu_values and name in gpu_values:
+            rec["gpu_value"] = gpu_values[name]
+        full[name] = rec
+    out["full_frames"] = full
+    return out
 
 
 def run_reference(args, rank, world):
+    """The FP64 oracle on this host's cores, on the benchmark's workload and metric: each step
+    is one bounded sample of a frame (every stage on the same fraction; see oracle_sample_step),
+    the same sample as the GPU arm's cpu_baseline (about half a second per step on 8 cores)."""
     if rank != 0:
         return
     from synth import configs
     w = configs.headline_8x1080p()
     frames_np = render_frames(w, list(range(RING)))
     threads = os.cpu_count() or 1
-    n_pixels = 2048
-    for i in range(max(3, args.warmup)):
-        oracle_step(w, frames_np, i + 1, n_pixels, seed=i, threads=threads)
-    t0 = time.perf_counter()
-    ests = []
-    for i in range(args.steps):
-        _, full = oracle_step(w, frames_np, i + 1, n_pixels, seed=100 + i, threads=threads)
-        ests.append(full)
-    wall = time.perf_counter() - t0
-    ms = statistics.mean(ests) * 1e3
+    # the same bounded sample per step as the cpu_baseline of the GPU arm, so that the two agree
+    n_pixels = ORACLE_SAMPLE_PIXELS
     tpx = w.targets[0].width * w.targets[0].height
-    value = tpx / (ms * 1e-3) / 1e6
+    for i in range(max(3, args.warmup)):
+        oracle_sample_step(w, frames_np, i + 1, n_pixels, seed=i, threads=threads)
+    t0 = time.perf_counter()
+    px, f = 0.0, 0.0
+    for i in range(args.steps):
+        _, f, _ = oracle_sample_step(w, frames_np, i + 1, n_pixels, seed=100 + i, threads=threads)
+        px += f * tpx
+    wall = time.perf_counter() - t0
+    ms = wall * 1e3 / max(args.steps, 1)
+    value = px / wall / 1e6
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "target Mpix/s", "n_gpus": world,
             "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(ms, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "inputs": "8x1920x1080", "target": "1920x1080",
-                       "num_samples": w.num_samples, "parallelism": "cpu"},
+                       "num_samples": w.num_samples, "parallelism": "cpu",
+                       "step": f"a bounded sample: {f:.5f} of a frame in every stage",
+                       "projected_ms_per_full_frame": round(ms / max(f, 1e-12), 1)},
             "cpu_baseline": {"value": round(value, 6), "unit": "target Mpix/s", "cores": threads, "kind": "oracle",
-                             "sample": (f"per step: full-frame refine, fuse on {n_pixels} random target px, splat on "
-                                        "a band of source rows of the same fraction; time scaled to the full frame")},
+                             "threads_by_stage": {"refine": 1, "fuse": threads, "splat": 1},
+                             "sample": (f"per step every stage on the same fraction ({f:.5f}) of one frame: "
+                                        "refinement and splat on a band of source rows of each view, fusion on as "
+                                        "many random target pixels; value = target pixels processed / measured "
+                                        "seconds")},
             "e2e": {"value": round(value, 6), "unit": "target Mpix/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},
             "wall_s": round(wall, 3)}
