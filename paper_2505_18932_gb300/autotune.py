@@ -18,7 +18,7 @@ import torch
 
 CACHE_PATH = os.environ.get("GVS_AUTOTUNE_CACHE",
                             os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json"))
-VARIANTS = (0, 1, 2, 3)
+VARIANTS = (0, 1, 2, 3, 4, 5)
 _lock = threading.Lock()
 
 

@@ -374,7 +374,7 @@ int bundle_count(int Wt, int Ht, int K, int variant) {
     int bx = 8, by = 4;
     if (K > 4 && K <= 16) {
         if (variant == 2) { bx = 16; by = 2; }
-        else if (variant == 3) { bx = 4; by = 8; }
+        else if (variant == 3 || variant == 4) { bx = 4; by = 8; }
     }
     return ((Wt + bx - 1) / bx) * ((Ht + by - 1) / by);
 }

@@ -96,23 +96,29 @@ constexpr int SKIP_COOL = 3;    // samples evaluated after both slab tests fail,
 //   lshort  : samples per segment in the second test when the first fails
 //   full    : the call has exactly KMAX views, so the per-view guard k < K
 //             compiles away and the unrolled views form one block of code
-template <int BX_, int BY_, int LLONG_, int LSHORT_, bool FULL_ = false>
+//   spt     : samples each lane evaluates at once in a run of evaluations
+//             (1 or 2: two keep twice the gathers in flight)
+template <int BX_, int BY_, int LLONG_, int LSHORT_, bool FULL_ = false, int SPT_ = 1>
 struct Tile {
-    static constexpr int bx = BX_, by = BY_, llong = LLONG_, lshort = LSHORT_;
+    static constexpr int bx = BX_, by = BY_, llong = LLONG_, lshort = LSHORT_, spt = SPT_;
     static constexpr bool full = FULL_;
     static_assert(bx * by == 32, "a bundle is one warp");
     static_assert(llong >= 1 && lshort >= 1, "skip lengths must advance the march");
+    static_assert(spt == 1 || spt == 2, "one or two samples at once");
 };
 template <typename T>
 struct FullTile;
-template <int BX_, int BY_, int LLONG_, int LSHORT_, bool FULL_>
-struct FullTile<Tile<BX_, BY_, LLONG_, LSHORT_, FULL_>> {
-    using type = Tile<BX_, BY_, LLONG_, LSHORT_, true>;
+template <int BX_, int BY_, int LLONG_, int LSHORT_, bool FULL_, int SPT_>
+struct FullTile<Tile<BX_, BY_, LLONG_, LSHORT_, FULL_, SPT_>> {
+    using type = Tile<BX_, BY_, LLONG_, LSHORT_, true, SPT_>;
 };
 using Tile0 = Tile<8, 4, 8, 2>;
 using Tile1 = Tile<8, 4, 16, 4>;
 using Tile2 = Tile<16, 2, 8, 2>;
 using Tile3 = Tile<4, 8, 8, 2>;
+using Tile4 = Tile<4, 8, 8, 2, false, 2>;
+using Tile5 = Tile<8, 4, 8, 2, false, 2>;
+constexpr int kFuseVariants = 6;
 
 struct Ray {
     float ax, ay, az;
@@ -228,6 +234,49 @@ __device__ __forceinline__ void evaluate_sample(const FuseArgs &a, const Ray (&r
     }
 }
 
+// Samples zs0 and zs1 at once (each exactly as evaluate_sample computes it): the
+// two samples' gathers of a view are independent, so a lane keeps both in flight.
+template <int KMAX, typename MT, bool FULL = false, bool PLANES = true>
+__device__ __forceinline__ void evaluate_sample2(const FuseArgs &a, const Ray (&ray)[KMAX], float zs0, float zs1,
+                                                 float &S0, float &W0, float &S1, float &W1) {
+    const size_t plane = (size_t)a.W * a.H;
+    S0 = W0 = S1 = W1 = 0.0f;
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+        if (FULL || k < a.K) {
+            const MT *plane_k = PLANES ? reinterpret_cast<const MT *>(a.vb[k])
+                                       : reinterpret_cast<const MT *>(a.dw) + (size_t)k * plane;
+            float hz[2], pd[2], pw[2];
+            bool in[2];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const float zs = j ? zs1 : zs0;
+                hz[j] = __fmaf_rn(zs, ray[k].az, a.xf[k].b[2]);
+                const float hx = __fmaf_rn(zs, ray[k].ax, a.xf[k].b[0]);
+                const float hy = __fmaf_rn(zs, ray[k].ay, a.xf[k].b[1]);
+                int u, v;
+                nearest_pixel(hx, hy, hz[j], u, v);
+                in[j] = hz[j] > 1e-6f && (unsigned)u < (unsigned)a.W && (unsigned)v < (unsigned)a.H &&
+                        GVS_IN_BOUNDS((size_t)k * plane + (size_t)v * a.W + u, (size_t)a.K * plane,
+                                      GVS_SITE_FUSE_MAP);
+                float2 p = make_float2(0.0f, 0.0f);
+                if (in[j]) p = load_map(plane_k + (v * a.W + u));
+                pd[j] = p.x;
+                pw[j] = p.y;
+            }
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const float sdf = (pd[j] - hz[j]) * a.inv_mu;
+                const float w = (in[j] && sdf >= -1.0f) ? pw[j] : 0.0f;
+                float &S = j ? S1 : S0;
+                float &Wsum = j ? W1 : W0;
+                S = fmaf(w, fminf(sdf, 1.0f), S);
+                Wsum += w;
+            }
+        }
+    }
+}
+
 // One warp per bundle of BX x BY target pixels.  The warp marches one sample
 // index s for all its rays: cooperative slab tests (lane = view x segment,
 // 32 / KMAX consecutive segments at once) skip runs of samples that hold no
@@ -337,35 +386,49 @@ __device__ __forceinline__ void march_bundle(const FuseArgs &a, int bundle, int 
             shorter = false;
             cool = SKIP_COOL;
         }
-        const float zs = __fmaf_rn((float)s, a.dz, a.zn);
         // every lane evaluates (the warp issues the sample anyway); lanes still marching record it
-        float S, Wsum;
-        evaluate_sample<KMAX, MT, T::full, PLANES>(a, ray, zs, S, Wsum);
-        if (!done) {
-            const float Wv = Wsum;
-            if (TMP && tw > 0.0f) {
-                const float sdf = (td - zs) * a.inv_mu;
-                if (sdf >= -1.0f) {
-                    S = fmaf(tw, fminf(sdf, 1.0f), S);
-                    Wsum += tw;
-                }
-            }
-            if (a.normalize && Wsum > 0.0f) S = S / Wsum;
-            if (have_prev && W_prev > 0.0f && Wsum > 0.0f && S_prev > 0.0f && S <= 0.0f) {
-                const float t = S_prev / (S_prev - S);
-                out = z_prev + (zs - z_prev) * t;
-                if (TMP) wview = Wv_prev + t * (Wv - Wv_prev);
-                idx = s - 1;
-                done = true;
-            }
-            S_prev = S;
-            W_prev = Wsum;
-            Wv_prev = Wv;
-            z_prev = zs;
+        const int nev = (T::spt == 2 && cool >= 2 && s + 1 < a.D) ? 2 : 1;
+        const float zs0 = __fmaf_rn((float)s, a.dz, a.zn);
+        float Se[2], We[2], ze[2];
+        ze[0] = zs0;
+        if (T::spt == 2 && nev == 2) {
+            ze[1] = __fmaf_rn((float)(s + 1), a.dz, a.zn);
+            evaluate_sample2<KMAX, MT, T::full, PLANES>(a, ray, ze[0], ze[1], Se[0], We[0], Se[1], We[1]);
+        } else {
+            evaluate_sample<KMAX, MT, T::full, PLANES>(a, ray, zs0, Se[0], We[0]);
         }
-        have_prev = true;
-        ++s;
-        if (cool > 0) --cool;
+#pragma unroll
+        for (int e = 0; e < T::spt; ++e) {
+            if (e < nev) {
+                const float zs = ze[e];
+                float S = Se[e], Wsum = We[e];
+                if (!done) {
+                    const float Wv = Wsum;
+                    if (TMP && tw > 0.0f) {
+                        const float sdf = (td - zs) * a.inv_mu;
+                        if (sdf >= -1.0f) {
+                            S = fmaf(tw, fminf(sdf, 1.0f), S);
+                            Wsum += tw;
+                        }
+                    }
+                    if (a.normalize && Wsum > 0.0f) S = S / Wsum;
+                    if (have_prev && W_prev > 0.0f && Wsum > 0.0f && S_prev > 0.0f && S <= 0.0f) {
+                        const float t = S_prev / (S_prev - S);
+                        out = z_prev + (zs - z_prev) * t;
+                        if (TMP) wview = Wv_prev + t * (Wv - Wv_prev);
+                        idx = s - 1;
+                        done = true;
+                    }
+                    S_prev = S;
+                    W_prev = Wsum;
+                    Wv_prev = Wv;
+                    z_prev = zs;
+                }
+                have_prev = true;
+                ++s;
+                if (cool > 0) --cool;
+            }
+        }
     }
     if (inside) {
         const size_t o = (size_t)j * a.Wt + i;
@@ -391,6 +454,8 @@ void by_variant(int K, int variant, Args... args) {
             case 1: full_or_not<KMAX, MT, F, Tile1>(K, args...); return;
             case 2: full_or_not<KMAX, MT, F, Tile2>(K, args...); return;
             case 3: full_or_not<KMAX, MT, F, Tile3>(K, args...); return;
+            case 4: full_or_not<KMAX, MT, F, Tile4>(K, args...); return;
+            case 5: full_or_not<KMAX, MT, F, Tile5>(K, args...); return;
             default: break;
         }
     }

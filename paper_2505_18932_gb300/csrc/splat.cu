@@ -286,6 +286,22 @@ __global__ void __launch_bounds__(256) splat_resolveP(const SplatArgs a, int k0)
     }
 }
 
+// 256-bit global accesses (sm_100 and later): the address must be 32-byte aligned.
+__device__ __forceinline__ void ld256(const unsigned long long *p, unsigned long long (&v)[4]) {
+    asm volatile("ld.global.v4.u64 {%0, %1, %2, %3}, [%4];" : "=l"(v[0]), "=l"(v[1]), "=l"(v[2]), "=l"(v[3]) : "l"(p));
+}
+__device__ __forceinline__ void st256_ones(unsigned long long *p) {
+    const unsigned long long o = ~0ull;
+    asm volatile("st.global.v4.u64 [%0], {%1, %1, %1, %1};" ::"l"(p), "l"(o) : "memory");
+}
+__device__ __forceinline__ void st256_cs(void *p, const uint32_t (&v)[8]) {
+    asm volatile("st.global.cs.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(v[0]), "r"(v[1]),
+                 "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
+
+inline bool aligned_to(const void *p, uintptr_t a) { return ((uintptr_t)p % a) == 0; }
+
 // ---------------------------------------------------------------------------
 // Differentiable colour splat.  The hard z-buffer (scatter above) fixes the
 // winner's depth z_w per target pixel; every covering source q inside the
@@ -396,6 +412,94 @@ __global__ void __launch_bounds__(256) soft_resolve4(const SplatArgs a, int k0) 
     }
 }
 
+__device__ __forceinline__ void ld256f(const float4 *p, float4 &x, float4 &y) {
+    asm volatile("ld.global.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=f"(x.x), "=f"(x.y), "=f"(x.z), "=f"(x.w), "=f"(y.x), "=f"(y.y), "=f"(y.z), "=f"(y.w)
+                 : "l"(p));
+}
+__device__ __forceinline__ void st256_zero(void *p) {
+    const unsigned long long z = 0ull;
+    asm volatile("st.global.v4.u64 [%0], {%1, %1, %1, %1};" ::"l"(p), "l"(z) : "memory");
+}
+__device__ __forceinline__ void st256f_cs(float4 *p, const float4 &x, const float4 &y) {
+    asm volatile("st.global.cs.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(x.x), "f"(x.y),
+                 "f"(x.z), "f"(x.w), "f"(y.x), "f"(y.y), "f"(y.z), "f"(y.w)
+                 : "memory");
+}
+
+// Eight consecutive target pixels per thread with 32-byte accesses (20 memory
+// instructions for 8 pixels instead of 40).  Needs Wt * Ht divisible by 8, the
+// keys, accumulators, winner, depth, weight-sum and colour arrays 32-byte aligned
+// and alpha 8-byte aligned (the caller checks).  Grid (ceil(Wt Ht / 2048), views).
+__global__ void __launch_bounds__(256) soft_resolve_wide(const SplatArgs a, int k0) {
+    const int64_t HWt = (int64_t)a.Wt * a.Ht;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int)(HWt / 8)) return;
+    const int kk = blockIdx.y;
+    const int k = k0 + kk;
+    unsigned long long *slot = a.keys + (size_t)kk * HWt + (size_t)t * 8;
+    float4 *acc = a.acc + (size_t)kk * HWt + (size_t)t * 8;
+    unsigned long long kv[8];
+    {
+        unsigned long long lo[4], hi[4];
+        ld256(slot, lo);
+        ld256(slot + 4, hi);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            kv[q] = lo[q];
+            kv[4 + q] = hi[q];
+        }
+    }
+    float4 sm[8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) ld256f(acc + 2 * q, sm[2 * q], sm[2 * q + 1]);
+    st256_ones(slot);  // ready for the next group of views
+    st256_ones(slot + 4);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) st256_zero(acc + 2 * q);
+    bool h[8];
+    int32_t w[8];
+    float z[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) decode(kv[q], h[q], w[q], z[q]);
+    const size_t o = (size_t)k * HWt + (size_t)t * 8;
+    uint32_t v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = (uint32_t)w[q];
+    st256_cs(a.winner + o, v);
+    if (a.warped_depth) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = __float_as_uint(z[q]);
+        st256_cs(a.warped_depth + o, v);
+    }
+    if (a.alpha) {
+        unsigned long long m = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) m |= (unsigned long long)h[q] << (8 * q);
+        __stcs(reinterpret_cast<unsigned long long *>(a.alpha + o), m);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = __float_as_uint(sm[q].w);
+    st256_cs(a.wsum + o, v);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        float4 c[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const float4 x = sm[2 * q + e];
+            const float r = (h[2 * q + e] && x.w > 0.0f) ? 1.0f / x.w : 0.0f;
+            c[e] = make_float4(x.x * r, x.y * r, x.z * r, 0.0f);
+        }
+        st256f_cs(a.out_color + o + 2 * q, c[0], c[1]);
+    }
+}
+
+inline bool wide_soft_resolve_ok(const SplatArgs &a, int64_t HWt) {
+    return HWt % 8 == 0 && aligned_to(a.keys, 32) && aligned_to(a.acc, 32) && aligned_to(a.winner, 32) &&
+           (!a.warped_depth || aligned_to(a.warped_depth, 32)) && aligned_to(a.wsum, 32) &&
+           aligned_to(a.out_color, 32) && (!a.alpha || aligned_to(a.alpha, 8));
+}
+
 // Grid as splat_scatter over all views: blocks of 32 x 8 source pixels, z = view.
 template <typename DT, typename CT>
 __global__ void __launch_bounds__(SC_BX * SC_BY) soft_bwd(const SplatArgs a) {
@@ -448,7 +552,9 @@ void soft_groups(const SplatArgs &a, int K, cudaStream_t st) {
         const int kn = (K - k0) < slots ? (K - k0) : slots;
         splat_scatter<DT><<<scatter_grid(a.W, a.H, kn), dim3(SC_BX, SC_BY), 0, st>>>(a, k0);
         soft_accum<DT, CT><<<scatter_grid(a.W, a.H, kn), dim3(SC_BX, SC_BY), 0, st>>>(a, k0);
-        if (HWt % 4 == 0)
+        if (wide_soft_resolve_ok(a, HWt))
+            soft_resolve_wide<<<dim3((unsigned)((HWt / 8 + 255) / 256), (unsigned)kn), 256, 0, st>>>(a, k0);
+        else if (HWt % 4 == 0)
             soft_resolve4<<<dim3((unsigned)((HWt / 4 + 255) / 256), (unsigned)kn), 256, 0, st>>>(a, k0);
         else
             soft_resolve<<<dim3((unsigned)((HWt + 255) / 256), (unsigned)kn), 256, 0, st>>>(a, k0);

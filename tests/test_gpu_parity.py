@@ -127,7 +127,7 @@ def test_fuse_full_size_sampled(gvs, oracle_mod):
     _, d = w.render_inputs(1)
     dd, tgt = to_dev(d), w.targets_at(1)[0]
     f0, c0 = gvs.fuse_depth(w.inputs, dd, tgt, w.num_samples, w.z_near, w.z_far, w.mu, variant=0)
-    for v in (1, 2, 3):
+    for v in (1, 2, 3, 4, 5):
         f, c = gvs.fuse_depth(w.inputs, dd, tgt, w.num_samples, w.z_near, w.z_far, w.mu, variant=v)
         torch.cuda.synchronize()
         assert torch.equal(f.view(torch.int32), f0.view(torch.int32)) and torch.equal(c, c0), v
