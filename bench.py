@@ -393,7 +393,9 @@ def run_gvs(args, rank, local_rank, world):
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(w, frames_np, gpu_values={
             "plain_320x240": forms["cfg1_plain_320x240"]["value"],
-            "diff_640x360_fwd_bwd": forms["fwd_bwd_640x360"]["value"]})
+            "diff_640x360_fwd_bwd": forms["fwd_bwd_640x360"]["value"],
+            "video_8x720p": forms["cfg2_video_8x720p"]["value"],
+            "mixed_16x1080p": forms["mixed_precision_16x1080p_stereo"]["value"]})
     print(json.dumps(line), flush=True)
 
 
@@ -1108,6 +1110,20 @@ def cpu_baseline(w, frames_np, gpu_values=None, budget_s=8.0):
             rec["gpu_value"] = gpu_values[name]
         full[name] = rec
     out["full_frames"] = full
+    # one frame of the 8 x 720p video and of the 16 x 1080p stereo workload, on bounded samples
+    sampled = {}
+    for name, wl in (("video_8x720p", configs.video_8x720p()), ("mixed_16x1080p", configs.mixed_16x1080p())):
+        fr = render_frames(wl, [0, 1])
+        px_frame = sum(t.width * t.height for t in wl.targets_at(0))
+        rec = {}
+        for th in (1, threads):
+            s, f, st = oracle_sample_step(wl, fr, 1, 4096, seed=7, threads=th)
+            rec[f"threads_{th}"] = {"value": _mpix(f * px_frame, s), "s": round(s, 3), "fraction": round(f, 5),
+                                    "stage_s": {k: round(v, 3) for k, v in st.items()}}
+        if gpu_values and name in gpu_values:
+            rec["gpu_value"] = gpu_values[name]
+        sampled[name] = rec
+    out["sampled_frames"] = sampled
     return out
 
 

@@ -605,6 +605,17 @@ GVS_API gvs_status gvs_blend(int32_t n_views, int32_t target_width, int32_t targ
                              size_t workspace_bytes, void *stream);
 
 /*
+ * gvs_take_device_status -- a service of the library (the paper has no counterpart).
+ * Kernels that stage their inputs in shared memory with asynchronous bulk copies
+ * (the hard splat's resolve) wait for those copies a bounded time (about 2^24
+ * polls of the completion barrier); a block whose wait gives up writes none of
+ * its outputs and is counted here.  Returns the count since the last call (0 in
+ * normal operation) and clears it; read it after the stream has synchronised.
+ * Nothing traps and nothing waits without a limit.
+ */
+GVS_API uint32_t gvs_take_device_status(void);
+
+/*
  * gvs_debug_bounds_error -- a service of the library (the paper has no counterpart).
  * In a build compiled with GVS_BOUNDS_CHECK every kernel checks its computed
  * gather / scatter indices (fusion map and bound tiles, splat keys and colour

@@ -1093,6 +1093,8 @@ gvs_status gvs_fuse_depth_sphere(const gvs_camera *in_cams, const void *in_depth
 // ---------------------------------------------------------------------------
 extern "C" {
 
+uint32_t gvs_take_device_status(void) { return gvs::async_timeouts_take(); }
+
 uint64_t gvs_debug_bounds_error(void) {
     const unsigned long long r[] = {gvs::bounds_take_fuse(),   gvs::bounds_take_fuse_batch(),
                                     gvs::bounds_take_fuse_bwd(), gvs::bounds_take_sphere(),

@@ -162,6 +162,8 @@ struct SplatArgs {
 };
 
 cudaError_t launch_splat(const SplatArgs &a, int K, cudaStream_t st);
+// Bulk copies whose wait gave up since the last call (read and cleared).
+unsigned async_timeouts_take();
 cudaError_t launch_soft_splat(const SplatArgs &a, int K, cudaStream_t st);
 cudaError_t launch_temporal_weight(const void *masks, int mask_dtype, const int32_t *winner, int K, int64_t HW,
                                    int64_t HWt, const float *w_tmp_prev, const float *w_view_prev, float beta_t,

@@ -302,6 +302,132 @@ __device__ __forceinline__ void st256_cs(void *p, const uint32_t (&v)[8]) {
 
 inline bool aligned_to(const void *p, uintptr_t a) { return ((uintptr_t)p % a) == 0; }
 
+// ---- TMA bulk copies (cp.async.bulk) and the mbarrier that completes them ----
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Bulk copies that did not complete within the wait limit (a status of the
+// library, read and cleared by gvs_take_device_status).
+__device__ unsigned g_async_timeouts = 0;
+
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_store(void *dst, const void *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+// Waits for phase 0 of the barrier, at most ~2^24 polls; false when it gave up.
+__device__ __forceinline__ bool wait_phase0(uint32_t bar) {
+    for (int i = 0; i < (1 << 24); ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
+            : "=r"(ok)
+            : "r"(bar)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// The resolve with its streams moved by TMA: per block 1024 consecutive target
+// pixels of one view.  One thread loads the block's keys (and fused depths) into
+// shared memory with bulk copies completed on an mbarrier; every thread decodes
+// four pixels (strided, so a warp reads 32 consecutive keys), gathers their
+// winners' colours and writes the outputs into shared memory; one thread then
+// stores the five outputs and the reset keys (~0) with bulk copies.  Only the
+// colour gathers are per-thread global loads.  Needs Wt * Ht divisible by 16
+// and every array 16-byte aligned (the caller checks).  Grid (ceil(Wt Ht /
+// 1024), views of the group).
+constexpr int RT_PX = 1024;
+__global__ void __launch_bounds__(256) splat_resolve_tma(const SplatArgs a, int k0) {
+    __shared__ __align__(128) unsigned long long s_key[RT_PX];
+    __shared__ __align__(128) float s_fused[RT_PX];
+    __shared__ __align__(128) int32_t s_win[RT_PX];
+    __shared__ __align__(128) uint32_t s_rgba[RT_PX];
+    __shared__ __align__(128) float s_dep[RT_PX];
+    __shared__ __align__(128) uint8_t s_alpha[RT_PX];
+    __shared__ __align__(128) uint8_t s_guided[RT_PX];
+    __shared__ __align__(8) unsigned long long s_bar;
+    const int64_t HWt = (int64_t)a.Wt * a.Ht;
+    const int64_t base = (int64_t)blockIdx.x * RT_PX;
+    const int n = (int)min((int64_t)RT_PX, HWt - base);
+    const int kk = blockIdx.y;
+    const int k = k0 + kk;
+    unsigned long long *slot = a.keys + (size_t)kk * HWt + base;
+    const uint32_t bar = smem_addr(&s_bar);
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const uint32_t kb = (uint32_t)n * 8u, fb = a.guided ? (uint32_t)n * 4u : 0u;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kb + fb) : "memory");
+        bulk_load(s_key, slot, kb, bar);
+        if (a.guided) bulk_load(s_fused, a.fused + base, fb, bar);
+    }
+    if (!__syncthreads_and(wait_phase0(bar))) {  // the same answer in every thread
+        if (tid == 0) atomicAdd(&g_async_timeouts, 1u);
+        wait_phase0(bar);  // the copies may still land in this block's shared memory: give them time
+        return;
+    }
+    const uint32_t *src = a.rgba + (size_t)k * a.W * a.H;
+    uint32_t c[RT_PX / 256];
+    int32_t wv[RT_PX / 256];
+#pragma unroll
+    for (int q = 0; q < RT_PX / 256; ++q) {
+        const int p = q * 256 + tid;
+        wv[q] = -1;
+        c[q] = 0u;
+        if (p < n) {
+            bool h;
+            float z;
+            decode(s_key[p], h, wv[q], z);
+            s_key[p] = ~0ull;  // ready for the next group of views
+            s_win[p] = wv[q];
+            s_dep[p] = z;
+            s_alpha[p] = (uint8_t)h;
+            if (a.guided) s_guided[p] = (uint8_t)(h && fabsf(z - s_fused[p]) <= a.mu_guide);
+            if (a.warped_rgba && h && GVS_IN_BOUNDS(wv[q], (size_t)a.W * a.H, GVS_SITE_SPLAT_SRC))
+                c[q] = __ldg(&src[wv[q]]);
+        }
+    }
+    if (a.warped_rgba) {
+#pragma unroll
+        for (int q = 0; q < RT_PX / 256; ++q)
+            if (q * 256 + tid < n) s_rgba[q * 256 + tid] = c[q];
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // shared writes -> the bulk copies
+    __syncthreads();
+    if (tid == 0) {
+        const size_t o = (size_t)k * HWt + base;
+        bulk_store(a.winner + o, s_win, (uint32_t)n * 4u);
+        if (a.warped_rgba) bulk_store(a.warped_rgba + o, s_rgba, (uint32_t)n * 4u);
+        if (a.warped_depth) bulk_store(a.warped_depth + o, s_dep, (uint32_t)n * 4u);
+        if (a.alpha) bulk_store(a.alpha + o, s_alpha, (uint32_t)n);
+        if (a.guided) bulk_store(a.guided + o, s_guided, (uint32_t)n);
+        bulk_store(slot, s_key, (uint32_t)n * 8u);
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    }
+}
+
+inline bool aligned16(const void *p) { return ((uintptr_t)p % 16) == 0; }
+
+// The TMA resolve applies: every bulk copy starts 16-byte aligned and moves a
+// multiple of 16 bytes (1-byte planes: Wt * Ht divisible by 16).
+inline bool tma_resolve_ok(const SplatArgs &a, int64_t HWt) {
+    return HWt % 16 == 0 && aligned16(a.keys) && aligned16(a.winner) && aligned16(a.rgba) &&
+           (!a.warped_rgba || aligned16(a.warped_rgba)) && (!a.warped_depth || aligned16(a.warped_depth)) &&
+           (!a.alpha || aligned16(a.alpha)) && (!a.guided || (aligned16(a.guided) && a.fused && aligned16(a.fused)));
+}
+
 // ---------------------------------------------------------------------------
 // Differentiable colour splat.  The hard z-buffer (scatter above) fixes the
 // winner's depth z_w per target pixel; every covering source q inside the
@@ -585,7 +711,9 @@ cudaError_t launch_splat(const SplatArgs &a, int K, cudaStream_t st) {
             if (a.guide_reject) splat_scatter<float, true><<<g, b, 0, st>>>(a, k0);
             else splat_scatter<float><<<g, b, 0, st>>>(a, k0);
         }
-        if (HWt % 8 == 0)
+        if (tma_resolve_ok(a, HWt))
+            splat_resolve_tma<<<dim3((unsigned)((HWt + RT_PX - 1) / RT_PX), (unsigned)kn), 256, 0, st>>>(a, k0);
+        else if (HWt % 8 == 0)
             splat_resolveP<8><<<dim3((unsigned)((HWt / 8 + 255) / 256), (unsigned)kn), 256, 0, st>>>(a, k0);
         else if (HWt % 4 == 0)
             splat_resolveP<4><<<dim3((unsigned)((HWt / 4 + 255) / 256), (unsigned)kn), 256, 0, st>>>(a, k0);
@@ -693,5 +821,12 @@ cudaError_t launch_guided_mask(const float *warped_depth, const uint8_t *alpha, 
 }
 
 GVS_BOUNDS_TAKE_FN(bounds_take_splat)
+
+unsigned async_timeouts_take() {
+    unsigned v = 0, z = 0;
+    cudaMemcpyFromSymbol(&v, g_async_timeouts, sizeof(v));
+    cudaMemcpyToSymbol(g_async_timeouts, &z, sizeof(z));
+    return v;
+}
 
 }  // namespace gvs

@@ -147,6 +147,7 @@ API = {
                                              ctypes.POINTER(GvsCamera), ctypes.POINTER(GvsSphereParams)] +
                               [ctypes.c_void_p] * 3 + [ctypes.c_size_t, ctypes.c_void_p]),
     "gvs_debug_bounds_error": (ctypes.c_uint64, []),
+    "gvs_take_device_status": (ctypes.c_uint32, []),
     "gvs_forward_splat_noalloc": (ctypes.c_int, [ctypes.POINTER(GvsCamera), ctypes.c_void_p, ctypes.c_void_p,
                                                  ctypes.c_int32, ctypes.POINTER(GvsCamera),
                                                  ctypes.POINTER(GvsSplatParams), ctypes.c_void_p, ctypes.c_void_p,
@@ -175,6 +176,12 @@ def _check(fn, status):
     if status != GVS_OK:
         lib = load()
         raise GvsError(fn, status, lib.gvs_last_error().decode(errors="replace"))
+
+
+def take_device_status() -> int:
+    """Bulk-copy waits that gave up since the last call (0 in normal operation); read after a
+    synchronize."""
+    return int(load().gvs_take_device_status())
 
 
 def camera_struct(c) -> GvsCamera:

@@ -195,6 +195,7 @@ def _splat_case(gvs, oracle_mod, w, frame=0, footprint=True, max_hw=2.0, slots=N
     # both sides get the same FP32 fused depth; |z - fused| of two floats within a factor
     # of two is exact in FP32, so the guided mask must match everywhere
     assert np.array_equal(out["guided"].cpu().numpy(), ref["guided"])
+    assert gvs.take_device_status() == 0   # no bulk-copy wait gave up
     return ref
 
 
@@ -202,6 +203,15 @@ def _splat_case(gvs, oracle_mod, w, frame=0, footprint=True, max_hw=2.0, slots=N
 def test_splat_tiny_ragged(gvs, oracle_mod, footprint):
     from synth import configs
     _splat_case(gvs, oracle_mod, configs.tiny(70, 45, 3, 24), footprint=footprint)
+
+
+@pytest.mark.parametrize("size", [(40, 24), (200, 56), (50, 30)])
+def test_splat_partial_blocks(gvs, oracle_mod, size):
+    """Target sizes whose pixel count is a multiple of 16 but not of the 1024-pixel block of
+    the bulk-copy resolve (a partial last block: 960 and 11200 pixels), and one that is not a
+    multiple of 16 (1500: the 4-pixel vector resolve)."""
+    from synth import configs
+    _splat_case(gvs, oracle_mod, configs.tiny(size[0], size[1], 3, 24), slots=2)
 
 
 @pytest.mark.parametrize("slots", [None, 2, 4])
