@@ -409,3 +409,37 @@ def fuse_depth_sphere(in_cams, depths, target, z_near, z_far, mu, weight_const=0
     if rc != 0:
         raise ValueError("orc_fuse_depth_sphere rejected its arguments")
     return {"depth": out, "evals": ev}
+
+
+def uniform_blend_loss(color, alpha, warped_depth, fused, gt, w_l1=0.8, w_depth=0.1):
+    """Sec. 3.3's training loss on the uniform blend of the views (Eq. 4 with every
+    w_k = 1, the denominator read as the sum over the views), written out in FP64:
+      A(p) = sum_k a_k(p),  B(p) = sum_k a_k I_k(p) / A(p)   (pixels with A > 0, n of them)
+      L1 = sum_{A>0} sum_rgb |B - GT| / (3 n)
+      Dbar(p) = sum_k a_k D_k(p) / A(p) (0 where A = 0),  v(p) = [A > 0 and F(p) > 0]
+      L_Depth = sum_p v |F - Dbar| / (K H W)        (the printed 1/(HWK))
+      L = w_l1 L1 + w_depth L_Depth
+    color [K, H, W, 3 or 4] (RGB used), alpha [K, H, W] (0/1), warped_depth [K, H, W],
+    fused [H, W], gt [H, W, 3].  Returns (L, L1, L_Depth, grads) with grads the derivatives
+    d L / d I_k (= a_k g_rgb), d L / d D_k (= a_k g_d) and d L / d F, as per-pixel
+    g_rgb [H, W, 3], g_d [H, W] and g_F [H, W] (|x|' = sign(x), 0 at 0)."""
+    I = np.asarray(color, np.float64)[..., :3]
+    a = np.asarray(alpha, np.float64)
+    D = np.asarray(warped_depth, np.float64)
+    F = np.asarray(fused, np.float64)
+    G = np.asarray(gt, np.float64)
+    K, H, W = a.shape
+    A = a.sum(0)
+    cov = A > 0
+    inv = np.where(cov, 1.0 / np.maximum(A, 1.0), 0.0)
+    B = (a[..., None] * I).sum(0) * inv[..., None]
+    n = max(int(cov.sum()), 1)
+    L1 = np.abs(B - G)[cov].sum() / (3.0 * n)
+    Dbar = (a * D).sum(0) * inv
+    v = cov & (F > 0)
+    LD = np.abs(F - Dbar)[v].sum() / (K * H * W)
+    g_rgb = w_l1 * np.sign(B - G) / (3.0 * n) * inv[..., None] * cov[..., None]
+    sd = np.sign(F - Dbar) * v
+    g_d = -w_depth * sd / (K * H * W) * inv
+    g_F = w_depth * sd / (K * H * W)
+    return w_l1 * L1 + w_depth * LD, L1, LD, {"rgb": g_rgb, "depth": g_d, "fused": g_F}
