@@ -306,6 +306,11 @@ def run_gvs(args, rank, local_rank, world):
     forms["fwd_bwd_eager"] = form_line("fwd_bwd_eager", w, time_form(FwdBwd(w, frames_np[:2], device),
                                                                      steps=min(K, 30)),
                                        "the same step launched op by op from Python (autograd)")
+    forms["fwd_bwd_torch_loss"] = form_line(
+        "fwd_bwd_torch_loss", w, time_form(FwdBwd(w, frames_np[:2], device, library_loss=False).capture(),
+                                           steps=min(K, 30)),
+        "the same step with the blend and the loss written as torch operations on the splat's outputs "
+        "(one CUDA graph per frame): the per-view upstream gradients are materialised")
     w256 = type(w)(**{**w.__dict__, "num_samples": 256})
     p256 = Pipeline(w256, frames_np, device)
     f256 = form_line("headline_d256", w256, time_form(p256, steps=min(K, 100)),
@@ -434,10 +439,11 @@ class FwdBwd:
     the loss 0.8 L1(blend, ground truth) + 0.1 L_Depth (Sec. 3.3, uniform blend weights),
     and both adjoints back to the input depths and colours."""
 
-    def __init__(self, w, frames_np, device):
+    def __init__(self, w, frames_np, device, library_loss=True):
         import torch
         from paper_2505_18932_gb300 import gvs
         self.torch, self.gvs, self.w = torch, gvs, w
+        self.library_loss = library_loss
         self.tgt = w.targets[0]
         self.depth = [torch.from_numpy(d).to(device) for _, d in frames_np]
         self.color = [torch.from_numpy(np.ascontiguousarray(c).view(np.uint8).reshape(c.shape + (4,))).to(device)
@@ -445,7 +451,7 @@ class FwdBwd:
         gts = []
         for t in range(len(frames_np)):
             rgb, _ = w.render_target_gt(self.tgt, t)
-            gts.append(torch.from_numpy(np.ascontiguousarray(rgb[..., :3], np.float32)).to(device) / 255.0)
+            gts.append((torch.from_numpy(np.ascontiguousarray(rgb[..., :3], np.float32)).to(device) / 255.0).contiguous())
         self.gt = gts
         self.cfg = dict(num_samples=w.num_samples, z_near=w.z_near, z_far=w.z_far, mu=w.mu)
         self.half = False
@@ -488,6 +494,12 @@ class FwdBwd:
         d = self.depth[cur].detach().requires_grad_(True)
         c = self.color[cur].detach().requires_grad_(True)
         fused, _ = gvs.FuseDepth.apply(d, w.inputs, self.tgt, self.cfg)
+        if self.library_loss:
+            # splat, blend, loss and the per-pixel upstream gradient in the library
+            loss = gvs.SoftSplatBlendLoss.apply(d, c, fused, w.inputs, self.tgt, self.gt[cur], {"mu_band": w.mu})
+            loss.backward()
+            self.last = (d.grad, c.grad, loss.detach())
+            return
         color, wdepth, alpha = gvs.SoftSplat.apply(d, c, w.inputs, self.tgt, {"mu_band": w.mu})
         asum = alpha.sum(0, dtype=torch.float32)
         valid = asum > 0
@@ -527,10 +539,11 @@ class TemporalOnline:
     refine (binary masks) -> weight map -> splat (winners) -> temporal weight ->
     fusion with the previous output as an extra input -> guided mask."""
 
-    def __init__(self, w, frames_np, device):
+    def __init__(self, w, frames_np, device, library_loss=True):
         import torch
         from paper_2505_18932_gb300 import gvs
         self.torch, self.gvs, self.w = torch, gvs, w
+        self.library_loss = library_loss
         self.half = False
         self.tgt = w.targets[0]
         self.rgba = [torch.from_numpy(c.view(np.int32)).to(device) for c, _ in frames_np]

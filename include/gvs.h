@@ -605,6 +605,55 @@ GVS_API gvs_status gvs_blend(int32_t n_views, int32_t target_width, int32_t targ
                              size_t workspace_bytes, void *stream);
 
 /*
+ * gvs_uniform_blend_loss -- the training loss of Sec. 3.3 (0.8 L1 + 0.1 L_Depth in
+ * the paper) on the blend of the differentiable splat's views with uniform weights
+ * (Eq. 4 with every w_k = 1, its denominator read as the sum over the views), and
+ * its gradient.  Per target pixel p, with a_k the views' alpha (0/1):
+ *   A = sum_k a_k,  B = sum_k a_k I_k / A   (I_k = warped_color RGB; n pixels have A > 0)
+ *   L1 = sum_{A > 0} sum_rgb |B - GT| / (3 n)
+ *   Dbar = sum_k a_k D_k / A,  v = [A > 0 and F > 0]   (D_k warped depth, F fused depth)
+ *   L_Depth = sum_p v |F - Dbar| / (n_views Ht Wt)       (the printed 1/(HWK))
+ *   L = w_l1 L1 + w_depth L_Depth
+ * FP32 per pixel, FP64 sums added in a fixed order (deterministic).
+ *   warped_color : float [n_views][Ht][Wt][4] (4th channel unused), 16-byte aligned
+ *   alpha        : uint8 [n_views][Ht][Wt];  warped_depth: float [n_views][Ht][Wt]
+ *   fused_depth  : float [Ht][Wt];  ground_truth: float [Ht][Wt][3]
+ *   loss         : device double[3] = {L, L1, L_Depth}
+ *   grad_pixel   : float [Ht][Wt][4] or NULL: dL/dI_k (RGB) and dL/dD_k (4th) shared by
+ *                  every view k with a_k = 1 at the pixel (0 at uncovered pixels):
+ *                  w_l1 sign(B - GT) / (3 n A) and -w_depth v sign(F - Dbar) / (n_views Ht Wt A)
+ *   grad_fused   : float [Ht][Wt] or NULL: dL/dF = w_depth v sign(F - Dbar) / (n_views Ht Wt)
+ *                  (|x|' = sign(x), 0 at 0)
+ *   workspace    : >= gvs_uniform_blend_loss_workspace_bytes(Wt, Ht), 256-byte aligned
+ * Errors: GVS_ERR_INVALID_ARG for bad sizes, weights, NULL or misaligned arrays;
+ * GVS_ERR_WORKSPACE for a short workspace.
+ */
+GVS_API size_t gvs_uniform_blend_loss_workspace_bytes(int32_t target_width, int32_t target_height);
+GVS_API gvs_status gvs_uniform_blend_loss(int32_t n_views, int32_t target_width, int32_t target_height,
+                                          const float *warped_color, const uint8_t *alpha,
+                                          const float *warped_depth, const float *fused_depth,
+                                          const float *ground_truth, float w_l1, float w_depth, double *loss,
+                                          float *grad_pixel, float *grad_fused, void *workspace,
+                                          size_t workspace_bytes, void *stream);
+
+/*
+ * gvs_soft_splat_backward_blended -- gvs_soft_splat_backward for a loss that sees the
+ * views only through their uniform blend (as gvs_uniform_blend_loss): the upstream
+ * gradients are one per target pixel, shared by every view that covers it,
+ * grad_pixel float [Ht][Wt][4] = (dL/d colour RGB, dL/d warped depth), in place of
+ * grad_color and grad_depth [n_views][Ht][Wt].  The result equals
+ * gvs_soft_splat_backward given grad_color_k = a_k grad_pixel.rgb and grad_depth_k =
+ * a_k grad_pixel.w, without those per-view arrays.  Other arguments, outputs and
+ * errors as gvs_soft_splat_backward.
+ */
+GVS_API gvs_status gvs_soft_splat_backward_blended(const gvs_camera *in_cams, const void *in_depths,
+                                                   const void *in_color, int32_t n_views, const gvs_camera *target,
+                                                   const gvs_soft_splat_params *params, const int32_t *winner,
+                                                   const float *warped_color, const float *warped_depth,
+                                                   const float *weight_sum, const float *grad_pixel,
+                                                   float *grad_in_depth, float *grad_in_color, void *stream);
+
+/*
  * gvs_take_device_status -- a service of the library (the paper has no counterpart).
  * Kernels that stage their inputs in shared memory with asynchronous bulk copies
  * (the hard splat's resolve) wait for those copies a bounded time (about 2^24

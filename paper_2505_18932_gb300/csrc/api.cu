@@ -659,6 +659,68 @@ gvs_status gvs_soft_splat_backward(const gvs_camera *in_cams, const void *in_dep
     return GVS_OK;
 }
 
+gvs_status gvs_soft_splat_backward_blended(const gvs_camera *in_cams, const void *in_depths, const void *in_color,
+                                           int32_t n_views, const gvs_camera *target,
+                                           const gvs_soft_splat_params *params, const int32_t *winner,
+                                           const float *warped_color, const float *warped_depth,
+                                           const float *weight_sum, const float *grad_pixel, float *grad_in_depth,
+                                           float *grad_in_color, void *stream) {
+    const Range nvtx_range("gvs_soft_splat_backward_blended");
+    gvs::SplatArgs a;
+    gvs_status s = soft_common(in_cams, in_depths, in_color, n_views, target, params, &a);
+    if (s != GVS_OK) return s;
+    if (n_views == 0) return GVS_OK;
+    const void *req[] = {winner, warped_color, warped_depth, weight_sum, grad_pixel, grad_in_depth, grad_in_color};
+    for (const void *q : req)
+        if (!q || !aligned(q, 16))
+            return fail(GVS_ERR_INVALID_ARG, "soft splat backward (blended): NULL or misaligned array");
+    a.winner = const_cast<int32_t *>(winner);
+    a.out_color = const_cast<float4 *>(reinterpret_cast<const float4 *>(warped_color));
+    a.warped_depth = const_cast<float *>(warped_depth);
+    a.wsum = const_cast<float *>(weight_sum);
+    a.grad_pixel = reinterpret_cast<const float4 *>(grad_pixel);
+    a.grad_in_depth = grad_in_depth;
+    a.grad_in_color = reinterpret_cast<float4 *>(grad_in_color);
+    cudaError_t e = gvs::launch_soft_splat_backward(a, n_views, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "soft splat backward (blended): launch");
+    return GVS_OK;
+}
+
+size_t gvs_uniform_blend_loss_workspace_bytes(int32_t target_width, int32_t target_height) {
+    if (target_width < 1 || target_height < 1 || target_width > GVS_MAX_DIM || target_height > GVS_MAX_DIM) return 0;
+    return gvs::blend_loss_layout((int64_t)target_width * target_height).total;
+}
+
+gvs_status gvs_uniform_blend_loss(int32_t n_views, int32_t target_width, int32_t target_height,
+                                  const float *warped_color, const uint8_t *alpha, const float *warped_depth,
+                                  const float *fused_depth, const float *ground_truth, float w_l1, float w_depth,
+                                  double *loss, float *grad_pixel, float *grad_fused, void *workspace,
+                                  size_t workspace_bytes, void *stream) {
+    const Range nvtx_range("gvs_uniform_blend_loss");
+    if (n_views < 1 || n_views > GVS_MAX_VIEWS)
+        return fail(GVS_ERR_INVALID_ARG, "blend loss: n_views must be in [1, %d]", GVS_MAX_VIEWS);
+    if (target_width < 1 || target_height < 1 || target_width > GVS_MAX_DIM || target_height > GVS_MAX_DIM)
+        return fail(GVS_ERR_INVALID_ARG, "blend loss: target size out of range");
+    if (!(isfinite(w_l1) && w_l1 >= 0.0f && isfinite(w_depth) && w_depth >= 0.0f))
+        return fail(GVS_ERR_INVALID_ARG, "blend loss: weights must be finite and >= 0");
+    if (!warped_color || !aligned(warped_color, 16) || !alpha || !warped_depth || !aligned(warped_depth, 4) ||
+        !fused_depth || !aligned(fused_depth, 4) || !ground_truth || !aligned(ground_truth, 4) || !loss ||
+        !aligned(loss, 8))
+        return fail(GVS_ERR_INVALID_ARG, "blend loss: NULL or misaligned input or loss");
+    if ((grad_pixel && !aligned(grad_pixel, 16)) || (grad_fused && !aligned(grad_fused, 4)))
+        return fail(GVS_ERR_INVALID_ARG, "blend loss: misaligned gradient output");
+    const int64_t HWt = (int64_t)target_width * target_height;
+    const size_t need = gvs::blend_loss_layout(HWt).total;
+    if (!workspace || workspace_bytes < need || !aligned(workspace, 256))
+        return fail(GVS_ERR_WORKSPACE, "blend loss: workspace needs %zu bytes, 256-byte aligned", need);
+    cudaError_t e = gvs::launch_blend_loss(n_views, HWt, reinterpret_cast<const float4 *>(warped_color), alpha,
+                                           warped_depth, fused_depth, ground_truth, w_l1, w_depth, loss,
+                                           reinterpret_cast<float4 *>(grad_pixel), grad_fused,
+                                           reinterpret_cast<char *>(workspace), (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "blend loss: launch");
+    return GVS_OK;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------

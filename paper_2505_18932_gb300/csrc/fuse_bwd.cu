@@ -29,17 +29,10 @@ namespace {
 // so they are bit-identical to it.
 // ---------------------------------------------------------------------------
 
-// FULL: the call has exactly KMAX views (no per-view guard).
+// One target pixel with a crossing: recompute its two bracketing samples and
+// add each contributing view's terms at the sampled input pixel.
 template <int KMAX, typename MT, bool FULL>
-__global__ void __launch_bounds__(128) fuse_bwd_scatter(const FuseArgs a, const int16_t *__restrict__ crossing,
-                                                        const float *__restrict__ grad_fused, float2 *__restrict__ acc) {
-    const int i = blockIdx.x * 16 + threadIdx.x;
-    const int j = blockIdx.y * 8 + threadIdx.y;
-    if (i >= a.Wt || j >= a.Ht) return;
-    const size_t o = (size_t)j * a.Wt + i;
-    const int s = crossing[o];
-    const float G = grad_fused[o];
-    if (s < 0 || s + 1 >= a.D || G == 0.0f) return;
+__device__ __forceinline__ void bwd_pixel(const FuseArgs &a, int i, int j, int s, float G, float2 *__restrict__ acc) {
     const float fi = (float)i, fj = (float)j;
     Ray ray[KMAX];
 #pragma unroll
@@ -87,10 +80,55 @@ __global__ void __launch_bounds__(128) fuse_bwd_scatter(const FuseArgs a, const 
     }
 }
 
+// Pass 1.  Only target pixels with a crossing (and a non-zero upstream
+// gradient) have work, about a third of them on the 8 x 1080p frame; so each
+// block of 128 threads first lists the pixels with work among its 16 x 32 tile
+// (in raster order, through a block-wide prefix count of warp ballots) and then
+// deals the list out to its threads, which keeps the warps full.
+// FULL: the call has exactly KMAX views (no per-view guard).
+constexpr int BS_TX = 16, BS_TY = 32, BS_THREADS = 128;
+template <int KMAX, typename MT, bool FULL>
+__global__ void __launch_bounds__(BS_THREADS) fuse_bwd_scatter(const FuseArgs a, const int16_t *__restrict__ crossing,
+                                                               const float *__restrict__ grad_fused,
+                                                               float2 *__restrict__ acc) {
+    constexpr int PER = BS_TX * BS_TY / BS_THREADS;  // pixels per thread in the listing pass
+    __shared__ int s_list[BS_TX * BS_TY];
+    __shared__ int s_warp[BS_THREADS / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int base = 0;
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+        const int e = r * BS_THREADS + tid;  // tile-local raster index
+        const int i = blockIdx.x * BS_TX + (e % BS_TX), j = blockIdx.y * BS_TY + (e / BS_TX);
+        bool work = false;
+        if (i < a.Wt && j < a.Ht) {
+            const size_t o = (size_t)j * a.Wt + i;
+            const int s = crossing[o];
+            work = s >= 0 && s + 1 < a.D && grad_fused[o] != 0.0f;
+        }
+        const unsigned ball = __ballot_sync(0xffffffffu, work);
+        if (lane == 0) s_warp[warp] = __popc(ball);
+        __syncthreads();
+        int before = base;
+        for (int w = 0; w < warp; ++w) before += s_warp[w];
+        int total = base;
+        for (int w = 0; w < BS_THREADS / 32; ++w) total += s_warp[w];
+        if (work) s_list[before + __popc(ball & ((1u << lane) - 1u))] = e;
+        __syncthreads();  // s_warp is rewritten by the next round
+        base = total;
+    }
+    for (int q = tid; q < base; q += BS_THREADS) {
+        const int e = s_list[q];
+        const int i = blockIdx.x * BS_TX + (e % BS_TX), j = blockIdx.y * BS_TY + (e / BS_TX);
+        const size_t o = (size_t)j * a.Wt + i;
+        bwd_pixel<KMAX, MT, FULL>(a, i, j, crossing[o], grad_fused[o], acc);
+    }
+}
+
 template <int KMAX, typename MT>
 void bwd_scatter_k(const FuseArgs &a, const int16_t *crossing, const float *grad_fused, float2 *acc,
                    cudaStream_t st) {
-    const dim3 grid((a.Wt + 15) / 16, (a.Ht + 7) / 8), block(16, 8);
+    const dim3 grid((a.Wt + BS_TX - 1) / BS_TX, (a.Ht + BS_TY - 1) / BS_TY), block(BS_THREADS);
     if (a.K == KMAX) fuse_bwd_scatter<KMAX, MT, true><<<grid, block, 0, st>>>(a, crossing, grad_fused, acc);
     else fuse_bwd_scatter<KMAX, MT, false><<<grid, block, 0, st>>>(a, crossing, grad_fused, acc);
 }

@@ -155,6 +155,7 @@ struct SplatArgs {
     float4 *out_color;         // [K][Ht][Wt] RGBA (A = 0)
     float *wsum;               // [K][Ht][Wt] sum g
     const float4 *grad_color;  // backward inputs [K][Ht][Wt]
+    const float4 *grad_pixel;  // or one per target pixel for every view: (d/d colour rgb, d/d warped depth)
     const float *grad_depth;   // [K][Ht][Wt] or null
     float *grad_in_depth;      // backward outputs [K][H][W]
     float4 *grad_in_color;     // [K][H][W]
@@ -162,6 +163,17 @@ struct SplatArgs {
 };
 
 cudaError_t launch_splat(const SplatArgs &a, int K, cudaStream_t st);
+// ---- the uniform-blend training loss ---------------------------------------
+struct BlendLossLayout {
+    int nblocks;
+    size_t off_code, off_partial, off_scale, total;
+};
+BlendLossLayout blend_loss_layout(int64_t HWt);
+// loss: device double[3] = {L, L1, L_Depth}; grad_pixel / grad_fused may be null
+cudaError_t launch_blend_loss(int K, int64_t HWt, const float4 *color, const uint8_t *alpha, const float *wdepth,
+                              const float *fused, const float *gt, float w_l1, float w_depth, double *loss,
+                              float4 *grad_pixel, float *grad_fused, char *ws, cudaStream_t st);
+
 // Bulk copies whose wait gave up since the last call (read and cleared).
 unsigned async_timeouts_take();
 cudaError_t launch_soft_splat(const SplatArgs &a, int K, cudaStream_t st);

@@ -90,11 +90,14 @@ __device__ __forceinline__ Geo contract(const SplatView &sv, int u, int v, float
 // rounded divisions.  The three quotients are taken with the fast approximate
 // division (at most 2 ulp from the exact quotient for divisors in
 // [2^-126, 2^126]); each bound is then an integer decision on a value within
-// eps of the contract's own value, with
-//   eps = 2e-6 * (|x| + hw)   (>= 3x the worst-case difference: 2.5 ulp of the
-//                              quotient, the rho product and the two roundings
-//                              of x -/+ hw),
-// so a value further than eps from every decision boundary (an integer for
+// eps of the contract's own value.  The worst-case difference of x -/+ hw
+// between the two: 2.5 ulp of the quotient x (2.98e-7 |x|), half of the
+// difference of rho (its quotient 2.5 ulp plus both products' roundings:
+// 4.2e-7 rho, so 4.2e-7 hw after the halving and the clamps) and the two
+// roundings of the sum (1.2e-7 (|x| + hw)): at most 5.4e-7 (|x| + hw); the
+// point mode's nearest pixel needs 3e-7 |x|.  With
+//   eps = 1e-6 * (|x| + hw)   (1.85x that bound),
+// a value further than eps from every decision boundary (an integer for
 // ceil/floor, a half-integer for round-to-nearest) gives the contract's bound.
 // Returns 1 (covered pixels in i0..j1), 0 (no pixel), or -1 when some value is
 // within eps of a boundary or out of the fast division's range: the caller
@@ -130,8 +133,8 @@ __device__ __forceinline__ int contract_bounds_fast(const SplatView &sv, int u, 
         const float hw = fminf(fmaxf(__fmul_rn(0.5f, rho), 0.5f), max_hw);
         const float a0 = __fsub_rn(x, hw), a1 = __fadd_rn(x, hw);
         const float b0 = __fsub_rn(y, hw), b1 = __fadd_rn(y, hw);
-        const float ex = 2e-6f * (fabsf(x) + hw) + 1e-30f;
-        const float ey = 2e-6f * (fabsf(y) + hw) + 1e-30f;
+        const float ex = 1e-6f * (fabsf(x) + hw) + 1e-30f;
+        const float ey = 1e-6f * (fabsf(y) + hw) + 1e-30f;
         if (!(fminf(dist_to_integer(a0), dist_to_integer(a1)) > ex) ||
             !(fminf(dist_to_integer(b0), dist_to_integer(b1)) > ey))
             return -1;
@@ -140,7 +143,7 @@ __device__ __forceinline__ int contract_bounds_fast(const SplatView &sv, int u, 
         loy = ceilf(b0);
         hiy = floorf(b1);
     } else {
-        const float ex = 2e-6f * fabsf(x) + 1e-30f, ey = 2e-6f * fabsf(y) + 1e-30f;
+        const float ex = 1e-6f * fabsf(x) + 1e-30f, ey = 1e-6f * fabsf(y) + 1e-30f;
         if (!(dist_to_integer(__fsub_rn(x, 0.5f)) > ex) || !(dist_to_integer(__fsub_rn(y, 0.5f)) > ey))
             return -1;
         lox = hix = rintf(x);
@@ -182,6 +185,20 @@ __global__ void __launch_bounds__(SC_BX * SC_BY) splat_scatter(const SplatArgs a
     if (!ok) return;
     const unsigned long long key = ((unsigned long long)__float_as_uint(b.z) << 32) | (unsigned)src;
     unsigned long long *slot = a.keys + (size_t)kk * a.Wt * a.Ht;
+    if (b.j1 - b.j0 <= 1 && b.i1 - b.i0 <= 1) {
+        // the usual pixel-sized footprint: at most 2 x 2 pixels, one predicated body
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int jj = b.j0 + (e >> 1), ii = b.i0 + (e & 1);
+            if (jj <= b.j1 && ii <= b.i1) {
+                const size_t t = (size_t)jj * a.Wt + ii;
+                if (!GVS_IN_BOUNDS(t, (size_t)a.Wt * a.Ht, GVS_SITE_SPLAT_KEY)) continue;
+                if (REJECT && b.z < __fsub_rn(__ldg(&a.fused[t]), a.mu_guide)) continue;
+                atomicMin(&slot[t], key);
+            }
+        }
+        return;
+    }
     for (int jj = b.j0; jj <= b.j1; ++jj)
         for (int ii = b.i0; ii <= b.i1; ++ii) {
             const size_t t = (size_t)jj * a.Wt + ii;
@@ -650,15 +667,20 @@ __global__ void __launch_bounds__(SC_BX * SC_BY) soft_bwd(const SplatArgs a) {
         const float inv_s2 = 1.0f / (sig * sig);
         for (int jj = g.j0; jj <= g.j1; ++jj)
             for (int ii = g.i0; ii <= g.i1; ++ii) {
-                const size_t o = (size_t)k * HWt + (size_t)jj * a.Wt + ii;
-                if (a.grad_depth && a.winner[o] == src) gd += a.grad_depth[o] * g.m2;
+                const size_t tp = (size_t)jj * a.Wt + ii;
+                const size_t o = (size_t)k * HWt + tp;
+                if (a.grad_pixel) {
+                    if (a.winner[o] == src) gd += a.grad_pixel[tp].w * g.m2;
+                } else if (a.grad_depth && a.winner[o] == src) {
+                    gd += a.grad_depth[o] * g.m2;
+                }
                 if (!(z <= __fadd_rn(a.warped_depth[o], a.mu_band))) continue;
                 const float ex = g.x - (float)ii, ey = g.y - (float)jj;
                 const float r2 = ex * ex + ey * ey;
                 const float w = expf(-0.5f * r2 * inv_s2);
                 const float dw_dd = w * (-(ex * dx_dd + ey * dy_dd) * inv_s2 + r2 * dsig_dd * inv_s2 / sig);
                 const float inv_sw = 1.0f / a.wsum[o];
-                const float4 G = a.grad_color[o];
+                const float4 G = a.grad_pixel ? a.grad_pixel[tp] : a.grad_color[o];
                 const float4 I = a.out_color[o];
                 gc.x += G.x * w * inv_sw;
                 gc.y += G.y * w * inv_sw;

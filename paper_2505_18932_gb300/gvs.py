@@ -129,6 +129,13 @@ API = {
     "gvs_soft_splat_backward": (ctypes.c_int, [ctypes.POINTER(GvsCamera), ctypes.c_void_p, ctypes.c_void_p,
                                                ctypes.c_int32, ctypes.POINTER(GvsCamera),
                                                ctypes.POINTER(GvsSoftSplatParams)] + [ctypes.c_void_p] * 9),
+    "gvs_soft_splat_backward_blended": (ctypes.c_int, [ctypes.POINTER(GvsCamera), ctypes.c_void_p, ctypes.c_void_p,
+                                                       ctypes.c_int32, ctypes.POINTER(GvsCamera),
+                                                       ctypes.POINTER(GvsSoftSplatParams)] + [ctypes.c_void_p] * 8),
+    "gvs_uniform_blend_loss_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32] * 2),
+    "gvs_uniform_blend_loss": (ctypes.c_int, [ctypes.c_int32] * 3 + [ctypes.c_void_p] * 5 +
+                               [ctypes.c_float, ctypes.c_float] + [ctypes.c_void_p] * 4 +
+                               [ctypes.c_size_t, ctypes.c_void_p]),
     "gvs_forward_splat": (ctypes.c_int, [ctypes.POINTER(GvsCamera), ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_int32, ctypes.POINTER(GvsCamera), ctypes.POINTER(GvsSplatParams),
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -233,6 +240,8 @@ def depth_dtype_of(t) -> int:
 def _want(t, dtype, shape, name):
     if t.dtype != dtype or tuple(t.shape) != tuple(shape):
         raise ValueError(f"gvs: {name} must be {dtype} of shape {tuple(shape)}, got {t.dtype} {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"gvs: {name} must be contiguous")
 
 
 def _check_views(in_cams, in_depths, per_pixel=()):
@@ -661,6 +670,82 @@ def soft_splat_backward(in_cams, in_depths, in_color, target, fwd, grad_color, g
                                      _ptr(grad_depth), _ptr(gd), _ptr(gc), _stream(stream))
     _check("gvs_soft_splat_backward", st)
     return gd, gc
+
+
+def soft_splat_backward_blended(in_cams, in_depths, in_color, target, fwd, grad_pixel, max_half_width=2.0,
+                                mu_band=0.04, stream=None):
+    """Adjoint of soft_splat for upstream gradients shared by the views per target pixel:
+    grad_pixel float32 [Ht, Wt, 4] (d/d colour RGB, d/d warped depth).  Returns the gradients
+    w.r.t. in_depths [N, H, W] and in_color [N, H, W, 4]."""
+    lib = load()
+    N = len(in_cams)
+    _check_views(in_cams, in_depths)
+    shape = (N, target.height, target.width)
+    if N and tuple(in_color.shape) != tuple(in_depths.shape) + (4,):
+        raise ValueError(f"gvs: in_color must have shape {tuple(in_depths.shape) + (4,)}, got {tuple(in_color.shape)}")
+    _check_outputs(fwd, {"winner": (shape, torch.int32), "color": (shape + (4,), torch.float32),
+                         "depth": (shape, torch.float32), "wsum": (shape, torch.float32)})
+    _want(grad_pixel, torch.float32, (target.height, target.width, 4), "grad_pixel")
+    gd = torch.empty(in_depths.shape, dtype=torch.float32, device=in_depths.device)
+    gc = torch.empty(tuple(in_color.shape[:3]) + (4,), dtype=torch.float32, device=in_depths.device)
+    p = GvsSoftSplatParams(float(max_half_width), float(mu_band), depth_dtype_of(in_depths) if N else GVS_F32,
+                           _color_dtype_of(in_color) if N else GVS_F32)
+    st = lib.gvs_soft_splat_backward_blended(camera_array(in_cams), _ptr(in_depths), _ptr(in_color), N,
+                                             ctypes.byref(camera_struct(target)), ctypes.byref(p),
+                                             _ptr(fwd["winner"]), _ptr(fwd["color"]), _ptr(fwd["depth"]),
+                                             _ptr(fwd["wsum"]), _ptr(grad_pixel), _ptr(gd), _ptr(gc), _stream(stream))
+    _check("gvs_soft_splat_backward_blended", st)
+    return gd, gc
+
+
+def uniform_blend_loss(color, alpha, warped_depth, fused, gt, w_l1=0.8, w_depth=0.1, want_grad=True, stream=None):
+    """Sec. 3.3's loss on the uniform blend of the views (gvs_uniform_blend_loss).
+    color float32 [N, Ht, Wt, 4], alpha uint8 [N, Ht, Wt], warped_depth float32 [N, Ht, Wt],
+    fused float32 [Ht, Wt], gt float32 [Ht, Wt, 3].  Returns (loss float64 [3] = L, L1, L_Depth on
+    the device, grad_pixel float32 [Ht, Wt, 4] or None, grad_fused float32 [Ht, Wt] or None)."""
+    lib = load()
+    N, Ht, Wt = alpha.shape
+    dev = alpha.device
+    _want(color, torch.float32, (N, Ht, Wt, 4), "color")
+    _want(alpha, torch.uint8, (N, Ht, Wt), "alpha")
+    _want(warped_depth, torch.float32, (N, Ht, Wt), "warped_depth")
+    _want(fused, torch.float32, (Ht, Wt), "fused")
+    _want(gt, torch.float32, (Ht, Wt, 3), "gt")
+    loss = torch.empty(3, dtype=torch.float64, device=dev)
+    gp = torch.empty((Ht, Wt, 4), dtype=torch.float32, device=dev) if want_grad else None
+    gf = torch.empty((Ht, Wt), dtype=torch.float32, device=dev) if want_grad else None
+    ws = workspace(int(lib.gvs_uniform_blend_loss_workspace_bytes(Wt, Ht)), dev)
+    st = lib.gvs_uniform_blend_loss(N, Wt, Ht, _ptr(color), _ptr(alpha), _ptr(warped_depth), _ptr(fused), _ptr(gt),
+                                    float(w_l1), float(w_depth), _ptr(loss), _ptr(gp), _ptr(gf), _ptr(ws),
+                                    ws.numel(), _stream(stream))
+    _check("gvs_uniform_blend_loss", st)
+    return loss, gp, gf
+
+
+class SoftSplatBlendLoss(torch.autograd.Function):
+    """L = SoftSplatBlendLoss.apply(in_depths, in_color, fused, cams, target, gt, cfg): the
+    differentiable splat of every view, blended with uniform weights and scored against gt by
+    Sec. 3.3's w_l1 L1 + w_depth L_Depth (cfg: mu_band, max_half_width=2.0, w_l1=0.8,
+    w_depth=0.1).  Returns L as a float32 scalar tensor; the gradient flows to in_depths and
+    in_color (through the splat's adjoint) and to fused."""
+
+    @staticmethod
+    def forward(ctx, in_depths, in_color, fused, in_cams, target, gt, cfg):
+        mhw = cfg.get("max_half_width", 2.0)
+        fwd = soft_splat(in_cams, in_depths, in_color, target, mhw, cfg["mu_band"])
+        loss, gp, gf = uniform_blend_loss(fwd["color"], fwd["alpha"], fwd["depth"], fused.detach().contiguous(), gt,
+                                          cfg.get("w_l1", 0.8), cfg.get("w_depth", 0.1))
+        ctx.save_for_backward(in_depths, in_color, fwd["winner"], fwd["color"], fwd["depth"], fwd["wsum"], gp, gf)
+        ctx.cams, ctx.target, ctx.cfg = in_cams, target, cfg
+        return loss[0].to(torch.float32)
+
+    @staticmethod
+    def backward(ctx, g):
+        in_depths, in_color, winner, color, depth, wsum, gp, gf = ctx.saved_tensors
+        fwd = {"winner": winner, "color": color, "depth": depth, "wsum": wsum}
+        gd, gc = soft_splat_backward_blended(ctx.cams, in_depths, in_color, ctx.target, fwd, gp * g,
+                                             ctx.cfg.get("max_half_width", 2.0), ctx.cfg["mu_band"])
+        return gd, gc.to(in_color.dtype), gf * g, None, None, None, None
 
 
 class SoftSplat(torch.autograd.Function):
