@@ -12,17 +12,25 @@ template <int KMAX, typename MT, typename T>
 __global__ void __launch_bounds__(32 * FZ_WARPS, GVS_FUSE_MIN_BLOCKS)
     fuse_batch_kernel(const BatchItem *__restrict__ items, int n_items, int total, unsigned *__restrict__ counter) {
     const int lane = threadIdx.x & 31;
+    // the warp's current item and its bundle range: a warp's bundles come in increasing
+    // order, mostly from the same item, so the table is searched only on a change of item
+    int cur = -1, cur_begin = 0, cur_end = 0;
     for (;;) {
         int b = 0;
         if (lane == 0) b = (int)atomicAdd(counter, 1u);
         b = __shfl_sync(0xffffffffu, b, 0);
         if (b >= total) break;
-        int lo = 0, hi = n_items - 1;  // last item whose first bundle is <= b
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (items[mid].bundle_begin <= b) lo = mid; else hi = mid - 1;
+        if (b < cur_begin || b >= cur_end) {
+            int lo = 0, hi = n_items - 1;  // last item whose first bundle is <= b
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (items[mid].bundle_begin <= b) lo = mid; else hi = mid - 1;
+            }
+            cur = lo;
+            cur_begin = items[lo].bundle_begin;
+            cur_end = lo + 1 < n_items ? items[lo + 1].bundle_begin : total;
         }
-        march_bundle<KMAX, MT, T, false, false>(items[lo].args, b - items[lo].bundle_begin, lane);
+        march_bundle<KMAX, MT, T, false, false>(items[cur].args, b - cur_begin, lane);
     }
 }
 

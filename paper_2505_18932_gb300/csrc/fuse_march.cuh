@@ -84,7 +84,7 @@ __device__ __forceinline__ void nearest_pixel(float hx, float hy, float hz, int 
 #endif
 constexpr int FZ_WARPS = GVS_FUSE_WARPS;
 #ifndef GVS_FUSE_MIN_BLOCKS
-#define GVS_FUSE_MIN_BLOCKS 8   // resident blocks per SM requested from the register allocator (64 registers)
+#define GVS_FUSE_MIN_BLOCKS 9   // resident blocks per SM requested from the register allocator (56 registers)
 #endif
 constexpr int SKIP_COOL = 3;    // samples evaluated after both slab tests fail, before testing again
 
