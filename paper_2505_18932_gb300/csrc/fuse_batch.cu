@@ -11,7 +11,11 @@ namespace {
 template <int KMAX, typename MT, typename T>
 __global__ void __launch_bounds__(32 * FZ_WARPS, GVS_FUSE_MIN_BLOCKS)
     fuse_batch_kernel(const BatchItem *__restrict__ items, int n_items, int total, unsigned *__restrict__ counter) {
-    const int lane = threadIdx.x & 31;
+    // each warp keeps its current item's arguments in shared memory (read there by the
+    // march, instead of from global memory at every use)
+    __shared__ FuseArgs s_args[FZ_WARPS];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    static_assert(sizeof(FuseArgs) % sizeof(int) == 0, "copied as words");
     // the warp's current item and its bundle range: a warp's bundles come in increasing
     // order, mostly from the same item, so the table is searched only on a change of item
     int cur = -1, cur_begin = 0, cur_end = 0;
@@ -29,8 +33,13 @@ __global__ void __launch_bounds__(32 * FZ_WARPS, GVS_FUSE_MIN_BLOCKS)
             cur = lo;
             cur_begin = items[lo].bundle_begin;
             cur_end = lo + 1 < n_items ? items[lo + 1].bundle_begin : total;
+            // every lane has left the previous march (the shuffle above synchronised them)
+            const int *src = reinterpret_cast<const int *>(&items[cur].args);
+            int *dst = reinterpret_cast<int *>(&s_args[warp]);
+            for (int i = lane; i < (int)(sizeof(FuseArgs) / sizeof(int)); i += 32) dst[i] = __ldg(&src[i]);
+            __syncwarp();
         }
-        march_bundle<KMAX, MT, T, false, false>(items[cur].args, b - cur_begin, lane);
+        march_bundle<KMAX, MT, T, false, false>(s_args[warp], b - cur_begin, lane);
     }
 }
 
