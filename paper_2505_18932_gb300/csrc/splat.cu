@@ -637,6 +637,90 @@ __global__ void __launch_bounds__(256) soft_resolve_wide(const SplatArgs a, int 
     }
 }
 
+// The differentiable splat's resolve with its streams moved by TMA: per block
+// 512 consecutive target pixels of one view.  One thread bulk-copies the keys
+// and the (sum g c, sum g) accumulators into shared memory (mbarrier, bounded
+// wait); every thread resolves two pixels (strided) and writes the winner,
+// depth, alpha, weight sum and colour into shared memory and clears the keys
+// (to ~0) and accumulators (to 0) in place; one thread bulk-stores the five
+// outputs and the two resets.  Needs Wt * Ht divisible by 16 and every array
+// 16-byte aligned (the caller checks).  Grid (ceil(Wt Ht / 512), views of the group).
+constexpr int ST_PX = 512;
+__global__ void __launch_bounds__(256) soft_resolve_tma(const SplatArgs a, int k0) {
+    __shared__ __align__(128) unsigned long long s_key[ST_PX];
+    __shared__ __align__(128) float4 s_acc[ST_PX];
+    __shared__ __align__(128) int32_t s_win[ST_PX];
+    __shared__ __align__(128) float s_dep[ST_PX];
+    __shared__ __align__(128) float s_wsum[ST_PX];
+    __shared__ __align__(128) float4 s_col[ST_PX];
+    __shared__ __align__(128) uint8_t s_alpha[ST_PX];
+    __shared__ __align__(8) unsigned long long s_bar;
+    const int64_t HWt = (int64_t)a.Wt * a.Ht;
+    const int64_t base = (int64_t)blockIdx.x * ST_PX;
+    const int n = (int)min((int64_t)ST_PX, HWt - base);
+    const int kk = blockIdx.y;
+    const int k = k0 + kk;
+    unsigned long long *slot = a.keys + (size_t)kk * HWt + base;
+    float4 *acc = a.acc + (size_t)kk * HWt + base;
+    const uint32_t bar = smem_addr(&s_bar);
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const uint32_t kb = (uint32_t)n * 8u, ab = (uint32_t)n * 16u;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kb + ab) : "memory");
+        bulk_load(s_key, slot, kb, bar);
+        bulk_load(s_acc, acc, ab, bar);
+    }
+    if (!__syncthreads_and(wait_phase0(bar))) {  // the same answer in every thread
+        if (tid == 0) atomicAdd(&g_async_timeouts, 1u);
+        wait_phase0(bar);  // the copies may still land in this block's shared memory: give them time
+        return;
+    }
+#pragma unroll
+    for (int q = 0; q < ST_PX / 256; ++q) {
+        const int p = q * 256 + tid;
+        if (p < n) {
+            bool h;
+            int32_t w;
+            float z;
+            decode(s_key[p], h, w, z);
+            const float4 sm = s_acc[p];
+            s_key[p] = ~0ull;  // ready for the next group of views
+            s_acc[p] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            s_win[p] = w;
+            s_dep[p] = z;
+            s_alpha[p] = (uint8_t)h;
+            s_wsum[p] = sm.w;
+            const float r = (h && sm.w > 0.0f) ? 1.0f / sm.w : 0.0f;
+            s_col[p] = make_float4(sm.x * r, sm.y * r, sm.z * r, 0.0f);
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // shared writes -> the bulk copies
+    __syncthreads();
+    if (tid == 0) {
+        const size_t o = (size_t)k * HWt + base;
+        bulk_store(a.winner + o, s_win, (uint32_t)n * 4u);
+        if (a.warped_depth) bulk_store(a.warped_depth + o, s_dep, (uint32_t)n * 4u);
+        if (a.alpha) bulk_store(a.alpha + o, s_alpha, (uint32_t)n);
+        bulk_store(a.wsum + o, s_wsum, (uint32_t)n * 4u);
+        bulk_store(a.out_color + o, s_col, (uint32_t)n * 16u);
+        bulk_store(slot, s_key, (uint32_t)n * 8u);
+        bulk_store(acc, s_acc, (uint32_t)n * 16u);
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    }
+}
+
+inline bool tma_soft_resolve_ok(const SplatArgs &a, int64_t HWt) {
+    return HWt % 16 == 0 && aligned16(a.keys) && aligned16(a.acc) && aligned16(a.winner) &&
+           (!a.warped_depth || aligned16(a.warped_depth)) && aligned16(a.wsum) && aligned16(a.out_color) &&
+           (!a.alpha || aligned16(a.alpha));
+}
+
 inline bool wide_soft_resolve_ok(const SplatArgs &a, int64_t HWt) {
     return HWt % 8 == 0 && aligned_to(a.keys, 32) && aligned_to(a.acc, 32) && aligned_to(a.winner, 32) &&
            (!a.warped_depth || aligned_to(a.warped_depth, 32)) && aligned_to(a.wsum, 32) &&
@@ -700,7 +784,9 @@ void soft_groups(const SplatArgs &a, int K, cudaStream_t st) {
         const int kn = (K - k0) < slots ? (K - k0) : slots;
         splat_scatter<DT><<<scatter_grid(a.W, a.H, kn), dim3(SC_BX, SC_BY), 0, st>>>(a, k0);
         soft_accum<DT, CT><<<scatter_grid(a.W, a.H, kn), dim3(SC_BX, SC_BY), 0, st>>>(a, k0);
-        if (wide_soft_resolve_ok(a, HWt))
+        if (tma_soft_resolve_ok(a, HWt))
+            soft_resolve_tma<<<dim3((unsigned)((HWt + ST_PX - 1) / ST_PX), (unsigned)kn), 256, 0, st>>>(a, k0);
+        else if (wide_soft_resolve_ok(a, HWt))
             soft_resolve_wide<<<dim3((unsigned)((HWt / 8 + 255) / 256), (unsigned)kn), 256, 0, st>>>(a, k0);
         else if (HWt % 4 == 0)
             soft_resolve4<<<dim3((unsigned)((HWt / 4 + 255) / 256), (unsigned)kn), 256, 0, st>>>(a, k0);
