@@ -637,6 +637,27 @@ GVS_API gvs_status gvs_uniform_blend_loss(int32_t n_views, int32_t target_width,
                                           size_t workspace_bytes, void *stream);
 
 /*
+ * gvs_uniform_blend_loss_grad -- the gradient of the loss that the last
+ * gvs_uniform_blend_loss call on `workspace` computed (same target size; the
+ * workspace keeps each pixel's blend signs and the two scales between the calls),
+ * multiplied by the upstream gradient *grad_loss: what a backward pass needs when
+ * the loss feeds further arithmetic, with the scalar read on the device (no host
+ * round trip, and the call can be captured in a CUDA graph).
+ *   grad_loss  : device float, or NULL for 1 (then the outputs equal those of
+ *                gvs_uniform_blend_loss bit for bit); otherwise each output is the
+ *                unit-upstream value times *grad_loss, rounded once
+ *   grad_pixel : float [Ht][Wt][4] or NULL, 16-byte aligned; grad_fused: float [Ht][Wt] or NULL
+ *                (as gvs_uniform_blend_loss defines them); at least one of the two
+ *   workspace  : the one the loss call used, not written in between; only read here
+ * Errors: GVS_ERR_INVALID_ARG for bad sizes, no output or misaligned arrays;
+ * GVS_ERR_WORKSPACE for a short or misaligned workspace.  A workspace that no loss
+ * call has filled gives undefined (finite or not) gradients, never an access outside it.
+ */
+GVS_API gvs_status gvs_uniform_blend_loss_grad(int32_t target_width, int32_t target_height, const float *grad_loss,
+                                               float *grad_pixel, float *grad_fused, const void *workspace,
+                                               size_t workspace_bytes, void *stream);
+
+/*
  * gvs_soft_splat_backward_blended -- gvs_soft_splat_backward for a loss that sees the
  * views only through their uniform blend (as gvs_uniform_blend_loss): the upstream
  * gradients are one per target pixel, shared by every view that covers it,

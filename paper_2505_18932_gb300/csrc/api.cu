@@ -721,6 +721,28 @@ gvs_status gvs_uniform_blend_loss(int32_t n_views, int32_t target_width, int32_t
     return GVS_OK;
 }
 
+gvs_status gvs_uniform_blend_loss_grad(int32_t target_width, int32_t target_height, const float *grad_loss,
+                                       float *grad_pixel, float *grad_fused, const void *workspace,
+                                       size_t workspace_bytes, void *stream) {
+    const Range nvtx_range("gvs_uniform_blend_loss_grad");
+    if (target_width < 1 || target_height < 1 || target_width > GVS_MAX_DIM || target_height > GVS_MAX_DIM)
+        return fail(GVS_ERR_INVALID_ARG, "blend loss gradient: target size out of range");
+    if (!grad_pixel && !grad_fused)
+        return fail(GVS_ERR_INVALID_ARG, "blend loss gradient: no output");
+    if ((grad_pixel && !aligned(grad_pixel, 16)) || (grad_fused && !aligned(grad_fused, 4)) ||
+        (grad_loss && !aligned(grad_loss, 4)))
+        return fail(GVS_ERR_INVALID_ARG, "blend loss gradient: misaligned array");
+    const int64_t HWt = (int64_t)target_width * target_height;
+    const size_t need = gvs::blend_loss_layout(HWt).total;
+    if (!workspace || workspace_bytes < need || !aligned(workspace, 256))
+        return fail(GVS_ERR_WORKSPACE, "blend loss gradient: workspace needs %zu bytes, 256-byte aligned", need);
+    cudaError_t e = gvs::launch_blend_loss_grad(HWt, reinterpret_cast<const char *>(workspace), grad_loss,
+                                                reinterpret_cast<float4 *>(grad_pixel), grad_fused,
+                                                (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "blend loss gradient: launch");
+    return GVS_OK;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------

@@ -56,16 +56,29 @@ __global__ void __launch_bounds__(256, 8) weight_map_kernel(const DT *__restrict
         // whole-view bounds, reduced into by depth_bounds with integer atomics on the float bits
         reinterpret_cast<uint4 *>(map + L.off_g)[k] = make_uint4(0x7f800000u, 0xff800000u, ~0u, ~0u);
     }
-    for (int e = tid; e < SW * SH; e += 256) {
-        const int sy = e / SW, sx = e - sy * SW;
-        const int gx = min(max(x0 + sx, 0), W - 1);
-        const int gy = min(max(y0 + sy, 0), H - 1);
-        const float d = as_stored(load_depth(&dep[(size_t)gy * W + gx]), (MT *)nullptr);
-        const float dv = valid_depth(d) ? d : __int_as_float(0x7fc00000);  // NaN marks invalid
-        tile[sy][sx] = make_float2(dv, dv);
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    {
+        // rows of the tile by thread row, columns by lane (a lane's two clamped columns
+        // computed once): the loads of all its rows are independent and in flight together
+        static_assert(SW - WM_TX <= WM_TX, "the halo columns fit one more pass of the lanes");
+        constexpr int TR = WM_TY / WM_P;  // thread rows
+        const int gxa = min(max(x0 + tx, 0), W - 1);
+        const int gxb = min(max(x0 + WM_TX + tx, 0), W - 1);
+        const bool has_b = tx < SW - WM_TX;
+#pragma unroll
+        for (int sy = ty; sy < SH; sy += TR) {
+            const DT *row = dep + (size_t)min(max(y0 + sy, 0), H - 1) * W;
+            const float da = as_stored(load_depth(&row[gxa]), (MT *)nullptr);
+            const float va = valid_depth(da) ? da : __int_as_float(0x7fc00000);  // NaN marks invalid
+            tile[sy][tx] = make_float2(va, va);
+            if (has_b) {
+                const float db = as_stored(load_depth(&row[gxb]), (MT *)nullptr);
+                const float vb = valid_depth(db) ? db : __int_as_float(0x7fc00000);
+                tile[sy][WM_TX + tx] = make_float2(vb, vb);
+            }
+        }
     }
     __syncthreads();
-    const int tx = threadIdx.x, ty = threadIdx.y;
     const int x = blockIdx.x * WM_TX + tx;
     const int yb = blockIdx.y * WM_TY + ty * WM_P;
     // Two vertically adjacent outputs take a neighbour they share in one packed

@@ -173,6 +173,10 @@ BlendLossLayout blend_loss_layout(int64_t HWt);
 cudaError_t launch_blend_loss(int K, int64_t HWt, const float4 *color, const uint8_t *alpha, const float *wdepth,
                               const float *fused, const float *gt, float w_l1, float w_depth, double *loss,
                               float4 *grad_pixel, float *grad_fused, char *ws, cudaStream_t st);
+// The gradient of the loss the last launch_blend_loss on ws computed, times *grad_loss
+// (device float; null for 1).  grad_pixel / grad_fused may be null.
+cudaError_t launch_blend_loss_grad(int64_t HWt, const char *ws, const float *grad_loss, float4 *grad_pixel,
+                                   float *grad_fused, cudaStream_t st);
 
 // Bulk copies whose wait gave up since the last call (read and cleared).
 unsigned async_timeouts_take();

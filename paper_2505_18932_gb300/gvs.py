@@ -136,6 +136,8 @@ API = {
     "gvs_uniform_blend_loss": (ctypes.c_int, [ctypes.c_int32] * 3 + [ctypes.c_void_p] * 5 +
                                [ctypes.c_float, ctypes.c_float] + [ctypes.c_void_p] * 4 +
                                [ctypes.c_size_t, ctypes.c_void_p]),
+    "gvs_uniform_blend_loss_grad": (ctypes.c_int, [ctypes.c_int32] * 2 + [ctypes.c_void_p] * 4 +
+                                    [ctypes.c_size_t, ctypes.c_void_p]),
     "gvs_forward_splat": (ctypes.c_int, [ctypes.POINTER(GvsCamera), ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_int32, ctypes.POINTER(GvsCamera), ctypes.POINTER(GvsSplatParams),
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -698,11 +700,14 @@ def soft_splat_backward_blended(in_cams, in_depths, in_color, target, fwd, grad_
     return gd, gc
 
 
-def uniform_blend_loss(color, alpha, warped_depth, fused, gt, w_l1=0.8, w_depth=0.1, want_grad=True, stream=None):
+def uniform_blend_loss(color, alpha, warped_depth, fused, gt, w_l1=0.8, w_depth=0.1, want_grad=True, ws=None,
+                       stream=None):
     """Sec. 3.3's loss on the uniform blend of the views (gvs_uniform_blend_loss).
     color float32 [N, Ht, Wt, 4], alpha uint8 [N, Ht, Wt], warped_depth float32 [N, Ht, Wt],
     fused float32 [Ht, Wt], gt float32 [Ht, Wt, 3].  Returns (loss float64 [3] = L, L1, L_Depth on
-    the device, grad_pixel float32 [Ht, Wt, 4] or None, grad_fused float32 [Ht, Wt] or None)."""
+    the device, grad_pixel float32 [Ht, Wt, 4] or None, grad_fused float32 [Ht, Wt] or None).
+    ws: a workspace of blend_loss_workspace_bytes(Ht, Wt) bytes to keep for
+    uniform_blend_loss_grad (a fresh one when None)."""
     lib = load()
     N, Ht, Wt = alpha.shape
     dev = alpha.device
@@ -714,12 +719,35 @@ def uniform_blend_loss(color, alpha, warped_depth, fused, gt, w_l1=0.8, w_depth=
     loss = torch.empty(3, dtype=torch.float64, device=dev)
     gp = torch.empty((Ht, Wt, 4), dtype=torch.float32, device=dev) if want_grad else None
     gf = torch.empty((Ht, Wt), dtype=torch.float32, device=dev) if want_grad else None
-    ws = workspace(int(lib.gvs_uniform_blend_loss_workspace_bytes(Wt, Ht)), dev)
+    if ws is None:
+        ws = workspace(blend_loss_workspace_bytes(Ht, Wt), dev)
     st = lib.gvs_uniform_blend_loss(N, Wt, Ht, _ptr(color), _ptr(alpha), _ptr(warped_depth), _ptr(fused), _ptr(gt),
                                     float(w_l1), float(w_depth), _ptr(loss), _ptr(gp), _ptr(gf), _ptr(ws),
                                     ws.numel(), _stream(stream))
     _check("gvs_uniform_blend_loss", st)
     return loss, gp, gf
+
+
+def blend_loss_workspace_bytes(Ht, Wt):
+    return int(load().gvs_uniform_blend_loss_workspace_bytes(Wt, Ht))
+
+
+def uniform_blend_loss_grad(ws, Ht, Wt, grad_loss=None, stream=None):
+    """gvs_uniform_blend_loss_grad: the gradient of the loss the last uniform_blend_loss on ws
+    computed, times grad_loss (a float32 scalar tensor on the device; None for 1).
+    Returns (grad_pixel float32 [Ht, Wt, 4], grad_fused float32 [Ht, Wt])."""
+    lib = load()
+    dev = ws.device
+    if grad_loss is not None:
+        if grad_loss.dtype != torch.float32 or grad_loss.numel() != 1 or grad_loss.device != dev:
+            raise ValueError("grad_loss: one float32 value on the workspace's device")
+        grad_loss = grad_loss.contiguous()
+    gp = torch.empty((Ht, Wt, 4), dtype=torch.float32, device=dev)
+    gf = torch.empty((Ht, Wt), dtype=torch.float32, device=dev)
+    st = lib.gvs_uniform_blend_loss_grad(Wt, Ht, _ptr(grad_loss), _ptr(gp), _ptr(gf), _ptr(ws), ws.numel(),
+                                         _stream(stream))
+    _check("gvs_uniform_blend_loss_grad", st)
+    return gp, gf
 
 
 class SoftSplatBlendLoss(torch.autograd.Function):
@@ -733,19 +761,23 @@ class SoftSplatBlendLoss(torch.autograd.Function):
     def forward(ctx, in_depths, in_color, fused, in_cams, target, gt, cfg):
         mhw = cfg.get("max_half_width", 2.0)
         fwd = soft_splat(in_cams, in_depths, in_color, target, mhw, cfg["mu_band"])
-        loss, gp, gf = uniform_blend_loss(fwd["color"], fwd["alpha"], fwd["depth"], fused.detach().contiguous(), gt,
-                                          cfg.get("w_l1", 0.8), cfg.get("w_depth", 0.1))
-        ctx.save_for_backward(in_depths, in_color, fwd["winner"], fwd["color"], fwd["depth"], fwd["wsum"], gp, gf)
+        Ht, Wt = target.height, target.width
+        ws = workspace(blend_loss_workspace_bytes(Ht, Wt), in_depths.device)
+        # the loss now; its gradient in backward, from the signs kept in ws, times the upstream
+        loss, _, _ = uniform_blend_loss(fwd["color"], fwd["alpha"], fwd["depth"], fused.detach().contiguous(), gt,
+                                        cfg.get("w_l1", 0.8), cfg.get("w_depth", 0.1), want_grad=False, ws=ws)
+        ctx.save_for_backward(in_depths, in_color, fwd["winner"], fwd["color"], fwd["depth"], fwd["wsum"], ws)
         ctx.cams, ctx.target, ctx.cfg = in_cams, target, cfg
         return loss[0].to(torch.float32)
 
     @staticmethod
     def backward(ctx, g):
-        in_depths, in_color, winner, color, depth, wsum, gp, gf = ctx.saved_tensors
+        in_depths, in_color, winner, color, depth, wsum, ws = ctx.saved_tensors
+        gp, gf = uniform_blend_loss_grad(ws, ctx.target.height, ctx.target.width, g.to(torch.float32))
         fwd = {"winner": winner, "color": color, "depth": depth, "wsum": wsum}
-        gd, gc = soft_splat_backward_blended(ctx.cams, in_depths, in_color, ctx.target, fwd, gp * g,
+        gd, gc = soft_splat_backward_blended(ctx.cams, in_depths, in_color, ctx.target, fwd, gp,
                                              ctx.cfg.get("max_half_width", 2.0), ctx.cfg["mu_band"])
-        return gd, gc.to(in_color.dtype), gf * g, None, None, None, None
+        return gd, gc.to(in_color.dtype), gf, None, None, None, None
 
 
 class SoftSplat(torch.autograd.Function):

@@ -179,6 +179,45 @@ def test_refine_rejects_bad_arguments(lib):
     assert lib.gvs_refine_depth(FAKE, FAKE, FAKE, FAKE, None, 1, 4, 4, None, None) == 1
 
 
+def test_blend_loss_rejects_bad_arguments(lib):
+    """gvs_uniform_blend_loss and its gradient stage check sizes, outputs, alignment and the
+    workspace on the host, before anything is enqueued."""
+    W, H = 64, 48
+    ws = lib.gvs_uniform_blend_loss_workspace_bytes(W, H)
+    assert ws >= W * H * 4
+    assert lib.gvs_uniform_blend_loss_workspace_bytes(0, H) == 0
+
+    def loss(n=2, W=W, H=H, color=FAKE, w_l1=0.8, lossp=FAKE, gp=FAKE, wsp=FAKE, wsb=ws):
+        return lib.gvs_uniform_blend_loss(n, W, H, color, FAKE, FAKE, FAKE, FAKE, w_l1, 0.1, lossp, gp, None,
+                                          wsp, wsb, None)
+
+    assert loss(n=0) == 1
+    assert loss(n=33) == 1
+    assert loss(W=0) == 1
+    assert loss(w_l1=-1.0) == 1
+    assert loss(w_l1=float("inf")) == 1
+    assert loss(color=None) == 1
+    assert loss(color=FAKE + 4) == 1
+    assert loss(lossp=FAKE + 4) == 1
+    assert loss(gp=FAKE + 4) == 1
+    assert loss(wsp=None) == 3
+    assert loss(wsb=ws - 1) == 3
+    assert loss(wsp=FAKE + 16) == 3
+
+    def grad(W=W, H=H, gl=FAKE, gp=FAKE, gf=FAKE, wsp=FAKE, wsb=ws):
+        return lib.gvs_uniform_blend_loss_grad(W, H, gl, gp, gf, wsp, wsb, None)
+
+    assert grad(W=0) == 1
+    assert grad(H=20000) == 1
+    assert grad(gp=None, gf=None) == 1
+    assert grad(gp=FAKE + 4) == 1
+    assert grad(gf=FAKE + 2) == 1
+    assert grad(gl=FAKE + 2) == 1
+    assert grad(wsp=None) == 3
+    assert grad(wsb=ws - 256) == 3
+    assert grad(wsp=FAKE + 16) == 3
+
+
 def test_status_strings(lib):
     for s in range(6):
         assert lib.gvs_status_string(s)

@@ -7,6 +7,9 @@ unit weights) and the differentiable splat's adjoint fed by its per-pixel gradie
   uncovered pixels.
 * gvs_soft_splat_backward_blended equals gvs_soft_splat_backward fed with the same gradient
   spread to every covering view, bit for bit (the same arithmetic per term).
+* gvs_uniform_blend_loss_grad, run later on the loss call's workspace, gives the loss call's
+  gradients bit for bit, and times an upstream scalar read on the device, the same values as
+  multiplying them afterwards; the loss itself is bit-reproducible.
 * SoftSplatBlendLoss gives the gradients of the library calls it wires together, and its
   loss equals the same step written with torch operations on the splat's outputs.
 """
@@ -69,6 +72,32 @@ def test_loss_matches_oracle(gvs, oracle_mod, shape):
     assert (gp[tied & (fused > 0)][:, 3] == 0).all() and (gf[tied] == 0).all()
     # the comparisons above cover nearly every pixel where the terms exist
     assert clear_rgb[A > 0].mean() > 0.99 and clear_d[(A > 0) & (fused > 0)].mean() > 0.99
+
+
+@pytest.mark.parametrize("shape", [(8, 360, 640), (3, 17, 29)])
+def test_grad_stage_on_kept_workspace(gvs, shape):
+    K, H, W = shape
+    rng = np.random.default_rng(7 + K)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    alpha = (rng.random((K, H, W)) < 0.7).astype(np.uint8)
+    color = rng.random((K, H, W, 4)).astype(np.float32) * alpha[..., None]
+    wd = (rng.random((K, H, W)) * 3 + 1).astype(np.float32) * alpha
+    fused = (rng.random((H, W)) * 3 + 1).astype(np.float32)
+    gt = rng.random((H, W, 3)).astype(np.float32)
+    args = (dev(color), dev(alpha), dev(wd), dev(fused), dev(gt))
+    ws = gvs.workspace(gvs.blend_loss_workspace_bytes(H, W), "cuda")
+    loss, gp, gf = gvs.uniform_blend_loss(*args, ws=ws)
+    loss2, _, _ = gvs.uniform_blend_loss(*args, want_grad=False)
+    g1, f1 = gvs.uniform_blend_loss_grad(ws, H, W)
+    torch.cuda.synchronize()
+    assert torch.equal(loss, loss2)  # the fixed-order reduction
+    assert torch.equal(g1, gp) and torch.equal(f1, gf)
+    assert gp.abs().sum() > 0 and gf.abs().sum() > 0
+    for u in (2.5, -0.3, 0.0):
+        gu = torch.tensor(u, dtype=torch.float32, device="cuda")
+        g2, f2 = gvs.uniform_blend_loss_grad(ws, H, W, gu)
+        torch.cuda.synchronize()
+        assert torch.equal(g2, gp * gu) and torch.equal(f2, gf * gu), u
 
 
 def _soft_case(gvs, name="diff_640x360"):
