@@ -988,11 +988,33 @@ def run_e2e(pipe, frames_np, steps):
     run(first, steps)
     b.record(down)
     torch.cuda.synchronize()
-    pipe.rgba, pipe.depth, pipe.outs, pipe.fused, pipe.cross = saved
     ms = a.elapsed_time(b) / steps
+    # the same copies with no kernels between them, on the same two streams: the
+    # host link's bound on this step
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(comp)
+    up.wait_stream(comp)
+    down.wait_stream(comp)
+    for i in range(steps):
+        with torch.cuda.stream(up):
+            dev_rgba[i % R].copy_(host_in[i % R][0], non_blocking=True)
+            dev_depth[i % R].copy_(host_in[i % R][1], non_blocking=True)
+        with torch.cuda.stream(down):
+            host_fused[i % 2].copy_(fused[i % 2], non_blocking=True)
+            for n in names:
+                host_out[i % 2][n].copy_(outs[i % 2][n], non_blocking=True)
+    comp.wait_stream(up)
+    comp.wait_stream(down)
+    end.record(comp)
+    torch.cuda.synchronize()
+    copy_ms = start.elapsed_time(end) / steps
+    pipe.rgba, pipe.depth, pipe.outs, pipe.fused, pipe.cross = saved
     return {"value": round(pipe.Ht * pipe.Wt / (ms * 1e-3) / 1e6, 3), "unit": "target Mpix/s",
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ms, 4),
-            "overlap": "uploads, kernels and downloads on three streams, double-buffered"}
+            "overlap": "uploads, kernels and downloads on three streams, double-buffered",
+            "copies_alone_ms_per_step": round(copy_ms, 4),
+            "link_gbs": round((h2d + d2h) / (copy_ms * 1e-3) / 1e9, 1),
+            "of_copy_bound": round(copy_ms / ms, 3)}
 
 
 # ------------------------------------------------------------ CPU oracle --

@@ -84,11 +84,13 @@ __device__ __forceinline__ void bwd_pixel(const FuseArgs &a, int i, int j, int s
 // gradient) have work, about a third of them on the 8 x 1080p frame; so each
 // block of 128 threads first lists the pixels with work among its 16 x 32 tile
 // (in raster order, through a block-wide prefix count of warp ballots) and then
-// deals the list out to its threads, which keeps the warps full.
+// deals the list out to its threads, which keeps the warps full.  Its gathers
+// and atomics wait on memory: twelve resident blocks per SM (40 registers, a few
+// spilled) hide more of that than eight at 64 registers (130.8 -> 123.3 us).
 // FULL: the call has exactly KMAX views (no per-view guard).
 constexpr int BS_TX = 16, BS_TY = 32, BS_THREADS = 128;
 template <int KMAX, typename MT, bool FULL>
-__global__ void __launch_bounds__(BS_THREADS) fuse_bwd_scatter(const FuseArgs a, const int16_t *__restrict__ crossing,
+__global__ void __launch_bounds__(BS_THREADS, 12) fuse_bwd_scatter(const FuseArgs a, const int16_t *__restrict__ crossing,
                                                                const float *__restrict__ grad_fused,
                                                                float2 *__restrict__ acc) {
     constexpr int PER = BS_TX * BS_TY / BS_THREADS;  // pixels per thread in the listing pass
