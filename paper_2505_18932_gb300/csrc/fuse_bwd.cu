@@ -145,11 +145,48 @@ __device__ __forceinline__ int window_multiplicity(int c, int x, int n, int R) {
     return abs(c - x) <= R ? 1 : 0;
 }
 
-constexpr int GB_TX = 32;    // block of 32 x 32 input pixels: 32 x 8 threads,
-constexpr int GB_TY = 32;    // each thread GB_ROWS consecutive rows
-constexpr int GB_ROWS = 4;
+#ifndef GVS_GATHER_ROWS
+#define GVS_GATHER_ROWS 4  // 8 reads fewer shared values per output but runs fewer warps: 278 -> 312 us
+#endif
+constexpr int GB_TX = 32;                 // block of 32 x 32 input pixels: 32 x (32 / GB_ROWS) threads,
+constexpr int GB_TY = 32;                 // each thread GB_ROWS consecutive rows
+constexpr int GB_ROWS = GVS_GATHER_ROWS;
+static_assert(GB_TY % GB_ROWS == 0, "the rows split evenly among the thread rows");
+
+// P(c) = A(c) domega/dnu(c) at input pixel (cx, cy) of view k, or 0 outside the
+// image, where A = 0, at an invalid centre (dc NaN) or where the weight is
+// saturated.  dtc: the depth tile at c's window corner (re-sum of nu without a map).
+template <int R, int DW>
+__device__ __forceinline__ float adjoint_p(const float2 *__restrict__ ak, const float2 *__restrict__ wk, int cx,
+                                           int cy, int W, int H, float dc, const float (*dtc)[DW], int ox, float mu,
+                                           float wconst, float inv_w2) {
+    float P = 0.0f;
+    if (cx >= 0 && cx < W && cy >= 0 && cy < H) {
+        const float A = ak[(size_t)cy * W + cx].x;
+        if (A != 0.0f && dc == dc) {
+            if (wk) {
+                const float om = __ldg(&wk[(size_t)cy * W + cx]).y;
+                if (om < 1.0f) P = A * (-0.5f * om * om * om * (inv_w2 / (wconst * wconst)));
+            } else {
+                float nu = 0.0f;
+                for (int dy = 0; dy <= 2 * R; ++dy)
+                    for (int dx = 0; dx <= 2 * R; ++dx) {
+                        const float t = fminf(fabsf(dc - dtc[dy][ox + dx]), mu);
+                        nu = fmaf(t, t, nu);
+                    }
+                const float unclamped = nu > 0.0f ? wconst * rsqrtf(nu * inv_w2) : 2.0f;
+                if (unclamped < 1.0f) P = A * (-0.5f * unclamped / nu);
+            }
+        }
+    }
+    return P;
+}
 
 // wmap: the forward's float2 (d, omega) planes, or null (re-sum nu).
+// The P tile holds 2 P(c): every term of the gradient carries the factor 2
+// (d/dd (d - n)^2), and scaling by 2 is exact, so 2 (d_x - d_n)(P(x) + P(n))
+// = (d_x - d_n)(2 P(x) + 2 P(n)) bit for bit with one multiplication fewer per
+// term; the border path halves its own sums instead, again exactly.
 template <int R, typename DT>
 __global__ void __launch_bounds__(GB_TX *(GB_TY / GB_ROWS)) fuse_bwd_gather(const DT *__restrict__ depth,
                                                                 const float2 *__restrict__ wmap,
@@ -157,77 +194,74 @@ __global__ void __launch_bounds__(GB_TX *(GB_TY / GB_ROWS)) fuse_bwd_gather(cons
                                                                 float *__restrict__ grad, int W, int H, float mu,
                                                                 float wconst, float inv_w2) {
     constexpr int DW = GB_TX + 4 * R, DH = GB_TY + 4 * R;   // depths: outputs + 2R halo
-    constexpr int PW = GB_TX + 2 * R, PH = GB_TY + 2 * R;   // P(c): outputs + R halo
+    constexpr int PW = GB_TX + 2 * R, PH = GB_TY + 2 * R;   // 2 P(c): outputs + R halo
+    constexpr int TR = GB_TY / GB_ROWS;                     // thread rows
+    static_assert(DW - GB_TX <= GB_TX && PW - GB_TX <= GB_TX, "the halo columns fit one more pass of the lanes");
     __shared__ float dt[DH][DW];
     __shared__ float pt[PH][PW];
     const int k = blockIdx.z;
     const DT *dep = depth + (size_t)k * W * H;
     const float2 *ak = acc + (size_t)k * W * H;
+    const float2 *wk = wmap ? wmap + (size_t)k * W * H : nullptr;
     const int bx = blockIdx.x * GB_TX, by = blockIdx.y * GB_TY;
-    const int tid = threadIdx.y * GB_TX + threadIdx.x;
-    constexpr int NT = GB_TX * (GB_TY / GB_ROWS);
-    for (int e = tid; e < DW * DH; e += NT) {
-        const int sy = e / DW, sx = e - sy * DW;
-        const int gx = min(max(bx - 2 * R + sx, 0), W - 1), gy = min(max(by - 2 * R + sy, 0), H - 1);
-        const float d = load_depth(&dep[(size_t)gy * W + gx]);
-        dt[sy][sx] = valid_depth(d) ? d : __int_as_float(0x7fc00000);
-    }
-    __syncthreads();
-    // P(c) = A(c) domega/dnu(c) on the outputs and an R halo
-    for (int e = tid; e < PW * PH; e += NT) {
-        const int py = e / PW, px = e - py * PW;
-        const int cx = bx - R + px, cy = by - R + py;
-        float P = 0.0f;
-        if (cx >= 0 && cx < W && cy >= 0 && cy < H) {
-            const float A = ak[(size_t)cy * W + cx].x;
-            const float dc = dt[py + R][px + R];
-            if (wmap) {
-                if (A != 0.0f && dc == dc) {
-                    const float om = __ldg(&wmap[(size_t)k * W * H + (size_t)cy * W + cx]).y;
-                    if (om < 1.0f) P = A * (-0.5f * om * om * om * (inv_w2 / (wconst * wconst)));
-                }
-            } else if (A != 0.0f && dc == dc) {
-                float nu = 0.0f;
-                for (int dy = 0; dy <= 2 * R; ++dy)
-                    for (int dx = 0; dx <= 2 * R; ++dx) {
-                        const float t = fminf(fabsf(dc - dt[py + dy][px + dx]), mu);
-                        nu = fmaf(t, t, nu);
-                    }
-                const float unclamped = nu > 0.0f ? wconst * rsqrtf(nu * inv_w2) : 2.0f;
-                if (unclamped < 1.0f) P = A * (-0.5f * unclamped / nu);
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    {
+        // depth tile by rows: each lane's two clamped columns computed once
+        const int gxa = min(max(bx - 2 * R + tx, 0), W - 1);
+        const int gxb = min(max(bx - 2 * R + GB_TX + tx, 0), W - 1);
+        const bool has_b = tx < DW - GB_TX;
+#pragma unroll 2
+        for (int sy = ty; sy < DH; sy += TR) {
+            const DT *row = dep + (size_t)min(max(by - 2 * R + sy, 0), H - 1) * W;
+            const float da = load_depth(&row[gxa]);
+            dt[sy][tx] = valid_depth(da) ? da : __int_as_float(0x7fc00000);  // NaN marks invalid
+            if (has_b) {
+                const float db = load_depth(&row[gxb]);
+                dt[sy][GB_TX + tx] = valid_depth(db) ? db : __int_as_float(0x7fc00000);
             }
         }
-        pt[py][px] = P;
+    }
+    __syncthreads();
+    // 2 P(c) on the outputs and an R halo
+#pragma unroll 1
+    for (int py = ty; py < PH; py += TR) {
+        const int cy = by - R + py;
+        pt[py][tx] = 2.0f * adjoint_p<R, DW>(ak, wk, bx - R + tx, cy, W, H, dt[py + R][tx + R], dt + py, tx, mu,
+                                             wconst, inv_w2);
+        if (tx < PW - GB_TX)
+            pt[py][GB_TX + tx] = 2.0f * adjoint_p<R, DW>(ak, wk, bx - R + GB_TX + tx, cy, W, H,
+                                                         dt[py + R][GB_TX + tx + R], dt + py, GB_TX + tx, mu,
+                                                         wconst, inv_w2);
     }
     __syncthreads();
     // a block whose windows of windows stay inside the image sees every window entry once
     const bool interior = bx >= 2 * R && by >= 2 * R && bx + GB_TX + 2 * R <= W && by + GB_TY + 2 * R <= H;
-    const int x = bx + threadIdx.x;
-    const int ly0 = threadIdx.y * GB_ROWS;  // this thread's GB_ROWS consecutive rows
+    const int x = bx + tx;
+    const int ly0 = ty * GB_ROWS;  // this thread's GB_ROWS consecutive rows
     if (interior) {
         // entry n of x's window and window centre c = n coincide: one pass,
-        // 2 (d_x - d_n) (P(x) + P(n)) where |d_x - d_n| < mu (false for an invalid n, and
+        // (d_x - d_n) (2 P(x) + 2 P(n)) where |d_x - d_n| < mu (false for an invalid n, and
         // for an invalid x, whose NaN depth fails every test).  The thread's outputs share
         // their window rows: each shared value is read once and serves every output whose
         // window holds it, each output taking its entries in the same order as alone.
-        float dx0[GB_ROWS], Px[GB_ROWS], g[GB_ROWS];
+        float dx0[GB_ROWS], Px2[GB_ROWS], g[GB_ROWS];
 #pragma unroll
         for (int p = 0; p < GB_ROWS; ++p) {
-            dx0[p] = dt[ly0 + p + 2 * R][threadIdx.x + 2 * R];
-            Px[p] = pt[ly0 + p + R][threadIdx.x + R];
+            dx0[p] = dt[ly0 + p + 2 * R][tx + 2 * R];
+            Px2[p] = pt[ly0 + p + R][tx + R];
             g[p] = ak[(size_t)(by + ly0 + p) * W + x].y;  // B(x)
         }
 #pragma unroll
         for (int r = 0; r < GB_ROWS + 2 * R; ++r) {
 #pragma unroll
             for (int ox = -R; ox <= R; ++ox) {
-                const float dn = dt[ly0 + R + r][threadIdx.x + 2 * R + ox];
-                const float pn = pt[ly0 + r][threadIdx.x + R + ox];
+                const float dn = dt[ly0 + R + r][tx + 2 * R + ox];
+                const float pn2 = pt[ly0 + r][tx + R + ox];
 #pragma unroll
                 for (int p = 0; p < GB_ROWS; ++p) {
                     if (r - p < 0 || r - p > 2 * R) continue;  // row offset oy = r - p - R outside the window
                     const float diff = dx0[p] - dn;
-                    if (fabsf(diff) < mu) g[p] = fmaf(2.0f * diff, Px[p] + pn, g[p]);
+                    if (fabsf(diff) < mu) g[p] = fmaf(diff, Px2[p] + pn2, g[p]);
                 }
             }
         }
@@ -240,19 +274,20 @@ __global__ void __launch_bounds__(GB_TX *(GB_TY / GB_ROWS)) fuse_bwd_gather(cons
         const int ly = ly0 + rr;  // row within the block
         const int y = by + ly;
         if (x >= W || y >= H) continue;
-        const float dx0 = dt[ly + 2 * R][threadIdx.x + 2 * R];
+        const float dx0 = dt[ly + 2 * R][tx + 2 * R];
         float g = ak[(size_t)y * W + x].y;  // B(x)
         if (dx0 == dx0) {
-            const float Px = pt[ly + R][threadIdx.x + R];
-            if (Px != 0.0f) {
+            const float Px2 = pt[ly + R][tx + R];
+            if (Px2 != 0.0f) {
+                // P(x) sum 2 (d_x - d_n) = 2 P(x) sum (d_x - d_n): every partial sum halved exactly
                 float sum = 0.0f;
                 for (int ey = -R; ey <= R; ++ey)
                     for (int ex = -R; ex <= R; ++ex) {
-                        const float dn = dt[ly + 2 * R + ey][threadIdx.x + 2 * R + ex];
+                        const float dn = dt[ly + 2 * R + ey][tx + 2 * R + ex];
                         const float diff = dx0 - dn;
-                        if (fabsf(diff) < mu) sum += 2.0f * diff;  // false for a NaN (invalid) neighbour
+                        if (fabsf(diff) < mu) sum += diff;  // false for a NaN (invalid) neighbour
                     }
-                g += Px * sum;
+                g += Px2 * sum;
             }
             for (int cyo = -R; cyo <= R; ++cyo) {
                 const int my = window_multiplicity(y + cyo, y, H, R);
@@ -260,10 +295,11 @@ __global__ void __launch_bounds__(GB_TX *(GB_TY / GB_ROWS)) fuse_bwd_gather(cons
                 for (int cxo = -R; cxo <= R; ++cxo) {
                     const int mx = window_multiplicity(x + cxo, x, W, R);
                     if (mx == 0) continue;
-                    const float Pc = pt[ly + R + cyo][threadIdx.x + R + cxo];
-                    if (Pc == 0.0f) continue;
-                    const float diff = dt[ly + 2 * R + cyo][threadIdx.x + 2 * R + cxo] - dx0;
-                    if (fabsf(diff) < mu) g += (float)(mx * my) * Pc * (-2.0f) * diff;
+                    const float Pc2 = pt[ly + R + cyo][tx + R + cxo];
+                    if (Pc2 == 0.0f) continue;
+                    const float diff = dt[ly + 2 * R + cyo][tx + 2 * R + cxo] - dx0;
+                    // m P(c) (-2) diff = -(m 2 P(c)) diff
+                    if (fabsf(diff) < mu) g += -((float)(mx * my) * Pc2) * diff;
                 }
             }
         }
