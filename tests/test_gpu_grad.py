@@ -85,6 +85,47 @@ def test_grad_f16_depth(gvs, oracle_mod):
     _case(gvs, oracle_mod, w, d.astype(np.float16).astype(np.float32), seed=6, half=True)
 
 
+@pytest.mark.parametrize("window", [7, 3])
+def test_grad_half_map(gvs, oracle_mod, window):
+    """The half2 map path of the adjoint, which re-sums nu from the depths instead of
+    reading the weight from the map: against the FP32-map adjoint of the same FP16
+    depths and against the oracle adjoint on those depths.  The forward's weights are
+    rounded to half there (relative spacing 2^-11), which moves every weighted sum and
+    so the gradient by about 1e-3 of its scale: the bar is 5e-3 of the scale per
+    element and a cosine of at least 0.9995."""
+    from synth import configs
+    w = configs.tiny(56, 40, 3, 96)
+    _, d = w.render_inputs(0)
+    d16 = d.astype(np.float16)
+    d32 = d16.astype(np.float32)
+    tgt = w.targets[0]
+    ref = oracle_mod.fuse_depth(w.inputs, d32, tgt, w.num_samples, w.z_near, w.z_far, w.mu, window=window)
+    G = np.random.default_rng(window).standard_normal((tgt.height, tgt.width))
+    G[ref["ambiguous"] == 1] = 0.0
+    dd = torch.from_numpy(d16).cuda()
+    N, H, W = d.shape
+    Gt = torch.from_numpy(G.astype(np.float32)).cuda()
+    grads = {}
+    for half in (True, False):
+        ws = gvs.workspace(gvs.fuse_workspace_bytes(N, W, H))
+        fused, cross = gvs.fuse_depth(w.inputs, dd, tgt, w.num_samples, w.z_near, w.z_far, w.mu, window=window,
+                                      ws=ws, map_half=half)
+        g = gvs.fuse_depth_backward(w.inputs, dd, tgt, w.num_samples, w.z_near, w.z_far, w.mu, ws, cross, Gt,
+                                    window=window, map_half=half)
+        torch.cuda.synchronize()
+        ok = ref["ambiguous"] == 0
+        assert np.array_equal(cross.cpu().numpy()[ok], ref["index"][ok]), half
+        grads[half] = g.cpu().numpy().astype(np.float64)
+    gr = oracle_mod.fuse_depth_grad(w.inputs, d32, tgt, w.num_samples, w.z_near, w.z_far, w.mu, G, window=window)
+    scale = np.abs(gr).max()
+    assert scale > 0
+    for a, b in ((grads[True], grads[False]), (grads[True], gr)):
+        assert np.abs(a - b).max() <= 5e-3 * scale + 1e-7, np.abs(a - b).max() / scale
+        cos = float((a * b).sum() / (np.linalg.norm(a) * np.linalg.norm(b)))
+        assert cos >= 0.9995, cos
+    _check(grads[False], gr)
+
+
 def test_grad_identity_and_sum_rule(gvs):
     from synth import camera_at
     from synth.configs import arc_cameras
