@@ -614,7 +614,9 @@ GVS_API gvs_status gvs_blend(int32_t n_views, int32_t target_width, int32_t targ
  *   Dbar = sum_k a_k D_k / A,  v = [A > 0 and F > 0]   (D_k warped depth, F fused depth)
  *   L_Depth = sum_p v |F - Dbar| / (n_views Ht Wt)       (the printed 1/(HWK))
  *   L = w_l1 L1 + w_depth L_Depth
- * FP32 per pixel, FP64 sums added in a fixed order (deterministic).
+ * FP32 per pixel and over each GPU thread's and warp's pixels (non-negative terms: each
+ * such sum within (terms + 5) 2^-24 of its value), FP64 beyond; every sum in an order
+ * fixed by the target size alone (deterministic).
  *   warped_color : float [n_views][Ht][Wt][4] (4th channel unused), 16-byte aligned
  *   alpha        : uint8 [n_views][Ht][Wt];  warped_depth: float [n_views][Ht][Wt]
  *   fused_depth  : float [Ht][Wt];  ground_truth: float [Ht][Wt][3]
