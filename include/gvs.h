@@ -117,10 +117,12 @@ typedef struct {
     int32_t normalize;         /* 0: S = sum w*clamp (paper); 1: S / W */
     int32_t depth_dtype;       /* GVS_F32 or GVS_F16: element type of in_depths */
     int32_t map_dtype;         /* GVS_F32: (d, omega) as float2; GVS_F16: as half2 (omega rounded to half) */
-    int32_t variant;           /* 0..5: bundle shape, slab-test lengths and samples evaluated at once by the
-                                  march (0: 8x4, 1: 8x4 longer segments, 2: 16x2, 3: 4x8, 4: 4x8 and 5: 8x4
-                                  with two samples at once); every variant gives the same result, the
-                                  autotuner picks the fastest (0 = default) */
+    int32_t variant;           /* 0..6: mapping, bundle shape, slab-test lengths and samples evaluated at
+                                  once by the march (lane per ray: 0: 8x4, 1: 8x4 longer segments, 2: 16x2,
+                                  3: 4x8, 4: 4x8 and 5: 8x4 with two samples at once, for 5..16 views;
+                                  warp per ray: 6, its lanes over views x consecutive samples, for 5..32
+                                  views); other view counts run variant 0.  Every variant gives the same
+                                  result, the autotuner picks the fastest (0 = default) */
 } gvs_fuse_params;
 
 /* Forward splat (Sec. 3.1, Supplement A.3). */

@@ -1,5 +1,6 @@
-"""Autotuner for the fusion march: picks the bundle shape / slab-test lengths
-(gvs_fuse_params.variant) that runs fastest on a given workload.
+"""Autotuner for the fusion march: picks the mapping (lane or warp per ray), bundle
+shape, slab-test lengths and samples in flight (gvs_fuse_params.variant) that run
+fastest on a given workload.
 
 Every variant computes the same fused depth bit for bit; only the time
 differs.  Each candidate is timed with CUDA events on the caller's stream
@@ -18,15 +19,18 @@ import torch
 
 CACHE_PATH = os.environ.get("GVS_AUTOTUNE_CACHE",
                             os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json"))
-VARIANTS = (0, 1, 2, 3, 4, 5)
+VARIANTS = (0, 1, 2, 3, 4, 5, 6)
 _lock = threading.Lock()
 
 
 def variants_for(n_views: int):
     """The variants that are distinct kernels for a call with n_views input views: the
-    bundle shapes are compiled for 5..16 views (8- and 16-view kernels); below and above
-    every variant runs the default shape."""
-    return VARIANTS if 5 <= n_views <= 16 else (0,)
+    lane-per-ray bundle shapes (0..5) are compiled for 5..16 views (8- and 16-view
+    kernels), the warp-per-ray mapping (6) for 5..32 views; otherwise a variant runs the
+    default shape."""
+    if 5 <= n_views <= 16:
+        return VARIANTS
+    return (0, 6) if n_views > 16 else (0,)
 
 
 def device_key() -> str:

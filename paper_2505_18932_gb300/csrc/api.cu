@@ -249,7 +249,7 @@ gvs_status check_fuse_common(const gvs_camera *in_cams, int32_t n_views, const g
         return fail(GVS_ERR_UNSUPPORTED, "fuse: depth_dtype must be GVS_F32 or GVS_F16");
     if (p.map_dtype != GVS_F32 && p.map_dtype != GVS_F16)
         return fail(GVS_ERR_UNSUPPORTED, "fuse: map_dtype must be GVS_F32 or GVS_F16");
-    if (p.variant < 0 || p.variant > 5) return fail(GVS_ERR_INVALID_ARG, "fuse: variant must be in [0, 5]");
+    if (p.variant < 0 || p.variant > 6) return fail(GVS_ERR_INVALID_ARG, "fuse: variant must be in [0, 6]");
     if (!fused_depth) return fail(GVS_ERR_INVALID_ARG, "fuse: fused_depth is NULL");
     if (!aligned(fused_depth, 16) || (crossing && !aligned(crossing, 16)))
         return fail(GVS_ERR_INVALID_ARG, "fuse: arrays must be 16-byte aligned");

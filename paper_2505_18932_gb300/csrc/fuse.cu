@@ -384,6 +384,7 @@ cudaError_t launch_weight_map(const void *depth, int depth_dtype, void *map, int
 }
 
 int bundle_count(int Wt, int Ht, int K, int variant) {
+    if (K > 4 && variant == 6) return Wt * Ht;  // one warp per ray (the 8, 16 and 32-view kernels)
     int bx = 8, by = 4;
     if (K > 4 && K <= 16) {
         if (variant == 2) { bx = 16; by = 2; }

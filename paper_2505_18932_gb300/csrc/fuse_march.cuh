@@ -98,19 +98,23 @@ constexpr int SKIP_COOL = 3;    // samples evaluated after both slab tests fail,
 //             compiles away and the unrolled views form one block of code
 //   spt     : samples each lane evaluates at once in a run of evaluations
 //             (1 or 2: two keep twice the gathers in flight)
-template <int BX_, int BY_, int LLONG_, int LSHORT_, bool FULL_ = false, int SPT_ = 1>
+//   warp    : the mapping.  false: lane per ray (a bundle of bx x by = 32 rays per
+//             warp); true: warp per ray (bx = by = 1), its lanes split into
+//             views x samples, so a step evaluates 32 / KMAX consecutive samples
+//             of the one ray at once and its slab tests hold for that ray alone
+template <int BX_, int BY_, int LLONG_, int LSHORT_, bool FULL_ = false, int SPT_ = 1, bool WARP_ = false>
 struct Tile {
     static constexpr int bx = BX_, by = BY_, llong = LLONG_, lshort = LSHORT_, spt = SPT_;
-    static constexpr bool full = FULL_;
-    static_assert(bx * by == 32, "a bundle is one warp");
+    static constexpr bool full = FULL_, warp = WARP_;
+    static_assert(warp ? (bx == 1 && by == 1 && spt == 1) : bx * by == 32, "a bundle is one warp, or one ray");
     static_assert(llong >= 1 && lshort >= 1, "skip lengths must advance the march");
     static_assert(spt == 1 || spt == 2, "one or two samples at once");
 };
 template <typename T>
 struct FullTile;
-template <int BX_, int BY_, int LLONG_, int LSHORT_, bool FULL_, int SPT_>
-struct FullTile<Tile<BX_, BY_, LLONG_, LSHORT_, FULL_, SPT_>> {
-    using type = Tile<BX_, BY_, LLONG_, LSHORT_, true, SPT_>;
+template <int BX_, int BY_, int LLONG_, int LSHORT_, bool FULL_, int SPT_, bool WARP_>
+struct FullTile<Tile<BX_, BY_, LLONG_, LSHORT_, FULL_, SPT_, WARP_>> {
+    using type = Tile<BX_, BY_, LLONG_, LSHORT_, true, SPT_, WARP_>;
 };
 using Tile0 = Tile<8, 4, 8, 2>;
 using Tile1 = Tile<8, 4, 16, 4>;
@@ -118,7 +122,8 @@ using Tile2 = Tile<16, 2, 8, 2>;
 using Tile3 = Tile<4, 8, 8, 2>;
 using Tile4 = Tile<4, 8, 8, 2, false, 2>;
 using Tile5 = Tile<8, 4, 8, 2, false, 2>;
-constexpr int kFuseVariants = 6;
+using Tile6 = Tile<1, 1, 8, 2, false, 1, true>;
+constexpr int kFuseVariants = 7;
 
 struct Ray {
     float ax, ay, az;
@@ -287,7 +292,7 @@ __device__ __forceinline__ void evaluate_sample2(const FuseArgs &a, const Ray (&
 // weight at the crossing are compiled in only where they are used.  PLANES as
 // in evaluate_sample.
 template <int KMAX, typename MT, typename T, bool TMP = false, bool PLANES = true>
-__device__ __forceinline__ void march_bundle(const FuseArgs &a, int bundle, int lane) {
+__device__ __forceinline__ void march_rays(const FuseArgs &a, int bundle, int lane) {
     constexpr int BX = T::bx, BY = T::by, SKIP_LONG = T::llong, SKIP_SHORT = T::lshort;
     constexpr int NSEG = 32 / KMAX;
     constexpr unsigned SEGMASK = KMAX == 32 ? 0xffffffffu : ((1u << KMAX) - 1u);
@@ -438,9 +443,151 @@ __device__ __forceinline__ void march_bundle(const FuseArgs &a, int bundle, int 
     }
 }
 
+// One warp per target ray (the warp-per-pixel mapping; `pixel` < Wt * Ht).  Lane
+// (q, k) = (lane / KMAX, lane % KMAX) takes view k: in a slab test, segment q of
+// the ray's own slab (its four corner rays are the ray itself); in a run of
+// evaluations, sample s + q.  Each sample's S and W are summed over the views in
+// view order from the lanes' terms, exactly as evaluate_sample sums them, and the
+// samples are then scanned in order, so the crossing, its index and its depth are
+// bit for bit those of march_rays (and of the full uniform march).  No temporal
+// input.
+template <int KMAX, typename MT, typename T, bool PLANES = true>
+__device__ __forceinline__ void march_ray_warp(const FuseArgs &a, int pixel, int lane) {
+    constexpr int NQ = 32 / KMAX;  // samples per step = segments per slab test
+    constexpr unsigned SEGMASK = KMAX == 32 ? 0xffffffffu : ((1u << KMAX) - 1u);
+    constexpr int SKIP_LONG = T::llong, SKIP_SHORT = T::lshort;
+    const int i = pixel % a.Wt, j = pixel / a.Wt;
+    const float fi = (float)i, fj = (float)j;
+    const int tk = lane % KMAX, tq = lane / KMAX;
+    const bool tview = T::full || tk < a.K;
+    const int kk = tview ? tk : 0;
+    const size_t plane = (size_t)a.W * a.H;
+    Ray corner[4];
+    float tb0, tb1, tb2;
+    {
+        const float *M = a.xf[kk].M;
+        tb0 = a.xf[kk].b[0];
+        tb1 = a.xf[kk].b[1];
+        tb2 = a.xf[kk].b[2];
+        corner[0].ax = __fmaf_rn(M[0], fi, __fmaf_rn(M[1], fj, M[2]));
+        corner[0].ay = __fmaf_rn(M[3], fi, __fmaf_rn(M[4], fj, M[5]));
+        corner[0].az = __fmaf_rn(M[6], fi, __fmaf_rn(M[7], fj, M[8]));
+        corner[1] = corner[2] = corner[3] = corner[0];
+    }
+    const Ray &ray = corner[0];
+    const MT *plane_k = PLANES ? reinterpret_cast<const MT *>(a.vb[kk])
+                               : reinterpret_cast<const MT *>(a.dw) + (size_t)kk * plane;
+    float S_prev = 0.0f, W_prev = 0.0f, z_prev = 0.0f;
+    bool have_prev = false;
+    float out = 0.0f;
+    int idx = -1;
+    int s = 0, cool = 0;
+    bool shorter = false;
+    while (s < a.D) {
+        if (cool == 0 && s < a.D - 1) {
+            const int L = shorter ? SKIP_SHORT : SKIP_LONG;
+            const int sa = s + tq * L;
+            bool f = false;
+            if (sa < a.D - 1) {
+                const int sb = min(sa + L, a.D - 1);
+                const float z0 = __fmaf_rn((float)sa, a.dz, a.zn), z1 = __fmaf_rn((float)sb, a.dz, a.zn);
+                f = !tview || slab_view_free(a, tk, corner, tb0, tb1, tb2, z0, z1);
+            }
+            const unsigned ball = __ballot_sync(0xffffffffu, f);
+            int nfree = 0;
+#pragma unroll
+            for (int g = 0; g < NQ; ++g) {
+                if (nfree == g && ((ball >> (g * KMAX)) & SEGMASK) == SEGMASK) ++nfree;
+            }
+            if (nfree > 0) {
+                s = min(s + nfree * L, a.D - 1);
+                if (s == a.D - 1) break;
+                have_prev = false;
+                shorter = false;
+                continue;
+            }
+            if (!shorter && SKIP_SHORT < SKIP_LONG) {
+                shorter = true;
+                continue;
+            }
+            shorter = false;
+            cool = SKIP_COOL;
+        }
+        // this lane's term of sample s + tq in view tk, as evaluate_sample forms it
+        float w = 0.0f, t = 0.0f;
+        if (s + tq < a.D && tview) {
+            const float zs = __fmaf_rn((float)(s + tq), a.dz, a.zn);
+            const float hz = __fmaf_rn(zs, ray.az, tb2);
+            const float hx = __fmaf_rn(zs, ray.ax, tb0);
+            const float hy = __fmaf_rn(zs, ray.ay, tb1);
+            int u, v;
+            nearest_pixel(hx, hy, hz, u, v);
+            const bool in = hz > 1e-6f && (unsigned)u < (unsigned)a.W && (unsigned)v < (unsigned)a.H &&
+                            GVS_IN_BOUNDS((size_t)kk * plane + (size_t)v * a.W + u, (size_t)a.K * plane,
+                                          GVS_SITE_FUSE_MAP);
+            float2 p = make_float2(0.0f, 0.0f);
+            if (in) p = load_map(plane_k + (v * a.W + u));  // v W + u < 2^28
+            const float sdf = (p.x - hz) * a.inv_mu;
+            w = (in && sdf >= -1.0f) ? p.y : 0.0f;
+            t = fminf(sdf, 1.0f);
+        }
+        // S and W of sample s + tq: its group's terms in view order
+        float S = 0.0f, Wsum = 0.0f;
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k) {
+            const float wk = __shfl_sync(0xffffffffu, w, tq * KMAX + k);
+            const float tk_ = __shfl_sync(0xffffffffu, t, tq * KMAX + k);
+            if (T::full || k < a.K) {
+                S = fmaf(wk, tk_, S);
+                Wsum += wk;
+            }
+        }
+        // the step's samples in order
+        bool done = false;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            float Sq = __shfl_sync(0xffffffffu, S, q * KMAX);
+            const float Wq = __shfl_sync(0xffffffffu, Wsum, q * KMAX);
+            if (!done && s < a.D) {
+                const float zs = __fmaf_rn((float)s, a.dz, a.zn);
+                if (a.normalize && Wq > 0.0f) Sq = Sq / Wq;
+                if (have_prev && W_prev > 0.0f && Wq > 0.0f && S_prev > 0.0f && Sq <= 0.0f) {
+                    const float tt = S_prev / (S_prev - Sq);
+                    out = z_prev + (zs - z_prev) * tt;
+                    idx = s - 1;
+                    done = true;
+                }
+                S_prev = Sq;
+                W_prev = Wq;
+                z_prev = zs;
+                have_prev = true;
+                ++s;
+                if (cool > 0) --cool;
+            }
+        }
+        if (done) break;
+    }
+    if (lane == 0) {
+        const size_t o = (size_t)j * a.Wt + i;
+        a.fused[o] = out;
+        if (a.crossing) a.crossing[o] = (int16_t)idx;
+    }
+}
+
+template <int KMAX, typename MT, typename T, bool TMP = false, bool PLANES = true>
+__device__ __forceinline__ void march_bundle(const FuseArgs &a, int bundle, int lane) {
+    if constexpr (T::warp) {
+        static_assert(!TMP, "the warp-per-ray march takes no temporal input");
+        march_ray_warp<KMAX, MT, T, PLANES>(a, bundle, lane);
+    } else {
+        march_rays<KMAX, MT, T, TMP, PLANES>(a, bundle, lane);
+    }
+}
+
 // Calls F<Tile_i>::run(...) for the variant, with the full form of the tile
 // when the call has exactly KMAX views; views counts other than 8 and 16 use
-// the default tile only (fewer instantiations to build).
+// the default tile only (fewer instantiations to build), except the
+// warp-per-ray variant 6, built for 8, 16 and 32 views (5 to 32 views).
 template <int KMAX, typename MT, template <int, typename, typename> class F, typename T, typename... Args>
 void full_or_not(int K, Args... args) {
     if (K == KMAX) F<KMAX, MT, typename FullTile<T>::type>::run(args...);
@@ -449,6 +596,12 @@ void full_or_not(int K, Args... args) {
 
 template <int KMAX, typename MT, template <int, typename, typename> class F, typename... Args>
 void by_variant(int K, int variant, Args... args) {
+    if constexpr (KMAX >= 8) {  // the warp-per-ray mapping: 8, 16 and 32-view kernels
+        if (variant == 6) {
+            full_or_not<KMAX, MT, F, Tile6>(K, args...);
+            return;
+        }
+    }
     if (KMAX == 8 || KMAX == 16) {
         switch (variant) {
             case 1: full_or_not<KMAX, MT, F, Tile1>(K, args...); return;

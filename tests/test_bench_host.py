@@ -66,12 +66,15 @@ def test_counter_record_only_for_its_own_kernel(bench, tmp_path, monkeypatch):
 
 
 def test_autotuner_chooses_only_between_distinct_kernels():
-    """Bundle shapes are compiled for 5..16 views; elsewhere every variant is the default
-    kernel, so there is nothing to time and the default comes back at once."""
+    """Bundle shapes are compiled for 5..16 views and the warp-per-ray mapping (variant 6)
+    for 5..32; elsewhere every variant is the default kernel, so there is nothing to time
+    and the default comes back at once."""
     from paper_2505_18932_gb300 import autotune
     assert autotune.variants_for(8) == autotune.VARIANTS and autotune.variants_for(16) == autotune.VARIANTS
-    assert autotune.variants_for(5) == autotune.VARIANTS
-    for k in (1, 4, 17, 32):
+    assert autotune.variants_for(5) == autotune.VARIANTS and 6 in autotune.VARIANTS
+    for k in (17, 32):
+        assert autotune.variants_for(k) == (0, 6)
+    for k in (1, 4):
         assert autotune.variants_for(k) == (0,)
     calls = []
     best, ms = autotune.choose({"k": 4}, lambda v: calls.append(v), candidates=autotune.variants_for(4))

@@ -27,14 +27,17 @@ def _targets(w):
             camera_at(64, 48, (-0.04, -0.02, -2.0))]
 
 
-@pytest.mark.parametrize("K", [8, 16])
+@pytest.mark.parametrize("K", [5, 8, 12, 16, 32])
 def test_variants_bit_identical(gvs, K):
+    """Every variant, the lane-per-ray bundle shapes and the warp-per-ray mapping, gives
+    the default's fused depth and crossing index bit for bit (K = 5 and 12 run the
+    per-view-guarded 8- and 16-view kernels, 32 the 32-view ones)."""
     from synth import configs
     w = configs.tiny(70, 45, K, 96)
     _, d = w.render_inputs(0)
     dd = to_dev(d)
     ref = None
-    for v in range(6):
+    for v in range(7):
         f, c = gvs.fuse_depth(w.inputs, dd, w.targets[0], w.num_samples, w.z_near, w.z_far, w.mu, variant=v)
         torch.cuda.synchronize()
         if ref is None:
@@ -54,7 +57,7 @@ def test_batched_equals_per_item(gvs):
         maps.append(gvs.weight_map(to_dev(d), w.mu))
     refs = [[gvs.fuse_depth_from_map(w.inputs, m, (8, 48, 64), t, w.num_samples, w.z_near, w.z_far, w.mu)
              for t in tg] for m in maps]
-    for v in range(6):
+    for v in range(7):
         outs = [[(torch.empty((t.height, t.width), device="cuda"), torch.empty((t.height, t.width),
                  dtype=torch.int16, device="cuda")) for t in tg] for _ in maps]
         items = [(maps[f], t, outs[f][n][0], outs[f][n][1]) for f in range(2) for n, t in enumerate(tg)]
@@ -81,7 +84,7 @@ def test_batch_plan_graph_matches_single_view_api(gvs, tmp_path, monkeypatch):
     dep = [to_dev(d) for _, d in frames]
     plan = batch.BatchPlan(w.inputs, tg, rgba, dep, w.num_samples, w.z_near, w.z_far, w.mu, tau=w.tau,
                            rgba_prev=to_dev(u32(rgb0)), state0=to_dev(d0), variant=None, graph=True)
-    assert plan.variant in range(6)
+    assert plan.variant in range(7)
     cache = json.load(open(autotune.CACHE_PATH))
     assert any(e["variant"] == plan.variant for e in cache.values())
     for rep in range(2):

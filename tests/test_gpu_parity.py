@@ -118,8 +118,8 @@ def test_blind_view_changes_nothing(gvs):
 def test_fuse_full_size_sampled(gvs, oracle_mod):
     """8 x 1920x1080 inputs, D=128, in the launch configuration the benchmark times;
     2048 seeded target pixels checked against the oracle one by one.  The benchmark's
-    pipeline runs the bundle shape its autotuner picks: every shape gives the default's
-    fused depth and crossing index bit for bit on the whole frame."""
+    pipeline runs the variant its autotuner picks: every bundle shape and the warp-per-ray
+    mapping give the default's fused depth and crossing index bit for bit on the whole frame."""
     w = _workload("headline_8x1080p")
     rng = np.random.default_rng(7)
     pix = np.stack([rng.integers(0, 1920, 2048), rng.integers(0, 1080, 2048)], 1).astype(np.int32)
@@ -127,7 +127,7 @@ def test_fuse_full_size_sampled(gvs, oracle_mod):
     _, d = w.render_inputs(1)
     dd, tgt = to_dev(d), w.targets_at(1)[0]
     f0, c0 = gvs.fuse_depth(w.inputs, dd, tgt, w.num_samples, w.z_near, w.z_far, w.mu, variant=0)
-    for v in (1, 2, 3, 4, 5):
+    for v in (1, 2, 3, 4, 5, 6):
         f, c = gvs.fuse_depth(w.inputs, dd, tgt, w.num_samples, w.z_near, w.z_far, w.mu, variant=v)
         torch.cuda.synchronize()
         assert torch.equal(f.view(torch.int32), f0.view(torch.int32)) and torch.equal(c, c0), v
