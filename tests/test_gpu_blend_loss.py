@@ -100,6 +100,41 @@ def test_grad_stage_on_kept_workspace(gvs, shape):
         assert torch.equal(g2, gp * gu) and torch.equal(f2, gf * gu), u
 
 
+def test_each_gradient_output_alone(gvs):
+    """Through the C ABI: either gradient output may be NULL, in the loss call and in the
+    gradient stage, and the other comes out as when both are asked for."""
+    lib = gvs.load()
+    K, H, W = 3, 24, 40
+    rng = np.random.default_rng(12)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    alpha = (rng.random((K, H, W)) < 0.7).astype(np.uint8)
+    color = dev(rng.random((K, H, W, 4)).astype(np.float32) * alpha[..., None])
+    wd = dev((rng.random((K, H, W)) * 3 + 1).astype(np.float32) * alpha)
+    fused = dev((rng.random((H, W)) * 3 + 1).astype(np.float32))
+    gt = dev(rng.random((H, W, 3)).astype(np.float32))
+    alpha = dev(alpha)
+    loss, gp, gf = gvs.uniform_blend_loss(color, alpha, wd, fused, gt)
+    P = gvs._ptr
+    for want_pixel in (True, False):
+        ws = gvs.workspace(gvs.blend_loss_workspace_bytes(H, W), "cuda")
+        l2 = torch.empty(3, dtype=torch.float64, device="cuda")
+        gp2 = torch.zeros((H, W, 4), device="cuda") if want_pixel else None
+        gf2 = None if want_pixel else torch.zeros((H, W), device="cuda")
+        st = lib.gvs_uniform_blend_loss(K, W, H, P(color), P(alpha), P(wd), P(fused), P(gt), 0.8, 0.1, P(l2),
+                                        P(gp2), P(gf2), P(ws), ws.numel(), None)
+        assert st == 0
+        gp3 = torch.zeros((H, W, 4), device="cuda") if want_pixel else None
+        gf3 = None if want_pixel else torch.zeros((H, W), device="cuda")
+        st = lib.gvs_uniform_blend_loss_grad(W, H, None, P(gp3), P(gf3), P(ws), ws.numel(), None)
+        assert st == 0
+        torch.cuda.synchronize()
+        assert torch.equal(l2, loss)
+        if want_pixel:
+            assert torch.equal(gp2, gp) and torch.equal(gp3, gp)
+        else:
+            assert torch.equal(gf2, gf) and torch.equal(gf3, gf)
+
+
 def _soft_case(gvs, name="diff_640x360"):
     from synth import configs
     w = getattr(configs, name)()
