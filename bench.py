@@ -205,6 +205,16 @@ class Pipeline:
         return n_refine + 3 + 1 + 1 + 2 * groups
 
 
+class VideoStream(Pipeline):
+    """A video as a stream: every frame resident in HBM, each refined against the one
+    before it (the last wraps to the first) and fused and splatted into that frame's own
+    target camera (the video's target moves)."""
+
+    def step(self, i, events=None):
+        self.tgt = self.w.targets_at(i % len(self.rgba))[0]
+        super().step(i, events)
+
+
 def algorithmic_fuse(cross_np, D, K):
     """Sample-views the method evaluates: every sample up to the crossing's second
     bracket (s + 2), all D where there is no crossing, times K views."""
@@ -345,6 +355,12 @@ def run_gvs(args, rank, local_rank, world):
         "cfg2_video_8x720p", w2, time_form(Pipeline(w2, render_frames(w2, range(RING)), device), steps=min(K, 100)),
         "one frame of the 8 x 1280x720 video (2x4 rig, sphere moving 1 cm per frame), D = 128: refine, weight map, "
         "fusion, splat of the 8 views")
+    forms["cfg2_video_stream_30f"] = form_line(
+        "cfg2_video_stream_30f", w2,
+        time_form(VideoStream(w2, render_frames(w2, range(w2.n_frames)), device), steps=min(K, 3 * w2.n_frames)),
+        f"the {w2.n_frames}-frame 8 x 1280x720 video as a stream, all frames in HBM: per frame refine against the "
+        "previous frame, weight map, fusion and splat of the 8 views into that frame's (moving) target; "
+        "ms_per_step is per frame")
     frd = render_frames(wd, [0, 1])
     forms["fwd_bwd_640x360"] = form_line("fwd_bwd_640x360", wd,
                                          time_form(FwdBwd(wd, frd, device).capture(), steps=min(K, 50)),
