@@ -911,14 +911,31 @@ __global__ void __launch_bounds__(256) temporal_weight_kernel(const MK *__restri
     w_tmp[p] = fminf(beta_t * (w_tmp_prev[p] + w_view_prev[p]) * keep, eta);
 }
 
+// One row of blocks per view (gridDim.y = K).  V = 4: four pixels per thread with 16-byte
+// depth and fused loads and 4-byte alpha and mask accesses (HWt a multiple of 4, planes
+// aligned); V = 1: one pixel per thread.
+template <int V>
 __global__ void __launch_bounds__(256) guided_mask_kernel(const float *__restrict__ warped_depth,
                                                           const uint8_t *__restrict__ alpha,
-                                                          const float *__restrict__ fused, int K, int64_t HWt,
+                                                          const float *__restrict__ fused, int64_t HWt,
                                                           float mu_guide, uint8_t *__restrict__ guided) {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= (int64_t)K * HWt) return;
-    const int64_t t = p % HWt;
-    guided[p] = (uint8_t)(alpha[p] && fabsf(warped_depth[p] - fused[t]) <= mu_guide);
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t base = (size_t)blockIdx.y * HWt;
+    if (V == 4) {
+        if (4 * q >= HWt) return;
+        const float4 d = __ldg(reinterpret_cast<const float4 *>(warped_depth + base) + q);
+        const float4 f = __ldg(reinterpret_cast<const float4 *>(fused) + q);
+        const uchar4 a = __ldg(reinterpret_cast<const uchar4 *>(alpha + base) + q);
+        uchar4 g;
+        g.x = (unsigned char)(a.x && fabsf(d.x - f.x) <= mu_guide);
+        g.y = (unsigned char)(a.y && fabsf(d.y - f.y) <= mu_guide);
+        g.z = (unsigned char)(a.z && fabsf(d.z - f.z) <= mu_guide);
+        g.w = (unsigned char)(a.w && fabsf(d.w - f.w) <= mu_guide);
+        reinterpret_cast<uchar4 *>(guided + base)[q] = g;
+    } else {
+        if (q >= HWt) return;
+        guided[base + q] = (uint8_t)(alpha[base + q] && fabsf(warped_depth[base + q] - fused[q]) <= mu_guide);
+    }
 }
 
 }  // namespace
@@ -940,9 +957,14 @@ cudaError_t launch_temporal_weight(const void *masks, int mask_dtype, const int3
 
 cudaError_t launch_guided_mask(const float *warped_depth, const uint8_t *alpha, const float *fused, int K,
                                int64_t HWt, float mu_guide, uint8_t *guided, cudaStream_t st) {
-    const int64_t n = (int64_t)K * HWt;
-    guided_mask_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(warped_depth, alpha, fused, K, HWt, mu_guide,
-                                                                    guided);
+    if (K == 0 || HWt == 0) return cudaSuccess;
+    if (HWt % 4 == 0 && aligned_to(warped_depth, 16) && aligned_to(fused, 16) && aligned_to(alpha, 4) &&
+        aligned_to(guided, 4))
+        guided_mask_kernel<4><<<dim3((unsigned)((HWt / 4 + 255) / 256), (unsigned)K), 256, 0, st>>>(
+            warped_depth, alpha, fused, HWt, mu_guide, guided);
+    else
+        guided_mask_kernel<1><<<dim3((unsigned)((HWt + 255) / 256), (unsigned)K), 256, 0, st>>>(
+            warped_depth, alpha, fused, HWt, mu_guide, guided);
     return cudaGetLastError();
 }
 

@@ -34,6 +34,28 @@ def test_temporal_weight_matches_oracle(gvs, oracle_mod, u8):
     np.testing.assert_allclose(tm.cpu().numpy(), M, rtol=1e-7)
 
 
+@pytest.mark.parametrize("shape", [(3, 20, 32), (4, 17, 23)])
+def test_guided_mask_matches_definition(gvs, shape):
+    """gvs_guided_mask (Sec. 3.3: the views' pixels within mu of the fused depth) bit for bit
+    against the definition in FP64, on depths in [1, 2] where |d - F| is exact in FP32, with
+    exact ties at mu planted; a target size divisible by 4 (four pixels per thread) and one
+    that is not (one per thread)."""
+    K, Ht, Wt = shape
+    rng = np.random.default_rng(K * Ht)
+    mu = 0.0625
+    fused = rng.uniform(1.0, 2.0, (Ht, Wt)).astype(np.float32)
+    wd = (fused[None] + rng.uniform(-0.2, 0.2, (K, Ht, Wt))).astype(np.float32)
+    wd = np.clip(wd, 1.0, 2.0).astype(np.float32)
+    tie = rng.random((K, Ht, Wt)) < 0.05
+    wd[tie] = np.clip(fused[None].repeat(K, 0)[tie] + mu, 1.0, 2.0)
+    alpha = (rng.random((K, Ht, Wt)) < 0.8).astype(np.uint8)
+    g = gvs.guided_mask(to_dev(wd), to_dev(alpha), to_dev(fused), mu)
+    torch.cuda.synchronize()
+    ref = (alpha > 0) & (np.abs(wd.astype(np.float64) - fused.astype(np.float64)[None]) <= mu)
+    assert np.array_equal(g.cpu().numpy(), ref.astype(np.uint8))
+    assert ref.any() and (~ref & (alpha > 0)).any()
+
+
 def test_fuse_temporal_matches_oracle(gvs, oracle_mod):
     from synth import configs
     w = configs.tiny(70, 45, 4, 96)
