@@ -205,6 +205,27 @@ class Pipeline:
         return n_refine + 3 + 1 + 1 + 2 * groups
 
 
+class SoftRefine:
+    """The paper's soft difference mask and blend (Sec. 3.2, Eq. 1-2 as printed: the mask at
+    quarter resolution, 3x3 max-pooled, bilinearly upsampled, D' = M D + (1 - M) D'_prev)
+    over the 8 input views of a frame, the state updated in place."""
+
+    def __init__(self, w, frames_np, device):
+        import torch
+        from paper_2505_18932_gb300 import gvs
+        self.gvs, self.w = gvs, w
+        self.rgba = [torch.from_numpy(c.view(np.int32)).to(device) for c, _ in frames_np]
+        self.depth = [torch.from_numpy(d).to(device) for _, d in frames_np]
+        self.state = self.depth[0].clone()
+        N, H, W = self.state.shape
+        self.ws = gvs.workspace(gvs.load().gvs_refine_soft_workspace_bytes(N, W, H), device)
+        self.alg_bytes = N * H * W * (4 + 4 + 4 + 4 + 4)  # both colours, the new depth, the state read and written
+
+    def step(self, i, events=None):
+        cur, prev = i % len(self.rgba), (i - 1) % len(self.rgba)
+        self.gvs.refine_depth_soft(self.rgba[cur], self.rgba[prev], self.depth[cur], self.state, ws=self.ws)
+
+
 class VideoStream(Pipeline):
     """A video as a stream: every frame resident in HBM, each refined against the one
     before it (the last wraps to the first) and fused and splatted into that frame's own
@@ -330,6 +351,12 @@ def run_gvs(args, rank, local_rank, world):
     torch.cuda.synchronize()
     f256["coverage"] = round(float((p256.cross >= 0).float().mean()), 4)
     forms["headline_d256"] = f256
+    sr = SoftRefine(w, frames_np, device)
+    forms["soft_mask_refine"] = form_line("soft_mask_refine", w, time_form(sr, steps=min(K, 100)),
+                                          "the paper's soft difference mask and blend (Sec. 3.2, Eq. 1-2: quarter "
+                                          "resolution, 3x3 max-pool, bilinear) over the 8 views; refinement only")
+    forms["soft_mask_refine"]["hbm_frac"] = round(
+        sr.alg_bytes / (forms["soft_mask_refine"]["ms_per_step"] * 1e-3) / 1e9 / measured_peaks()[0], 4)
     forms["temporal_online"] = form_line("temporal_online", w, time_form(TemporalOnline(w, frames_np, device),
                                                                          steps=min(K, 100)),
                                          "refine + splat + temporal weight + fusion with the previous output "
@@ -1221,7 +1248,7 @@ def run_reference(args, rank, world):
 
 
 FORM_CLASSES = ("plain", "f16_storage", "fwd_bwd", "fwd_bwd_640x360", "gauss_render", "network_frame_k4",
-                "sphere_trace_fusion", "temporal_online", "batched", "mixed")
+                "sphere_trace_fusion", "temporal_online", "soft_mask_refine", "batched", "mixed")
 
 
 def run_only_form(args):
@@ -1252,7 +1279,7 @@ def run_only_form(args):
         frames_np = render_frames(w, [0, 1] if name.startswith("fwd_bwd") else rank_frames(0))
         cls = {"plain": Pipeline, "f16_storage": Pipeline, "fwd_bwd": FwdBwd, "fwd_bwd_640x360": FwdBwd,
                "gauss_render": GaussRender, "network_frame_k4": NetworkFrame, "sphere_trace_fusion": SphereTrace,
-               "temporal_online": TemporalOnline}[name]
+               "temporal_online": TemporalOnline, "soft_mask_refine": SoftRefine}[name]
         form = cls(w, frames_np, device, half=True) if name == "f16_storage" else cls(w, frames_np, device)
         for i in range(max(3, args.warmup)):
             form.step(i)

@@ -90,17 +90,16 @@ void launch_typed(const uint32_t *rgba_t, const uint32_t *rgba_prev, const void 
 //   3x3 max-pool, bilinear upsample,  D' = M D + (1 - M) D'_prev.
 // Three small passes: quarter cells (4x4 block means of the per-pixel largest
 // channel difference), the pooled quarter grid, then the full-resolution
-// upsample and blend.  Quarter grids live in the workspace.
+// upsample and blend.  Quarter grids live in the workspace.  Each pass runs on
+// blocks of 32 x 8 cells or pixels with the view in blockIdx.z (no index division).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) soft_quarter(const uint32_t *__restrict__ rgba_t,
                                                     const uint32_t *__restrict__ rgba_prev, float *__restrict__ mq,
                                                     int W, int H, int Wq, int Hq, int K, float inv_lambda,
                                                     float beta) {
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= (int64_t)K * Wq * Hq) return;
-    const int k = (int)(q / ((int64_t)Wq * Hq));
-    const int r = (int)(q - (int64_t)k * Wq * Hq);
-    const int qy = r / Wq, qx = r - qy * Wq;
+    const int qx = blockIdx.x * 32 + threadIdx.x, qy = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+    if (qx >= Wq || qy >= Hq) return;
+    const size_t q = ((size_t)k * Hq + qy) * Wq + qx;
     const size_t off = (size_t)k * W * H;
     float sum = 0.0f;
     int cnt = 0;
@@ -118,11 +117,9 @@ __global__ void __launch_bounds__(256) soft_quarter(const uint32_t *__restrict__
 
 __global__ void __launch_bounds__(256) soft_pool(const float *__restrict__ mq, float *__restrict__ pq, int Wq,
                                                  int Hq, int K) {
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= (int64_t)K * Wq * Hq) return;
-    const int k = (int)(q / ((int64_t)Wq * Hq));
-    const int r = (int)(q - (int64_t)k * Wq * Hq);
-    const int qy = r / Wq, qx = r - qy * Wq;
+    const int qx = blockIdx.x * 32 + threadIdx.x, qy = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+    if (qx >= Wq || qy >= Hq) return;
+    const size_t q = ((size_t)k * Hq + qy) * Wq + qx;
     const float *m = mq + (size_t)k * Wq * Hq;
     float best = -1.0f;
     for (int dy = -1; dy <= 1; ++dy)
@@ -139,30 +136,42 @@ __device__ __forceinline__ void st_depth(float *p, float v) { *p = v; }
 __device__ __forceinline__ void st_depth(__half *p, float v) { *p = __float2half_rn(v); }
 __device__ __forceinline__ bool valid_d(float d) { return isfinite(d) && d > 0.0f; }
 
+// SB_V consecutive pixels of a row per thread: they share the row's vertical
+// interpolation terms and keep more loads in flight; each pixel's arithmetic is
+// the single-pixel form, in the same order.
+constexpr int SB_V = 4;
+
 template <typename T>
 __global__ void __launch_bounds__(256) soft_blend(const float *__restrict__ pq, const T *__restrict__ depth_t,
                                                   T *__restrict__ state, float *__restrict__ mask, int W, int H,
                                                   int Wq, int Hq, int K) {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= (int64_t)K * W * H) return;
-    const int k = (int)(p / ((int64_t)W * H));
-    const int r = (int)(p - (int64_t)k * W * H);
-    const int y = r / W, x = r - y * W;
+    const int xs = (blockIdx.x * 32 + threadIdx.x) * SB_V, y = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+    if (xs >= W || y >= H) return;
     const float *m = pq + (size_t)k * Wq * Hq;
-    const float sx = fminf(fmaxf((x + 0.5f) * 0.25f - 0.5f, 0.0f), (float)(Wq - 1));
     const float sy = fminf(fmaxf((y + 0.5f) * 0.25f - 0.5f, 0.0f), (float)(Hq - 1));
-    const int x0 = (int)sx, y0 = (int)sy;
-    const int x1 = min(x0 + 1, Wq - 1), y1 = min(y0 + 1, Hq - 1);
-    const float fx = sx - (float)x0, fy = sy - (float)y0;
-    const float M = (1.0f - fy) * ((1.0f - fx) * m[y0 * Wq + x0] + fx * m[y0 * Wq + x1]) +
-                    fy * ((1.0f - fx) * m[y1 * Wq + x0] + fx * m[y1 * Wq + x1]);
-    if (mask) mask[p] = M;
-    const float dn = ld_depth(&depth_t[p]), dp = ld_depth(&state[p]);
-    float out;
-    if (!valid_d(dp)) out = dn;
-    else if (!valid_d(dn)) out = dp;
-    else out = fmaf(M, dn - dp, dp);  // M dn + (1 - M) dp
-    st_depth(&state[p], out);
+    const int y0 = (int)sy;
+    const int y1 = min(y0 + 1, Hq - 1);
+    const float fy = sy - (float)y0;
+    const float *m0 = m + y0 * Wq, *m1 = m + y1 * Wq;
+    const size_t row = ((size_t)k * H + y) * W;
+#pragma unroll
+    for (int e = 0; e < SB_V; ++e) {
+        const int x = xs + e;
+        if (x >= W) break;
+        const size_t p = row + x;
+        const float sx = fminf(fmaxf((x + 0.5f) * 0.25f - 0.5f, 0.0f), (float)(Wq - 1));
+        const int x0 = (int)sx;
+        const int x1 = min(x0 + 1, Wq - 1);
+        const float fx = sx - (float)x0;
+        const float M = (1.0f - fy) * ((1.0f - fx) * m0[x0] + fx * m0[x1]) + fy * ((1.0f - fx) * m1[x0] + fx * m1[x1]);
+        if (mask) mask[p] = M;
+        const float dn = ld_depth(&depth_t[p]), dp = ld_depth(&state[p]);
+        float out;
+        if (!valid_d(dp)) out = dn;
+        else if (!valid_d(dn)) out = dp;
+        else out = fmaf(M, dn - dp, dp);  // M dn + (1 - M) dp
+        st_depth(&state[p], out);
+    }
 }
 
 template <typename T>
@@ -172,11 +181,12 @@ cudaError_t launch_soft_typed(const uint32_t *rgba_t, const uint32_t *rgba_prev,
     const int Wq = (W + 3) / 4, Hq = (H + 3) / 4;
     const int64_t nq = (int64_t)K * Wq * Hq, n = (int64_t)K * W * H;
     float *mq = ws, *pq = ws + nq;
-    soft_quarter<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(rgba_t, rgba_prev, mq, W, H, Wq, Hq, K,
-                                                              1.0f / lambda_t, beta);
-    soft_pool<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(mq, pq, Wq, Hq, K);
-    soft_blend<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(pq, reinterpret_cast<const T *>(depth_t),
-                                                               reinterpret_cast<T *>(state), mask, W, H, Wq, Hq, K);
+    (void)n;
+    const dim3 block(32, 8), gq((Wq + 31) / 32, (Hq + 7) / 8, K), gp((W + 32 * SB_V - 1) / (32 * SB_V), (H + 7) / 8, K);
+    soft_quarter<<<gq, block, 0, st>>>(rgba_t, rgba_prev, mq, W, H, Wq, Hq, K, 1.0f / lambda_t, beta);
+    soft_pool<<<gq, block, 0, st>>>(mq, pq, Wq, Hq, K);
+    soft_blend<T><<<gp, block, 0, st>>>(pq, reinterpret_cast<const T *>(depth_t), reinterpret_cast<T *>(state), mask,
+                                        W, H, Wq, Hq, K);
     return cudaGetLastError();
 }
 
