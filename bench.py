@@ -213,7 +213,7 @@ class SoftRefine:
     def __init__(self, w, frames_np, device):
         import torch
         from paper_2505_18932_gb300 import gvs
-        self.gvs, self.w = gvs, w
+        self.gvs, self.w, self.half = gvs, w, False
         self.rgba = [torch.from_numpy(c.view(np.int32)).to(device) for c, _ in frames_np]
         self.depth = [torch.from_numpy(d).to(device) for _, d in frames_np]
         self.state = self.depth[0].clone()
